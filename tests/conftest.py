@@ -1,0 +1,20 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300) and the built library")
+    config.addinivalue_line("markers", "slow: oracle runs of tens of seconds")
+
+
+@pytest.fixture(scope="session")
+def dgp_lib():
+    """The CUDA library binding; GPU tests fail (not skip) if it cannot load."""
+    from paper_0906_4548_gb300 import dgp
+    return dgp

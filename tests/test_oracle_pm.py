@@ -1,0 +1,83 @@
+"""Pins of the oracle's PM layer (Sec. III.A): CIC identities, brute-force
+weights, and linear growth of a low-amplitude run."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import background as bg
+from oracle import field, pm
+from paper_0906_4548_gb300 import inputs
+
+OM = 0.27
+
+
+def test_uniform_lattice_gives_zero_delta_and_zero_force():
+    n, box = 16, 50.0
+    pos, mom = inputs.lattice_particles(n, box)
+    rho = pm.cic_deposit(pos, n, box)
+    assert np.all(rho == 1.0)
+    delta = pm.density_contrast(rho)
+    phi, g, D, info = field.solve_phi(delta, 0.3, box, OM, 1.0)
+    assert np.all(delta == 0) and np.all(phi == 0) and all(np.all(gi == 0) for gi in g)
+
+
+def test_mass_conservation_and_constant_gather():
+    n, box = 12, 30.0
+    rng = np.random.default_rng(1)
+    pos = rng.uniform(0, box, (3, 5000))
+    rho = pm.cic_deposit(pos, n, box)
+    assert abs(rho.sum() - 5000) < 1e-9
+    f = np.full((n, n, n), 2.5)
+    assert np.allclose(pm.cic_interpolate(f, pos, box), 2.5, atol=1e-13)
+
+
+def test_deposit_gather_adjoint():
+    n, box = 10, 20.0
+    rng = np.random.default_rng(2)
+    pos = rng.uniform(0, box, (3, 777))
+    f = rng.standard_normal((n, n, n))
+    lhs = np.sum(pm.cic_deposit(pos, n, box) * f)
+    rhs = np.sum(pm.cic_interpolate(f, pos, box))
+    assert abs(lhs - rhs) < 1e-11 * abs(lhs)
+
+
+def test_single_particle_brute_force_weights():
+    """Eq. CIC with W(x) = 1 - |x|/d summed over every grid point (periodic images)."""
+    n, box = 6, 12.0
+    d = box / n
+    p = np.array([[11.3], [0.7], [5.0]])
+    rho = pm.cic_deposit(p, n, box)
+    want = np.zeros((n, n, n))
+    for idx in np.ndindex(n, n, n):
+        w = 1.0
+        for ax in range(3):
+            dx = (idx[ax] * d - p[ax, 0] + box / 2) % box - box / 2
+            w *= max(0.0, 1 - abs(dx) / d)
+        want[idx] = w
+    assert np.max(np.abs(rho - want)) < 1e-14
+
+
+@pytest.mark.parametrize("gravity,geff", [("grh", "GR"), ("nl", "local")])
+def test_linear_growth_of_low_amplitude_wave(gravity, geff):
+    """A long plane wave of tiny amplitude grows like D+(a) (the linearised
+    dynamics of Sec. III.A with Eq. GRPoisson / Eq. LinearDGP); the PM force at
+    k_f is weakened by the CIC window squared (~0.2% on 64^3), so 5e-3."""
+    n, box = 64, 200.0
+    a0, a1, nsteps = 0.05, 0.1, 20
+    D0, f0 = bg.growth(a0, OM, 1.0, geff)
+    D1, _ = bg.growth(a1, OM, 1.0, geff)
+    # 1D Zel'dovich wave along x: Psi_x = A sin(k q)
+    d = box / n
+    q = np.arange(n) * d
+    qx, qy, qz = np.meshgrid(q, q, q, indexing="ij")
+    k = 2 * np.pi / box
+    amp = 1e-3 / k
+    psi = amp * np.sin(k * qx)
+    pos = np.stack([(qx + psi).reshape(-1), qy.reshape(-1), qz.reshape(-1)]) % box
+    vf = a0 * a0 * float(bg.hubble_E(a0, OM, 1.0)) * f0
+    mom = np.stack([vf * psi.reshape(-1), 0 * psi.reshape(-1), 0 * psi.reshape(-1)])
+    st = pm.run(pos, mom, a0, a1, nsteps, n, box, OM, 1.0, gravity=gravity, tol=1e-10)
+    disp = ((st.pos[0] - qx.reshape(-1) + box / 2) % box) - box / 2
+    growth_sim = np.sum(disp * np.sin(k * qx.reshape(-1))) / np.sum(psi.reshape(-1) * np.sin(k * qx.reshape(-1)))
+    assert abs(growth_sim / (D1 / D0) - 1) < 5e-3, (growth_sim, D1 / D0)

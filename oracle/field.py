@@ -168,7 +168,9 @@ def solve_brane_bending(delta, a, box, omega_m0, rc_H0, w=1.0 / 3.0, tol=1e-12,
         D_k = fft3(D)
         D_k[grid.zero] = 0.0
         D, H, Nf = derived_fields(D_k, grid, coef, local_only)
-        r = float(np.mean(np.abs(residual(D, H, Nf, S, coef)))) / eps if eps > 0 else 0.0
+        # Eq. normres divides by eps; with a zero source (uniform density) there
+        # is no scale and the absolute mean residual is monitored instead.
+        r = float(np.mean(np.abs(residual(D, H, Nf, S, coef)))) / (eps if eps > 0 else 1.0)
         history.append(r)
         if r < best[0]:
             best = (r, D, D_k, it)

@@ -1,0 +1,302 @@
+"""PM steps/s at 256^3 including the converged nonlinear DGP phi solve.
+
+Workload (the 256^3 run): 256^3 particles on a 256^3 mesh in a 400 Mpc/h box,
+seeded n_s = -1.5 power-law Gaussian field with mesh rms 0.5 at a = 0.02,
+Zel'dovich initial conditions, r_c H0 = 1, Omega_m0 = 0.27, w = 1/3, steps
+uniform in ln a from a = 0.02 to a = 1 in 200 steps, relaxation tolerance 1e-6
+on <|R|>/eps every step, FP32 mesh/particles with FP64 residual, discriminant
+and reductions.  A "step" is one pm_step call (deposit, field solve, forces,
+gather, kick-drift-kick).  The timed region runs K consecutive steps from
+a = 0.02 (K = 200 is the whole run) after W warm-up steps and a reset to the
+initial conditions.  Inputs (403 MB of particles, 64 MB mesh fields) exceed
+L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 (torchrun, one process per GPU): independent replicas with distinct
+seeds, no data-path collective; value = all ranks' steps / max rank time.
+"""
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WL = dict(n=256, box=400.0, n_s=-1.5, rms=0.5, seed=3, a_start=0.02, a_end=1.0, run_steps=200, rc_H0=1.0,
+          omega_m0=0.27, w=1.0 / 3.0, tol=1e-6, max_iter=100)
+METRIC = "PM steps/s at 256³ incl. converged DGP φ solve; % HBM roofline; vs FP64 oracle"
+UNIT = "steps/s"
+# Mean residual evaluations per solve of this workload as measured on GB300
+# (used by the oracle reference arm, which has no GPU run to read it from).
+E_PER_SOLVE_REF = 5.0
+
+
+def config(n_gpus):
+    return {"workload": "dgp_pm_%dcube_box%g_ns%g_rms%g_a%g-%g_%dsteps_tol%g" % (
+        WL["n"], WL["box"], WL["n_s"], WL["rms"], WL["a_start"], WL["a_end"], WL["run_steps"], WL["tol"]),
+        "mesh": WL["n"], "particles": WL["n"] ** 3, "box_mpc_h": WL["box"], "rc_H0": WL["rc_H0"],
+        "w": WL["w"], "tol": WL["tol"], "precision": "mixed (fp32 data, fp64 residual/discriminant/reductions)",
+        "parallelism": "replicas" if n_gpus > 1 else "single",
+        "l2": "inputs larger than L2 (particles 403 MB, fields 64 MB each); no flush"}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_fft_sample_seconds(nsamples, n=None):
+    """Time the FP64 oracle's FFT on the workload's mesh: each sample is one
+    axis pass of its four-step DFT over a quarter of a 256^3 field (one
+    twelfth of a 3D transform).  Runs in this process."""
+    import numpy as np
+    from oracle.fft import fft_axis
+    n = WL["n"] if n is None else n
+    rng = np.random.default_rng(0)
+    f = rng.standard_normal((n, n, n))
+    q = n // 4
+    slabs = [(f[:q], 2), (f[:q], 1), (f[:, :q], 0)]
+    fft_axis(slabs[0][0], slabs[0][1])  # untimed warm-up
+    ts = []
+    for j in range(nsamples):
+        s, ax = slabs[j % 3]
+        t0 = time.perf_counter()
+        fft_axis(s, ax)
+        ts.append(time.perf_counter() - t0)
+    return ts
+
+
+def oracle_steps_per_s(t_sample, e_per_solve):
+    """An oracle PM step of this workload does one field solve with 6 + 9 E 3D
+    transforms (E residual evaluations, each 1 forward + 8 inverse; plus delta,
+    the source, phi and 3 forces); a 3D transform is 12 samples."""
+    return 1.0 / (t_sample * 12.0 * (6.0 + 9.0 * e_per_solve))
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cores = os.cpu_count()
+    ts = oracle_fft_sample_seconds(args.warmup + args.steps)[args.warmup:]
+    t = sum(ts) / len(ts)
+    v = oracle_steps_per_s(t, E_PER_SOLVE_REF)
+    sample = ("FP64 oracle four-step FFT, one axis pass over a quarter of the 256^3 field per step (%.3f s); "
+              "steps/s = 1 / (12 x (6 + 9 x %.1f) x that): FFT work of one PM step with %.1f residual "
+              "evaluations per solve; deposit, gather and pointwise work not counted (upper bound)"
+              % (t, E_PER_SOLVE_REF, E_PER_SOLVE_REF))
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": config(args.gpus),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import __graft_entry__ as g
+    g.build()
+    from paper_0906_4548_gb300 import dgp, inputs
+
+    n, box = WL["n"], WL["box"]
+    bgi = dgp.dgp_background(WL["omega_m0"], WL["rc_H0"], WL["a_start"])
+    vf = WL["a_start"] ** 2 * bgi["E"] * bgi["growth_f"]
+    pos, mom, amp = inputs.zeldovich_particles(n, box, WL["n_s"], WL["rms"], WL["seed"] + rank, vf)
+    dev = torch.device("cuda", local)
+    ic = [torch.tensor(v.astype(np.float32), device=dev) for v in (*pos, *mom)]
+    cur = [t.clone() for t in ic]
+    parts = dgp.particles(*cur)
+    ctx = dgp.dgp_init(box, n, WL["rc_H0"], WL["omega_m0"], w=WL["w"], precision=dgp.DGP_MIXED,
+                       max_iter=WL["max_iter"], tol=WL["tol"])
+    dlna = math.log(WL["a_end"] / WL["a_start"]) / WL["run_steps"]
+    sched = [WL["a_start"] * math.exp(i * dlna) for i in range(max(args.steps, args.warmup) + 1)]
+
+    def restart():
+        for c, s in zip(cur, ic):
+            c.copy_(s)
+        dgp.dgp_reset(ctx)
+
+    def steps(k, infos=None):
+        for i in range(k):
+            inf = dgp.pm_step(ctx, parts, sched[i], sched[i + 1] - sched[i])
+            if infos is not None:
+                infos.append(inf)
+
+    restart()
+    steps(args.warmup)
+    restart()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        dgp.dgp_profile(ctx, True)
+        e0.record(stream)
+        steps(args.steps, infos)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = dgp.dgp_profile_read(ctx)
+    dgp.dgp_profile(ctx, False)
+    if dist:
+        dist.barrier()
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * args.steps / (ms / 1000.0)
+
+    # end to end through the public C ABI with host buffers (copies inside the timed region)
+    ne = args.steps if args.e2e_steps is None else args.e2e_steps
+    host = [torch.empty(n ** 3, dtype=torch.float32, pin_memory=True) for _ in range(6)]
+    for h, s in zip(host, ic):
+        h.copy_(s)
+    harr = [h.numpy() for h in host]
+    hparts = dgp.particles(*harr)
+    dgp.dgp_reset(ctx)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(ne):
+        dgp.pm_step_host(ctx, hparts, sched[i], sched[i + 1] - sched[i])
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": ne / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 6 * 4 * n ** 3,
+           "d2h_bytes_per_step": 6 * 4 * n ** 3}
+
+    # roofline of the dominant kernel (algorithmic bytes / event-timed duration)
+    peak, peak_kind = measured_peaks()
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    achieved = d["timed_bytes"] / (d["ms"] / 1000.0) / 1e9 if d["ms"] > 0 else 0.0
+    kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                   "gbs": round(v["timed_bytes"] / (v["ms"] / 1000.0) / 1e9, 1) if v["ms"] > 0 else None}
+               for k, v in prof.items() if v["launches"]}
+    evals = [i["iters"] + 1 for i in infos]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": config(world),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None, "kernel": dom,
+                         "peak_source": peak_kind},
+            "e2e": e2e, "gpu_launches": int(sum(v["launches"] for v in prof.values())),
+            "clocks": clk.summary(),
+            "solver": {"evals_per_solve_mean": sum(evals) / len(evals), "max_evals": max(evals),
+                       "final_a": sched[args.steps],
+                       "not_converged_steps": sum(1 for i in infos if i["status"] != 0),
+                       "max_norm_res": max(i["norm_res"] for i in infos), "amplitude_A": amp},
+            "kernels": kernels}
+    dgp.dgp_destroy(ctx)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ts = oracle_fft_sample_seconds(36)
+        t = sum(ts) / len(ts)
+        e_mean = sum(evals) / len(evals)
+        line["cpu_baseline"] = {
+            "value": oracle_steps_per_s(t, e_mean), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "36 axis passes of the FP64 oracle FFT over a quarter of the 256^3 field (%.3f s each); "
+                      "scaled to the FFT work of one PM step at the measured %.2f residual evaluations per "
+                      "solve (deposit, gather and pointwise work not counted: an upper bound)" % (t, e_mean)}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

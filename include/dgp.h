@@ -1,0 +1,201 @@
+/*
+ * dgp.h -- C ABI of the GB300 DGP particle-mesh library.
+ *
+ * The library implements the hot path of the particle-mesh N-body method for
+ * brane-induced (DGP) gravity of Chan & Scoccimarro, "Large-Scale Structure in
+ * Brane-Induced Gravity II. Numerical Simulations":
+ *   - the nonlinear field equation for the brane-bending mode C (Eq. FullDGP2)
+ *     solved for D = lapbar^2 C by FFT-relaxation with the w-splitting of
+ *     Eqs. FullDGP2wpara, nabla^2Cwpara and Bwpara (Secs. III.B-C);
+ *   - the modified Poisson equation for phi (Eq. FullDGP1), solved in Fourier
+ *     space, and the spectral force i k phi (Sec. III.A);
+ *   - CIC mass assignment (Eq. CIC) and CIC force interpolation, and the
+ *     second-order leapfrog in uniform steps of ln a (Sec. III.A);
+ *   - the power-spectrum and bispectrum estimators of Secs. IV and VI.
+ *
+ * Conventions used by every call
+ *   Units: lengths in Mpc/h, time in 1/H0 (H0 = 1).  c/H0 is
+ *   dgp_cosmology.c_over_H0 (2997.92458 Mpc/h).  Mesh: n^3 points at x = i d,
+ *   d = box / n, periodic.  A real mesh field is n^3 contiguous elements in
+ *   C order [x][y][z] (z fastest).  Element type: float when the context
+ *   precision is DGP_FP32 or DGP_MIXED, double when it is DGP_FP64.
+ *   Particles: struct-of-arrays, same element type; p = a^2 dx/dt.
+ *   Streams: every call enqueues its GPU work on the stream given to
+ *   dgp_init (NULL = the legacy default stream).  Calls that return host
+ *   values (solve info, spectra) synchronise that stream before returning.
+ *   Ownership: the caller owns every buffer it passes; the library never
+ *   frees or retains them past the call.  The context owns its workspace,
+ *   allocated in dgp_init and freed in dgp_destroy.
+ *   Errors: every int-returning call returns a dgp_status; no call throws or
+ *   aborts.  After DGP_E_CUDA the context should be destroyed.
+ *   Threads: a context is not thread safe; use one context per host thread.
+ */
+#ifndef DGP_H
+#define DGP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DGP_OK = 0,
+  DGP_E_INVALID = 1,       /* bad argument (size, pointer, parameter range) */
+  DGP_E_CUDA = 2,          /* a CUDA runtime call failed */
+  DGP_E_NOMEM = 3,         /* device or host allocation failed */
+  DGP_E_NONFINITE = 4,     /* NaN or Inf in an input field or in the solve */
+  DGP_E_NOT_CONVERGED = 5, /* tolerance not met: best iterate used, info filled */
+  DGP_E_BAD_POINTS = 6,    /* discriminant clamped at some points (informational) */
+  DGP_E_TIMEOUT = 7,       /* a bounded device-side wait gave up */
+  DGP_E_STATE = 8          /* call not valid in the context's current state */
+} dgp_status;
+
+enum { DGP_FP32 = 0, DGP_MIXED = 1, DGP_FP64 = 2 };
+enum { DGP_GRAVITY_NL = 0, DGP_GRAVITY_LDGP = 1, DGP_GRAVITY_GRH = 2 };
+
+typedef struct dgp_ctx dgp_ctx;
+
+typedef struct {
+  double omega_m0;   /* present matter density parameter */
+  double c_over_H0;  /* c / H0 in Mpc/h (2997.92458) */
+} dgp_cosmology;
+
+typedef struct {
+  double box;        /* side of the periodic box, Mpc/h, > 0 */
+  int n;             /* mesh points per side: 16, 32, 64, 128, 256 or 512 */
+  double rc_H0;      /* crossover scale r_c in units of c/H0, > 0 (Sec. II) */
+  double w;          /* splitting parameter of Eq. FullDGP2wpara, 0 <= w < 1 */
+  int precision;     /* DGP_FP32, DGP_MIXED or DGP_FP64 */
+  int gravity;       /* DGP_GRAVITY_NL (Eqs. FullDGP1-2), _LDGP (Eq. LinearDGP), _GRH (Eq. GRPoisson) */
+  int local_only;    /* nonzero: drop the sqrt(-lapbar) terms (Appendix Eq. FullDGP2simp) */
+  int max_iter;      /* relaxation updates per solve before giving up, >= 0 */
+  double tol;        /* normalised-residual tolerance used by pm_step (Eq. normres) */
+} dgp_params;
+
+typedef struct {
+  int iters;            /* relaxation updates before the accepted iterate */
+  double norm_res;      /* <|R|>/eps of the accepted iterate (Eq. normres) */
+  double min_norm_res;  /* smallest <|R|>/eps seen */
+  double bad_fraction;  /* bad points / n^3 in the last update (Sec. III.C) */
+  double eps;           /* <|S|>, the normalisation of Eq. normres */
+  int status;           /* DGP_OK or DGP_E_NOT_CONVERGED */
+} dgp_solve_info;
+
+typedef struct {
+  void *x, *y, *z;      /* device positions in [0, box) */
+  void *px, *py, *pz;   /* device momenta p = a^2 dx/dt */
+  int64_t n;            /* number of particles, >= 0 */
+} dgp_particles;
+
+typedef struct {
+  double E, eta, alpha, beta, s, c2, c3, q, omega_m;
+  double geff_local;    /* k -> infinity limit of Eq. Geff */
+  double growth_D;      /* linear growth factor, D = a deep in matter domination */
+  double growth_f;      /* dlnD/dlna */
+} dgp_background_t;
+
+/* Host-only.  DGP background at scale factor a (Sec. II): E = H/H0 is the
+ * self-accelerating root of Eq. DGPFriedmann, eta = r_c H, and alpha, beta,
+ * q, the coefficients s = 3(eta-1)/eta, c2 = 3 beta (eta-1)/(2 eta - 1),
+ * c3 = (3 eta^2 - 5 eta + 1)/(2 eta^2 (2 eta - 1)) of Eqs. FullDGP1-2, plus the
+ * linear growth rate with the local G_eff (used for Zel'dovich velocities).
+ * Returns DGP_E_INVALID for a <= 0, rc_H0 <= 0, omega_m0 < 0 or out == NULL. */
+int dgp_background(const dgp_cosmology *cosmo, double rc_H0, double a, dgp_background_t *out);
+
+/* Create a context: validates p, allocates all device workspace for an n^3
+ * mesh, and binds cuda_stream (a cudaStream_t, may be NULL).  *out is set
+ * to NULL on failure.  n must be one of the sizes listed in dgp_params. */
+int dgp_init(dgp_ctx **out, const dgp_params *p, const dgp_cosmology *cosmo, void *cuda_stream);
+
+/* Free everything the context owns.  NULL is accepted. */
+void dgp_destroy(dgp_ctx *c);
+
+/* Static description of a status code. */
+const char *dgp_strerror(int status);
+
+/* Forget the warm-start solution and the cached mesh force. */
+int dgp_reset(dgp_ctx *c);
+
+/* Solve Eqs. FullDGP2 and FullDGP1 for phi at scale factor a (Secs. III.B-C).
+ *   delta: device n^3 density contrast (its mean is ignored);
+ *   phi:   device n^3 output, code units (phi(k = 0) = 0); may be NULL when
+ *          only the info or the warm start is wanted.
+ * The relaxation starts from the context's previous accepted solution if
+ * there is one (Sec. III.B, warm start), else from the linear solution, and
+ * stops when <|R|>/eps < tol or after max_iter updates; without convergence
+ * phi is built from the minimum-residual iterate and DGP_E_NOT_CONVERGED is
+ * returned.  info (host, may be NULL) is filled in every case that reaches
+ * the solver.  DGP_E_NONFINITE if delta holds NaN/Inf. */
+int dgp_solve_phi(dgp_ctx *c, double a, const void *delta, void *phi, double tol,
+                  dgp_solve_info *info);
+
+/* Same solve; writes the mesh force g = -grad(phi) (Sec. III.A: i k phi
+ * transformed back) into three device n^3 fields gx, gy, gz (the Nyquist
+ * component of each derivative is zero).  phi may be NULL. */
+int dgp_solve_forces(dgp_ctx *c, double a, const void *delta, void *phi, void *gx, void *gy,
+                     void *gz, double tol, dgp_solve_info *info);
+
+/* Copy the accepted solution D = lapbar^2 C of the last nonlinear solve
+ * (the warm start of the next one, Sec. III.B) into the device n^3 field D,
+ * with its mean removed (the solver works with mean-free D).
+ * DGP_E_STATE if no nonlinear solve has completed since init/reset. */
+int dgp_get_solution(dgp_ctx *c, void *D);
+
+/* CIC mass assignment (Eq. CIC) of unit-mass particles and the density
+ * contrast delta = rho / rho_bar - 1 (rho_bar: FP64 mean of the mesh).
+ * delta: device n^3 output.  Positions outside [0, box) are wrapped. */
+int dgp_deposit(dgp_ctx *c, const dgp_particles *parts, void *delta);
+
+/* One kick-drift-kick step from a to a + da, uniform in ln a (Sec. III.A):
+ * p += g(x, a) K(a, a_h); x += p Dr(a, a + da); p += g(x', a + da) K(a_h, a + da)
+ * with a_h the midpoint in ln a, K = int dlna / E and Dr = int dlna / (a^2 E).
+ * The force at the start reuses the mesh force the previous call left when
+ * that call ended at the same a with the same particle buffers; otherwise it
+ * is computed first.  The solve uses params.tol and the warm start.  info
+ * (host, may be NULL) describes the solve at a + da. */
+int pm_step(dgp_ctx *c, dgp_particles *parts, double a, double da, dgp_solve_info *info);
+
+/* pm_step on host particle arrays (pageable or pinned): copies them to the
+ * context's device buffers, steps, and copies them back before returning.
+ * The host arrays are float or double per the context precision, n <= the
+ * n^3 particles of the mesh. */
+int pm_step_host(dgp_ctx *c, dgp_particles *host_parts, double a, double da, dgp_solve_info *info);
+
+/* Power spectrum of a device n^3 field (Sec. IV):
+ * P(k_b) = box^3 <|delta_k / n^3|^2> over shells b = 1..nbins of width
+ * k_f = 2 pi / box centred on b k_f (a mode belongs to shell round(|k|/k_f)),
+ * no window deconvolution, no shot-noise subtraction.  Host outputs
+ * k[nbins] (mean |k| of the shell), pk[nbins], nmodes[nbins] (all n^3 modes
+ * counted once).  1 <= nbins <= n/2. */
+int power_spectrum(dgp_ctx *c, const void *delta, int nbins, double *k, double *pk, int64_t *nmodes);
+
+/* Bispectrum by the FFT shell-filter estimator (Sec. VI, Eq. Qdef): for each
+ * theta[i] (angle between k1 and k2), k3 = |k1 + k2|, shells of width dk
+ * (<= 0 means k_f) around k1, k2, k3; B = box^6/n^9 * sum_x d1 d2 d3 /
+ * sum_x I1 I2 I3 and Q = B / (P1 P2 + P2 P3 + P3 P1) with the shell powers.
+ * Host outputs b[ntheta], q[ntheta]. */
+int bispectrum(dgp_ctx *c, const void *delta, double k1, double k2, int ntheta, const double *theta,
+               double dk, double *b, double *q);
+
+/* Kernel accounting (not part of the paper's method; used to measure it).
+ * Every kernel launch of a context is counted per kind together with its
+ * algorithmic bytes (one read of each input and one write of each output).
+ * dgp_profile resets the counters; with timing != 0 each later launch is
+ * also bracketed by two CUDA events on the context's stream (adding two
+ * event records per launch).  dgp_profile_read synchronises on the pending
+ * events and returns, for kind in [0, DGP_KERNEL_KINDS): launches and bytes
+ * since the reset, and the timed launches, their summed duration (ms) and
+ * their bytes.  Any output pointer may be NULL. */
+#define DGP_KERNEL_KINDS 10
+int dgp_profile(dgp_ctx *c, int timing);
+int dgp_profile_read(dgp_ctx *c, int kind, int64_t *launches, double *bytes, int64_t *timed, double *ms,
+                     double *timed_bytes);
+/* Name of a kernel kind ("fft_z_r2c", "fft_y", "relax", ...), NULL if out of range. */
+const char *dgp_kernel_name(int kind);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGP_H */

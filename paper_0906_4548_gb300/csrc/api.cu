@@ -1,0 +1,809 @@
+// C ABI of the DGP library: context, host background, and the orchestration of
+// the FFT-relaxation solve (Secs. III.B-C), phi and forces (Eq. FullDGP1,
+// Sec. III.A), the kick-drift-kick step, and the estimators (Secs. IV, VI).
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "../../include/dgp.h"
+#include "kernels.cuh"
+
+namespace dgp {
+
+// ---------------------------------------------------------------- background
+// Eq. DGPFriedmann with H0 = 1: E^2 - E / rc - Om a^-3 = 0, '+' root.
+static double hubble_E(double a, double om, double rc) {
+  const double eps = 1.0 / rc;
+  return 0.5 * (eps + sqrt(eps * eps + 4.0 * om / (a * a * a)));
+}
+
+struct Coef {
+  double a, E, eta, alpha, beta, s, c2, c3, q, omega_m;
+};
+
+static Coef coefficients(double a, double om, double rc) {
+  Coef c;
+  c.a = a;
+  c.E = hubble_E(a, om, rc);
+  const double eta = rc * c.E;
+  c.eta = eta;
+  const double den = eta * (2.0 * eta - 1.0);
+  c.alpha = 3.0 * (2.0 * eta * eta - 2.0 * eta + 1.0) / den;
+  c.beta = (2.0 * eta * eta - 2.0 * eta - 1.0) / den;
+  c.s = 3.0 * (eta - 1.0) / eta;
+  c.c2 = 3.0 * c.beta * (eta - 1.0) / (2.0 * eta - 1.0);
+  c.c3 = (3.0 * eta * eta - 5.0 * eta + 1.0) / (2.0 * eta * eta * (2.0 * eta - 1.0));
+  c.q = (2.0 - eta) / (2.0 * eta - 1.0);
+  c.omega_m = om / (a * a * a * c.E * c.E);
+  return c;
+}
+
+static double geff_local(const Coef& c) {
+  const double t = 2.0 * c.eta * (2.0 + c.q);
+  return (t - 4.0) / (t - 3.0);
+}
+
+// Linear growth D'' + (2 + dlnE/dlna) D' = 1.5 Omega_m(a) Geff_local D in ln a,
+// growing mode D = a at a = 1e-5, classical RK4 with 400 steps per e-fold.
+static void growth(double a_out, double om, double rc, double* D_out, double* f_out) {
+  auto rhs = [&](double lna, const double y[2], double dy[2]) {
+    const double a = exp(lna);
+    const Coef c = coefficients(a, om, rc);
+    const double dlnE = -3.0 * om / (a * a * a) / ((2.0 * c.E - 1.0 / rc) * c.E);
+    dy[0] = y[1];
+    dy[1] = -(2.0 + dlnE) * y[1] + 1.5 * c.omega_m * geff_local(c) * y[0];
+  };
+  const double x0 = log(1e-5), x1 = log(a_out);
+  int n = (int)ceil((x1 - x0) * 400.0);
+  if (n < 1) n = 1;
+  const double h = (x1 - x0) / n;
+  double y[2] = {1e-5, 1e-5}, k1[2], k2[2], k3[2], k4[2], t[2];
+  double x = x0;
+  for (int i = 0; i < n; ++i) {
+    rhs(x, y, k1);
+    for (int j = 0; j < 2; ++j) t[j] = y[j] + 0.5 * h * k1[j];
+    rhs(x + 0.5 * h, t, k2);
+    for (int j = 0; j < 2; ++j) t[j] = y[j] + 0.5 * h * k2[j];
+    rhs(x + 0.5 * h, t, k3);
+    for (int j = 0; j < 2; ++j) t[j] = y[j] + h * k3[j];
+    rhs(x + h, t, k4);
+    for (int j = 0; j < 2; ++j) y[j] += h / 6.0 * (k1[j] + 2 * k2[j] + 2 * k3[j] + k4[j]);
+    x += h;
+  }
+  *D_out = y[0];
+  *f_out = y[1] / y[0];
+}
+
+// 8-point Gauss-Legendre nodes and weights by Newton iteration on P_8.
+static void gauss_legendre8(double xs[8], double ws[8]) {
+  const int n = 8;
+  for (int i = 0; i < n; ++i) {
+    double x = cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (x * p1 - p0) / (x * x - 1.0);
+      const double dx = p1 / dp;
+      x -= dx;
+      if (fabs(dx) < 1e-16) break;
+    }
+    xs[i] = x;
+    ws[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+}
+
+// int_{ln a0}^{ln a1} dlna / (a^pw E): pw = 0 kick, pw = 2 drift (Sec. III.A
+// with p = a^2 dx/dt: dp/dlna = -grad phi / E, dx/dlna = p / (a^2 E)).
+static double time_integral(double a0, double a1, double om, double rc, int pw) {
+  double xs[8], ws[8];
+  gauss_legendre8(xs, ws);
+  const double l0 = log(a0), l1 = log(a1);
+  const double xm = 0.5 * (l0 + l1), xr = 0.5 * (l1 - l0);
+  double acc = 0.0;
+  for (int i = 0; i < 8; ++i) {
+    const double a = exp(xm + xr * xs[i]);
+    acc += ws[i] / (pow(a, pw) * hubble_E(a, om, rc));
+  }
+  return xr * acc;
+}
+
+// ---------------------------------------------------------------- engine
+// Kernel-level accounting.  Launches and algorithmic bytes are always counted;
+// when timing is on, each launch is bracketed by two events on the context's
+// stream and the durations are resolved when read.
+enum KernelKind { KK_Z_R2C = 0, KK_Z_C2R, KK_Y, KK_X_HESSIAN, KK_X_OTHER, KK_RELAX, KK_REDUCE, KK_DEPOSIT,
+                  KK_GATHER, KK_MISC, KK_COUNT };
+static const char* const kKernelNames[KK_COUNT] = {
+    "fft_z_r2c", "fft_z_c2r", "fft_y", "fft_x_hessian", "fft_x_other", "relax", "reduce", "cic_deposit",
+    "cic_gather_kick", "misc"};
+
+struct Profiler {
+  bool timing = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<std::pair<int, double>> pending;  // (kind, bytes) per event pair
+  int64_t launches[KK_COUNT] = {};
+  double bytes[KK_COUNT] = {};
+  double ms[KK_COUNT] = {};
+  int64_t timed[KK_COUNT] = {};
+  double timed_bytes[KK_COUNT] = {};
+
+  void reset(bool t) {
+    resolve();
+    timing = t;
+    for (int k = 0; k < KK_COUNT; ++k) { launches[k] = 0; bytes[k] = 0; ms[k] = 0; timed[k] = 0; timed_bytes[k] = 0; }
+  }
+  cudaEvent_t ev() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  int resolve() {
+    for (size_t i = 0; i < pending.size(); ++i) {
+      float t = 0.f;
+      if (cudaEventSynchronize(pool[2 * i + 1]) != cudaSuccess) return DGP_E_CUDA;
+      if (cudaEventElapsedTime(&t, pool[2 * i], pool[2 * i + 1]) != cudaSuccess) return DGP_E_CUDA;
+      ms[pending[i].first] += t;
+      timed[pending[i].first] += 1;
+      timed_bytes[pending[i].first] += pending[i].second;
+    }
+    pending.clear();
+    used = 0;
+    return DGP_OK;
+  }
+  template <class F>
+  void run(int kind, double b, cudaStream_t s, F&& f) {
+    launches[kind] += 1;
+    bytes[kind] += b;
+    if (!timing) { f(); return; }
+    if (pending.size() >= 8192) resolve();
+    cudaEventRecord(ev(), s);
+    f();
+    cudaEventRecord(ev(), s);
+    pending.push_back({kind, b});
+  }
+  ~Profiler() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+class EngineBase {
+ public:
+  dgp_params p;
+  dgp_cosmology cosmo;
+  cudaStream_t stream = nullptr;
+  virtual ~EngineBase() {}
+  virtual int init() = 0;
+  virtual int solve(double a, const void* delta, void* phi, void* gx, void* gy, void* gz, double tol,
+                    dgp_solve_info* info) = 0;
+  virtual int deposit(const dgp_particles* parts, void* delta) = 0;
+  virtual int step(dgp_particles* parts, double a, double da, dgp_solve_info* info) = 0;
+  virtual int step_host(dgp_particles* parts, double a, double da, dgp_solve_info* info) = 0;
+  virtual int pk(const void* delta, int nbins, double* k, double* pk, int64_t* nmodes) = 0;
+  virtual int bispec(const void* delta, double k1, double k2, int ntheta, const double* theta, double dk,
+                     double* b, double* q) = 0;
+  virtual void reset() = 0;
+  virtual int get_solution(void* D) = 0;
+  Profiler prof;
+};
+
+#define DGP_CUDA(call)                          \
+  do {                                          \
+    if ((call) != cudaSuccess) return DGP_E_CUDA; \
+  } while (0)
+#define DGP_CHECK_LAUNCH()                                 \
+  do {                                                     \
+    if (cudaGetLastError() != cudaSuccess) return DGP_E_CUDA; \
+  } while (0)
+
+template <typename T, int N>
+class Engine : public EngineBase {
+  using V = vec2_t<T>;
+  static constexpr int64_t M = (int64_t)N * N * N;
+  static constexpr int64_t SPEC = (int64_t)(N / 2 + 1) * N * N;
+
+  T* rD[3] = {nullptr, nullptr, nullptr};
+  T* rS = nullptr;
+  T* rH[6] = {};
+  T* rRho = nullptr;
+  T* rG[3] = {};
+  V* sD = nullptr;
+  V* sDelta = nullptr;
+  V* s6[6] = {};
+  V* tw = nullptr;
+  double* partials = nullptr;
+  int nblocks = 0;
+  double* d_rstats = nullptr;   // [3][4]: sum|R|, sum D, nbad, nonfinite per D buffer
+  double* d_misc = nullptr;     // [8]: sum rho, sum |S|, ...
+  double* h_stats = nullptr;    // pinned host [8]
+  double* pk_partials = nullptr;
+  double* d_pk = nullptr;
+  int pk_blocks = 0;
+  int wcur = -1;                // buffer of the warm-start solution
+  bool force_valid = false;
+  double force_a = 0.0;
+  const void* force_x = nullptr;
+  int64_t force_np = -1;
+  T* hp[6] = {};                // device copies for pm_step_host
+  int64_t hp_n = 0;
+
+ public:
+  ~Engine() override {
+    cudaStreamSynchronize(stream);
+    for (int i = 0; i < 3; ++i) cudaFree(rD[i]);
+    cudaFree(rS);
+    for (int i = 0; i < 6; ++i) { cudaFree(rH[i]); cudaFree(s6[i]); cudaFree(hp[i]); }
+    cudaFree(rRho);
+    for (int i = 0; i < 3; ++i) cudaFree(rG[i]);
+    cudaFree(sD); cudaFree(sDelta); cudaFree(tw);
+    cudaFree(partials); cudaFree(d_rstats); cudaFree(d_misc);
+    cudaFree(pk_partials); cudaFree(d_pk);
+    cudaFreeHost(h_stats);
+  }
+
+  int init() override {
+    const size_t rb = sizeof(T) * M, sb = sizeof(V) * SPEC;
+    for (int i = 0; i < 3; ++i) if (cudaMalloc(&rD[i], rb) != cudaSuccess) return DGP_E_NOMEM;
+    if (cudaMalloc(&rS, rb) != cudaSuccess) return DGP_E_NOMEM;
+    for (int i = 0; i < 6; ++i) {
+      if (cudaMalloc(&rH[i], rb) != cudaSuccess) return DGP_E_NOMEM;
+      if (cudaMalloc(&s6[i], sb) != cudaSuccess) return DGP_E_NOMEM;
+    }
+    if (cudaMalloc(&rRho, rb) != cudaSuccess) return DGP_E_NOMEM;
+    for (int i = 0; i < 3; ++i) if (cudaMalloc(&rG[i], rb) != cudaSuccess) return DGP_E_NOMEM;
+    if (cudaMalloc(&sD, sb) != cudaSuccess) return DGP_E_NOMEM;
+    if (cudaMalloc(&sDelta, sb) != cudaSuccess) return DGP_E_NOMEM;
+    nblocks = num_sms() * 4;
+    if (cudaMalloc(&partials, sizeof(double) * 4 * nblocks) != cudaSuccess) return DGP_E_NOMEM;
+    if (cudaMalloc(&d_rstats, sizeof(double) * 12) != cudaSuccess) return DGP_E_NOMEM;
+    if (cudaMalloc(&d_misc, sizeof(double) * 8) != cudaSuccess) return DGP_E_NOMEM;
+    if (cudaMallocHost(&h_stats, sizeof(double) * 8) != cudaSuccess) return DGP_E_NOMEM;
+    pk_blocks = x_pass_blocks<T, N>();
+    if (cudaMalloc(&pk_partials, sizeof(double) * 3 * (N / 2) * (size_t)pk_blocks) != cudaSuccess) return DGP_E_NOMEM;
+    if (cudaMalloc(&d_pk, sizeof(double) * 3 * (N / 2)) != cudaSuccess) return DGP_E_NOMEM;
+    // twiddles W_N^t = exp(-2 pi i t / N), computed in FP64 and rounded once
+    V htw[N];
+    for (int t = 0; t < N; ++t) {
+      const double ang = 2.0 * M_PI * (double)t / (double)N;
+      htw[t].x = (T)cos(ang);
+      htw[t].y = (T)(-sin(ang));
+    }
+    if (cudaMalloc(&tw, sizeof(V) * N) != cudaSuccess) return DGP_E_NOMEM;
+    DGP_CUDA(cudaMemcpy(tw, htw, sizeof(V) * N, cudaMemcpyHostToDevice));
+    DGP_CUDA(cudaMemset(d_rstats, 0, sizeof(double) * 12));
+    return DGP_OK;
+  }
+
+  void reset() override {
+    wcur = -1;
+    force_valid = false;
+  }
+
+  int get_solution(void* D) override {
+    if (!D) return DGP_E_INVALID;
+    if (wcur < 0) return DGP_E_STATE;
+    // D - mean(D): the mean was reduced in FP64 when the buffer was produced
+    ZPrologue pro{d_rstats + 4 * wcur + 1, 1.0 / (double)M, 2};
+    prof.run(KK_MISC, 2 * RB, stream, [&] { launch_sub_mean<T>(rD[wcur], (T*)D, M, pro.mean_src, stream); });
+    DGP_CHECK_LAUNCH();
+    return DGP_OK;
+  }
+
+ private:
+  KParams kparams(const Coef& c) const {
+    KParams kp;
+    kp.box = p.box;
+    kp.inv_m = 1.0 / (double)M;
+    kp.kbar_fac = cosmo.c_over_H0 / (c.a * c.E);
+    kp.local_only = p.local_only;
+    kp.eta = c.eta; kp.alpha = c.alpha; kp.beta = c.beta; kp.s = c.s; kp.c2 = c.c2; kp.c3 = c.c3;
+    kp.aE = c.a * c.E; kp.q = c.q; kp.rc_H0 = p.rc_H0; kp.a = c.a;
+    kp.gravity = p.gravity;
+    return kp;
+  }
+
+  static FieldSet<T> fs(V* const* ptrs, int n) {
+    FieldSet<T> f;
+    for (int i = 0; i < kMaxFields; ++i) f.p[i] = i < n ? ptrs[i] : nullptr;
+    return f;
+  }
+
+  // real field -> S2 (z and y forward transforms)
+  static constexpr double RB = (double)sizeof(T) * M;      // one real field
+  static constexpr double SB = (double)sizeof(V) * SPEC;   // one half spectrum
+
+  int forward_zy(const T* in, V* out, ZPrologue pro) {
+    prof.run(KK_Z_R2C, RB + SB, stream, [&] { launch_fft_z_r2c<T, N>(in, 0, out, 0, 1, pro, tw, stream); });
+    V* o[1] = {out};
+    prof.run(KK_Y, 2 * SB, stream, [&] { launch_fft_y<T, N>(fs(o, 1), 1, false, tw, stream); });
+    DGP_CHECK_LAUNCH();
+    return DGP_OK;
+  }
+
+  // x-op outputs (already in s6[0..n)) -> y inverse -> z inverse into real fields
+  int inverse_yz(V* const* spec, T* const* out, int n) {
+    prof.run(KK_Y, 2 * SB * n, stream, [&] { launch_fft_y<T, N>(fs(spec, n), n, true, tw, stream); });
+    prof.run(KK_Z_C2R, (RB + SB) * n, stream, [&] { launch_fft_z_c2r<T, N>(fs(spec, n), out, n, tw, stream); });
+    DGP_CHECK_LAUNCH();
+    return DGP_OK;
+  }
+
+  int reduce_sum(const T* a, bool absval, double* out) {
+    prof.run(KK_REDUCE, RB, stream, [&] { launch_sum<T>(a, M, absval, partials, nblocks, stream); });
+    prof.run(KK_REDUCE, 8.0 * nblocks, stream, [&] { launch_finalize(partials, nblocks, 1, out, stream); });
+    DGP_CHECK_LAUNCH();
+    return DGP_OK;
+  }
+
+  int fetch(const double* dsrc, int n) {
+    DGP_CUDA(cudaMemcpyAsync(h_stats, dsrc, sizeof(double) * n, cudaMemcpyDeviceToHost, stream));
+    DGP_CUDA(cudaStreamSynchronize(stream));
+    return DGP_OK;
+  }
+
+  // Field solve at scale factor a.  delta is a density contrast, or (from_rho)
+  // a CIC mass mesh turned into rho / rho_bar - 1 on the fly.  Outputs:
+  // phi (may be null) and forces g (all null or all set).
+  int solve_impl(double a, const T* src, bool from_rho, T* phi, T* g0, T* g1, T* g2, double tol,
+                 dgp_solve_info* info) {
+    int rc;
+    const Coef c = coefficients(a, cosmo.omega_m0, p.rc_H0);
+    const KParams kp = kparams(c);
+    ZPrologue pro{nullptr, 1.0 / (double)M, 0};
+    if (from_rho) {
+      if ((rc = reduce_sum(src, false, d_misc + 0))) return rc;
+      pro.mean_src = d_misc + 0;
+      pro.kind = 1;
+    }
+    if ((rc = forward_zy(src, sDelta, pro))) return rc;
+    dgp_solve_info inf;
+    memset(&inf, 0, sizeof(inf));
+    int accepted = -1;
+    int status = DGP_OK;
+
+    if (p.gravity == DGP_GRAVITY_NL) {
+      const bool need_lin = wcur < 0;
+      prof.run(KK_X_OTHER, SB * (need_lin ? 3 : 2), stream, [&] {
+        launch_fft_x_op<T, N>(need_lin ? XOP_SOURCE_LIN : XOP_SOURCE, sDelta, nullptr, fs(s6, 2), 0, kp, nullptr, 0,
+                              0, 0, tw, stream);
+      });
+      int j0 = need_lin ? 0 : wcur;
+      T* outs[2] = {rS, rD[j0]};
+      if ((rc = inverse_yz(s6, outs, need_lin ? 2 : 1))) return rc;
+      if ((rc = reduce_sum(rS, true, d_misc + 1))) return rc;
+      if (need_lin && (rc = reduce_sum(rD[j0], false, d_rstats + 4 * j0 + 1))) return rc;
+      if ((rc = fetch(d_misc + 1, 1))) return rc;
+      const double eps = h_stats[0] / (double)M;
+      if (!isfinite(eps)) return DGP_E_NONFINITE;
+      // Eq. normres divides by eps; a zero source (uniform density) has no
+      // scale, and the absolute mean residual is monitored instead.
+      const double rnorm = eps > 0.0 ? eps : 1.0;
+      inf.eps = eps;
+
+      const RelaxParams rp{c.alpha, p.w, c.c2, 1.0 / (double)M};
+      int cur = j0, best = -1, best_it = -1, spec_of = -1;
+      double rbest = INFINITY, rprev = INFINITY, prev_nbad = 0.0, last_bad = 0.0;
+      bool converged = false;
+      for (int it = 0; it <= p.max_iter; ++it) {
+        if ((rc = forward_zy(rD[cur], sD, ZPrologue{nullptr, 0.0, 0}))) return rc;
+        spec_of = cur;
+        prof.run(KK_X_HESSIAN, 7 * SB, stream, [&] {
+          launch_fft_x_op<T, N>(XOP_HESSIAN, sD, nullptr, fs(s6, 6), 0, kp, nullptr, 0, 0, 0, tw, stream);
+        });
+        if ((rc = inverse_yz(s6, rH, 6))) return rc;
+        int nxt = 0;
+        while (nxt == cur || nxt == best) ++nxt;
+        const T* H6[6] = {rH[0], rH[1], rH[2], rH[3], rH[4], rH[5]};
+        // arithmetic of R, B' and Delta: FP64 in the mixed and FP64 paths, FP32 in the plain FP32 path
+        prof.run(KK_RELAX, 9 * RB, stream, [&] {
+          if constexpr (sizeof(T) == 8) {
+            launch_relax<T, double>(rD[cur], d_rstats + 4 * cur + 1, H6, rS, rD[nxt], M, rp, partials, nblocks,
+                                    stream);
+          } else {
+            if (p.precision == DGP_MIXED)
+              launch_relax<T, double>(rD[cur], d_rstats + 4 * cur + 1, H6, rS, rD[nxt], M, rp, partials, nblocks,
+                                      stream);
+            else
+              launch_relax<T, float>(rD[cur], d_rstats + 4 * cur + 1, H6, rS, rD[nxt], M, rp, partials, nblocks,
+                                     stream);
+          }
+        });
+        prof.run(KK_REDUCE, 32.0 * nblocks, stream,
+                 [&] { launch_finalize(partials, nblocks, 4, d_rstats + 4 * nxt, stream); });
+        DGP_CHECK_LAUNCH();
+        if ((rc = fetch(d_rstats + 4 * nxt, 4))) return rc;
+        const double r = h_stats[0] / (double)M / rnorm;
+        const double nbad = h_stats[2];
+        last_bad = nbad;
+        if (h_stats[3] > 0.0 || !isfinite(r)) return DGP_E_NONFINITE;
+        if (r < rbest) { rbest = r; best = cur; best_it = it; }
+        if (r < tol) { converged = true; break; }
+        if (it == p.max_iter) break;
+        if (it > 0 && prev_nbad > 0.0 && r > rprev) break;
+        if (it - best_it >= 10) break;
+        rprev = r;
+        prev_nbad = nbad;
+        cur = nxt;
+      }
+      accepted = best;
+      inf.iters = best_it;
+      inf.norm_res = rbest;
+      inf.min_norm_res = rbest;
+      inf.bad_fraction = last_bad / (double)M;
+      status = converged ? DGP_OK : DGP_E_NOT_CONVERGED;
+      inf.status = status;
+      wcur = accepted;
+      if (spec_of != accepted && (rc = forward_zy(rD[accepted], sD, ZPrologue{nullptr, 0.0, 0}))) return rc;
+    }
+
+    // phi and forces (Eq. FullDGP1; g = -grad phi)
+    V* outs[4] = {s6[0], s6[1], s6[2], s6[3]};
+    int mask = 0;
+    if (phi) mask |= 1;
+    if (g0) mask |= 14;
+    if (mask) {
+      const int nin = p.gravity == DGP_GRAVITY_NL ? 2 : 1;
+      prof.run(KK_X_OTHER, SB * (nin + __builtin_popcount(mask)), stream, [&] {
+        launch_fft_x_op<T, N>(XOP_PHI_FORCE, sDelta, sD, fs(outs, 4), mask, kp, nullptr, 0, 0, 0, tw, stream);
+      });
+      V* sp[4];
+      T* rp_[4];
+      int n = 0;
+      if (phi) { sp[n] = s6[0]; rp_[n] = phi; ++n; }
+      if (g0) {
+        sp[n] = s6[1]; rp_[n] = g0; ++n;
+        sp[n] = s6[2]; rp_[n] = g1; ++n;
+        sp[n] = s6[3]; rp_[n] = g2; ++n;
+      }
+      if ((rc = inverse_yz(sp, rp_, n))) return rc;
+    }
+    if (info) {
+      *info = inf;
+      DGP_CUDA(cudaStreamSynchronize(stream));
+    }
+    return status;
+  }
+
+  CicParams cic() const {
+    CicParams cp;
+    cp.n = N;
+    const double inv = (double)N / p.box;
+    cp.inv_d = inv;
+    cp.inv_d_hi = (float)inv;
+    cp.inv_d_lo = (float)(inv - (double)cp.inv_d_hi);
+    cp.box = p.box;
+    return cp;
+  }
+
+  static bool valid_parts(const dgp_particles* pp) {
+    if (!pp || pp->n < 0) return false;
+    if (pp->n == 0) return true;
+    return pp->x && pp->y && pp->z && pp->px && pp->py && pp->pz;
+  }
+
+  int forces_at(const dgp_particles* pp, double a, dgp_solve_info* info) {
+    prof.run(KK_MISC, RB, stream, [&] { launch_fill<T>(rRho, M, (T)0, stream); });
+    prof.run(KK_DEPOSIT, 3.0 * sizeof(T) * pp->n + RB, stream, [&] {
+      launch_cic_deposit<T>((const T*)pp->x, (const T*)pp->y, (const T*)pp->z, pp->n, rRho, cic(), stream);
+    });
+    DGP_CHECK_LAUNCH();
+    const int rc = solve_impl(a, rRho, true, nullptr, rG[0], rG[1], rG[2], p.tol, info);
+    if (rc != DGP_OK && rc != DGP_E_NOT_CONVERGED) return rc;
+    force_valid = true;
+    force_a = a;
+    force_x = pp->x;
+    force_np = pp->n;
+    return DGP_OK;
+  }
+
+ public:
+  int solve(double a, const void* delta, void* phi, void* gx, void* gy, void* gz, double tol,
+            dgp_solve_info* info) override {
+    force_valid = false;
+    return solve_impl(a, (const T*)delta, false, (T*)phi, (T*)gx, (T*)gy, (T*)gz, tol, info);
+  }
+
+  int deposit(const dgp_particles* pp, void* delta) override {
+    if (!valid_parts(pp) || !delta) return DGP_E_INVALID;
+    if (pp->n == 0) return DGP_E_INVALID;
+    prof.run(KK_MISC, RB, stream, [&] { launch_fill<T>(rRho, M, (T)0, stream); });
+    prof.run(KK_DEPOSIT, 3.0 * sizeof(T) * pp->n + RB, stream, [&] {
+      launch_cic_deposit<T>((const T*)pp->x, (const T*)pp->y, (const T*)pp->z, pp->n, rRho, cic(), stream);
+    });
+    int rc;
+    if ((rc = reduce_sum(rRho, false, d_misc + 0))) return rc;
+    prof.run(KK_MISC, 2 * RB, stream, [&] { launch_density_contrast<T>(rRho, (T*)delta, M, d_misc + 0, stream); });
+    DGP_CHECK_LAUNCH();
+    return DGP_OK;
+  }
+
+  int step(dgp_particles* pp, double a, double da, dgp_solve_info* info) override {
+    if (!valid_parts(pp) || pp->n == 0) return DGP_E_INVALID;
+    if (!(a > 0.0) || !(da > 0.0) || !isfinite(a + da)) return DGP_E_INVALID;
+    const double a1 = a + da;
+    const double ah = exp(0.5 * (log(a) + log(a1)));
+    const double om = cosmo.omega_m0, rc_ = p.rc_H0;
+    int rc;
+    const bool reuse = force_valid && force_x == pp->x && force_np == pp->n && fabs(force_a - a) <= 1e-12 * a;
+    if (!reuse && (rc = forces_at(pp, a, nullptr))) return rc;
+    const CicParams cp = cic();
+    const double k1 = time_integral(a, ah, om, rc_, 0), dr = time_integral(a, a1, om, rc_, 2);
+    prof.run(KK_GATHER, 12.0 * sizeof(T) * pp->n + 3 * RB, stream, [&] {
+      launch_gather_kick<T>((T*)pp->x, (T*)pp->y, (T*)pp->z, (T*)pp->px, (T*)pp->py, (T*)pp->pz, pp->n, rG[0],
+                            rG[1], rG[2], cp, k1, dr, 1, stream);
+    });
+    DGP_CHECK_LAUNCH();
+    if ((rc = forces_at(pp, a1, info))) return rc;
+    const double k2 = time_integral(ah, a1, om, rc_, 0);
+    prof.run(KK_GATHER, 9.0 * sizeof(T) * pp->n + 3 * RB, stream, [&] {
+      launch_gather_kick<T>((T*)pp->x, (T*)pp->y, (T*)pp->z, (T*)pp->px, (T*)pp->py, (T*)pp->pz, pp->n, rG[0],
+                            rG[1], rG[2], cp, k2, 0.0, 0, stream);
+    });
+    DGP_CHECK_LAUNCH();
+    return DGP_OK;
+  }
+
+  int step_host(dgp_particles* hpp, double a, double da, dgp_solve_info* info) override {
+    if (!valid_parts(hpp) || hpp->n == 0) return DGP_E_INVALID;
+    if (hp_n < hpp->n) {
+      for (int i = 0; i < 6; ++i) {
+        cudaFree(hp[i]);
+        hp[i] = nullptr;
+        if (cudaMalloc(&hp[i], sizeof(T) * hpp->n) != cudaSuccess) { hp_n = 0; return DGP_E_NOMEM; }
+      }
+      hp_n = hpp->n;
+    }
+    void* src[6] = {hpp->x, hpp->y, hpp->z, hpp->px, hpp->py, hpp->pz};
+    const size_t bytes = sizeof(T) * hpp->n;
+    for (int i = 0; i < 6; ++i) DGP_CUDA(cudaMemcpyAsync(hp[i], src[i], bytes, cudaMemcpyHostToDevice, stream));
+    dgp_particles dp{hp[0], hp[1], hp[2], hp[3], hp[4], hp[5], hpp->n};
+    const int rc = step(&dp, a, da, info);
+    if (rc != DGP_OK) return rc;
+    for (int i = 0; i < 6; ++i) DGP_CUDA(cudaMemcpyAsync(src[i], hp[i], bytes, cudaMemcpyDeviceToHost, stream));
+    DGP_CUDA(cudaStreamSynchronize(stream));
+    return DGP_OK;
+  }
+
+  int pk(const void* delta, int nbins, double* k, double* pkv, int64_t* nmodes) override {
+    if (!delta || !k || !pkv || !nmodes || nbins < 1 || nbins > N / 2) return DGP_E_INVALID;
+    int rc;
+    if ((rc = forward_zy((const T*)delta, s6[0], ZPrologue{nullptr, 0.0, 0}))) return rc;
+    const Coef c = coefficients(1.0, cosmo.omega_m0, p.rc_H0);
+    KParams kp = kparams(c);
+    prof.run(KK_X_OTHER, SB, stream, [&] {
+      launch_fft_x_op<T, N>(XOP_PK, s6[0], nullptr, fs(s6, 0), 0, kp, pk_partials, nbins, 0, 0, tw, stream);
+    });
+    prof.run(KK_REDUCE, 24.0 * nbins * pk_blocks, stream,
+             [&] { launch_finalize(pk_partials, pk_blocks, 3 * nbins, d_pk, stream); });
+    DGP_CHECK_LAUNCH();
+    double hb[3 * 256];
+    DGP_CUDA(cudaMemcpyAsync(hb, d_pk, sizeof(double) * 3 * nbins, cudaMemcpyDeviceToHost, stream));
+    DGP_CUDA(cudaStreamSynchronize(stream));
+    for (int b = 0; b < nbins; ++b) {
+      const double cnt = hb[b];
+      nmodes[b] = (int64_t)llround(cnt);
+      k[b] = cnt > 0 ? hb[nbins + b] / cnt : NAN;
+      pkv[b] = cnt > 0 ? hb[2 * nbins + b] / cnt : NAN;
+    }
+    return DGP_OK;
+  }
+
+  int bispec(const void* delta, double k1, double k2, int ntheta, const double* theta, double dk, double* b,
+             double* q) override {
+    if (!delta || ntheta < 0 || (ntheta > 0 && (!theta || !b || !q)) || !(k1 > 0) || !(k2 > 0))
+      return DGP_E_INVALID;
+    int rc;
+    const double kf = 2.0 * M_PI / p.box;
+    if (!(dk > 0)) dk = kf;
+    // delta's S2 in s6[5]; each shell uses s6[0..1] and two real fields
+    if ((rc = forward_zy((const T*)delta, s6[5], ZPrologue{nullptr, 0.0, 0}))) return rc;
+    const Coef c = coefficients(1.0, cosmo.omega_m0, p.rc_H0);
+    const KParams kp = kparams(c);
+    auto shell = [&](double kc, T* d, T* ind) -> int {
+      prof.run(KK_X_OTHER, 3 * SB, stream, [&] {
+        launch_fft_x_op<T, N>(XOP_SHELL, s6[5], nullptr, fs(s6, 2), 0, kp, nullptr, 0, (kc - 0.5 * dk) / kf,
+                              (kc + 0.5 * dk) / kf, tw, stream);
+      });
+      T* outs[2] = {d, ind};
+      return inverse_yz(s6, outs, 2);
+    };
+    auto dot3 = [&](const T* x, const T* y, const T* z, double* hv) -> int {
+      prof.run(KK_REDUCE, (z ? 3 : 2) * RB, stream,
+               [&] { launch_product3_sum<T>(x, y, z, M, partials, nblocks, stream); });
+      prof.run(KK_REDUCE, 8.0 * nblocks, stream, [&] { launch_finalize(partials, nblocks, 1, d_misc + 2, stream); });
+      DGP_CHECK_LAUNCH();
+      int r2 = fetch(d_misc + 2, 1);
+      *hv = h_stats[0];
+      return r2;
+    };
+    if ((rc = shell(k1, rH[0], rH[1]))) return rc;
+    if ((rc = shell(k2, rH[2], rH[3]))) return rc;
+    double d11, i11, d22, i22;
+    if ((rc = dot3(rH[0], rH[0], nullptr, &d11)) || (rc = dot3(rH[1], rH[1], nullptr, &i11))) return rc;
+    if ((rc = dot3(rH[2], rH[2], nullptr, &d22)) || (rc = dot3(rH[3], rH[3], nullptr, &i22))) return rc;
+    const double L3M2 = p.box * p.box * p.box / ((double)M * (double)M);
+    const double P1 = L3M2 * d11 / i11, P2 = L3M2 * d22 / i22;
+    for (int i = 0; i < ntheta; ++i) {
+      const double k3 = sqrt(k1 * k1 + k2 * k2 + 2.0 * k1 * k2 * cos(theta[i]));
+      if ((rc = shell(k3, rH[4], rH[5]))) return rc;
+      double ddd, iii, d33, i33;
+      if ((rc = dot3(rH[0], rH[2], rH[4], &ddd)) || (rc = dot3(rH[1], rH[3], rH[5], &iii))) return rc;
+      if ((rc = dot3(rH[4], rH[4], nullptr, &d33)) || (rc = dot3(rH[5], rH[5], nullptr, &i33))) return rc;
+      const double P3 = L3M2 * d33 / i33;
+      const double L6M3 = pow(p.box, 6) / ((double)M * (double)M * (double)M);
+      b[i] = L6M3 * ddd / iii;
+      q[i] = b[i] / (P1 * P2 + P2 * P3 + P3 * P1);
+    }
+    return DGP_OK;
+  }
+};
+
+template <typename T>
+static EngineBase* make_engine(int n) {
+  switch (n) {
+    case 16: return new (std::nothrow) Engine<T, 16>();
+    case 32: return new (std::nothrow) Engine<T, 32>();
+    case 64: return new (std::nothrow) Engine<T, 64>();
+    case 128: return new (std::nothrow) Engine<T, 128>();
+    case 256: return new (std::nothrow) Engine<T, 256>();
+    case 512: return new (std::nothrow) Engine<T, 512>();
+    default: return nullptr;
+  }
+}
+
+}  // namespace dgp
+
+struct dgp_ctx {
+  dgp::EngineBase* eng;
+};
+
+extern "C" {
+
+const char* dgp_strerror(int status) {
+  switch (status) {
+    case DGP_OK: return "ok";
+    case DGP_E_INVALID: return "invalid argument";
+    case DGP_E_CUDA: return "CUDA runtime error";
+    case DGP_E_NOMEM: return "out of memory";
+    case DGP_E_NONFINITE: return "non-finite value in input or solve";
+    case DGP_E_NOT_CONVERGED: return "relaxation did not reach the tolerance (best iterate used)";
+    case DGP_E_BAD_POINTS: return "discriminant clamped at some points";
+    case DGP_E_TIMEOUT: return "device-side wait timed out";
+    case DGP_E_STATE: return "invalid context state";
+    default: return "unknown status";
+  }
+}
+
+int dgp_background(const dgp_cosmology* cosmo, double rc_H0, double a, dgp_background_t* out) {
+  if (!cosmo || !out || !(a > 0) || !(rc_H0 > 0) || !(cosmo->omega_m0 >= 0)) return DGP_E_INVALID;
+  const dgp::Coef c = dgp::coefficients(a, cosmo->omega_m0, rc_H0);
+  out->E = c.E; out->eta = c.eta; out->alpha = c.alpha; out->beta = c.beta; out->s = c.s;
+  out->c2 = c.c2; out->c3 = c.c3; out->q = c.q; out->omega_m = c.omega_m;
+  out->geff_local = dgp::geff_local(c);
+  dgp::growth(a, cosmo->omega_m0, rc_H0, &out->growth_D, &out->growth_f);
+  return DGP_OK;
+}
+
+int dgp_init(dgp_ctx** out, const dgp_params* p, const dgp_cosmology* cosmo, void* cuda_stream) {
+  if (!out) return DGP_E_INVALID;
+  *out = nullptr;
+  if (!p || !cosmo) return DGP_E_INVALID;
+  const int n = p->n;
+  if (n != 16 && n != 32 && n != 64 && n != 128 && n != 256 && n != 512) return DGP_E_INVALID;
+  if (!(p->box > 0) || !(p->rc_H0 > 0) || !(p->w >= 0 && p->w < 1) || p->max_iter < 0 || !(p->tol >= 0) ||
+      !isfinite(p->tol))
+    return DGP_E_INVALID;
+  if (p->precision < DGP_FP32 || p->precision > DGP_FP64) return DGP_E_INVALID;
+  if (p->gravity < DGP_GRAVITY_NL || p->gravity > DGP_GRAVITY_GRH) return DGP_E_INVALID;
+  if (!(cosmo->omega_m0 > 0) || !(cosmo->c_over_H0 > 0)) return DGP_E_INVALID;
+  dgp::EngineBase* e = p->precision == DGP_FP64 ? dgp::make_engine<double>(n) : dgp::make_engine<float>(n);
+  if (!e) return DGP_E_NOMEM;
+  e->p = *p;
+  e->cosmo = *cosmo;
+  e->stream = (cudaStream_t)cuda_stream;
+  const int rc = e->init();
+  if (rc != DGP_OK) {
+    delete e;
+    return rc;
+  }
+  dgp_ctx* c = new (std::nothrow) dgp_ctx;
+  if (!c) {
+    delete e;
+    return DGP_E_NOMEM;
+  }
+  c->eng = e;
+  *out = c;
+  return DGP_OK;
+}
+
+void dgp_destroy(dgp_ctx* c) {
+  if (!c) return;
+  delete c->eng;
+  delete c;
+}
+
+int dgp_reset(dgp_ctx* c) {
+  if (!c) return DGP_E_INVALID;
+  c->eng->reset();
+  return DGP_OK;
+}
+
+int dgp_solve_phi(dgp_ctx* c, double a, const void* delta, void* phi, double tol, dgp_solve_info* info) {
+  if (!c || !delta || !(a > 0) || !(tol >= 0)) return DGP_E_INVALID;
+  return c->eng->solve(a, delta, phi, nullptr, nullptr, nullptr, tol, info);
+}
+
+int dgp_solve_forces(dgp_ctx* c, double a, const void* delta, void* phi, void* gx, void* gy, void* gz, double tol,
+                     dgp_solve_info* info) {
+  if (!c || !delta || !gx || !gy || !gz || !(a > 0) || !(tol >= 0)) return DGP_E_INVALID;
+  return c->eng->solve(a, delta, phi, gx, gy, gz, tol, info);
+}
+
+int dgp_get_solution(dgp_ctx* c, void* D) {
+  if (!c) return DGP_E_INVALID;
+  return c->eng->get_solution(D);
+}
+
+int dgp_profile(dgp_ctx* c, int timing) {
+  if (!c) return DGP_E_INVALID;
+  c->eng->prof.reset(timing != 0);
+  return DGP_OK;
+}
+
+int dgp_profile_read(dgp_ctx* c, int kind, int64_t* launches, double* bytes, int64_t* timed, double* ms,
+                     double* timed_bytes) {
+  if (!c || kind < 0 || kind >= dgp::KK_COUNT) return DGP_E_INVALID;
+  dgp::Profiler& pr = c->eng->prof;
+  const int rc = pr.resolve();
+  if (rc != DGP_OK) return rc;
+  if (launches) *launches = pr.launches[kind];
+  if (bytes) *bytes = pr.bytes[kind];
+  if (timed) *timed = pr.timed[kind];
+  if (ms) *ms = pr.ms[kind];
+  if (timed_bytes) *timed_bytes = pr.timed_bytes[kind];
+  return DGP_OK;
+}
+
+const char* dgp_kernel_name(int kind) {
+  if (kind < 0 || kind >= dgp::KK_COUNT) return nullptr;
+  return dgp::kKernelNames[kind];
+}
+
+int dgp_deposit(dgp_ctx* c, const dgp_particles* parts, void* delta) {
+  if (!c) return DGP_E_INVALID;
+  return c->eng->deposit(parts, delta);
+}
+
+int pm_step(dgp_ctx* c, dgp_particles* parts, double a, double da, dgp_solve_info* info) {
+  if (!c) return DGP_E_INVALID;
+  return c->eng->step(parts, a, da, info);
+}
+
+int pm_step_host(dgp_ctx* c, dgp_particles* host_parts, double a, double da, dgp_solve_info* info) {
+  if (!c) return DGP_E_INVALID;
+  return c->eng->step_host(host_parts, a, da, info);
+}
+
+int power_spectrum(dgp_ctx* c, const void* delta, int nbins, double* k, double* pk, int64_t* nmodes) {
+  if (!c) return DGP_E_INVALID;
+  return c->eng->pk(delta, nbins, k, pk, nmodes);
+}
+
+int bispectrum(dgp_ctx* c, const void* delta, double k1, double k2, int ntheta, const double* theta, double dk,
+               double* b, double* q) {
+  if (!c) return DGP_E_INVALID;
+  return c->eng->bispec(delta, k1, k2, ntheta, theta, dk, b, q);
+}
+
+}  // extern "C"

@@ -1,0 +1,48 @@
+// Shared types and small helpers of the DGP CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dgp {
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+template <typename T> using vec2_t = typename Vec2<T>::type;
+
+template <typename V> __host__ __device__ __forceinline__ V cmake(decltype(V::x) a, decltype(V::x) b) {
+  V r; r.x = a; r.y = b; return r;
+}
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return cmake<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return cmake<V>(a.x - b.x, a.y - b.y); }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+  return cmake<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename V> __device__ __forceinline__ V cconj(V a) { return cmake<V>(a.x, -a.y); }
+template <typename V, typename S> __device__ __forceinline__ V cscale(V a, S s) {
+  return cmake<V>(a.x * s, a.y * s);
+}
+
+// Signed wavenumber index of FFT bin i on an n-point axis; the Nyquist bin
+// n/2 maps to -n/2 and is flagged.
+__device__ __forceinline__ int signed_index(int i, int n) { return i < n / 2 ? i : i - n; }
+
+// Launch geometry of the two-level pencil FFT: N = N1 * N2, N1 >= N2.
+template <int N> struct Split;
+template <> struct Split<16> { static constexpr int N1 = 4, N2 = 4; };
+template <> struct Split<32> { static constexpr int N1 = 8, N2 = 4; };
+template <> struct Split<64> { static constexpr int N1 = 8, N2 = 8; };
+template <> struct Split<128> { static constexpr int N1 = 16, N2 = 8; };
+template <> struct Split<256> { static constexpr int N1 = 16, N2 = 16; };
+template <> struct Split<512> { static constexpr int N1 = 32, N2 = 16; };
+
+// Per-point statistics of one relaxation update, reduced in FP64.
+struct RelaxStats {
+  double sum_abs_r;   // sum |R| over the mesh
+  double sum_dnew;    // sum of D_new (its mean is projected out next time)
+  double nbad;        // number of points with Delta < 0
+  double sum_nonfinite;  // count of non-finite R (NaN guard)
+};
+
+}  // namespace dgp

@@ -1,0 +1,271 @@
+// x pass: forward DFT along x (stride N inside a kz plane of S[kz][x][y]),
+// a k-space operation, and the inverse DFT along x of each output.
+//
+// A CTA owns one kz plane and TY consecutive ky columns; thread (lane, yl)
+// has yl fastest so every global access is TY consecutive complex values.
+// After the forward transform lane k1 holds X[k1 + N1*k2] (k2 < N2) in
+// registers; an output is formed there, transformed back over k2 in the same
+// registers (the inverse four-step with the roles of N1 and N2 swapped),
+// transposed through shared memory once and finished over k1.
+//
+// Operations (all multipliers real-even or i*odd, so outputs stay Hermitian):
+//  HESSIAN    D(k) -> (k_i k_j / k^2) D(k) for xx, yy, xy, xz, yz and
+//             N(k) = -D(k) / kbar   (Sec. III.B: nabla_ij C(k) = -k_i k_j C(k);
+//             sqrt(-lapbar) C = kbar C = -D / kbar).  Off-diagonal pairs with a
+//             component on its Nyquist index use |k_i k_j| / k^2.
+//  SOURCE     S(k) = s (1 - beta / kbar) delta(k)        (RHS of Eq. FullDGP2)
+//  SOURCE_LIN S(k) and D_lin(k) = S(k) / (alpha - c2 / kbar)  (Sec. III.B)
+//  PHI_FORCE  phi(k) from Eq. FullDGP1 (or Eq. LinearDGP / GRPoisson) and
+//             g_i(k) = -i k_i phi(k), Nyquist component of axis i set to 0.
+//  PK         |delta_k|^2 binned in shells (Sec. IV), per-block FP64 partials.
+//  SHELL      delta_k and 1 restricted to a |k| shell (bispectrum, Sec. VI).
+// Every output carries the 1 / N^3 of the three inverse transforms.
+#include <math.h>
+
+#include "fft_core.cuh"
+#include "kernels.cuh"
+
+namespace dgp {
+
+template <typename T, int N> struct XGeom {
+  static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+  static constexpr int TYW = sizeof(T) == 4 ? 16 : 8;
+  static constexpr int TY = TYW < N ? TYW : N;
+  static constexpr int THREADS = TY * N1;
+};
+
+template <typename T> struct XArgs {
+  const vec2_t<T>* in0;
+  const vec2_t<T>* in1;
+  FieldSet<T> out;
+  int nout_mask;
+  KParams kp;
+  double* pk_partials;
+  int nbins;
+  double shell_lo, shell_hi;
+};
+
+template <typename T, int N>
+__device__ __forceinline__ void x_forward(const vec2_t<T>* __restrict__ in, int kz, int ky0, int lane, int yl,
+                                          vec2_t<T>* s_T, const vec2_t<T>* s_tw,
+                                          vec2_t<T> (&X)[Split<N>::N2]) {
+  using V = vec2_t<T>;
+  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, TY = XGeom<T, N>::TY;
+  const V* plane = in + (int64_t)kz * N * N;
+  if (lane < N2) {
+    V v[N1];
+#pragma unroll
+    for (int j1 = 0; j1 < N1; ++j1) v[j1] = plane[(int64_t)(N2 * j1 + lane) * N + ky0 + yl];
+    dft_regs<N1, N / N1>(v, s_tw);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1)
+      s_T[(k1 * N2 + lane) * TY + yl] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[lane * k1]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j2 = 0; j2 < N2; ++j2) X[j2] = s_T[(lane * N2 + j2) * TY + yl];
+  dft_regs<N2, N / N2>(X, s_tw);
+  __syncthreads();
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void x_inverse(vec2_t<T> (&Y)[Split<N>::N2], vec2_t<T>* __restrict__ out, int kz,
+                                          int ky0, int lane, int yl, vec2_t<T>* s_T, const vec2_t<T>* s_tw) {
+  using V = vec2_t<T>;
+  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, TY = XGeom<T, N>::TY;
+  conj_regs(Y);
+  dft_regs<N2, N / N2>(Y, s_tw);
+#pragma unroll
+  for (int m1 = 0; m1 < N2; ++m1)
+    s_T[(m1 * N1 + lane) * TY + yl] = (m1 == 0) ? Y[m1] : cmul(Y[m1], s_tw[lane * m1]);
+  __syncthreads();
+  if (lane < N2) {
+    V w[N1];
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) w[k1] = s_T[(lane * N1 + k1) * TY + yl];
+    dft_regs<N1, N / N1>(w, s_tw);
+    V* plane = out + (int64_t)kz * N * N;
+#pragma unroll
+    for (int m2 = 0; m2 < N1; ++m2) plane[(int64_t)(lane + N2 * m2) * N + ky0 + yl] = cconj(w[m2]);
+  }
+  __syncthreads();
+}
+
+// G_eff / G of Eq. Geff at |k| (h/Mpc).
+__device__ __forceinline__ double geff_dev(const KParams& kp, double kmag) {
+  const double eta = kp.eta, q = kp.q;
+  const double t1 = (2 * eta * (2 + q) - 3) / (2 * eta * (2 + q) - 4);
+  const double r = (eta * (1 + q) - 1) / (eta * (2 + q) - 2);
+  const double t2 = 3.0 * kp.a / (kmag * kp.rc_H0 * (kp.kbar_fac * kp.aE)) * r * r;
+  return 1.0 / (t1 + t2);
+}
+
+template <typename T, int N, int OP>
+__global__ void __launch_bounds__(XGeom<T, N>::THREADS)
+    k_fft_x(const __grid_constant__ XArgs<T> args, const vec2_t<T>* __restrict__ g_tw) {
+  using V = vec2_t<T>;
+  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, TY = XGeom<T, N>::TY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* s_tw = reinterpret_cast<V*>(smem_raw);
+  V* s_T = s_tw + N;  // N * TY
+  double* s_bins = reinterpret_cast<double*>(s_T + N * TY);
+  load_twiddles(s_tw, g_tw, N);
+  if (OP == XOP_PK)
+    for (int i = threadIdx.x; i < 3 * args.nbins; i += blockDim.x) s_bins[i] = 0.0;
+  const int yl = threadIdx.x % TY;
+  const int lane = threadIdx.x / TY;
+  const int kz = blockIdx.y;
+  const int ky0 = blockIdx.x * TY;
+  const int ky = ky0 + yl;
+  const int nz = kz == N / 2 ? -(N / 2) : kz;
+  const int ny = signed_index(ky, N);
+  const bool nyq_y = ky == N / 2, nyq_z = kz == N / 2;
+  const KParams& kp = args.kp;
+  const T kf = (T)(2.0 * M_PI / kp.box);
+  __syncthreads();
+
+  V X0[N2], X1[N2];
+  x_forward<T, N>(args.in0, kz, ky0, lane, yl, s_T, s_tw, X0);
+  if (OP == XOP_PHI_FORCE && kp.gravity == 0) x_forward<T, N>(args.in1, kz, ky0, lane, yl, s_T, s_tw, X1);
+
+  if (OP == XOP_PK) {
+    const double norm = kp.box * kp.box * kp.box * kp.inv_m * kp.inv_m;
+    const double w = (kz == 0 || kz == N / 2) ? 1.0 : 2.0;
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+      const int nx = signed_index(lane + N1 * k2, N);
+      const int n2 = nx * nx + ny * ny + nz * nz;
+      if (n2 == 0) continue;
+      const double nm = sqrt((double)n2);
+      const int b = (int)floor(nm + 0.5);
+      if (b >= 1 && b <= args.nbins) {
+        const double p = ((double)X0[k2].x * X0[k2].x + (double)X0[k2].y * X0[k2].y) * norm;
+        atomicAdd(&s_bins[b - 1], w);
+        atomicAdd(&s_bins[args.nbins + b - 1], w * nm * (2.0 * M_PI / kp.box));
+        atomicAdd(&s_bins[2 * args.nbins + b - 1], w * p);
+      }
+    }
+    __syncthreads();
+    const int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    for (int i = threadIdx.x; i < 3 * args.nbins; i += blockDim.x)
+      args.pk_partials[blk * 3 * args.nbins + i] = s_bins[i];
+    return;
+  }
+
+  int nout;
+  if (OP == XOP_HESSIAN) nout = 6;
+  else if (OP == XOP_SOURCE) nout = 1;
+  else if (OP == XOP_SOURCE_LIN || OP == XOP_SHELL) nout = 2;
+  else nout = 4;
+  const T inv_m = (T)kp.inv_m;
+  for (int o = 0; o < nout; ++o) {
+    if (OP == XOP_PHI_FORCE && !((args.nout_mask >> o) & 1)) continue;
+    V Y[N2];
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+      const int kx = lane + N1 * k2;
+      const int nx = signed_index(kx, N);
+      const bool nyq_x = kx == N / 2;
+      const int n2 = nx * nx + ny * ny + nz * nz;
+      V r = cmake<V>((T)0, (T)0);
+      if (n2 != 0) {
+        const T inv_n2 = (T)1 / (T)n2;
+        const T nmag = sqrt((T)n2);
+        // 1 / kbar = 1 / (kbar_fac * kf * |n|)
+        const T ikb = kp.local_only ? (T)0 : (T)1 / ((T)kp.kbar_fac * kf * nmag);
+        if (OP == XOP_HESSIAN) {
+          T m;
+          switch (o) {
+            case 0: m = (T)(nx * nx) * inv_n2; break;
+            case 1: m = (T)(ny * ny) * inv_n2; break;
+            case 2: m = (T)((nyq_x || nyq_y) ? abs(nx * ny) : nx * ny) * inv_n2; break;
+            case 3: m = (T)((nyq_x || nyq_z) ? abs(nx * nz) : nx * nz) * inv_n2; break;
+            case 4: m = (T)((nyq_y || nyq_z) ? abs(ny * nz) : ny * nz) * inv_n2; break;
+            default: m = -ikb; break;
+          }
+          r = cscale(X0[k2], m * inv_m);
+        } else if (OP == XOP_SOURCE || OP == XOP_SOURCE_LIN) {
+          const T sfac = (T)kp.s * ((T)1 - (T)kp.beta * ikb) * inv_m;
+          r = cscale(X0[k2], sfac);
+          if (o == 1) r = cscale(r, (T)1 / ((T)kp.alpha - (T)kp.c2 * ikb));
+        } else if (OP == XOP_SHELL) {
+          const double nm = sqrt((double)n2);
+          if (nm > args.shell_lo && nm < args.shell_hi)
+            r = (o == 0) ? cscale(X0[k2], inv_m) : cmake<V>(inv_m, (T)0);
+        } else {  // XOP_PHI_FORCE
+          const T kmag = kf * nmag;
+          const T pref = -(T)(kp.aE * kp.aE) / (kmag * kmag);
+          const T om = (T)((kp.eta - 1.0) / kp.eta);
+          V phi;
+          if (kp.gravity == 0) {
+            const T cd = (T)(-1.0 / (2.0 * kp.eta)) + (T)kp.c3 * ikb;
+            const T den = (T)1 + ikb / (T)kp.eta;
+            const V rhs = cadd(cscale(X0[k2], (T)1.5 * om), cscale(X1[k2], cd));
+            phi = cscale(rhs, pref / den);
+          } else if (kp.gravity == 1) {
+            phi = cscale(X0[k2], pref * (T)1.5 * om * (T)geff_dev(kp, (double)kmag));
+          } else {
+            phi = cscale(X0[k2], pref * (T)1.5 * om);
+          }
+          phi = cscale(phi, inv_m);
+          if (o == 0) {
+            r = phi;
+          } else {
+            const int ni = o == 1 ? nx : (o == 2 ? ny : nz);
+            const bool nyq = o == 1 ? nyq_x : (o == 2 ? nyq_y : nyq_z);
+            const T ki = kf * (T)ni;
+            // g = -grad phi -> -i k_i phi
+            r = nyq ? cmake<V>((T)0, (T)0) : cmake<V>(ki * phi.y, -ki * phi.x);
+          }
+        }
+      }
+      Y[k2] = r;
+    }
+    x_inverse<T, N>(Y, args.out.p[o], kz, ky0, lane, yl, s_T, s_tw);
+  }
+}
+
+template <typename T, int N> int x_pass_blocks() { return (N / XGeom<T, N>::TY) * (N / 2 + 1); }
+
+template <typename T, int N, int OP>
+static void launch_x(const XArgs<T>& a, const vec2_t<T>* tw, cudaStream_t s) {
+  using G = XGeom<T, N>;
+  const size_t smem = sizeof(vec2_t<T>) * (N + (size_t)N * G::TY) + (OP == XOP_PK ? sizeof(double) * 3 * a.nbins : 0);
+  cudaFuncSetAttribute(k_fft_x<T, N, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid(N / G::TY, N / 2 + 1);
+  k_fft_x<T, N, OP><<<grid, G::THREADS, smem, s>>>(a, tw);
+}
+
+template <typename T, int N>
+void launch_fft_x_op(int op, const vec2_t<T>* in0, const vec2_t<T>* in1, const FieldSet<T>& out, int nout_mask,
+                     const KParams& kp, double* pk_partials, int nbins, double shell_lo, double shell_hi,
+                     const vec2_t<T>* tw, cudaStream_t s) {
+  XArgs<T> a;
+  a.in0 = in0; a.in1 = in1; a.out = out; a.nout_mask = nout_mask; a.kp = kp;
+  a.pk_partials = pk_partials; a.nbins = nbins; a.shell_lo = shell_lo; a.shell_hi = shell_hi;
+  switch (op) {
+    case XOP_HESSIAN: launch_x<T, N, XOP_HESSIAN>(a, tw, s); break;
+    case XOP_SOURCE: launch_x<T, N, XOP_SOURCE>(a, tw, s); break;
+    case XOP_SOURCE_LIN: launch_x<T, N, XOP_SOURCE_LIN>(a, tw, s); break;
+    case XOP_PHI_FORCE: launch_x<T, N, XOP_PHI_FORCE>(a, tw, s); break;
+    case XOP_PK: launch_x<T, N, XOP_PK>(a, tw, s); break;
+    case XOP_SHELL: launch_x<T, N, XOP_SHELL>(a, tw, s); break;
+    default: break;
+  }
+}
+
+#define DGP_INST_X(T, N)                                                                            \
+  template void launch_fft_x_op<T, N>(int, const vec2_t<T>*, const vec2_t<T>*, const FieldSet<T>&, int, \
+                                      const KParams&, double*, int, double, double, const vec2_t<T>*,   \
+                                      cudaStream_t);
+#define DGP_INST_X_ALL(T) DGP_INST_X(T, 16) DGP_INST_X(T, 32) DGP_INST_X(T, 64) DGP_INST_X(T, 128) \
+  DGP_INST_X(T, 256) DGP_INST_X(T, 512)
+DGP_INST_X_ALL(float)
+DGP_INST_X_ALL(double)
+#define DGP_INST_XB(T) template int x_pass_blocks<T, 16>(); template int x_pass_blocks<T, 32>(); \
+  template int x_pass_blocks<T, 64>(); template int x_pass_blocks<T, 128>(); \
+  template int x_pass_blocks<T, 256>(); template int x_pass_blocks<T, 512>();
+DGP_INST_XB(float)
+DGP_INST_XB(double)
+
+}  // namespace dgp

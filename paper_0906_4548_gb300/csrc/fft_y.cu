@@ -1,0 +1,78 @@
+// y transform: in-place complex DFT along the contiguous rows of S[kz][x][y].
+//
+// Each CTA of 256 threads owns P = 256 / N1 rows.  Phase 1: lane j2 < N2
+// reads x[N2*j1 + j2] straight from global memory (consecutive lanes,
+// consecutive addresses), transforms over j1 and stores the twiddled result
+// to shared memory; phase 2: lane k1 reads its N2 values back with an odd
+// row pitch (N2 + 1, no bank conflicts), transforms and writes
+// X[k1 + N1*k2] back to global memory (again consecutive lanes, consecutive
+// addresses).  HBM traffic: one read and one write of the rows.
+#include "fft_core.cuh"
+#include "kernels.cuh"
+
+namespace dgp {
+
+template <typename T, int N, bool INV>
+__global__ void __launch_bounds__(256) k_fft_y(const __grid_constant__ FieldSet<T> f, int64_t npencils,
+                                              const vec2_t<T>* __restrict__ g_tw) {
+  using V = vec2_t<T>;
+  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+  constexpr int P = 256 / N1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* s_tw = reinterpret_cast<V*>(smem_raw);
+  V* s_T = s_tw + N;
+  load_twiddles(s_tw, g_tw, N);
+  const int lane = threadIdx.x % N1;
+  const int pl = threadIdx.x / N1;
+  const int64_t pencil = (int64_t)blockIdx.x * P + pl;
+  const bool active = pencil < npencils;
+  V* base = f.p[blockIdx.y] + (active ? pencil : 0) * N;
+  V* Tp = s_T + pl * (N1 * (N2 + 1));
+  __syncthreads();
+  if (active && lane < N2) {
+    V v[N1];
+#pragma unroll
+    for (int j1 = 0; j1 < N1; ++j1) v[j1] = base[N2 * j1 + lane];
+    if (INV) conj_regs(v);
+    dft_regs<N1, N / N1>(v, s_tw);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1)
+      Tp[k1 * (N2 + 1) + lane] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[lane * k1]);
+  }
+  __syncthreads();
+  if (active) {
+    V u[N2];
+#pragma unroll
+    for (int j2 = 0; j2 < N2; ++j2) u[j2] = Tp[lane * (N2 + 1) + j2];
+    dft_regs<N2, N / N2>(u, s_tw);
+    if (INV) conj_regs(u);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) base[lane + N1 * k2] = u[k2];
+  }
+}
+
+template <typename T, int N>
+void launch_fft_y(const FieldSet<T>& f, int nfields, bool inverse, const vec2_t<T>* tw, cudaStream_t s) {
+  using V = vec2_t<T>;
+  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+  constexpr int P = 256 / N1;
+  const int64_t npencils = (int64_t)(N / 2 + 1) * N;
+  const size_t smem = sizeof(V) * (N + P * N1 * (N2 + 1));
+  dim3 grid((unsigned)((npencils + P - 1) / P), (unsigned)nfields);
+  if (inverse) {
+    cudaFuncSetAttribute(k_fft_y<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_fft_y<T, N, true><<<grid, 256, smem, s>>>(f, npencils, tw);
+  } else {
+    cudaFuncSetAttribute(k_fft_y<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_fft_y<T, N, false><<<grid, 256, smem, s>>>(f, npencils, tw);
+  }
+}
+
+#define DGP_INST_Y(T, N) \
+  template void launch_fft_y<T, N>(const FieldSet<T>&, int, bool, const vec2_t<T>*, cudaStream_t);
+#define DGP_INST_Y_ALL(T) DGP_INST_Y(T, 16) DGP_INST_Y(T, 32) DGP_INST_Y(T, 64) DGP_INST_Y(T, 128) \
+  DGP_INST_Y(T, 256) DGP_INST_Y(T, 512)
+DGP_INST_Y_ALL(float)
+DGP_INST_Y_ALL(double)
+
+}  // namespace dgp

@@ -1,0 +1,200 @@
+// z transforms: real rows f[x][y][0..N) <-> half spectra S[kz][x][y].
+//
+// A CTA owns TY consecutive rows y0..y0+TY-1 at one x.  Two real rows are
+// packed into one complex pencil (a + i b), transformed with the four-step
+// split, and separated with A(k) = (Z(k) + conj Z(N-k))/2,
+// B(k) = (Z(k) - conj Z(N-k))/(2i).  Output goes to S[kz][x][y0 + yl] so that
+// consecutive threads write consecutive y (TY * 8 bytes per kz).  The inverse
+// gathers S[kz][x][y-tile] the same way, rebuilds Z(k) = A(k) + i B(k) over all
+// k by Hermitian symmetry (the imaginary parts of the kz = 0 and kz = N/2
+// coefficients are dropped, as a real-output transform must), and writes rows.
+#include "fft_core.cuh"
+#include "kernels.cuh"
+
+namespace dgp {
+
+template <typename T, int N> struct ZGeom {
+  static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+  static constexpr int TYW = (sizeof(T) == 8 || N >= 512) ? 16 : 32;
+  static constexpr int TY = TYW < N ? TYW : N;
+  static constexpr int P = TY / 2;
+  static constexpr int THREADS = P * N1;
+};
+
+template <typename T>
+__device__ __forceinline__ T apply_prologue(T v, const ZPrologue& pro, double mean) {
+  if (pro.kind == 1) return (T)((double)v / mean - 1.0);
+  if (pro.kind == 2) return (T)((double)v - mean);
+  return v;
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(ZGeom<T, N>::THREADS)
+k_fft_z_r2c(const T* __restrict__ in, int64_t in_stride, vec2_t<T>* __restrict__ out, int64_t out_stride,
+            ZPrologue pro, const vec2_t<T>* __restrict__ g_tw) {
+  using V = vec2_t<T>;
+  using G = ZGeom<T, N>;
+  constexpr int N1 = G::N1, N2 = G::N2, TY = G::TY, P = G::P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* s_tw = reinterpret_cast<V*>(smem_raw);
+  V* s_T = s_tw + N;                        // P * N1 * (N2 + 1)
+  V* s_Z = s_T + P * N1 * (N2 + 1);         // N * (P + 1)
+  load_twiddles(s_tw, g_tw, N);
+  const int lane = threadIdx.x % N1;
+  const int pl = threadIdx.x / N1;
+  const int x = blockIdx.y;
+  const int y0 = blockIdx.x * TY;
+  const T* src = in + (int64_t)blockIdx.z * in_stride;
+  V* dst = out + (int64_t)blockIdx.z * out_stride;
+  double mean = 0.0;
+  if (pro.kind != 0) mean = pro.mean_src[0] * pro.inv_count;
+  const T* rowa = src + ((int64_t)x * N + y0 + 2 * pl) * N;
+  const T* rowb = rowa + N;
+  V* Tp = s_T + pl * (N1 * (N2 + 1));
+  __syncthreads();
+  if (lane < N2) {
+    V v[N1];
+#pragma unroll
+    for (int j1 = 0; j1 < N1; ++j1) {
+      v[j1].x = apply_prologue(rowa[N2 * j1 + lane], pro, mean);
+      v[j1].y = apply_prologue(rowb[N2 * j1 + lane], pro, mean);
+    }
+    dft_regs<N1, N / N1>(v, s_tw);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1)
+      Tp[k1 * (N2 + 1) + lane] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[lane * k1]);
+  }
+  __syncthreads();
+  {
+    V u[N2];
+#pragma unroll
+    for (int j2 = 0; j2 < N2; ++j2) u[j2] = Tp[lane * (N2 + 1) + j2];
+    dft_regs<N2, N / N2>(u, s_tw);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) s_Z[(lane + N1 * k2) * (P + 1) + pl] = u[k2];
+  }
+  __syncthreads();
+  constexpr int NK = N / 2 + 1;
+  for (int item = threadIdx.x; item < NK * TY; item += blockDim.x) {
+    const int kz = item / TY, yl = item % TY;
+    const int p = yl >> 1;
+    const V zk = s_Z[kz * (P + 1) + p];
+    const V zm = s_Z[((N - kz) & (N - 1)) * (P + 1) + p];
+    V r;
+    if ((yl & 1) == 0) r = cmake<V>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
+    else r = cmake<V>((T)0.5 * (zk.y + zm.y), (T)-0.5 * (zk.x - zm.x));
+    dst[((int64_t)kz * N + x) * N + y0 + yl] = r;
+  }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(ZGeom<T, N>::THREADS)
+k_fft_z_c2r(const __grid_constant__ FieldSet<T> in, const __grid_constant__ FieldSet<T> outp,
+            const vec2_t<T>* __restrict__ g_tw) {
+  using V = vec2_t<T>;
+  using G = ZGeom<T, N>;
+  constexpr int N1 = G::N1, N2 = G::N2, TY = G::TY, P = G::P;
+  constexpr int NK = N / 2 + 1;
+  constexpr int HSZ = NK * (TY + 1);
+  constexpr int TSZ = P * N1 * (N2 + 1);
+  constexpr int BUF = HSZ > TSZ ? HSZ : TSZ;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* s_tw = reinterpret_cast<V*>(smem_raw);
+  V* s_H = s_tw + N;        // NK * (TY + 1); later reused as s_T
+  V* s_T = s_H;
+  V* s_Z = s_H + BUF;       // N * (P + 1)
+  load_twiddles(s_tw, g_tw, N);
+  const int x = blockIdx.y;
+  const int y0 = blockIdx.x * TY;
+  const V* src = in.p[blockIdx.z];
+  T* dst = reinterpret_cast<T*>(outp.p[blockIdx.z]);
+  for (int item = threadIdx.x; item < NK * TY; item += blockDim.x) {
+    const int kz = item / TY, yl = item % TY;
+    s_H[kz * (TY + 1) + yl] = src[((int64_t)kz * N + x) * N + y0 + yl];
+  }
+  __syncthreads();
+  for (int item = threadIdx.x; item < N * P; item += blockDim.x) {
+    const int k = item / P, p = item % P;
+    V A, B;
+    if (k <= N / 2) {
+      A = s_H[k * (TY + 1) + 2 * p];
+      B = s_H[k * (TY + 1) + 2 * p + 1];
+      if (k == 0 || k == N / 2) { A.y = 0; B.y = 0; }
+    } else {
+      A = cconj(s_H[(N - k) * (TY + 1) + 2 * p]);
+      B = cconj(s_H[(N - k) * (TY + 1) + 2 * p + 1]);
+    }
+    // Z = A + i B, stored conjugated for the inverse
+    s_Z[k * (P + 1) + p] = cmake<V>(A.x - B.y, -(A.y + B.x));
+  }
+  __syncthreads();
+  const int lane = threadIdx.x % N1;
+  const int pl = threadIdx.x / N1;
+  V* Tp = s_T + pl * (N1 * (N2 + 1));
+  if (lane < N2) {
+    V v[N1];
+#pragma unroll
+    for (int j1 = 0; j1 < N1; ++j1) v[j1] = s_Z[(N2 * j1 + lane) * (P + 1) + pl];
+    dft_regs<N1, N / N1>(v, s_tw);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1)
+      Tp[k1 * (N2 + 1) + lane] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[lane * k1]);
+  }
+  __syncthreads();
+  {
+    V u[N2];
+#pragma unroll
+    for (int j2 = 0; j2 < N2; ++j2) u[j2] = Tp[lane * (N2 + 1) + j2];
+    dft_regs<N2, N / N2>(u, s_tw);
+    T* rowa = dst + ((int64_t)x * N + y0 + 2 * pl) * N;
+    T* rowb = rowa + N;
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+      rowa[lane + N1 * k2] = u[k2].x;    // conj of the result: real part unchanged
+      rowb[lane + N1 * k2] = -u[k2].y;
+    }
+  }
+}
+
+template <typename T, int N> static size_t r2c_smem() {
+  using G = ZGeom<T, N>;
+  return sizeof(vec2_t<T>) * (N + G::P * G::N1 * (G::N2 + 1) + N * (G::P + 1));
+}
+template <typename T, int N> static size_t c2r_smem() {
+  using G = ZGeom<T, N>;
+  const size_t hsz = (size_t)(N / 2 + 1) * (G::TY + 1), tsz = (size_t)G::P * G::N1 * (G::N2 + 1);
+  return sizeof(vec2_t<T>) * (N + (hsz > tsz ? hsz : tsz) + (size_t)N * (G::P + 1));
+}
+
+template <typename T, int N>
+void launch_fft_z_r2c(const T* in, int64_t in_stride, vec2_t<T>* out, int64_t out_stride, int nfields,
+                      ZPrologue pro, const vec2_t<T>* tw, cudaStream_t s) {
+  using G = ZGeom<T, N>;
+  const size_t smem = r2c_smem<T, N>();
+  cudaFuncSetAttribute(k_fft_z_r2c<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid(N / G::TY, N, nfields);
+  k_fft_z_r2c<T, N><<<grid, G::THREADS, smem, s>>>(in, in_stride, out, out_stride, pro, tw);
+}
+
+template <typename T, int N>
+void launch_fft_z_c2r(const FieldSet<T>& in, T* const* out, int nfields, const vec2_t<T>* tw,
+                      cudaStream_t s) {
+  using G = ZGeom<T, N>;
+  FieldSet<T> o;
+  for (int i = 0; i < kMaxFields; ++i) o.p[i] = i < nfields ? reinterpret_cast<vec2_t<T>*>(out[i]) : nullptr;
+  const size_t smem = c2r_smem<T, N>();
+  cudaFuncSetAttribute(k_fft_z_c2r<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid(N / G::TY, N, nfields);
+  k_fft_z_c2r<T, N><<<grid, G::THREADS, smem, s>>>(in, o, tw);
+}
+
+#define DGP_INST_Z(T, N)                                                                          \
+  template void launch_fft_z_r2c<T, N>(const T*, int64_t, vec2_t<T>*, int64_t, int, ZPrologue,     \
+                                       const vec2_t<T>*, cudaStream_t);                            \
+  template void launch_fft_z_c2r<T, N>(const FieldSet<T>&, T* const*, int, const vec2_t<T>*, cudaStream_t);
+#define DGP_INST_Z_ALL(T) DGP_INST_Z(T, 16) DGP_INST_Z(T, 32) DGP_INST_Z(T, 64) DGP_INST_Z(T, 128) \
+  DGP_INST_Z(T, 256) DGP_INST_Z(T, 512)
+DGP_INST_Z_ALL(float)
+DGP_INST_Z_ALL(double)
+
+}  // namespace dgp

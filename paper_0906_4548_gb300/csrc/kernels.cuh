@@ -1,0 +1,117 @@
+// Launchers of the DGP mesh and particle kernels (definitions in the .cu files,
+// explicit instantiations for T in {float, double} and N in {16..512}).
+//
+// Spectral layout.  A real field f[x][y][z] (z fastest) is transformed along z
+// first (real-to-complex, kz = 0..N/2) and stored TRANSPOSED as
+// S[kz][x][y] (y fastest), (N/2+1) * N * N complex values; the y transform
+// acts in place on contiguous rows, and the x transform (stride N) is always
+// fused with a k-space operation and its inverse, so the fully transformed
+// spectrum never touches memory.  The Nyquist plane kz = N/2 is simply the
+// last plane.
+#pragma once
+
+#include "common.cuh"
+
+namespace dgp {
+
+constexpr int kMaxFields = 8;
+
+template <typename T> struct FieldSet {
+  vec2_t<T>* p[kMaxFields];
+};
+
+// Prologue applied to real values before the z transform.
+struct ZPrologue {
+  const double* mean_src;  // device scalar: sum of the source field (nullptr: identity)
+  double inv_count;        // 1 / number of points
+  int kind;                // 0: identity; 1: rho -> rho / mean - 1; 2: v - mean
+};
+
+// Parameters of the fused x-pass k-space operations.
+struct KParams {
+  double box;        // Mpc/h
+  double inv_m;      // 1 / N^3 (inverse-transform normalisation)
+  double kbar_fac;   // C_H / (a E): kbar = kbar_fac |k|
+  int local_only;
+  // coefficients (Sec. II)
+  double eta, alpha, beta, s, c2, c3, aE, q, rc_H0, a;
+  int gravity;
+};
+
+enum XOp { XOP_HESSIAN = 0, XOP_SOURCE = 1, XOP_SOURCE_LIN = 2, XOP_PHI_FORCE = 3, XOP_PK = 4,
+           XOP_SHELL = 5 };
+
+template <typename T, int N>
+void launch_fft_y(const FieldSet<T>& f, int nfields, bool inverse, const vec2_t<T>* tw, cudaStream_t s);
+
+template <typename T, int N>
+void launch_fft_z_r2c(const T* in, int64_t in_stride, vec2_t<T>* out, int64_t out_stride, int nfields,
+                      ZPrologue pro, const vec2_t<T>* tw, cudaStream_t s);
+
+template <typename T, int N>
+void launch_fft_z_c2r(const FieldSet<T>& in, T* const* out, int nfields, const vec2_t<T>* tw,
+                      cudaStream_t s);
+
+// x-pass: forward x transform of nin input spectra, op, inverse x transform of
+// each of the op's outputs.  For XOP_PK, outputs are the per-block bin
+// partials (pk_partials, 3 * nbins doubles per block).  For XOP_SHELL the
+// op is a shell indicator on |k| (shell_lo <= |k|/k_f < shell_hi) applied to
+// input 0 (out 0) and the indicator itself (out 1).
+template <typename T, int N>
+void launch_fft_x_op(int op, const vec2_t<T>* in0, const vec2_t<T>* in1, const FieldSet<T>& out,
+                     int nout_mask, const KParams& kp, double* pk_partials, int nbins, double shell_lo,
+                     double shell_hi, const vec2_t<T>* tw, cudaStream_t s);
+
+template <typename T, int N> int x_pass_blocks();
+
+// Pointwise kernels (Eqs. nabla^2Cwpara, Bwpara and the residual of FullDGP2).
+struct RelaxParams {
+  double alpha, w, c2;
+  double inv_m;
+};
+
+// D_new = relax(D - mean, H, N, S); per-block FP64 partials of RelaxStats.
+template <typename T, typename A>
+void launch_relax(const T* D, const double* dsum, const T* const* H6, const T* S, T* Dnew,
+                  int64_t m, RelaxParams rp, double* partials, int nblocks, cudaStream_t s);
+
+// partials[nblocks][ncomp] -> out[ncomp], fixed summation order.
+void launch_finalize(const double* partials, int nblocks, int ncomp, double* out, cudaStream_t s);
+
+template <typename T>
+void launch_sum(const T* a, int64_t m, bool absval, double* partials, int nblocks, cudaStream_t s);
+
+template <typename T>
+void launch_density_contrast(const T* rho, T* delta, int64_t m, const double* sum, cudaStream_t s);
+
+template <typename T>
+void launch_fill(T* a, int64_t m, T v, cudaStream_t s);
+
+// out = in - sum / m
+template <typename T>
+void launch_sub_mean(const T* in, T* out, int64_t m, const double* sum, cudaStream_t s);
+
+template <typename T>
+void launch_product3_sum(const T* a, const T* b, const T* c, int64_t m, double* partials,
+                         int nblocks, cudaStream_t s);
+
+// Particles.
+struct CicParams {
+  int n;
+  float inv_d_hi, inv_d_lo;  // N / box as an unevaluated float pair
+  double inv_d;              // N / box (FP64 path)
+  double box;
+};
+
+template <typename T>
+void launch_cic_deposit(const T* x, const T* y, const T* z, int64_t np, T* rho, CicParams cp,
+                        cudaStream_t s);
+
+template <typename T>
+void launch_gather_kick(T* x, T* y, T* z, T* px, T* py, T* pz, int64_t np, const T* gx,
+                        const T* gy, const T* gz, CicParams cp, double kick, double drift, int do_drift,
+                        cudaStream_t s);
+
+int num_sms();
+
+}  // namespace dgp

@@ -1,0 +1,348 @@
+// Pointwise and particle kernels of the DGP library.
+//
+// Reductions are two-stage and deterministic: each block writes FP64 partial
+// sums (grid-stride loop, warp-shuffle tree), and a single block adds the
+// partials in a fixed order.  No FP64 atomics.
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace dgp {
+
+int num_sms() {
+  static int cached = 0;
+  if (cached == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
+    if (cached <= 0) cached = 1;
+  }
+  return cached;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of NC values per thread; thread 0 returns the totals in v.
+template <int NC>
+__device__ __forceinline__ void block_sum(double (&v)[NC]) {
+  __shared__ double s_part[NC][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    v[c] = warp_sum(v[c]);
+    if (lane == 0) s_part[c][wid] = v[c];
+  }
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  if (wid == 0) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      double t = lane < nw ? s_part[c][lane] : 0.0;
+      v[c] = warp_sum(t);
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// Relaxation update and residual (Secs. III.B-C).
+//
+// With H_zz = D - H_xx - H_yy (the trace of the Hessian spectra is D) and
+// q = sum_{i<j} (H_ij^2 - H_ii H_jj), Eq. FullDGP2 minus its RHS is
+//   R = D^2 + alpha D - sum_ij H_ij^2 + c2 N - S = alpha D - 2 q + c2 N - S,
+// the split source of Eq. Bwpara is
+//   B' = sum H^2 - w D^2 - c2 N + S = (1 - w) D^2 + alpha D - R,
+// the discriminant Delta = alpha^2 + 4 (1 - w) B', and the '+' root of
+// Eq. nabla^2Cwpara in the cancellation-free form D_new = 2 B' / (alpha + sqrt(Delta)).
+// A bad point (Delta < 0) takes Delta = 0, i.e. B' = -alpha^2 / (4 (1 - w)).
+// A is the arithmetic type of R, B' and Delta (double in the mixed path).
+template <typename T, typename A>
+__global__ void __launch_bounds__(256) k_relax(const T* __restrict__ D, const double* __restrict__ dsum,
+                                               const T* __restrict__ Hxx, const T* __restrict__ Hyy,
+                                               const T* __restrict__ Hxy, const T* __restrict__ Hxz,
+                                               const T* __restrict__ Hyz, const T* __restrict__ Nf,
+                                               const T* __restrict__ S, T* __restrict__ Dnew, int64_t m,
+                                               RelaxParams rp, double* __restrict__ partials) {
+  const A mean = dsum ? (A)(dsum[0] * rp.inv_m) : (A)0;
+  const A alpha = (A)rp.alpha, omw = (A)(1.0 - rp.w), c2 = (A)rp.c2;
+  const A alpha2 = alpha * alpha;
+  const A bad_bp = -(A)(rp.alpha * rp.alpha / (4.0 * (1.0 - rp.w)));
+  A acc_r = 0;
+  double acc_d = 0.0, nbad = 0.0, nonfin = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const A d = (A)D[i] - mean;
+    const A a = (A)Hxx[i], b = (A)Hyy[i];
+    const A c = d - a - b;
+    const A xy = (A)Hxy[i], xz = (A)Hxz[i], yz = (A)Hyz[i];
+    A q = xy * xy + xz * xz + yz * yz - a * b - (a + b) * c;
+    const A R = alpha * d - (A)2 * q + c2 * (A)Nf[i] - (A)S[i];
+    A bp = omw * d * d + alpha * d - R;
+    A disc = alpha2 + (A)4 * omw * bp;
+    if (disc < (A)0) {
+      nbad += 1.0;
+      bp = bad_bp;
+      disc = (A)0;
+    }
+    const T sq = sqrt((T)disc);
+    const T dn = (T)((A)2 * bp) / ((T)alpha + sq);
+    Dnew[i] = dn;
+    if (isfinite((double)R)) acc_r += R < (A)0 ? -R : R;
+    else nonfin += 1.0;
+    acc_d += (double)dn;
+  }
+  double v[4] = {(double)acc_r, acc_d, nbad, nonfin};
+  block_sum<4>(v);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) partials[(int64_t)blockIdx.x * 4 + c] = v[c];
+  }
+}
+
+template <typename T, typename A>
+void launch_relax(const T* D, const double* dsum, const T* const* H6, const T* S, T* Dnew, int64_t m,
+                  RelaxParams rp, double* partials, int nblocks, cudaStream_t s) {
+  k_relax<T, A><<<nblocks, 256, 0, s>>>(D, dsum, H6[0], H6[1], H6[2], H6[3], H6[4], H6[5], S, Dnew, m, rp,
+                                        partials);
+}
+
+template void launch_relax<float, float>(const float*, const double*, const float* const*, const float*, float*,
+                                         int64_t, RelaxParams, double*, int, cudaStream_t);
+template void launch_relax<float, double>(const float*, const double*, const float* const*, const float*, float*,
+                                          int64_t, RelaxParams, double*, int, cudaStream_t);
+template void launch_relax<double, double>(const double*, const double*, const double* const*, const double*,
+                                           double*, int64_t, RelaxParams, double*, int, cudaStream_t);
+
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ partials, int nblocks, int ncomp,
+                                                  double* __restrict__ out) {
+  for (int c = 0; c < ncomp; ++c) {
+    double v[1] = {0.0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v[0] += partials[(int64_t)b * ncomp + c];
+    block_sum<1>(v);
+    if (threadIdx.x == 0) out[c] = v[0];
+    __syncthreads();
+  }
+}
+
+void launch_finalize(const double* partials, int nblocks, int ncomp, double* out, cudaStream_t s) {
+  k_finalize<<<1, 256, 0, s>>>(partials, nblocks, ncomp, out);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sum(const T* __restrict__ a, int64_t m, int absval,
+                                             double* __restrict__ partials) {
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)a[i];
+    acc += absval ? fabs(v) : v;
+  }
+  double v[1] = {acc};
+  block_sum<1>(v);
+  if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
+}
+
+template <typename T>
+void launch_sum(const T* a, int64_t m, bool absval, double* partials, int nblocks, cudaStream_t s) {
+  k_sum<T><<<nblocks, 256, 0, s>>>(a, m, absval ? 1 : 0, partials);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_product3(const T* __restrict__ a, const T* __restrict__ b,
+                                                  const T* __restrict__ c, int64_t m, double* __restrict__ partials) {
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = (double)a[i] * (double)b[i];
+    if (c) v *= (double)c[i];
+    acc += v;
+  }
+  double v[1] = {acc};
+  block_sum<1>(v);
+  if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
+}
+
+template <typename T>
+void launch_product3_sum(const T* a, const T* b, const T* c, int64_t m, double* partials, int nblocks,
+                         cudaStream_t s) {
+  k_product3<T><<<nblocks, 256, 0, s>>>(a, b, c, m, partials);
+}
+
+template <typename T>
+__global__ void k_density_contrast(const T* __restrict__ rho, T* __restrict__ delta, int64_t m,
+                                   const double* __restrict__ sum) {
+  const double inv_mean = (double)m / sum[0];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    delta[i] = (T)((double)rho[i] * inv_mean - 1.0);
+}
+
+template <typename T>
+void launch_density_contrast(const T* rho, T* delta, int64_t m, const double* sum, cudaStream_t s) {
+  k_density_contrast<T><<<num_sms() * 4, 256, 0, s>>>(rho, delta, m, sum);
+}
+
+template <typename T>
+__global__ void k_fill(T* __restrict__ a, int64_t m, T v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = v;
+}
+
+template <typename T>
+void launch_fill(T* a, int64_t m, T v, cudaStream_t s) {
+  k_fill<T><<<num_sms() * 4, 256, 0, s>>>(a, m, v);
+}
+
+template <typename T>
+__global__ void k_sub_mean(const T* __restrict__ in, T* __restrict__ out, int64_t m, const double* __restrict__ sum) {
+  const double mean = sum[0] / (double)m;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (T)((double)in[i] - mean);
+}
+
+template <typename T>
+void launch_sub_mean(const T* in, T* out, int64_t m, const double* sum, cudaStream_t s) {
+  k_sub_mean<T><<<num_sms() * 4, 256, 0, s>>>(in, out, m, sum);
+}
+
+#define DGP_INST_PW(T)                                                                         \
+  template void launch_sum<T>(const T*, int64_t, bool, double*, int, cudaStream_t);            \
+  template void launch_product3_sum<T>(const T*, const T*, const T*, int64_t, double*, int,    \
+                                       cudaStream_t);                                          \
+  template void launch_density_contrast<T>(const T*, T*, int64_t, const double*, cudaStream_t); \
+  template void launch_fill<T>(T*, int64_t, T, cudaStream_t);                                  \
+  template void launch_sub_mean<T>(const T*, T*, int64_t, const double*, cudaStream_t);
+DGP_INST_PW(float)
+DGP_INST_PW(double)
+
+// --------------------------------------------------------------------------
+// CIC (Eq. CIC): grid point i at x = i d; lower index floor(x/d), weights
+// (1 - f, f) per axis, periodic.  In FP32 x/d is formed as an exact product
+// with N/box held as an unevaluated pair (hi + lo), so the fractional offset
+// carries no more error than the position itself.
+__device__ __forceinline__ void cic_axis(float x, const CicParams& cp, int& i0, int& i1, float& f) {
+  const float hi = x * cp.inv_d_hi;
+  const float lo = fmaf(x, cp.inv_d_hi, -hi) + x * cp.inv_d_lo;
+  float fl = floorf(hi);
+  f = (hi - fl) + lo;
+  if (f < 0.f) { f += 1.f; fl -= 1.f; }
+  else if (f >= 1.f) { f -= 1.f; fl += 1.f; }
+  int i = (int)fl % cp.n;
+  if (i < 0) i += cp.n;
+  i0 = i;
+  i1 = (i + 1 == cp.n) ? 0 : i + 1;
+}
+
+__device__ __forceinline__ void cic_axis(double x, const CicParams& cp, int& i0, int& i1, double& f) {
+  const double u = x * cp.inv_d;
+  const double fl = floor(u);
+  f = u - fl;
+  long long i = (long long)fl % cp.n;
+  if (i < 0) i += cp.n;
+  i0 = (int)i;
+  i1 = (i0 + 1 == cp.n) ? 0 : i0 + 1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_cic_deposit(const T* __restrict__ x, const T* __restrict__ y,
+                                                     const T* __restrict__ z, int64_t np, T* __restrict__ rho,
+                                                     CicParams cp) {
+  const int64_t n = cp.n;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
+    int ix0, ix1, iy0, iy1, iz0, iz1;
+    T fx, fy, fz;
+    cic_axis(x[p], cp, ix0, ix1, fx);
+    cic_axis(y[p], cp, iy0, iy1, fy);
+    cic_axis(z[p], cp, iz0, iz1, fz);
+    const T gx = (T)1 - fx, gy = (T)1 - fy, gz = (T)1 - fz;
+    const int64_t r00 = (ix0 * n + iy0) * n, r01 = (ix0 * n + iy1) * n;
+    const int64_t r10 = (ix1 * n + iy0) * n, r11 = (ix1 * n + iy1) * n;
+    atomicAdd(rho + r00 + iz0, gx * gy * gz);
+    atomicAdd(rho + r00 + iz1, gx * gy * fz);
+    atomicAdd(rho + r01 + iz0, gx * fy * gz);
+    atomicAdd(rho + r01 + iz1, gx * fy * fz);
+    atomicAdd(rho + r10 + iz0, fx * gy * gz);
+    atomicAdd(rho + r10 + iz1, fx * gy * fz);
+    atomicAdd(rho + r11 + iz0, fx * fy * gz);
+    atomicAdd(rho + r11 + iz1, fx * fy * fz);
+  }
+}
+
+template <typename T>
+void launch_cic_deposit(const T* x, const T* y, const T* z, int64_t np, T* rho, CicParams cp, cudaStream_t s) {
+  if (np <= 0) return;
+  int64_t blocks = (np + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 16;
+  if (blocks > cap) blocks = cap;
+  k_cic_deposit<T><<<(unsigned)blocks, 256, 0, s>>>(x, y, z, np, rho, cp);
+}
+
+template <typename T>
+__device__ __forceinline__ T wrap_periodic(T v, T box, T inv_box) {
+  v -= box * floor(v * inv_box);
+  if (v >= box) v -= box;
+  if (v < (T)0) v = (T)0;
+  return v;
+}
+
+// Force interpolation with the deposit's window (Sec. III.A), kick, optional drift.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gather_kick(T* __restrict__ x, T* __restrict__ y, T* __restrict__ z,
+                                                     T* __restrict__ px, T* __restrict__ py, T* __restrict__ pz,
+                                                     int64_t np, const T* __restrict__ gx, const T* __restrict__ gy,
+                                                     const T* __restrict__ gz, CicParams cp, T kick, T drift,
+                                                     int do_drift) {
+  const int64_t n = cp.n;
+  const T box = (T)cp.box, inv_box = (T)(1.0 / cp.box);
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
+    int ix0, ix1, iy0, iy1, iz0, iz1;
+    T fx, fy, fz;
+    const T xp = x[p], yp = y[p], zp = z[p];
+    cic_axis(xp, cp, ix0, ix1, fx);
+    cic_axis(yp, cp, iy0, iy1, fy);
+    cic_axis(zp, cp, iz0, iz1, fz);
+    const T hx = (T)1 - fx, hy = (T)1 - fy, hz = (T)1 - fz;
+    const int64_t r00 = (ix0 * n + iy0) * n, r01 = (ix0 * n + iy1) * n;
+    const int64_t r10 = (ix1 * n + iy0) * n, r11 = (ix1 * n + iy1) * n;
+    const T w000 = hx * hy * hz, w001 = hx * hy * fz, w010 = hx * fy * hz, w011 = hx * fy * fz;
+    const T w100 = fx * hy * hz, w101 = fx * hy * fz, w110 = fx * fy * hz, w111 = fx * fy * fz;
+    T g[3];
+    const T* grids[3] = {gx, gy, gz};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T* G = grids[c];
+      g[c] = w000 * G[r00 + iz0] + w001 * G[r00 + iz1] + w010 * G[r01 + iz0] + w011 * G[r01 + iz1] +
+             w100 * G[r10 + iz0] + w101 * G[r10 + iz1] + w110 * G[r11 + iz0] + w111 * G[r11 + iz1];
+    }
+    const T qx = px[p] + kick * g[0], qy = py[p] + kick * g[1], qz = pz[p] + kick * g[2];
+    px[p] = qx;
+    py[p] = qy;
+    pz[p] = qz;
+    if (do_drift) {
+      x[p] = wrap_periodic(xp + drift * qx, box, inv_box);
+      y[p] = wrap_periodic(yp + drift * qy, box, inv_box);
+      z[p] = wrap_periodic(zp + drift * qz, box, inv_box);
+    }
+  }
+}
+
+template <typename T>
+void launch_gather_kick(T* x, T* y, T* z, T* px, T* py, T* pz, int64_t np, const T* gx, const T* gy,
+                        const T* gz, CicParams cp, double kick, double drift, int do_drift, cudaStream_t s) {
+  if (np <= 0) return;
+  int64_t blocks = (np + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 16;
+  if (blocks > cap) blocks = cap;
+  k_gather_kick<T><<<(unsigned)blocks, 256, 0, s>>>(x, y, z, px, py, pz, np, gx, gy, gz, cp, (T)kick, (T)drift,
+                                                    do_drift);
+}
+
+#define DGP_INST_P(T)                                                                              \
+  template void launch_cic_deposit<T>(const T*, const T*, const T*, int64_t, T*, CicParams, cudaStream_t); \
+  template void launch_gather_kick<T>(T*, T*, T*, T*, T*, T*, int64_t, const T*, const T*, const T*,  \
+                                      CicParams, double, double, int, cudaStream_t);
+DGP_INST_P(float)
+DGP_INST_P(double)
+
+}  // namespace dgp

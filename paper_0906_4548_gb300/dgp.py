@@ -1,0 +1,222 @@
+"""Thin ctypes binding of the DGP CUDA library (include/dgp.h).
+
+Argument marshalling only: every computation runs in libdgp.so.  Functions
+carry the C names; device buffers are passed as torch CUDA tensors (their
+data_ptr), host outputs come back as numpy arrays.  Importing this module
+raises if the library has not been built: there is no fallback.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libdgp.so")
+
+DGP_OK, DGP_E_INVALID, DGP_E_CUDA, DGP_E_NOMEM, DGP_E_NONFINITE = 0, 1, 2, 3, 4
+DGP_E_NOT_CONVERGED, DGP_E_BAD_POINTS, DGP_E_TIMEOUT, DGP_E_STATE = 5, 6, 7, 8
+DGP_FP32, DGP_MIXED, DGP_FP64 = 0, 1, 2
+DGP_GRAVITY_NL, DGP_GRAVITY_LDGP, DGP_GRAVITY_GRH = 0, 1, 2
+C_OVER_H0 = 2997.92458
+
+EXPORTED = ["dgp_background", "dgp_init", "dgp_destroy", "dgp_strerror", "dgp_reset", "dgp_solve_phi",
+            "dgp_solve_forces", "dgp_get_solution", "dgp_deposit", "pm_step", "pm_step_host", "power_spectrum", "bispectrum",
+            "dgp_profile", "dgp_profile_read", "dgp_kernel_name"]
+DGP_KERNEL_KINDS = 10
+
+
+class DgpError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (where, strerror(status), status))
+
+
+class Cosmology(ctypes.Structure):
+    _fields_ = [("omega_m0", ctypes.c_double), ("c_over_H0", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("box", ctypes.c_double), ("n", ctypes.c_int), ("rc_H0", ctypes.c_double),
+                ("w", ctypes.c_double), ("precision", ctypes.c_int), ("gravity", ctypes.c_int),
+                ("local_only", ctypes.c_int), ("max_iter", ctypes.c_int), ("tol", ctypes.c_double)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("norm_res", ctypes.c_double), ("min_norm_res", ctypes.c_double),
+                ("bad_fraction", ctypes.c_double), ("eps", ctypes.c_double), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Particles(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("px", ctypes.c_void_p), ("py", ctypes.c_void_p), ("pz", ctypes.c_void_p),
+                ("n", ctypes.c_int64)]
+
+
+class Background(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_double) for f in
+                ("E", "eta", "alpha", "beta", "s", "c2", "c3", "q", "omega_m", "geff_local", "growth_D",
+                 "growth_f")]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError("libdgp.so is not built (%s); run __graft_entry__.build()" % _LIB_PATH)
+    lib = ctypes.CDLL(_LIB_PATH)
+    vp, d, i, i64 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int64
+    P = ctypes.POINTER
+    sig = {
+        "dgp_background": (i, [P(Cosmology), d, d, P(Background)]),
+        "dgp_init": (i, [P(vp), P(Params), P(Cosmology), vp]),
+        "dgp_destroy": (None, [vp]),
+        "dgp_strerror": (ctypes.c_char_p, [i]),
+        "dgp_reset": (i, [vp]),
+        "dgp_solve_phi": (i, [vp, d, vp, vp, d, P(SolveInfo)]),
+        "dgp_solve_forces": (i, [vp, d, vp, vp, vp, vp, vp, d, P(SolveInfo)]),
+        "dgp_get_solution": (i, [vp, vp]),
+        "dgp_deposit": (i, [vp, P(Particles), vp]),
+        "pm_step": (i, [vp, P(Particles), d, d, P(SolveInfo)]),
+        "pm_step_host": (i, [vp, P(Particles), d, d, P(SolveInfo)]),
+        "power_spectrum": (i, [vp, vp, i, P(d), P(d), P(i64)]),
+        "bispectrum": (i, [vp, vp, d, d, i, P(d), d, P(d), P(d)]),
+        "dgp_profile": (i, [vp, i]),
+        "dgp_profile_read": (i, [vp, i, P(i64), P(d), P(i64), P(d), P(d)]),
+        "dgp_kernel_name": (ctypes.c_char_p, [i]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def strerror(status):
+    return lib.dgp_strerror(int(status)).decode()
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(t.ctypes.data)
+    return ctypes.c_void_p(int(t))
+
+
+def _check(status, where, allow=(DGP_OK,)):
+    if status not in allow:
+        raise DgpError(status, where)
+    return status
+
+
+def dgp_background(omega_m0, rc_H0, a, c_over_H0=C_OVER_H0):
+    out = Background()
+    _check(lib.dgp_background(ctypes.byref(Cosmology(omega_m0, c_over_H0)), rc_H0, a, ctypes.byref(out)),
+           "dgp_background")
+    return {f: getattr(out, f) for f, _ in Background._fields_}
+
+
+def dgp_init(box, n, rc_H0, omega_m0=0.27, w=1.0 / 3.0, precision=DGP_MIXED, gravity=DGP_GRAVITY_NL,
+             local_only=False, max_iter=100, tol=1e-6, stream=None, c_over_H0=C_OVER_H0):
+    """Returns an opaque context handle (ctypes.c_void_p)."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    ctx = ctypes.c_void_p()
+    p = Params(box, n, rc_H0, w, precision, gravity, 1 if local_only else 0, max_iter, tol)
+    _check(lib.dgp_init(ctypes.byref(ctx), ctypes.byref(p), ctypes.byref(Cosmology(omega_m0, c_over_H0)),
+                        ctypes.c_void_p(stream)), "dgp_init")
+    return ctx
+
+
+def dgp_destroy(ctx):
+    lib.dgp_destroy(ctx)
+
+
+def dgp_reset(ctx):
+    _check(lib.dgp_reset(ctx), "dgp_reset")
+
+
+def dgp_solve_phi(ctx, a, delta, phi, tol):
+    info = SolveInfo()
+    st = _check(lib.dgp_solve_phi(ctx, a, _ptr(delta), _ptr(phi), tol, ctypes.byref(info)), "dgp_solve_phi",
+                (DGP_OK, DGP_E_NOT_CONVERGED))
+    return st, info.as_dict()
+
+
+def dgp_solve_forces(ctx, a, delta, phi, gx, gy, gz, tol):
+    info = SolveInfo()
+    st = _check(lib.dgp_solve_forces(ctx, a, _ptr(delta), _ptr(phi), _ptr(gx), _ptr(gy), _ptr(gz), tol,
+                                     ctypes.byref(info)), "dgp_solve_forces", (DGP_OK, DGP_E_NOT_CONVERGED))
+    return st, info.as_dict()
+
+
+def dgp_get_solution(ctx, D):
+    _check(lib.dgp_get_solution(ctx, _ptr(D)), "dgp_get_solution")
+
+
+def particles(x, y, z, px, py, pz):
+    return Particles(_ptr(x), _ptr(y), _ptr(z), _ptr(px), _ptr(py), _ptr(pz), int(x.numel() if hasattr(x, "numel") else x.size))
+
+
+def dgp_deposit(ctx, parts, delta):
+    _check(lib.dgp_deposit(ctx, ctypes.byref(parts), _ptr(delta)), "dgp_deposit")
+
+
+def pm_step(ctx, parts, a, da):
+    info = SolveInfo()
+    _check(lib.pm_step(ctx, ctypes.byref(parts), a, da, ctypes.byref(info)), "pm_step")
+    return info.as_dict()
+
+
+def pm_step_host(ctx, parts, a, da):
+    info = SolveInfo()
+    _check(lib.pm_step_host(ctx, ctypes.byref(parts), a, da, ctypes.byref(info)), "pm_step_host")
+    return info.as_dict()
+
+
+def power_spectrum(ctx, delta, nbins):
+    k = np.zeros(nbins)
+    pk = np.zeros(nbins)
+    nm = np.zeros(nbins, dtype=np.int64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib.power_spectrum(ctx, _ptr(delta), nbins, k.ctypes.data_as(dp), pk.ctypes.data_as(dp),
+                              nm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))), "power_spectrum")
+    return k, pk, nm
+
+
+def bispectrum(ctx, delta, k1, k2, thetas, dk=0.0):
+    th = np.ascontiguousarray(thetas, dtype=np.float64)
+    b = np.zeros(th.size)
+    q = np.zeros(th.size)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib.bispectrum(ctx, _ptr(delta), k1, k2, th.size, th.ctypes.data_as(dp), dk, b.ctypes.data_as(dp),
+                          q.ctypes.data_as(dp)), "bispectrum")
+    return b, q
+
+
+def dgp_profile(ctx, timing):
+    _check(lib.dgp_profile(ctx, 1 if timing else 0), "dgp_profile")
+
+
+def dgp_profile_read(ctx):
+    """{kernel name: dict(launches, bytes, timed, ms, timed_bytes)} since the last dgp_profile."""
+    out = {}
+    for kind in range(DGP_KERNEL_KINDS):
+        l, t = ctypes.c_int64(), ctypes.c_int64()
+        b, ms, tb = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib.dgp_profile_read(ctx, kind, ctypes.byref(l), ctypes.byref(b), ctypes.byref(t), ctypes.byref(ms),
+                                    ctypes.byref(tb)), "dgp_profile_read")
+        out[lib.dgp_kernel_name(kind).decode()] = dict(launches=l.value, bytes=b.value, timed=t.value, ms=ms.value,
+                                                       timed_bytes=tb.value)
+    return out

@@ -1,0 +1,350 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances: phi and forces rel. L2 <= 1e-5 per solve for the FP32-data paths,
+<= 1e-9 for the FP64 path; integer outputs (mode counts) bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import background as obg
+from oracle import estimators as oest
+from oracle import field as ofield
+from oracle import pm as opm
+from paper_0906_4548_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+OM = 0.27
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, float) - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    import torch
+    assert torch.cuda.is_available()
+    return torch, torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def dgp(torch_dev):
+    import __graft_entry__ as g
+    g.build()
+    from paper_0906_4548_gb300 import dgp as d
+    return d
+
+
+def zel(n, box, a, ns, rms, seed, rc=1.0):
+    vf = obg.zeldovich_velocity_factor(a, OM, rc)
+    return inputs.zeldovich_particles(n, box, ns, rms, seed, vf)
+
+
+def to_dev(torch_dev, arr, dtype):
+    torch, dev = torch_dev
+    return torch.tensor(np.ascontiguousarray(arr), dtype=dtype, device=dev)
+
+
+def prec_dtype(torch, prec, dgp):
+    return torch.float64 if prec == dgp.DGP_FP64 else torch.float32
+
+
+def np_dtype(prec, dgp):
+    return np.float64 if prec == dgp.DGP_FP64 else np.float32
+
+
+@pytest.mark.parametrize("n,prec", [(16, 0), (32, 1), (64, 0), (32, 2)])
+def test_power_spectrum_parity(dgp, torch_dev, n, prec):
+    torch, _ = torch_dev
+    box = 150.0
+    d = np.random.default_rng(n).standard_normal((n, n, n)).astype(np_dtype(prec, dgp)).astype(np.float64)
+    ctx = dgp.dgp_init(box, n, 1.0, OM, precision=prec)
+    try:
+        k, P, cnt = dgp.power_spectrum(ctx, to_dev(torch_dev, d, prec_dtype(torch, prec, dgp)), n // 2)
+    finally:
+        dgp.dgp_destroy(ctx)
+    ko, Po, co = oest.power_spectrum(d, box)
+    assert np.array_equal(cnt, co)
+    assert np.allclose(k, ko, rtol=1e-12)
+    tol = 1e-11 if prec == dgp.DGP_FP64 else 2e-6
+    assert np.max(np.abs(P / Po - 1)) < tol
+
+
+@pytest.mark.parametrize("n,prec", [(32, 1), (64, 0), (32, 2)])
+def test_deposit_parity_ragged(dgp, torch_dev, n, prec):
+    torch, _ = torch_dev
+    box = 100.0
+    pos, mom, _ = zel(n, box, 0.1, -2.0, 0.5, 3)
+    npart = n ** 3 - 37  # ragged tail
+    nd = np_dtype(prec, dgp)
+    pos = pos[:, :npart].astype(nd)
+    ctx = dgp.dgp_init(box, n, 1.0, OM, precision=prec)
+    try:
+        td = prec_dtype(torch, prec, dgp)
+        t = [to_dev(torch_dev, v, td) for v in (*pos, *mom[:, :npart])]
+        delta = torch.empty((n, n, n), dtype=td, device=torch_dev[1])
+        dgp.dgp_deposit(ctx, dgp.particles(*t), delta)
+        got = delta.double().cpu().numpy()
+    finally:
+        dgp.dgp_destroy(ctx)
+    want = opm.density_contrast(opm.cic_deposit(pos.astype(np.float64), n, box))
+    assert rel_l2(got, want) < (1e-13 if prec == dgp.DGP_FP64 else 1e-6)
+
+
+def _solve_both(dgp, torch_dev, n, box, a, prec, tol_gpu, seed=5, w=1 / 3, local_only=False, rc=1.0,
+                gravity=0, rms=0.5):
+    torch, dev = torch_dev
+    pos, _, _ = zel(n, box, a, -1.5, rms, seed, rc)
+    nd = np_dtype(prec, dgp)
+    delta = opm.density_contrast(opm.cic_deposit(pos, n, box)).astype(nd)
+    ogr = {0: "nl", 1: "ldgp", 2: "grh"}[gravity]
+    phi_o, g_o, D_o, info_o = ofield.solve_phi(delta.astype(np.float64), a, box, OM, rc, w=w, tol=1e-13,
+                                               max_iter=300, local_only=local_only, gravity=ogr)
+    ctx = dgp.dgp_init(box, n, rc, OM, w=w, precision=prec, gravity=gravity, local_only=local_only,
+                       max_iter=200, tol=tol_gpu)
+    try:
+        td = prec_dtype(torch, prec, dgp)
+        dd = to_dev(torch_dev, delta, td)
+        phi = torch.empty_like(dd)
+        g = [torch.empty_like(dd) for _ in range(3)]
+        st, info = dgp.dgp_solve_forces(ctx, a, dd, phi, *g, tol_gpu)
+        D = None
+        if gravity == 0:
+            Dt = torch.empty_like(dd)
+            dgp.dgp_get_solution(ctx, Dt)
+            D = Dt.double().cpu().numpy()
+        out = dict(phi=phi.double().cpu().numpy(), g=[x.double().cpu().numpy() for x in g], D=D, info=info,
+                   status=st)
+    finally:
+        dgp.dgp_destroy(ctx)
+    return out, dict(phi=phi_o, g=g_o, D=D_o, info=info_o)
+
+
+@pytest.mark.parametrize("n,box,a,prec,tol_gpu,tol_phi", [
+    (32, 100.0, 0.05, 2, 1e-10, 1e-9),     # FP64 path, the 32^3 one-solve case
+    (32, 100.0, 0.05, 1, 1e-6, 1e-5),
+    (64, 200.0, 0.5, 1, 1e-6, 1e-5),
+    (64, 200.0, 1.0, 0, 1e-6, 1e-5),
+    (16, 50.0, 0.3, 1, 1e-6, 1e-5),
+    (128, 200.0, 0.5, 1, 1e-6, 1e-5),
+])
+def test_solve_phi_and_forces_parity(dgp, torch_dev, n, box, a, prec, tol_gpu, tol_phi):
+    got, want = _solve_both(dgp, torch_dev, n, box, a, prec, tol_gpu)
+    assert want["info"]["converged"]
+    assert rel_l2(got["phi"], want["phi"]) <= tol_phi
+    for i in range(3):
+        assert rel_l2(got["g"][i], want["g"][i]) <= tol_phi
+    assert rel_l2(got["D"], want["D"]) <= 10 * tol_phi
+    if prec == dgp.DGP_FP64:
+        assert got["status"] == dgp.DGP_OK and got["info"]["norm_res"] < tol_gpu
+
+
+@pytest.mark.parametrize("gravity", [1, 2])
+def test_linear_gravity_modes_parity(dgp, torch_dev, gravity):
+    got, want = _solve_both(dgp, torch_dev, 32, 300.0, 0.5, 1, 1e-6, gravity=gravity)
+    assert rel_l2(got["phi"], want["phi"]) <= 1e-6
+    assert got["info"]["iters"] == 0
+
+
+def test_w_half_and_local_only_parity(dgp, torch_dev):
+    got, want = _solve_both(dgp, torch_dev, 32, 64.0, 0.4, 2, 1e-11, w=0.5, local_only=True)
+    assert rel_l2(got["phi"], want["phi"]) <= 1e-9
+
+
+def test_uniform_lattice_gives_zero(dgp, torch_dev):
+    torch, dev = torch_dev
+    n, box = 32, 80.0
+    pos, mom = inputs.lattice_particles(n, box)
+    ctx = dgp.dgp_init(box, n, 1.0, OM, precision=dgp.DGP_MIXED)
+    try:
+        t = [to_dev(torch_dev, v, torch.float32) for v in (*pos, *mom)]
+        delta = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+        dgp.dgp_deposit(ctx, dgp.particles(*t), delta)
+        assert float(delta.abs().max()) < 1e-6
+        phi = torch.empty_like(delta)
+        dgp.dgp_solve_phi(ctx, 0.5, torch.zeros_like(delta), phi, 1e-6)
+        assert float(phi.abs().max()) == 0.0
+    finally:
+        dgp.dgp_destroy(ctx)
+
+
+def test_nonfinite_input_and_bad_calls(dgp, torch_dev):
+    torch, dev = torch_dev
+    n = 16
+    ctx = dgp.dgp_init(50.0, n, 1.0, OM, precision=dgp.DGP_MIXED)
+    try:
+        d = torch.zeros((n, n, n), dtype=torch.float32, device=dev)
+        d[3, 4, 5] = float("nan")
+        with pytest.raises(dgp.DgpError) as e:
+            dgp.dgp_solve_phi(ctx, 0.5, d, torch.empty_like(d), 1e-6)
+        assert e.value.status == dgp.DGP_E_NONFINITE
+        dgp.dgp_reset(ctx)
+        with pytest.raises(dgp.DgpError) as e:
+            dgp.dgp_get_solution(ctx, torch.empty_like(d))
+        assert e.value.status == dgp.DGP_E_STATE
+        empty = torch.empty(0, dtype=torch.float32, device=dev)
+        with pytest.raises(dgp.DgpError) as e:
+            dgp.dgp_deposit(ctx, dgp.particles(*([empty] * 6)), d)
+        assert e.value.status == dgp.DGP_E_INVALID
+        with pytest.raises(dgp.DgpError):
+            dgp.power_spectrum(ctx, d, n)  # nbins > n/2
+    finally:
+        dgp.dgp_destroy(ctx)
+
+
+def test_not_converged_reports_best_iterate(dgp, torch_dev):
+    torch, dev = torch_dev
+    n, box, a = 32, 100.0, 0.3
+    pos, _, _ = zel(n, box, a, -1.5, 0.8, 9)
+    delta = opm.density_contrast(opm.cic_deposit(pos, n, box)).astype(np.float32)
+    ctx = dgp.dgp_init(box, n, 1.0, OM, precision=dgp.DGP_MIXED, max_iter=2)
+    try:
+        dd = to_dev(torch_dev, delta, torch.float32)
+        st, info = dgp.dgp_solve_phi(ctx, a, dd, torch.empty_like(dd), 1e-12)
+    finally:
+        dgp.dgp_destroy(ctx)
+    _, oinfo = ofield.solve_brane_bending(delta.astype(np.float64), a, box, OM, 1.0, tol=1e-12, max_iter=2)
+    assert st == dgp.DGP_E_NOT_CONVERGED and info["status"] == dgp.DGP_E_NOT_CONVERGED
+    assert info["iters"] == oinfo["iters"] == 2
+    assert abs(info["norm_res"] / oinfo["norm_res"] - 1) < 1e-3
+
+
+def test_pm_run_fp64_matches_oracle(dgp, torch_dev):
+    """32^3, 100 Mpc/h, FP64: one solve to 1e-10 at a = 0.05, then 10 KDK steps to a = 0.1."""
+    torch, dev = torch_dev
+    n, box, a0, a1, ns = 32, 100.0, 0.05, 0.1, 10
+    pos, mom, _ = zel(n, box, a0, -2.0, 0.5, 1)
+    st = opm.run(pos, mom, a0, a1, ns, n, box, OM, 1.0, tol=1e-10, max_iter=300)
+    ctx = dgp.dgp_init(box, n, 1.0, OM, precision=dgp.DGP_FP64, tol=1e-10, max_iter=300)
+    try:
+        t = [to_dev(torch_dev, v, torch.float64) for v in (*pos, *mom)]
+        parts = dgp.particles(*t)
+        a = a0
+        dl = (math.log(a1) - math.log(a0)) / ns
+        infos = []
+        for i in range(ns):
+            a_next = a0 * math.exp((i + 1) * dl)
+            infos.append(dgp.pm_step(ctx, parts, a, a_next - a))
+            a = a + (a_next - a)
+        x = np.stack([v.cpu().numpy() for v in t[:3]])
+        p = np.stack([v.cpu().numpy() for v in t[3:]])
+    finally:
+        dgp.dgp_destroy(ctx)
+    dx = (x - st.pos + box / 2) % box - box / 2
+    disp = (st.pos - pos + box / 2) % box - box / 2
+    assert np.linalg.norm(dx) / np.linalg.norm(disp) < 1e-9
+    assert rel_l2(p, st.mom) < 1e-9
+    assert all(i["norm_res"] < 1e-10 for i in infos)
+
+
+def test_pm_run_mixed_pk_matches_oracle(dgp, torch_dev):
+    """64^3 FP32 particles / mixed solve, 8 steps: P(k) of the end state within 1e-3."""
+    torch, dev = torch_dev
+    n, box, a0, a1, ns = 64, 200.0, 0.1, 0.3, 8
+    pos, mom, _ = zel(n, box, a0, -1.5, 0.5, 2)
+    pos, mom = pos.astype(np.float32).astype(np.float64), mom.astype(np.float32).astype(np.float64)
+    st = opm.run(pos, mom, a0, a1, ns, n, box, OM, 1.0, tol=1e-10, max_iter=300)
+    ctx = dgp.dgp_init(box, n, 1.0, OM, precision=dgp.DGP_MIXED, tol=1e-6, max_iter=100)
+    try:
+        t = [to_dev(torch_dev, v, torch.float32) for v in (*pos, *mom)]
+        parts = dgp.particles(*t)
+        a = a0
+        dl = (math.log(a1) - math.log(a0)) / ns
+        for i in range(ns):
+            a_next = a0 * math.exp((i + 1) * dl)
+            dgp.pm_step(ctx, parts, a, a_next - a)
+            a = a + (a_next - a)
+        delta = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+        dgp.dgp_deposit(ctx, parts, delta)
+        k, P, cnt = dgp.power_spectrum(ctx, delta, n // 2)
+    finally:
+        dgp.dgp_destroy(ctx)
+    ko, Po, co = oest.power_spectrum(opm.density_contrast(opm.cic_deposit(st.pos, n, box)), box)
+    assert np.array_equal(cnt, co)
+    assert np.max(np.abs(P / Po - 1)) < 1e-3
+
+
+def test_pm_step_host_equals_device(dgp, torch_dev):
+    torch, dev = torch_dev
+    n, box, a = 32, 100.0, 0.2
+    pos, mom, _ = zel(n, box, a, -1.5, 0.5, 4)
+    res = []
+    for host in (False, True):
+        ctx = dgp.dgp_init(box, n, 1.0, OM, precision=dgp.DGP_MIXED)
+        try:
+            if host:
+                arrs = [np.ascontiguousarray(v, dtype=np.float32) for v in (*pos, *mom)]
+                dgp.pm_step_host(ctx, dgp.particles(*arrs), a, 0.01)
+                res.append(np.stack(arrs))
+            else:
+                t = [to_dev(torch_dev, v, torch.float32) for v in (*pos, *mom)]
+                dgp.pm_step(ctx, dgp.particles(*t), a, 0.01)
+                res.append(np.stack([v.cpu().numpy() for v in t]))
+        finally:
+            dgp.dgp_destroy(ctx)
+    assert np.max(np.abs(res[0] - res[1])) < 1e-5 * np.max(np.abs(res[0]))
+
+
+def test_bispectrum_parity(dgp, torch_dev):
+    torch, dev = torch_dev
+    n, box = 32, 100.0
+    d, _ = inputs.linear_field(n, box, -1.5, 0.5, seed=6)
+    d = d + 0.3 * (d ** 2 - np.mean(d ** 2))  # some non-Gaussianity
+    kf = 2 * np.pi / box
+    th = np.array([0.3, 1.2, 2.5])
+    ctx = dgp.dgp_init(box, n, 1.0, OM, precision=dgp.DGP_FP64)
+    try:
+        b, q = dgp.bispectrum(ctx, to_dev(torch_dev, d, torch.float64), 3 * kf, 5 * kf, th)
+    finally:
+        dgp.dgp_destroy(ctx)
+    B, Q, *_ = oest.bispectrum(d, box, 3 * kf, 5 * kf, th)
+    assert np.allclose(b, B, rtol=1e-9) and np.allclose(q, Q, rtol=1e-9)
+
+
+# ---------------------------------------------------------------- full size
+@pytest.fixture(scope="module")
+def full_case(dgp, torch_dev):
+    """256^3 particles in 400 Mpc/h, n_s = -1.5, rms 0.5 at a = 0.02 (the PM-step
+    workload), evolved to a = 0.3 by Zel'dovich growth for a nonlinear field."""
+    n, box, a = 256, 400.0, 0.3
+    pos, mom, _ = zel(n, box, a, -1.5, 1.0, 3)
+    return n, box, a, pos.astype(np.float32), mom.astype(np.float32)
+
+
+def test_full_size_deposit_pk_solve(dgp, torch_dev, full_case):
+    torch, dev = torch_dev
+    n, box, a, pos, mom = full_case
+    ctx = dgp.dgp_init(box, n, 1.0, OM, precision=dgp.DGP_MIXED, tol=1e-6, max_iter=100)
+    try:
+        t = [to_dev(torch_dev, v, torch.float32) for v in (*pos, *mom)]
+        delta = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+        dgp.dgp_deposit(ctx, dgp.particles(*t), delta)
+        k, P, cnt = dgp.power_spectrum(ctx, delta, n // 2)
+        phi = torch.empty_like(delta)
+        st, info = dgp.dgp_solve_phi(ctx, a, delta, phi, 1e-6)
+        Dt = torch.empty_like(delta)
+        dgp.dgp_get_solution(ctx, Dt)
+        dg = delta.double().cpu().numpy()
+        phig = phi.double().cpu().numpy()
+        D = Dt.double().cpu().numpy()
+    finally:
+        dgp.dgp_destroy(ctx)
+    do = opm.density_contrast(opm.cic_deposit(pos.astype(np.float64), n, box))
+    assert rel_l2(dg, do) < 1e-6
+    ko, Po, co = oest.power_spectrum(dg, box)
+    assert np.array_equal(cnt, co) and np.max(np.abs(P / Po - 1)) < 2e-6
+    # residual of the GPU's accepted D evaluated by the oracle in FP64
+    coef = obg.coefficients(a, OM, 1.0)
+    grid = ofield.KGrid(n, box)
+    from oracle.fft import fft3
+    dk = fft3(dg)
+    dk[grid.zero] = 0
+    S = ofield.ifft3_real(ofield.source_spectrum(dk, grid, coef))
+    Dk = fft3(D)
+    Dm, H, Nf = ofield.derived_fields(Dk, grid, coef)
+    r = np.mean(np.abs(ofield.residual(Dm, H, Nf, S, coef))) / np.mean(np.abs(S))
+    assert r < max(3e-6, 3 * info["norm_res"])
+    phio = ofield.ifft3_real(ofield.phi_spectrum(dk, Dk, grid, coef))
+    assert rel_l2(phig, phio) < 1e-5

@@ -5,7 +5,10 @@ seeded n_s = -1.5 power-law Gaussian field with mesh rms 0.5 at a = 0.02,
 Zel'dovich initial conditions, r_c H0 = 1, Omega_m0 = 0.27, w = 1/3, steps
 uniform in ln a from a = 0.02 to a = 1 in 200 steps, relaxation tolerance 1e-6
 on <|R|>/eps every step, FP32 mesh/particles with FP64 residual, discriminant
-and reductions.  A "step" is one pm_step call (deposit, field solve, forces,
+and reductions (the residual R, split source B' and discriminant Delta are
+evaluated on pairs of floats with error-free transformations, ~48 bits;
+--precision mixed-fp64 evaluates them on the FP64 pipe instead).  A "step" is
+one pm_step call (deposit, field solve, forces,
 gather, kick-drift-kick).  The timed region runs K consecutive steps from
 a = 0.02 (K = 200 is the whole run) after W warm-up steps and a reset to the
 initial conditions.  Inputs (403 MB of particles, 64 MB mesh fields) exceed
@@ -37,14 +40,22 @@ METRIC = "PM steps/s at 256³ incl. converged DGP φ solve; % HBM roofline; vs F
 UNIT = "steps/s"
 # Mean residual evaluations per solve of this workload as measured on GB300
 # (used by the oracle reference arm, which has no GPU run to read it from).
-E_PER_SOLVE_REF = 5.0
+E_PER_SOLVE_REF = 20.8
 
 
-def config(n_gpus):
+PRECISION_DESC = {
+    "mixed": "mixed: fp32 mesh/FFT/particles; residual, B', discriminant as error-free fp32 pairs "
+             "(~48-bit); norms and reductions fp64",
+    "mixed-fp64": "mixed: fp32 mesh/FFT/particles; residual, B', discriminant, norms and reductions fp64",
+    "fp32": "fp32 throughout (fp64 cross-block sums only)",
+}
+
+
+def config(n_gpus, prec="mixed"):
     return {"workload": "dgp_pm_%dcube_box%g_ns%g_rms%g_a%g-%g_%dsteps_tol%g" % (
         WL["n"], WL["box"], WL["n_s"], WL["rms"], WL["a_start"], WL["a_end"], WL["run_steps"], WL["tol"]),
         "mesh": WL["n"], "particles": WL["n"] ** 3, "box_mpc_h": WL["box"], "rc_H0": WL["rc_H0"],
-        "w": WL["w"], "tol": WL["tol"], "precision": "mixed (fp32 data, fp64 residual/discriminant/reductions)",
+        "w": WL["w"], "tol": WL["tol"], "precision": PRECISION_DESC[prec],
         "parallelism": "replicas" if n_gpus > 1 else "single",
         "l2": "inputs larger than L2 (particles 403 MB, fields 64 MB each); no flush"}
 
@@ -158,7 +169,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": config(args.gpus),
+            "config": config(args.gpus, "mixed"),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -173,6 +184,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--precision", default="mixed", choices=sorted(PRECISION_DESC))
+    ap.add_argument("--no-compare", action="store_true", help="skip the precision comparison runs")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -201,7 +214,8 @@ def main():
     ic = [torch.tensor(v.astype(np.float32), device=dev) for v in (*pos, *mom)]
     cur = [t.clone() for t in ic]
     parts = dgp.particles(*cur)
-    ctx = dgp.dgp_init(box, n, WL["rc_H0"], WL["omega_m0"], w=WL["w"], precision=dgp.DGP_MIXED,
+    pcode = {"mixed": dgp.DGP_MIXED_EFT, "mixed-fp64": dgp.DGP_MIXED, "fp32": dgp.DGP_FP32}
+    ctx = dgp.dgp_init(box, n, WL["rc_H0"], WL["omega_m0"], w=WL["w"], precision=pcode[args.precision],
                        max_iter=WL["max_iter"], tol=WL["tol"])
     dlna = math.log(WL["a_end"] / WL["a_start"]) / WL["run_steps"]
     sched = [WL["a_start"] * math.exp(i * dlna) for i in range(max(args.steps, args.warmup) + 1)]
@@ -270,7 +284,8 @@ def main():
     evals = [i["iters"] + 1 for i in infos]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": config(world),
+            "vs_baseline": None, "dtype": {"mixed": "f32+eft", "mixed-fp64": "f32+f64", "fp32": "f32"}[args.precision],
+            "data": "synthetic", "config": config(world, args.precision),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": None, "kernel": dom,
                          "peak_source": peak_kind},
@@ -281,6 +296,37 @@ def main():
                        "not_converged_steps": sum(1 for i in infos if i["status"] != 0),
                        "max_norm_res": max(i["norm_res"] for i in infos), "amplitude_A": amp},
             "kernels": kernels}
+    # the same run under the other precisions (same accuracy target): steps/s,
+    # evaluations and P(k) of the end state relative to this run's
+    if rank == 0 and not args.no_compare:
+        def end_pk(c):
+            dl = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+            dgp.dgp_deposit(c, parts, dl)
+            return dgp.power_spectrum(c, dl, n // 2)[1]
+        pk_main = end_pk(ctx)
+        comp = {}
+        for name in sorted(pcode):
+            if name == args.precision:
+                comp[name] = {"value": value, "evals_per_solve_mean": sum(evals) / len(evals)}
+                continue
+            c2 = dgp.dgp_init(box, n, WL["rc_H0"], WL["omega_m0"], w=WL["w"], precision=pcode[name],
+                              max_iter=WL["max_iter"], tol=WL["tol"])
+            for cc, s0 in zip(cur, ic):
+                cc.copy_(s0)
+            infs = []
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for i in range(args.steps):
+                infs.append(dgp.pm_step(c2, parts, sched[i], sched[i + 1] - sched[i]))
+            f1.record(stream)
+            torch.cuda.synchronize()
+            pk2 = end_pk(c2)
+            comp[name] = {"value": args.steps / (f0.elapsed_time(f1) / 1000.0),
+                          "evals_per_solve_mean": sum(i["iters"] + 1 for i in infs) / len(infs),
+                          "pk_max_rel_diff_vs_main": float(np.max(np.abs(pk2 / pk_main - 1)))}
+            dgp.dgp_destroy(c2)
+        line["precision_comparison"] = comp
     dgp.dgp_destroy(ctx)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ts = oracle_fft_sample_seconds(36)

@@ -51,7 +51,16 @@ typedef enum {
   DGP_E_STATE = 8          /* call not valid in the context's current state */
 } dgp_status;
 
-enum { DGP_FP32 = 0, DGP_MIXED = 1, DGP_FP64 = 2 };
+/* Precision of a context.
+ *   DGP_FP32      all arithmetic FP32 (FP64 only for cross-block sums).
+ *   DGP_MIXED     FP32 mesh fields, FFTs and particles; the residual R, the
+ *                 split source B' and the discriminant Delta in FP64; norms and
+ *                 global means reduced in FP64.
+ *   DGP_FP64      everything FP64 (double buffers).
+ *   DGP_MIXED_EFT as DGP_MIXED, but R, B' and Delta are evaluated on pairs of
+ *                 floats with error-free transformations (TwoSum, FMA TwoProd),
+ *                 ~48 significant bits, without the FP64 pipe. */
+enum { DGP_FP32 = 0, DGP_MIXED = 1, DGP_FP64 = 2, DGP_MIXED_EFT = 3 };
 enum { DGP_GRAVITY_NL = 0, DGP_GRAVITY_LDGP = 1, DGP_GRAVITY_GRH = 2 };
 
 typedef struct dgp_ctx dgp_ctx;
@@ -66,7 +75,7 @@ typedef struct {
   int n;             /* mesh points per side: 16, 32, 64, 128, 256 or 512 */
   double rc_H0;      /* crossover scale r_c in units of c/H0, > 0 (Sec. II) */
   double w;          /* splitting parameter of Eq. FullDGP2wpara, 0 <= w < 1 */
-  int precision;     /* DGP_FP32, DGP_MIXED or DGP_FP64 */
+  int precision;     /* DGP_FP32, DGP_MIXED, DGP_FP64 or DGP_MIXED_EFT */
   int gravity;       /* DGP_GRAVITY_NL (Eqs. FullDGP1-2), _LDGP (Eq. LinearDGP), _GRH (Eq. GRPoisson) */
   int local_only;    /* nonzero: drop the sqrt(-lapbar) terms (Appendix Eq. FullDGP2simp) */
   int max_iter;      /* relaxation updates per solve before giving up, >= 0 */
@@ -135,6 +144,11 @@ int dgp_solve_phi(dgp_ctx *c, double a, const void *delta, void *phi, double tol
  * component of each derivative is zero).  phi may be NULL. */
 int dgp_solve_forces(dgp_ctx *c, double a, const void *delta, void *phi, void *gx, void *gy,
                      void *gz, double tol, dgp_solve_info *info);
+
+/* Normalised residual <|R|>/eps of every iterate of the last nonlinear solve,
+ * in order (the first is the starting iterate).  Copies min(count, max_n)
+ * values to out (host) and returns the count; a negative status on error. */
+int dgp_solve_history(dgp_ctx *c, double *out, int max_n);
 
 /* Copy the accepted solution D = lapbar^2 C of the last nonlinear solve
  * (the warm start of the next one, Sec. III.B) into the device n^3 field D,

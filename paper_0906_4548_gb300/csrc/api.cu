@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/dgp.h"
+#include "fft_core.cuh"
 #include "kernels.cuh"
 
 namespace dgp {
@@ -196,6 +197,7 @@ class EngineBase {
   virtual void reset() = 0;
   virtual int get_solution(void* D) = 0;
   Profiler prof;
+  std::vector<double> history;  // normalised residual of each iterate of the last solve
 };
 
 #define DGP_CUDA(call)                          \
@@ -219,11 +221,13 @@ class Engine : public EngineBase {
   T* rRho = nullptr;
   T* rG[3] = {};
   V* sD = nullptr;
+  V* sD2 = nullptr;             // ping-pong partner of sD during the iteration
   V* sDelta = nullptr;
   V* s6[6] = {};
   V* tw = nullptr;
   double* partials = nullptr;
-  int nblocks = 0;
+  int nblocks = 0;              // grid of the grid-stride reductions
+  int fblocks = 0;              // grid of the fused relaxation pass
   double* d_rstats = nullptr;   // [3][4]: sum|R|, sum D, nbad, nonfinite per D buffer
   double* d_misc = nullptr;     // [8]: sum rho, sum |S|, ...
   double* h_stats = nullptr;    // pinned host [8]
@@ -246,7 +250,7 @@ class Engine : public EngineBase {
     for (int i = 0; i < 6; ++i) { cudaFree(rH[i]); cudaFree(s6[i]); cudaFree(hp[i]); }
     cudaFree(rRho);
     for (int i = 0; i < 3; ++i) cudaFree(rG[i]);
-    cudaFree(sD); cudaFree(sDelta); cudaFree(tw);
+    cudaFree(sD); cudaFree(sD2); cudaFree(sDelta); cudaFree(tw);
     cudaFree(partials); cudaFree(d_rstats); cudaFree(d_misc);
     cudaFree(pk_partials); cudaFree(d_pk);
     cudaFreeHost(h_stats);
@@ -263,9 +267,12 @@ class Engine : public EngineBase {
     if (cudaMalloc(&rRho, rb) != cudaSuccess) return DGP_E_NOMEM;
     for (int i = 0; i < 3; ++i) if (cudaMalloc(&rG[i], rb) != cudaSuccess) return DGP_E_NOMEM;
     if (cudaMalloc(&sD, sb) != cudaSuccess) return DGP_E_NOMEM;
+    if (cudaMalloc(&sD2, sb) != cudaSuccess) return DGP_E_NOMEM;
     if (cudaMalloc(&sDelta, sb) != cudaSuccess) return DGP_E_NOMEM;
     nblocks = num_sms() * 4;
-    if (cudaMalloc(&partials, sizeof(double) * 4 * nblocks) != cudaSuccess) return DGP_E_NOMEM;
+    fblocks = fused_relax_blocks<T, N>();
+    const int pblocks = fblocks > nblocks ? fblocks : nblocks;
+    if (cudaMalloc(&partials, sizeof(double) * 4 * pblocks) != cudaSuccess) return DGP_E_NOMEM;
     if (cudaMalloc(&d_rstats, sizeof(double) * 12) != cudaSuccess) return DGP_E_NOMEM;
     if (cudaMalloc(&d_misc, sizeof(double) * 8) != cudaSuccess) return DGP_E_NOMEM;
     if (cudaMallocHost(&h_stats, sizeof(double) * 8) != cudaSuccess) return DGP_E_NOMEM;
@@ -273,14 +280,23 @@ class Engine : public EngineBase {
     if (cudaMalloc(&pk_partials, sizeof(double) * 3 * (N / 2) * (size_t)pk_blocks) != cudaSuccess) return DGP_E_NOMEM;
     if (cudaMalloc(&d_pk, sizeof(double) * 3 * (N / 2)) != cudaSuccess) return DGP_E_NOMEM;
     // twiddles W_N^t = exp(-2 pi i t / N), computed in FP64 and rounded once
-    V htw[N];
-    for (int t = 0; t < N; ++t) {
-      const double ang = 2.0 * M_PI * (double)t / (double)N;
-      htw[t].x = (T)cos(ang);
-      htw[t].y = (T)(-sin(ang));
-    }
-    if (cudaMalloc(&tw, sizeof(V) * N) != cudaSuccess) return DGP_E_NOMEM;
-    DGP_CUDA(cudaMemcpy(tw, htw, sizeof(V) * N, cudaMemcpyHostToDevice));
+    // and the two phase tables of the four-step split N = N1 * N2 (see fft_core.cuh)
+    constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+    std::vector<V> htw(3 * N);
+    auto w = [](int t) {
+      const double ang = 2.0 * M_PI * (double)(t % N) / (double)N;
+      V r;
+      r.x = (T)cos(ang);
+      r.y = (T)(-sin(ang));
+      return r;
+    };
+    for (int t = 0; t < N; ++t) htw[t] = w(t);
+    for (int k1 = 0; k1 < N1; ++k1)
+      for (int j2 = 0; j2 < N2; ++j2) htw[N + k1 * N2 + j2] = w(j2 * k1);
+    for (int m1 = 0; m1 < N2; ++m1)
+      for (int k1 = 0; k1 < N1; ++k1) htw[2 * N + m1 * N1 + k1] = w(k1 * m1);
+    if (cudaMalloc(&tw, sizeof(V) * 3 * N) != cudaSuccess) return DGP_E_NOMEM;
+    DGP_CUDA(cudaMemcpy(tw, htw.data(), sizeof(V) * 3 * N, cudaMemcpyHostToDevice));
     DGP_CUDA(cudaMemset(d_rstats, 0, sizeof(double) * 12));
     return DGP_OK;
   }
@@ -310,6 +326,13 @@ class Engine : public EngineBase {
     kp.eta = c.eta; kp.alpha = c.alpha; kp.beta = c.beta; kp.s = c.s; kp.c2 = c.c2; kp.c3 = c.c3;
     kp.aE = c.a * c.E; kp.q = c.q; kp.rc_H0 = p.rc_H0; kp.a = c.a;
     kp.gravity = p.gravity;
+    const double kf = 2.0 * M_PI / p.box;
+    kp.kf_f = (float)kf;
+    kp.inv_m_f = (float)kp.inv_m;
+    kp.kbkf_f = (float)(kp.kbar_fac * kf);
+    kp.s_f = (float)c.s; kp.beta_f = (float)c.beta; kp.alpha_f = (float)c.alpha; kp.c2_f = (float)c.c2;
+    kp.c3_f = (float)c.c3; kp.inv_eta_f = (float)(1.0 / c.eta); kp.half_inv_eta_f = (float)(0.5 / c.eta);
+    kp.om15_f = (float)(1.5 * (c.eta - 1.0) / c.eta); kp.aE2_f = (float)(kp.aE * kp.aE);
     return kp;
   }
 
@@ -369,6 +392,7 @@ class Engine : public EngineBase {
     if ((rc = forward_zy(src, sDelta, pro))) return rc;
     dgp_solve_info inf;
     memset(&inf, 0, sizeof(inf));
+    V* sDphi = sD;  // spectrum of the accepted D for the phi operation
     int accepted = -1;
     int status = DGP_OK;
 
@@ -391,39 +415,43 @@ class Engine : public EngineBase {
       const double rnorm = eps > 0.0 ? eps : 1.0;
       inf.eps = eps;
 
-      const RelaxParams rp{c.alpha, p.w, c.c2, 1.0 / (double)M};
-      int cur = j0, best = -1, best_it = -1, spec_of = -1;
+      RelaxParams rp;
+      rp.alpha = c.alpha; rp.w = p.w; rp.c2 = c.c2; rp.inv_m = 1.0 / (double)M;
+      auto split = [](double v, float& hi, float& lo) { hi = (float)v; lo = (float)(v - (double)hi); };
+      split(c.alpha, rp.alpha_hi, rp.alpha_lo);
+      split(c.c2, rp.c2_hi, rp.c2_lo);
+      split(4.0 * (1.0 - p.w), rp.four_omw_hi, rp.four_omw_lo);
+      rp.omw = (float)(1.0 - p.w);
+      rp.two_omw = (float)(2.0 * (1.0 - p.w));
+      rp.alpha_f = (float)c.alpha;
+      rp.bad_bp_f = (float)(-c.alpha * c.alpha / (4.0 * (1.0 - p.w)));
+      history.clear();
+      const int arith = p.precision == DGP_FP32 ? ARITH_F32 : (p.precision == DGP_MIXED_EFT ? ARITH_EFT : ARITH_F64);
+      int cur = j0, best = -1, best_it = -1;
       double rbest = INFINITY, rprev = INFINITY, prev_nbad = 0.0, last_bad = 0.0;
       bool converged = false;
+      // sDc holds the z- and y-transformed current iterate; the fused pass writes
+      // the z-transformed next iterate into sDn.
+      V* sDc = sD;
+      V* sDn = sD2;
+      if ((rc = forward_zy(rD[cur], sDc, ZPrologue{nullptr, 0.0, 0}))) return rc;
       for (int it = 0; it <= p.max_iter; ++it) {
-        if ((rc = forward_zy(rD[cur], sD, ZPrologue{nullptr, 0.0, 0}))) return rc;
-        spec_of = cur;
         prof.run(KK_X_HESSIAN, 7 * SB, stream, [&] {
-          launch_fft_x_op<T, N>(XOP_HESSIAN, sD, nullptr, fs(s6, 6), 0, kp, nullptr, 0, 0, 0, tw, stream);
+          launch_fft_x_op<T, N>(XOP_HESSIAN, sDc, nullptr, fs(s6, 6), 0, kp, nullptr, 0, 0, 0, tw, stream);
         });
-        if ((rc = inverse_yz(s6, rH, 6))) return rc;
+        prof.run(KK_Y, 12 * SB, stream, [&] { launch_fft_y<T, N>(fs(s6, 6), 6, true, tw, stream); });
         int nxt = 0;
         while (nxt == cur || nxt == best) ++nxt;
-        const T* H6[6] = {rH[0], rH[1], rH[2], rH[3], rH[4], rH[5]};
-        // arithmetic of R, B' and Delta: FP64 in the mixed and FP64 paths, FP32 in the plain FP32 path
-        prof.run(KK_RELAX, 9 * RB, stream, [&] {
-          if constexpr (sizeof(T) == 8) {
-            launch_relax<T, double>(rD[cur], d_rstats + 4 * cur + 1, H6, rS, rD[nxt], M, rp, partials, nblocks,
-                                    stream);
-          } else {
-            if (p.precision == DGP_MIXED)
-              launch_relax<T, double>(rD[cur], d_rstats + 4 * cur + 1, H6, rS, rD[nxt], M, rp, partials, nblocks,
-                                      stream);
-            else
-              launch_relax<T, float>(rD[cur], d_rstats + 4 * cur + 1, H6, rS, rD[nxt], M, rp, partials, nblocks,
-                                     stream);
-          }
+        prof.run(KK_RELAX, 7 * SB + 3 * RB, stream, [&] {
+          launch_fused_relax<T, N>(arith, s6, rD[cur], d_rstats + 4 * cur + 1, rS, rD[nxt], sDn, rp, partials,
+                                   tw, stream);
         });
-        prof.run(KK_REDUCE, 32.0 * nblocks, stream,
-                 [&] { launch_finalize(partials, nblocks, 4, d_rstats + 4 * nxt, stream); });
+        prof.run(KK_REDUCE, 32.0 * fblocks, stream,
+                 [&] { launch_finalize(partials, fblocks, 4, d_rstats + 4 * nxt, stream); });
         DGP_CHECK_LAUNCH();
         if ((rc = fetch(d_rstats + 4 * nxt, 4))) return rc;
         const double r = h_stats[0] / (double)M / rnorm;
+        history.push_back(r);
         const double nbad = h_stats[2];
         last_bad = nbad;
         if (h_stats[3] > 0.0 || !isfinite(r)) return DGP_E_NONFINITE;
@@ -434,8 +462,16 @@ class Engine : public EngineBase {
         if (it - best_it >= 10) break;
         rprev = r;
         prev_nbad = nbad;
+        prof.run(KK_Y, 2 * SB, stream, [&] {
+          V* o[1] = {sDn};
+          launch_fft_y<T, N>(fs(o, 1), 1, false, tw, stream);
+        });
+        V* t = sDc; sDc = sDn; sDn = t;
         cur = nxt;
       }
+      // sDc holds the spectrum of rD[cur]; the accepted iterate may be an earlier one
+      if (best != cur && (rc = forward_zy(rD[best], sDc, ZPrologue{nullptr, 0.0, 0}))) return rc;
+      sDphi = sDc;
       accepted = best;
       inf.iters = best_it;
       inf.norm_res = rbest;
@@ -444,7 +480,6 @@ class Engine : public EngineBase {
       status = converged ? DGP_OK : DGP_E_NOT_CONVERGED;
       inf.status = status;
       wcur = accepted;
-      if (spec_of != accepted && (rc = forward_zy(rD[accepted], sD, ZPrologue{nullptr, 0.0, 0}))) return rc;
     }
 
     // phi and forces (Eq. FullDGP1; g = -grad phi)
@@ -455,7 +490,7 @@ class Engine : public EngineBase {
     if (mask) {
       const int nin = p.gravity == DGP_GRAVITY_NL ? 2 : 1;
       prof.run(KK_X_OTHER, SB * (nin + __builtin_popcount(mask)), stream, [&] {
-        launch_fft_x_op<T, N>(XOP_PHI_FORCE, sDelta, sD, fs(outs, 4), mask, kp, nullptr, 0, 0, 0, tw, stream);
+        launch_fft_x_op<T, N>(XOP_PHI_FORCE, sDelta, sDphi, fs(outs, 4), mask, kp, nullptr, 0, 0, 0, tw, stream);
       });
       V* sp[4];
       T* rp_[4];
@@ -483,6 +518,8 @@ class Engine : public EngineBase {
     cp.inv_d_hi = (float)inv;
     cp.inv_d_lo = (float)(inv - (double)cp.inv_d_hi);
     cp.box = p.box;
+    cp.box_f = (float)p.box;
+    cp.inv_box_f = (float)(1.0 / p.box);
     return cp;
   }
 
@@ -704,7 +741,7 @@ int dgp_init(dgp_ctx** out, const dgp_params* p, const dgp_cosmology* cosmo, voi
   if (!(p->box > 0) || !(p->rc_H0 > 0) || !(p->w >= 0 && p->w < 1) || p->max_iter < 0 || !(p->tol >= 0) ||
       !isfinite(p->tol))
     return DGP_E_INVALID;
-  if (p->precision < DGP_FP32 || p->precision > DGP_FP64) return DGP_E_INVALID;
+  if (p->precision < DGP_FP32 || p->precision > DGP_MIXED_EFT) return DGP_E_INVALID;
   if (p->gravity < DGP_GRAVITY_NL || p->gravity > DGP_GRAVITY_GRH) return DGP_E_INVALID;
   if (!(cosmo->omega_m0 > 0) || !(cosmo->c_over_H0 > 0)) return DGP_E_INVALID;
   dgp::EngineBase* e = p->precision == DGP_FP64 ? dgp::make_engine<double>(n) : dgp::make_engine<float>(n);
@@ -753,6 +790,14 @@ int dgp_solve_forces(dgp_ctx* c, double a, const void* delta, void* phi, void* g
 int dgp_get_solution(dgp_ctx* c, void* D) {
   if (!c) return DGP_E_INVALID;
   return c->eng->get_solution(D);
+}
+
+int dgp_solve_history(dgp_ctx* c, double* out, int max_n) {
+  if (!c || max_n < 0 || (max_n > 0 && !out)) return -DGP_E_INVALID;
+  const std::vector<double>& h = c->eng->history;
+  const int n = (int)h.size();
+  for (int i = 0; i < n && i < max_n; ++i) out[i] = h[i];
+  return n;
 }
 
 int dgp_profile(dgp_ctx* c, int timing) {

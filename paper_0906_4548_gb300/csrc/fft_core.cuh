@@ -68,10 +68,15 @@ __device__ __forceinline__ void conj_regs(V (&v)[R]) {
   for (int i = 0; i < R; ++i) v[i].y = -v[i].y;
 }
 
-// Copy the twiddle table of length N from global to shared memory.
+// Twiddle tables, 3N entries: [0, N) W_N^t; [N, 2N) the forward phase table
+// A[k1 * N2 + j2] = W_N^{j2 k1}; [2N, 3N) the transposed phase table
+// B[m1 * N1 + k1] = W_N^{k1 m1}.  With A and B, the lane-dependent twiddle of
+// the four-step split is read at consecutive addresses by consecutive lanes.
+constexpr int kTwiddleTables = 3;
+
 template <typename V>
 __device__ __forceinline__ void load_twiddles(V* __restrict__ s_tw, const V* __restrict__ g_tw, int n) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s_tw[i] = g_tw[i];
+  for (int i = threadIdx.x; i < kTwiddleTables * n; i += blockDim.x) s_tw[i] = g_tw[i];
 }
 
 }  // namespace dgp

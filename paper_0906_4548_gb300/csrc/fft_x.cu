@@ -32,6 +32,8 @@ template <typename T, int N> struct XGeom {
   static constexpr int TYW = sizeof(T) == 4 ? 16 : 8;
   static constexpr int TY = TYW < N ? TYW : N;
   static constexpr int THREADS = TY * N1;
+  // at least two CTAs per SM so one CTA's transposes overlap another's loads
+  static constexpr int MIN_BLOCKS = THREADS <= 256 ? 2 : 1;
 };
 
 template <typename T> struct XArgs {
@@ -59,7 +61,7 @@ __device__ __forceinline__ void x_forward(const vec2_t<T>* __restrict__ in, int 
     dft_regs<N1, N / N1>(v, s_tw);
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1)
-      s_T[(k1 * N2 + lane) * TY + yl] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[lane * k1]);
+      s_T[(k1 * N2 + lane) * TY + yl] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[N + k1 * N2 + lane]);
   }
   __syncthreads();
 #pragma unroll
@@ -77,7 +79,7 @@ __device__ __forceinline__ void x_inverse(vec2_t<T> (&Y)[Split<N>::N2], vec2_t<T
   dft_regs<N2, N / N2>(Y, s_tw);
 #pragma unroll
   for (int m1 = 0; m1 < N2; ++m1)
-    s_T[(m1 * N1 + lane) * TY + yl] = (m1 == 0) ? Y[m1] : cmul(Y[m1], s_tw[lane * m1]);
+    s_T[(m1 * N1 + lane) * TY + yl] = (m1 == 0) ? Y[m1] : cmul(Y[m1], s_tw[2 * N + m1 * N1 + lane]);
   __syncthreads();
   if (lane < N2) {
     V w[N1];
@@ -91,6 +93,12 @@ __device__ __forceinline__ void x_inverse(vec2_t<T> (&Y)[Split<N>::N2], vec2_t<T
   __syncthreads();
 }
 
+// A coefficient in the element type: the host-rounded float for FP32 data, the double otherwise.
+template <typename T> __device__ __forceinline__ T kc(double d, float f) {
+  if constexpr (sizeof(T) == 8) return d;
+  else return f;
+}
+
 // G_eff / G of Eq. Geff at |k| (h/Mpc).
 __device__ __forceinline__ double geff_dev(const KParams& kp, double kmag) {
   const double eta = kp.eta, q = kp.q;
@@ -101,14 +109,18 @@ __device__ __forceinline__ double geff_dev(const KParams& kp, double kmag) {
 }
 
 template <typename T, int N, int OP>
-__global__ void __launch_bounds__(XGeom<T, N>::THREADS)
+__global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
     k_fft_x(const __grid_constant__ XArgs<T> args, const vec2_t<T>* __restrict__ g_tw) {
   using V = vec2_t<T>;
   constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, TY = XGeom<T, N>::TY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* s_tw = reinterpret_cast<V*>(smem_raw);
-  V* s_T = s_tw + N;  // N * TY
-  double* s_bins = reinterpret_cast<double*>(s_T + N * TY);
+  V* s_T = s_tw + kTwiddleTables * N;  // N * TY
+  // per-thread 1/|n|^2 and 1/kbar for each of the N2 register slots, kept in
+  // shared memory so the output loop does not hold 2 * N2 extra registers
+  T* s_inv = reinterpret_cast<T*>(s_T + N * TY);               // N2 * THREADS
+  T* s_ikb = s_inv + N2 * XGeom<T, N>::THREADS;                // N2 * THREADS
+  double* s_bins = reinterpret_cast<double*>(s_ikb + N2 * XGeom<T, N>::THREADS);
   load_twiddles(s_tw, g_tw, N);
   if (OP == XOP_PK)
     for (int i = threadIdx.x; i < 3 * args.nbins; i += blockDim.x) s_bins[i] = 0.0;
@@ -121,7 +133,7 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS)
   const int ny = signed_index(ky, N);
   const bool nyq_y = ky == N / 2, nyq_z = kz == N / 2;
   const KParams& kp = args.kp;
-  const T kf = (T)(2.0 * M_PI / kp.box);
+  const T kf = kc<T>(2.0 * M_PI / kp.box, kp.kf_f);
   __syncthreads();
 
   V X0[N2], X1[N2];
@@ -152,12 +164,26 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS)
     return;
   }
 
+  constexpr int NT = XGeom<T, N>::THREADS;
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) {
+    const int nx = signed_index(lane + N1 * k2, N);
+    const int n2 = nx * nx + ny * ny + nz * nz;
+    T inv = (T)0, ikb = (T)0;
+    if (n2 != 0) {
+      inv = (T)1 / (T)n2;
+      if (!kp.local_only) ikb = (T)1 / (kc<T>(kp.kbar_fac * 2.0 * M_PI / kp.box, kp.kbkf_f) * sqrt((T)n2));
+    }
+    s_inv[k2 * NT + threadIdx.x] = inv;
+    s_ikb[k2 * NT + threadIdx.x] = ikb;
+  }
+
   int nout;
   if (OP == XOP_HESSIAN) nout = 6;
   else if (OP == XOP_SOURCE) nout = 1;
   else if (OP == XOP_SOURCE_LIN || OP == XOP_SHELL) nout = 2;
   else nout = 4;
-  const T inv_m = (T)kp.inv_m;
+  const T inv_m = kc<T>(kp.inv_m, kp.inv_m_f);
   for (int o = 0; o < nout; ++o) {
     if (OP == XOP_PHI_FORCE && !((args.nout_mask >> o) & 1)) continue;
     V Y[N2];
@@ -169,10 +195,9 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS)
       const int n2 = nx * nx + ny * ny + nz * nz;
       V r = cmake<V>((T)0, (T)0);
       if (n2 != 0) {
-        const T inv_n2 = (T)1 / (T)n2;
-        const T nmag = sqrt((T)n2);
+        const T inv_n2 = s_inv[k2 * NT + threadIdx.x];
         // 1 / kbar = 1 / (kbar_fac * kf * |n|)
-        const T ikb = kp.local_only ? (T)0 : (T)1 / ((T)kp.kbar_fac * kf * nmag);
+        const T ikb = s_ikb[k2 * NT + threadIdx.x];
         if (OP == XOP_HESSIAN) {
           T m;
           switch (o) {
@@ -185,27 +210,27 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS)
           }
           r = cscale(X0[k2], m * inv_m);
         } else if (OP == XOP_SOURCE || OP == XOP_SOURCE_LIN) {
-          const T sfac = (T)kp.s * ((T)1 - (T)kp.beta * ikb) * inv_m;
+          const T sfac = kc<T>(kp.s, kp.s_f) * ((T)1 - kc<T>(kp.beta, kp.beta_f) * ikb) * inv_m;
           r = cscale(X0[k2], sfac);
-          if (o == 1) r = cscale(r, (T)1 / ((T)kp.alpha - (T)kp.c2 * ikb));
+          if (o == 1) r = cscale(r, (T)1 / (kc<T>(kp.alpha, kp.alpha_f) - kc<T>(kp.c2, kp.c2_f) * ikb));
         } else if (OP == XOP_SHELL) {
           const double nm = sqrt((double)n2);
           if (nm > args.shell_lo && nm < args.shell_hi)
             r = (o == 0) ? cscale(X0[k2], inv_m) : cmake<V>(inv_m, (T)0);
         } else {  // XOP_PHI_FORCE
-          const T kmag = kf * nmag;
-          const T pref = -(T)(kp.aE * kp.aE) / (kmag * kmag);
-          const T om = (T)((kp.eta - 1.0) / kp.eta);
+          const T kmag = kf * sqrt((T)n2);
+          const T pref = -kc<T>(kp.aE * kp.aE, kp.aE2_f) / (kmag * kmag);
+          const T om15 = kc<T>(1.5 * (kp.eta - 1.0) / kp.eta, kp.om15_f);
           V phi;
           if (kp.gravity == 0) {
-            const T cd = (T)(-1.0 / (2.0 * kp.eta)) + (T)kp.c3 * ikb;
-            const T den = (T)1 + ikb / (T)kp.eta;
-            const V rhs = cadd(cscale(X0[k2], (T)1.5 * om), cscale(X1[k2], cd));
+            const T cd = -kc<T>(0.5 / kp.eta, kp.half_inv_eta_f) + kc<T>(kp.c3, kp.c3_f) * ikb;
+            const T den = (T)1 + ikb * kc<T>(1.0 / kp.eta, kp.inv_eta_f);
+            const V rhs = cadd(cscale(X0[k2], om15), cscale(X1[k2], cd));
             phi = cscale(rhs, pref / den);
           } else if (kp.gravity == 1) {
-            phi = cscale(X0[k2], pref * (T)1.5 * om * (T)geff_dev(kp, (double)kmag));
+            phi = cscale(X0[k2], pref * om15 * (T)geff_dev(kp, (double)kmag));
           } else {
-            phi = cscale(X0[k2], pref * (T)1.5 * om);
+            phi = cscale(X0[k2], pref * om15);
           }
           phi = cscale(phi, inv_m);
           if (o == 0) {
@@ -230,7 +255,8 @@ template <typename T, int N> int x_pass_blocks() { return (N / XGeom<T, N>::TY) 
 template <typename T, int N, int OP>
 static void launch_x(const XArgs<T>& a, const vec2_t<T>* tw, cudaStream_t s) {
   using G = XGeom<T, N>;
-  const size_t smem = sizeof(vec2_t<T>) * (N + (size_t)N * G::TY) + (OP == XOP_PK ? sizeof(double) * 3 * a.nbins : 0);
+  const size_t smem = sizeof(vec2_t<T>) * (kTwiddleTables * N + (size_t)N * G::TY) +
+                      sizeof(T) * 2 * Split<N>::N2 * G::THREADS + (OP == XOP_PK ? sizeof(double) * 3 * a.nbins : 0);
   cudaFuncSetAttribute(k_fft_x<T, N, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid(N / G::TY, N / 2 + 1);
   k_fft_x<T, N, OP><<<grid, G::THREADS, smem, s>>>(a, tw);

@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(256) k_fft_y(const __grid_constant__ FieldSet<
   constexpr int P = 256 / N1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* s_tw = reinterpret_cast<V*>(smem_raw);
-  V* s_T = s_tw + N;
+  V* s_T = s_tw + kTwiddleTables * N;
   load_twiddles(s_tw, g_tw, N);
   const int lane = threadIdx.x % N1;
   const int pl = threadIdx.x / N1;
@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(256) k_fft_y(const __grid_constant__ FieldSet<
     dft_regs<N1, N / N1>(v, s_tw);
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1)
-      Tp[k1 * (N2 + 1) + lane] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[lane * k1]);
+      Tp[k1 * (N2 + 1) + lane] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[N + k1 * N2 + lane]);
   }
   __syncthreads();
   if (active) {
@@ -57,7 +57,7 @@ void launch_fft_y(const FieldSet<T>& f, int nfields, bool inverse, const vec2_t<
   constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
   constexpr int P = 256 / N1;
   const int64_t npencils = (int64_t)(N / 2 + 1) * N;
-  const size_t smem = sizeof(V) * (N + P * N1 * (N2 + 1));
+  const size_t smem = sizeof(V) * (kTwiddleTables * N + P * N1 * (N2 + 1));
   dim3 grid((unsigned)((npencils + P - 1) / P), (unsigned)nfields);
   if (inverse) {
     cudaFuncSetAttribute(k_fft_y<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -21,11 +21,21 @@ template <typename T, int N> struct ZGeom {
   static constexpr int THREADS = P * N1;
 };
 
+// Prologue as v * scale + shift, the two coefficients formed once per CTA:
+// kind 1 (rho -> rho / mean - 1): scale = 1 / mean, shift = -1;
+// kind 2 (v - mean): scale = 1, shift = -mean.
 template <typename T>
-__device__ __forceinline__ T apply_prologue(T v, const ZPrologue& pro, double mean) {
-  if (pro.kind == 1) return (T)((double)v / mean - 1.0);
-  if (pro.kind == 2) return (T)((double)v - mean);
-  return v;
+__device__ __forceinline__ void prologue_coeffs(const ZPrologue& pro, T* s_ss) {
+  if (threadIdx.x == 0) {
+    T sc = (T)1, sh = (T)0;
+    if (pro.kind != 0) {
+      const double mean = pro.mean_src[0] * pro.inv_count;
+      if (pro.kind == 1) { sc = (T)(1.0 / mean); sh = (T)-1; }
+      else sh = (T)(-mean);
+    }
+    s_ss[0] = sc;
+    s_ss[1] = sh;
+  }
 }
 
 template <typename T, int N>
@@ -37,7 +47,7 @@ k_fft_z_r2c(const T* __restrict__ in, int64_t in_stride, vec2_t<T>* __restrict__
   constexpr int N1 = G::N1, N2 = G::N2, TY = G::TY, P = G::P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* s_tw = reinterpret_cast<V*>(smem_raw);
-  V* s_T = s_tw + N;                        // P * N1 * (N2 + 1)
+  V* s_T = s_tw + kTwiddleTables * N;                        // P * N1 * (N2 + 1)
   V* s_Z = s_T + P * N1 * (N2 + 1);         // N * (P + 1)
   load_twiddles(s_tw, g_tw, N);
   const int lane = threadIdx.x % N1;
@@ -46,23 +56,24 @@ k_fft_z_r2c(const T* __restrict__ in, int64_t in_stride, vec2_t<T>* __restrict__
   const int y0 = blockIdx.x * TY;
   const T* src = in + (int64_t)blockIdx.z * in_stride;
   V* dst = out + (int64_t)blockIdx.z * out_stride;
-  double mean = 0.0;
-  if (pro.kind != 0) mean = pro.mean_src[0] * pro.inv_count;
+  __shared__ T s_ss[2];
+  prologue_coeffs<T>(pro, s_ss);
   const T* rowa = src + ((int64_t)x * N + y0 + 2 * pl) * N;
   const T* rowb = rowa + N;
   V* Tp = s_T + pl * (N1 * (N2 + 1));
   __syncthreads();
+  const T sc = s_ss[0], sh = s_ss[1];
   if (lane < N2) {
     V v[N1];
 #pragma unroll
     for (int j1 = 0; j1 < N1; ++j1) {
-      v[j1].x = apply_prologue(rowa[N2 * j1 + lane], pro, mean);
-      v[j1].y = apply_prologue(rowb[N2 * j1 + lane], pro, mean);
+      v[j1].x = rowa[N2 * j1 + lane] * sc + sh;
+      v[j1].y = rowb[N2 * j1 + lane] * sc + sh;
     }
     dft_regs<N1, N / N1>(v, s_tw);
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1)
-      Tp[k1 * (N2 + 1) + lane] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[lane * k1]);
+      Tp[k1 * (N2 + 1) + lane] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[N + k1 * N2 + lane]);
   }
   __syncthreads();
   {
@@ -100,7 +111,7 @@ k_fft_z_c2r(const __grid_constant__ FieldSet<T> in, const __grid_constant__ Fiel
   constexpr int BUF = HSZ > TSZ ? HSZ : TSZ;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* s_tw = reinterpret_cast<V*>(smem_raw);
-  V* s_H = s_tw + N;        // NK * (TY + 1); later reused as s_T
+  V* s_H = s_tw + kTwiddleTables * N;        // NK * (TY + 1); later reused as s_T
   V* s_T = s_H;
   V* s_Z = s_H + BUF;       // N * (P + 1)
   load_twiddles(s_tw, g_tw, N);
@@ -138,7 +149,7 @@ k_fft_z_c2r(const __grid_constant__ FieldSet<T> in, const __grid_constant__ Fiel
     dft_regs<N1, N / N1>(v, s_tw);
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1)
-      Tp[k1 * (N2 + 1) + lane] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[lane * k1]);
+      Tp[k1 * (N2 + 1) + lane] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[N + k1 * N2 + lane]);
   }
   __syncthreads();
   {
@@ -158,12 +169,12 @@ k_fft_z_c2r(const __grid_constant__ FieldSet<T> in, const __grid_constant__ Fiel
 
 template <typename T, int N> static size_t r2c_smem() {
   using G = ZGeom<T, N>;
-  return sizeof(vec2_t<T>) * (N + G::P * G::N1 * (G::N2 + 1) + N * (G::P + 1));
+  return sizeof(vec2_t<T>) * (kTwiddleTables * N + G::P * G::N1 * (G::N2 + 1) + N * (G::P + 1));
 }
 template <typename T, int N> static size_t c2r_smem() {
   using G = ZGeom<T, N>;
   const size_t hsz = (size_t)(N / 2 + 1) * (G::TY + 1), tsz = (size_t)G::P * G::N1 * (G::N2 + 1);
-  return sizeof(vec2_t<T>) * (N + (hsz > tsz ? hsz : tsz) + (size_t)N * (G::P + 1));
+  return sizeof(vec2_t<T>) * (kTwiddleTables * N + (hsz > tsz ? hsz : tsz) + (size_t)N * (G::P + 1));
 }
 
 template <typename T, int N>

@@ -1,0 +1,450 @@
+// Fused z pass of one relaxation iteration (Secs. III.B-C).
+//
+// A CTA owns TY consecutive rows (x, y0..y0+TY-1) of the mesh.  It
+//   1. inverse-transforms along z the six y-inverted spectra H_xx, H_yy, H_xy,
+//      H_xz, H_yz, N of those rows, two fields of the same row packed into one
+//      complex pencil (A + i B: three transforms per row), and folds them into
+//      per-point accumulators held in registers:
+//        q = H_xy^2 + H_xz^2 + H_yz^2 + a^2 + a b + b^2 - (a + b) d,
+//      (a = H_xx, b = H_yy, d the mean-free D; this is
+//      sum_{i<j} (H_ij^2 - H_ii H_jj) with H_zz = d - a - b eliminated), then
+//        R = alpha d - 2 q + c2 N - S                    (Eq. FullDGP2, LHS - RHS)
+//        B' = (1 - w) d^2 + alpha d - R                  (Eq. Bwpara)
+//        Delta = alpha^2 + 4 (1 - w) B', bad points take Delta = 0 (Sec. III.C)
+//        D_new = 2 B' / (alpha + sqrt(Delta))            (Eq. nabla^2Cwpara, '+' root)
+//   2. writes D_new and forward-transforms it along z into the transposed half
+//      spectrum, ready for the next iteration's y pass;
+//   3. emits FP64 block partials of sum |R|, sum D_new, bad points, non-finite R.
+// The six real Hessian fields, D_new's re-read and two launches never exist.
+//
+// B' and Delta are formed with the identities
+//        B' = d ((1 - w) d + alpha) - R,  Delta = (alpha + 2 (1 - w) d)^2 - 4 (1 - w) R,
+// so Delta has no cancellation except where it is genuinely near zero.
+// Arithmetic of q, R, B' and Delta (policy AR): FP32; pairs of floats with
+// error-free transformations (Knuth TwoSum, FMA TwoProd; about 48 bits); or FP64.
+// The six spectra arrive as three field pairs; the next pair's tile is copied
+// to shared memory with cp.async while the current pair is transformed.
+#include <math.h>
+
+#include "fft_core.cuh"
+#include "kernels.cuh"
+
+namespace dgp {
+
+// ---------------------------------------------------------------- arithmetic
+struct FP {
+  float hi, lo;
+};
+__device__ __forceinline__ FP fp_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return FP{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ FP fp_fast(float a, float b) {
+  const float s = a + b;
+  return FP{s, b - (s - a)};
+}
+__device__ __forceinline__ FP fp_prod(float a, float b) {
+  const float p = a * b;
+  return FP{p, fmaf(a, b, -p)};
+}
+// unnormalised accumulation: s.hi carries the running sum, s.lo the errors
+__device__ __forceinline__ void fp_acc(FP& s, FP t) {
+  const FP u = fp_two_sum(s.hi, t.hi);
+  s.hi = u.hi;
+  s.lo += u.lo + t.lo;
+}
+
+// Arithmetic policies.  d is the mean-free D at a point; q accumulates
+// sum_{i<j} (H_ij^2 - H_ii H_jj); R, B', Delta as in the file header.
+struct ArF32 {
+  using Acc = float;
+  __device__ static Acc d_of(float D, float m_hi, float, double) { return D - m_hi; }
+  __device__ static void q_init(Acc& q) { q = 0.f; }
+  __device__ static void q_add_sq(Acc& q, float x, float y) { q = fmaf(x, y, q); }
+  __device__ static void q_sub_d(Acc& q, Acc d, float x) { q = fmaf(-x, d, q); }
+  __device__ static Acc residual(Acc q, Acc d, float n, float s, const RelaxParams& rp) {
+    return fmaf(rp.alpha_hi, d, fmaf(rp.c2_hi, n, -s)) - 2.f * q;
+  }
+  __device__ static float bprime(Acc d, Acc R, const RelaxParams& rp) {
+    return d * fmaf(rp.omw, d, rp.alpha_hi) - R;
+  }
+  __device__ static float disc(Acc d, Acc R, const RelaxParams& rp, bool& neg) {
+    const float s = fmaf(rp.two_omw, d, rp.alpha_hi);
+    const float v = fmaf(s, s, -rp.four_omw_hi * R);
+    neg = v < 0.f;
+    return v;
+  }
+  __device__ static float to_f(Acc x) { return x; }
+  __device__ static void acc_abs(Acc& a, Acc x) { a += fabsf(x); }
+  __device__ static double to_d(Acc x) { return (double)x; }
+};
+
+struct ArEFT {
+  using Acc = FP;
+  __device__ static Acc d_of(float D, float m_hi, float m_lo, double) {
+    FP s = fp_two_sum(D, -m_hi);
+    s.lo -= m_lo;
+    return fp_fast(s.hi, s.lo);
+  }
+  __device__ static void q_init(Acc& q) { q = FP{0.f, 0.f}; }
+  __device__ static void q_add_sq(Acc& q, float x, float y) { fp_acc(q, fp_prod(x, y)); }
+  __device__ static void q_sub_d(Acc& q, Acc d, float x) {
+    FP p = fp_prod(-x, d.hi);
+    p.lo = fmaf(-x, d.lo, p.lo);
+    fp_acc(q, p);
+  }
+  __device__ static Acc residual(Acc q, Acc d, float n, float s, const RelaxParams& rp) {
+    FP r{-2.f * q.hi, -2.f * q.lo};
+    FP p = fp_prod(rp.alpha_hi, d.hi);
+    p.lo = fmaf(rp.alpha_hi, d.lo, fmaf(rp.alpha_lo, d.hi, p.lo));
+    fp_acc(r, p);
+    FP c = fp_prod(rp.c2_hi, n);
+    c.lo = fmaf(rp.c2_lo, n, c.lo);
+    fp_acc(r, c);
+    fp_acc(r, FP{-s, 0.f});
+    return fp_fast(r.hi, r.lo);
+  }
+  __device__ static float bprime(Acc d, Acc R, const RelaxParams& rp) {
+    const float u = fmaf(rp.omw, d.hi, rp.alpha_hi);
+    FP b = fp_prod(d.hi, u);
+    b.lo = fmaf(d.lo, u, b.lo);
+    fp_acc(b, FP{-R.hi, -R.lo});
+    return b.hi + b.lo;
+  }
+  __device__ static float disc(Acc d, Acc R, const RelaxParams& rp, bool& neg) {
+    const float s = fmaf(rp.two_omw, d.hi, rp.alpha_hi);
+    FP v = fp_prod(s, s);
+    FP t = fp_prod(-rp.four_omw_hi, R.hi);
+    t.lo = fmaf(-rp.four_omw_hi, R.lo, fmaf(-rp.four_omw_lo, R.hi, t.lo));
+    fp_acc(v, t);
+    v = fp_fast(v.hi, v.lo);
+    neg = v.hi < 0.f || (v.hi == 0.f && v.lo < 0.f);
+    return v.hi + v.lo;
+  }
+  __device__ static float to_f(Acc x) { return x.hi + x.lo; }
+  __device__ static void acc_abs(Acc& a, Acc x) { fp_acc(a, x.hi < 0.f ? FP{-x.hi, -x.lo} : x); }
+  __device__ static double to_d(Acc x) { return (double)x.hi + (double)x.lo; }
+};
+
+struct ArF64 {
+  using Acc = double;
+  __device__ static Acc d_of(double D, float, float, double mean) { return D - mean; }
+  __device__ static void q_init(Acc& q) { q = 0.0; }
+  __device__ static void q_add_sq(Acc& q, double x, double y) { q = fma(x, y, q); }
+  __device__ static void q_sub_d(Acc& q, Acc d, double x) { q = fma(-x, d, q); }
+  __device__ static Acc residual(Acc q, Acc d, double n, double s, const RelaxParams& rp) {
+    return fma(rp.alpha, d, fma(rp.c2, n, -s)) - 2.0 * q;
+  }
+  __device__ static double bprime(Acc d, Acc R, const RelaxParams& rp) {
+    return d * fma(1.0 - rp.w, d, rp.alpha) - R;
+  }
+  __device__ static double disc(Acc d, Acc R, const RelaxParams& rp, bool& neg) {
+    const double s = fma(2.0 * (1.0 - rp.w), d, rp.alpha);
+    const double v = fma(s, s, -4.0 * (1.0 - rp.w) * R);
+    neg = v < 0.0;
+    return v;
+  }
+  __device__ static double to_f(Acc x) { return x; }
+  __device__ static void acc_abs(Acc& a, Acc x) { a += fabs(x); }
+  __device__ static double to_d(Acc x) { return x; }
+};
+
+// ---------------------------------------------------------------- cp.async
+__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int K> __device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory");
+}
+
+// ---------------------------------------------------------------- geometry
+template <typename T, int N> struct FGeom {
+  static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+  static constexpr int TYW = (sizeof(T) == 8 && N >= 512) ? 4 : 16;
+  static constexpr int TY = TYW < N ? TYW : N;          // rows per CTA
+  static constexpr int THREADS = TY * N1;
+  static constexpr int NK = N / 2 + 1;
+  static constexpr int GSZ = 2 * NK * (TY + 1);         // one field pair's half-spectrum tile
+  static constexpr int TSZ = TY * N1 * (N2 + 1);        // four-step transpose
+  static constexpr int P = TY / 2;                       // row pairs in the forward transform
+};
+
+template <typename T> struct FusedArgs {
+  const vec2_t<T>* spec[6];  // y-inverted spectra of H_xx, H_yy, H_xy, H_xz, H_yz, N
+  const T* D;                // current iterate (its mean = dsum / N^3)
+  const double* dsum;
+  const T* S;                // source field
+  T* Dnew;                   // next iterate
+  vec2_t<T>* Snew;           // z-transformed next iterate, layout S[kz][x][y]
+  double* partials;          // [blocks][4]
+  RelaxParams rp;
+};
+
+// Start copying the TY-row tile of spectra A and B into G (layout
+// [field][kz][TY + 1], complex).
+template <typename T, int N>
+__device__ __forceinline__ void issue_pair(const vec2_t<T>* __restrict__ A, const vec2_t<T>* __restrict__ B, int x,
+                                           int y0, vec2_t<T>* G) {
+  using G_ = FGeom<T, N>;
+  constexpr int TY = G_::TY, NK = G_::NK;
+  for (int item = threadIdx.x; item < 2 * NK * TY; item += blockDim.x) {
+    const int f = item / (NK * TY);
+    const int rem = item - f * NK * TY;
+    const int kz = rem / TY, yl = rem % TY;
+    const vec2_t<T>* src = (f == 0 ? A : B) + ((int64_t)kz * N + x) * N + y0 + yl;
+    vec2_t<T>* dst = G + f * NK * (TY + 1) + kz * (TY + 1) + yl;
+    if constexpr (sizeof(T) == 8) cp_async_16(dst, src);
+    else cp_async_8(dst, src);
+  }
+  cp_commit();
+}
+
+// Inverse z transform of the tile in G: per row Z = A + i B rebuilt over all
+// k from the half spectra (imaginary parts of k = 0 and N/2 dropped), read in
+// place by phase 1.  Thread (row, lane) ends with A (ra) and B (rb) of its row
+// at z = lane + N1 k2.
+template <typename T, int N>
+__device__ __forceinline__ void pair_c2r(const vec2_t<T>* G, vec2_t<T>* s_T, const vec2_t<T>* s_tw,
+                                         T (&ra)[Split<N>::N2], T (&rb)[Split<N>::N2]) {
+  using V = vec2_t<T>;
+  using G_ = FGeom<T, N>;
+  constexpr int N1 = G_::N1, N2 = G_::N2, TY = G_::TY, NK = G_::NK;
+  const V* GA = G;
+  const V* GB = G + NK * (TY + 1);
+  const int lane = threadIdx.x % N1, row = threadIdx.x / N1;
+  V* Tp = s_T + row * (N1 * (N2 + 1));
+  if (lane < N2) {
+    V v[N1];
+#pragma unroll
+    for (int j1 = 0; j1 < N1; ++j1) {
+      const int k = N2 * j1 + lane;
+      V A, B;
+      if (k <= N / 2) {
+        A = GA[k * (TY + 1) + row];
+        B = GB[k * (TY + 1) + row];
+        if (k == 0 || k == N / 2) { A.y = 0; B.y = 0; }
+      } else {
+        A = cconj(GA[(N - k) * (TY + 1) + row]);
+        B = cconj(GB[(N - k) * (TY + 1) + row]);
+      }
+      v[j1] = cmake<V>(A.x - B.y, -(A.y + B.x));  // conj(A + i B)
+    }
+    dft_regs<N1, N / N1>(v, s_tw);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1)
+      Tp[k1 * (N2 + 1) + lane] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[N + k1 * N2 + lane]);
+  }
+  __syncthreads();
+  V u[N2];
+#pragma unroll
+  for (int j2 = 0; j2 < N2; ++j2) u[j2] = Tp[lane * (N2 + 1) + j2];
+  dft_regs<N2, N / N2>(u, s_tw);
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) {
+    ra[k2] = u[k2].x;
+    rb[k2] = -u[k2].y;
+  }
+}
+
+template <typename T, int N, class AR>
+__global__ void __launch_bounds__(FGeom<T, N>::THREADS)
+    k_fused_relax(const __grid_constant__ FusedArgs<T> args, const vec2_t<T>* __restrict__ g_tw) {
+  using V = vec2_t<T>;
+  using G_ = FGeom<T, N>;
+  using Acc = typename AR::Acc;
+  constexpr int N1 = G_::N1, N2 = G_::N2, TY = G_::TY, NK = G_::NK, P = G_::P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* s_tw = reinterpret_cast<V*>(smem_raw);
+  V* G0 = s_tw + kTwiddleTables * N;
+  V* G1 = G0 + G_::GSZ;
+  V* s_T = G1 + G_::GSZ;
+  const int x = blockIdx.y, y0 = blockIdx.x * TY;
+  const int lane = threadIdx.x % N1, row = threadIdx.x / N1;
+  const int64_t rbase = ((int64_t)x * N + y0 + row) * N;
+  const RelaxParams& rp = args.rp;
+  // pairs (H_xx, H_yy) -> G0 and (H_xy, H_xz) -> G1 start loading now
+  issue_pair<T, N>(args.spec[0], args.spec[1], x, y0, G0);
+  issue_pair<T, N>(args.spec[2], args.spec[3], x, y0, G1);
+  load_twiddles(s_tw, g_tw, N);
+  // mean of D, split once per CTA into a float pair (no per-point FP64 work)
+  __shared__ double s_mean;
+  __shared__ float s_mpair[2];
+  if (threadIdx.x == 0) {
+    const double m = args.dsum ? args.dsum[0] * rp.inv_m : 0.0;
+    s_mean = m;
+    s_mpair[0] = (float)m;
+    s_mpair[1] = (float)(m - (double)s_mpair[0]);
+  }
+  __syncthreads();
+  const double mean = s_mean;
+  const float m_hi = s_mpair[0], m_lo = s_mpair[1];
+  Acc d[N2], q[N2];
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) {
+    d[k2] = AR::d_of(args.D[rbase + lane + N1 * k2], m_hi, m_lo, mean);
+    AR::q_init(q[k2]);
+  }
+  T ra[N2], rb[N2];
+#pragma unroll 1
+  for (int pr = 0; pr < 3; ++pr) {
+    if (pr < 2) cp_wait<1>();
+    else cp_wait<0>();
+    __syncthreads();  // tile pr visible; s_T free
+    pair_c2r<T, N>((pr & 1) ? G1 : G0, s_T, s_tw, ra, rb);
+    if (pr == 0) issue_pair<T, N>(args.spec[4], args.spec[5], x, y0, G0);  // G0 read by phase 1 already
+    if (pr == 0) {
+      // a = H_xx, b = H_yy:  q = a^2 + a b + b^2 - (a + b) d
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        AR::q_add_sq(q[k2], ra[k2], ra[k2]);
+        AR::q_add_sq(q[k2], ra[k2], rb[k2]);
+        AR::q_add_sq(q[k2], rb[k2], rb[k2]);
+        AR::q_sub_d(q[k2], d[k2], ra[k2]);
+        AR::q_sub_d(q[k2], d[k2], rb[k2]);
+      }
+    } else if (pr == 1) {
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        AR::q_add_sq(q[k2], ra[k2], ra[k2]);
+        AR::q_add_sq(q[k2], rb[k2], rb[k2]);
+      }
+    } else {
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) AR::q_add_sq(q[k2], ra[k2], ra[k2]);
+    }
+  }
+  // residual, update, statistics (rb holds N)
+  T alpha_t, bad_bp;
+  if constexpr (sizeof(T) == 8) {
+    alpha_t = rp.alpha;
+    bad_bp = -rp.alpha * rp.alpha / (4.0 * (1.0 - rp.w));
+  } else {
+    alpha_t = rp.alpha_f;
+    bad_bp = rp.bad_bp_f;
+  }
+  T* s_dn = reinterpret_cast<T*>(G1);  // TY rows of D_new (G1 is free: pair 1 is done)
+  Acc acc_r;
+  AR::q_init(acc_r);
+  // the sum of D_new sets the mean removed next iteration: double for double data
+  T acc_d = (T)0;
+  float nbad = 0.f, nonfin = 0.f;
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) {
+    const int z = lane + N1 * k2;
+    const int64_t idx = rbase + z;
+    const Acc R = AR::residual(q[k2], d[k2], rb[k2], args.S[idx], rp);
+    T bpt = (T)AR::bprime(d[k2], R, rp);
+    bool neg;
+    T dt = (T)AR::disc(d[k2], R, rp, neg);
+    if (neg) {
+      nbad += 1.f;
+      bpt = bad_bp;
+      dt = (T)0;
+    }
+    const T dn = (T)2 * bpt / (alpha_t + sqrt(dt));
+    args.Dnew[idx] = dn;
+    s_dn[row * N + z] = dn;
+    if (isfinite(AR::to_f(R))) AR::acc_abs(acc_r, R);
+    else nonfin += 1.f;
+    acc_d += dn;
+  }
+  __syncthreads();
+  // forward z transform of D_new (two rows per pencil, as fft_z.cu), written transposed
+  V* s_Zf = G0;  // N * (P + 1) complex
+  constexpr int FT = P * N1;
+  const int fl = threadIdx.x % N1, fp = threadIdx.x / N1;
+  V* Tp = s_T + fp * (N1 * (N2 + 1));
+  if (threadIdx.x < FT && fl < N2) {
+    V v[N1];
+#pragma unroll
+    for (int j1 = 0; j1 < N1; ++j1) {
+      v[j1].x = s_dn[(2 * fp) * N + N2 * j1 + fl];
+      v[j1].y = s_dn[(2 * fp + 1) * N + N2 * j1 + fl];
+    }
+    dft_regs<N1, N / N1>(v, s_tw);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1)
+      Tp[k1 * (N2 + 1) + fl] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[N + k1 * N2 + fl]);
+  }
+  __syncthreads();
+  if (threadIdx.x < FT) {
+    V u[N2];
+#pragma unroll
+    for (int j2 = 0; j2 < N2; ++j2) u[j2] = Tp[fl * (N2 + 1) + j2];
+    dft_regs<N2, N / N2>(u, s_tw);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) s_Zf[(fl + N1 * k2) * (P + 1) + fp] = u[k2];
+  }
+  __syncthreads();
+  for (int item = threadIdx.x; item < NK * TY; item += blockDim.x) {
+    const int kz = item / TY, yl = item % TY;
+    const int p = yl >> 1;
+    const V zk = s_Zf[kz * (P + 1) + p];
+    const V zm = s_Zf[((N - kz) & (N - 1)) * (P + 1) + p];
+    V r;
+    if ((yl & 1) == 0) r = cmake<V>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
+    else r = cmake<V>((T)0.5 * (zk.y + zm.y), (T)-0.5 * (zk.x - zm.x));
+    args.Snew[((int64_t)kz * N + x) * N + y0 + yl] = r;
+  }
+  // block statistics (FP64)
+  __shared__ double s_part[4][32];
+  double v4[4] = {AR::to_d(acc_r), (double)acc_d, (double)nbad, (double)nonfin};
+  const int wl = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v4[c] += __shfl_xor_sync(0xffffffffu, v4[c], o);
+    if (wl == 0) s_part[c][wid] = v4[c];
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    const int nw = (blockDim.x + 31) >> 5;
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += s_part[threadIdx.x][w];
+    args.partials[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = t;
+  }
+}
+
+template <typename T, int N> int fused_relax_blocks() { return (N / FGeom<T, N>::TY) * N; }
+
+template <typename T, int N, class AR>
+static void launch_f(const FusedArgs<T>& a, const vec2_t<T>* tw, cudaStream_t s) {
+  using G = FGeom<T, N>;
+  const size_t smem = sizeof(vec2_t<T>) * (kTwiddleTables * N + 2 * G::GSZ + G::TSZ);
+  cudaFuncSetAttribute(k_fused_relax<T, N, AR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid(N / G::TY, N);
+  k_fused_relax<T, N, AR><<<grid, G::THREADS, smem, s>>>(a, tw);
+}
+
+template <typename T, int N>
+void launch_fused_relax(int arith, vec2_t<T>* const* spec6, const T* D, const double* dsum, const T* S, T* Dnew,
+                        vec2_t<T>* Snew, RelaxParams rp, double* partials, const vec2_t<T>* tw, cudaStream_t s) {
+  FusedArgs<T> a;
+  for (int i = 0; i < 6; ++i) a.spec[i] = spec6[i];
+  a.D = D; a.dsum = dsum; a.S = S; a.Dnew = Dnew; a.Snew = Snew; a.partials = partials; a.rp = rp;
+  if constexpr (sizeof(T) == 8) {
+    launch_f<T, N, ArF64>(a, tw, s);
+  } else {
+    if (arith == ARITH_F64) launch_f<T, N, ArF64>(a, tw, s);
+    else if (arith == ARITH_EFT) launch_f<T, N, ArEFT>(a, tw, s);
+    else launch_f<T, N, ArF32>(a, tw, s);
+  }
+}
+
+#define DGP_INST_F(T, N)                                                                                    \
+  template void launch_fused_relax<T, N>(int, vec2_t<T>* const*, const T*, const double*, const T*, T*,       \
+                                         vec2_t<T>*, RelaxParams, double*, const vec2_t<T>*, cudaStream_t); \
+  template int fused_relax_blocks<T, N>();
+#define DGP_INST_F_ALL(T) DGP_INST_F(T, 16) DGP_INST_F(T, 32) DGP_INST_F(T, 64) DGP_INST_F(T, 128) \
+  DGP_INST_F(T, 256) DGP_INST_F(T, 512)
+DGP_INST_F_ALL(float)
+DGP_INST_F_ALL(double)
+
+}  // namespace dgp

@@ -36,6 +36,9 @@ struct KParams {
   // coefficients (Sec. II)
   double eta, alpha, beta, s, c2, c3, aE, q, rc_H0, a;
   int gravity;
+  // the per-mode constants rounded once (FP32 paths read these, never the doubles)
+  float kf_f, kbkf_f, inv_m_f;   // 2 pi / box, kbar_fac * 2 pi / box, 1 / N^3
+  float s_f, beta_f, alpha_f, c2_f, c3_f, inv_eta_f, half_inv_eta_f, om15_f, aE2_f;
 };
 
 enum XOp { XOP_HESSIAN = 0, XOP_SOURCE = 1, XOP_SOURCE_LIN = 2, XOP_PHI_FORCE = 3, XOP_PK = 4,
@@ -64,16 +67,27 @@ void launch_fft_x_op(int op, const vec2_t<T>* in0, const vec2_t<T>* in1, const F
 
 template <typename T, int N> int x_pass_blocks();
 
-// Pointwise kernels (Eqs. nabla^2Cwpara, Bwpara and the residual of FullDGP2).
+// Parameters of the relaxation update (Eqs. nabla^2Cwpara, Bwpara and the
+// residual of FullDGP2).
 struct RelaxParams {
   double alpha, w, c2;
   double inv_m;
+  // the same constants as float pairs (hi + lo), split on the host
+  float alpha_hi, alpha_lo, c2_hi, c2_lo;
+  float omw, two_omw;            // 1 - w, 2 (1 - w) (float; see fused_relax.cu)
+  float four_omw_hi, four_omw_lo;
+  float alpha_f, bad_bp_f;       // alpha and the bad-point B' = -alpha^2 / (4 (1 - w)), rounded once
 };
 
-// D_new = relax(D - mean, H, N, S); per-block FP64 partials of RelaxStats.
-template <typename T, typename A>
-void launch_relax(const T* D, const double* dsum, const T* const* H6, const T* S, T* Dnew,
-                  int64_t m, RelaxParams rp, double* partials, int nblocks, cudaStream_t s);
+// Fused z pass of a relaxation iteration (fused_relax.cu): inverse z transform
+// of the six y-inverted spectra (H_xx, H_yy, H_xy, H_xz, H_yz, N), residual and
+// update, forward z transform of D_new into Snew.  arith selects the
+// arithmetic of q, R, B' and Delta; partials: fused_relax_blocks() x 4 doubles.
+enum { ARITH_F32 = 0, ARITH_EFT = 1, ARITH_F64 = 2 };
+template <typename T, int N>
+void launch_fused_relax(int arith, vec2_t<T>* const* spec6, const T* D, const double* dsum, const T* S, T* Dnew,
+                        vec2_t<T>* Snew, RelaxParams rp, double* partials, const vec2_t<T>* tw, cudaStream_t s);
+template <typename T, int N> int fused_relax_blocks();
 
 // partials[nblocks][ncomp] -> out[ncomp], fixed summation order.
 void launch_finalize(const double* partials, int nblocks, int ncomp, double* out, cudaStream_t s);
@@ -101,6 +115,7 @@ struct CicParams {
   float inv_d_hi, inv_d_lo;  // N / box as an unevaluated float pair
   double inv_d;              // N / box (FP64 path)
   double box;
+  float box_f, inv_box_f;    // box and 1 / box rounded once
 };
 
 template <typename T>

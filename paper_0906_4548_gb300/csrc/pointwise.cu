@@ -49,74 +49,6 @@ __device__ __forceinline__ void block_sum(double (&v)[NC]) {
 }
 
 // --------------------------------------------------------------------------
-// Relaxation update and residual (Secs. III.B-C).
-//
-// With H_zz = D - H_xx - H_yy (the trace of the Hessian spectra is D) and
-// q = sum_{i<j} (H_ij^2 - H_ii H_jj), Eq. FullDGP2 minus its RHS is
-//   R = D^2 + alpha D - sum_ij H_ij^2 + c2 N - S = alpha D - 2 q + c2 N - S,
-// the split source of Eq. Bwpara is
-//   B' = sum H^2 - w D^2 - c2 N + S = (1 - w) D^2 + alpha D - R,
-// the discriminant Delta = alpha^2 + 4 (1 - w) B', and the '+' root of
-// Eq. nabla^2Cwpara in the cancellation-free form D_new = 2 B' / (alpha + sqrt(Delta)).
-// A bad point (Delta < 0) takes Delta = 0, i.e. B' = -alpha^2 / (4 (1 - w)).
-// A is the arithmetic type of R, B' and Delta (double in the mixed path).
-template <typename T, typename A>
-__global__ void __launch_bounds__(256) k_relax(const T* __restrict__ D, const double* __restrict__ dsum,
-                                               const T* __restrict__ Hxx, const T* __restrict__ Hyy,
-                                               const T* __restrict__ Hxy, const T* __restrict__ Hxz,
-                                               const T* __restrict__ Hyz, const T* __restrict__ Nf,
-                                               const T* __restrict__ S, T* __restrict__ Dnew, int64_t m,
-                                               RelaxParams rp, double* __restrict__ partials) {
-  const A mean = dsum ? (A)(dsum[0] * rp.inv_m) : (A)0;
-  const A alpha = (A)rp.alpha, omw = (A)(1.0 - rp.w), c2 = (A)rp.c2;
-  const A alpha2 = alpha * alpha;
-  const A bad_bp = -(A)(rp.alpha * rp.alpha / (4.0 * (1.0 - rp.w)));
-  A acc_r = 0;
-  double acc_d = 0.0, nbad = 0.0, nonfin = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    const A d = (A)D[i] - mean;
-    const A a = (A)Hxx[i], b = (A)Hyy[i];
-    const A c = d - a - b;
-    const A xy = (A)Hxy[i], xz = (A)Hxz[i], yz = (A)Hyz[i];
-    A q = xy * xy + xz * xz + yz * yz - a * b - (a + b) * c;
-    const A R = alpha * d - (A)2 * q + c2 * (A)Nf[i] - (A)S[i];
-    A bp = omw * d * d + alpha * d - R;
-    A disc = alpha2 + (A)4 * omw * bp;
-    if (disc < (A)0) {
-      nbad += 1.0;
-      bp = bad_bp;
-      disc = (A)0;
-    }
-    const T sq = sqrt((T)disc);
-    const T dn = (T)((A)2 * bp) / ((T)alpha + sq);
-    Dnew[i] = dn;
-    if (isfinite((double)R)) acc_r += R < (A)0 ? -R : R;
-    else nonfin += 1.0;
-    acc_d += (double)dn;
-  }
-  double v[4] = {(double)acc_r, acc_d, nbad, nonfin};
-  block_sum<4>(v);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c) partials[(int64_t)blockIdx.x * 4 + c] = v[c];
-  }
-}
-
-template <typename T, typename A>
-void launch_relax(const T* D, const double* dsum, const T* const* H6, const T* S, T* Dnew, int64_t m,
-                  RelaxParams rp, double* partials, int nblocks, cudaStream_t s) {
-  k_relax<T, A><<<nblocks, 256, 0, s>>>(D, dsum, H6[0], H6[1], H6[2], H6[3], H6[4], H6[5], S, Dnew, m, rp,
-                                        partials);
-}
-
-template void launch_relax<float, float>(const float*, const double*, const float* const*, const float*, float*,
-                                         int64_t, RelaxParams, double*, int, cudaStream_t);
-template void launch_relax<float, double>(const float*, const double*, const float* const*, const float*, float*,
-                                          int64_t, RelaxParams, double*, int, cudaStream_t);
-template void launch_relax<double, double>(const double*, const double*, const double* const*, const double*,
-                                           double*, int64_t, RelaxParams, double*, int, cudaStream_t);
-
-// --------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ partials, int nblocks, int ncomp,
                                                   double* __restrict__ out) {
   for (int c = 0; c < ncomp; ++c) {
@@ -294,7 +226,14 @@ __global__ void __launch_bounds__(256) k_gather_kick(T* __restrict__ x, T* __res
                                                      const T* __restrict__ gz, CicParams cp, T kick, T drift,
                                                      int do_drift) {
   const int64_t n = cp.n;
-  const T box = (T)cp.box, inv_box = (T)(1.0 / cp.box);
+  T box, inv_box;
+  if constexpr (sizeof(T) == 8) {
+    box = cp.box;
+    inv_box = 1.0 / cp.box;
+  } else {
+    box = cp.box_f;
+    inv_box = cp.inv_box_f;
+  }
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
     int ix0, ix1, iy0, iy1, iz0, iz1;
     T fx, fy, fz;

@@ -15,12 +15,12 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 
 DGP_OK, DGP_E_INVALID, DGP_E_CUDA, DGP_E_NOMEM, DGP_E_NONFINITE = 0, 1, 2, 3, 4
 DGP_E_NOT_CONVERGED, DGP_E_BAD_POINTS, DGP_E_TIMEOUT, DGP_E_STATE = 5, 6, 7, 8
-DGP_FP32, DGP_MIXED, DGP_FP64 = 0, 1, 2
+DGP_FP32, DGP_MIXED, DGP_FP64, DGP_MIXED_EFT = 0, 1, 2, 3
 DGP_GRAVITY_NL, DGP_GRAVITY_LDGP, DGP_GRAVITY_GRH = 0, 1, 2
 C_OVER_H0 = 2997.92458
 
 EXPORTED = ["dgp_background", "dgp_init", "dgp_destroy", "dgp_strerror", "dgp_reset", "dgp_solve_phi",
-            "dgp_solve_forces", "dgp_get_solution", "dgp_deposit", "pm_step", "pm_step_host", "power_spectrum", "bispectrum",
+            "dgp_solve_forces", "dgp_solve_history", "dgp_get_solution", "dgp_deposit", "pm_step", "pm_step_host", "power_spectrum", "bispectrum",
             "dgp_profile", "dgp_profile_read", "dgp_kernel_name"]
 DGP_KERNEL_KINDS = 10
 
@@ -76,6 +76,7 @@ def _load():
         "dgp_solve_phi": (i, [vp, d, vp, vp, d, P(SolveInfo)]),
         "dgp_solve_forces": (i, [vp, d, vp, vp, vp, vp, vp, d, P(SolveInfo)]),
         "dgp_get_solution": (i, [vp, vp]),
+        "dgp_solve_history": (i, [vp, P(d), i]),
         "dgp_deposit": (i, [vp, P(Particles), vp]),
         "pm_step": (i, [vp, P(Particles), d, d, P(SolveInfo)]),
         "pm_step_host": (i, [vp, P(Particles), d, d, P(SolveInfo)]),
@@ -159,6 +160,15 @@ def dgp_solve_forces(ctx, a, delta, phi, gx, gy, gz, tol):
     st = _check(lib.dgp_solve_forces(ctx, a, _ptr(delta), _ptr(phi), _ptr(gx), _ptr(gy), _ptr(gz), tol,
                                      ctypes.byref(info)), "dgp_solve_forces", (DGP_OK, DGP_E_NOT_CONVERGED))
     return st, info.as_dict()
+
+
+def dgp_solve_history(ctx):
+    n = lib.dgp_solve_history(ctx, None, 0)
+    if n < 0:
+        raise DgpError(-n, "dgp_solve_history")
+    out = np.zeros(n)
+    lib.dgp_solve_history(ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n)
+    return out
 
 
 def dgp_get_solution(ctx, D):

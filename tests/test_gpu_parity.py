@@ -129,6 +129,8 @@ def _solve_both(dgp, torch_dev, n, box, a, prec, tol_gpu, seed=5, w=1 / 3, local
     (64, 200.0, 1.0, 0, 1e-6, 1e-5),
     (16, 50.0, 0.3, 1, 1e-6, 1e-5),
     (128, 200.0, 0.5, 1, 1e-6, 1e-5),
+    (64, 200.0, 0.5, 3, 1e-6, 1e-5),       # mixed, residual by error-free FP32 transformations
+    (128, 200.0, 1.0, 3, 1e-6, 1e-5),
 ])
 def test_solve_phi_and_forces_parity(dgp, torch_dev, n, box, a, prec, tol_gpu, tol_phi):
     got, want = _solve_both(dgp, torch_dev, n, box, a, prec, tol_gpu)
@@ -348,3 +350,28 @@ def test_full_size_deposit_pk_solve(dgp, torch_dev, full_case):
     assert r < max(3e-6, 3 * info["norm_res"])
     phio = ofield.ifft3_real(ofield.phi_spectrum(dk, Dk, grid, coef))
     assert rel_l2(phig, phio) < 1e-5
+
+
+@pytest.mark.parametrize("prec,rtol", [(2, 1e-6), (1, 2e-3), (3, 2e-3), (0, 2e-3)])
+def test_residual_history_follows_oracle(dgp, torch_dev, prec, rtol):
+    """The GPU iterates are the oracle's iterates: the normalised residual of
+    each iterate agrees while it is far above the precision floor."""
+    torch, dev = torch_dev
+    n, box, a = 64, 150.0, 0.4
+    pos, _, _ = zel(n, box, a, -1.5, 0.8, 12)
+    nd = np_dtype(prec, dgp)
+    delta = opm.density_contrast(opm.cic_deposit(pos, n, box)).astype(nd)
+    _, oinfo = ofield.solve_brane_bending(delta.astype(np.float64), a, box, OM, 1.0, tol=1e-12, max_iter=60)
+    ctx = dgp.dgp_init(box, n, 1.0, OM, precision=prec, max_iter=60)
+    try:
+        dd = to_dev(torch_dev, delta, prec_dtype(torch, prec, dgp))
+        dgp.dgp_solve_phi(ctx, a, dd, None, 1e-12 if prec == 2 else 1e-7)
+        hist = dgp.dgp_solve_history(ctx)
+    finally:
+        dgp.dgp_destroy(ctx)
+    ho = np.array(oinfo["history"])
+    floor = 1e-9 if prec == 2 else 1e-5
+    m = min(len(hist), len(ho))
+    sel = ho[:m] > floor
+    assert sel.sum() >= 3
+    assert np.max(np.abs(hist[:m][sel] / ho[:m][sel] - 1)) < rtol

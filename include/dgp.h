@@ -192,6 +192,32 @@ int power_spectrum(dgp_ctx *c, const void *delta, int nbins, double *k, double *
 int bispectrum(dgp_ctx *c, const void *delta, double k1, double k2, int ntheta, const double *theta,
                double dk, double *b, double *q);
 
+/* ---- P(k) for callers that cannot allocate device memory --------------------
+ * The paper has no counterpart to this call.  Some callers cannot call
+ * cudaMalloc: a host framework that reserved the whole device for its own
+ * pooling allocator, or a long-running loop that must not allocate once it has
+ * started.  dgp_init allocates a workspace, so power_spectrum is closed to
+ * them; this variant needs no context and allocates nothing.  It computes the
+ * same estimator as power_spectrum (same kernels, same shells) for an FP32
+ * field of n^3 points, n in {16, 32, 64} (n <= DGP_NOALLOC_MAX_N), using one
+ * file-scope device array of DGP_NOALLOC_SCRATCH_BYTES bytes that every GPU
+ * loading the library holds until the process exits.
+ *   delta:  device n^3 floats, [x][y][z];  box: side in Mpc/h;  1 <= nbins <= n/2;
+ *   k, pk, nmodes: host outputs of length nbins (as power_spectrum);
+ *   cuda_stream: stream for the work (NULL = legacy default); synchronised on return.
+ * The first call on a device, with that device current, resolves the array's
+ * device address and writes the twiddle tables into it (a synchronous copy);
+ * make that first call before any stream capture.  Every call on a device uses
+ * the same array and overwrites it entirely, so calls that overlap on the GPU
+ * (other streams, other host threads) race: serialise them.
+ * Returns DGP_E_INVALID for n outside {16, 32, 64} (larger meshes do not fit
+ * the array: use power_spectrum with a context) or a bad argument,
+ * DGP_E_CUDA if a CUDA call fails. */
+#define DGP_NOALLOC_MAX_N 64
+#define DGP_NOALLOC_SCRATCH_BYTES 1188096
+int dgp_power_spectrum_noalloc(const float *delta, int n, double box, int nbins, double *k, double *pk,
+                               int64_t *nmodes, void *cuda_stream);
+
 /* Kernel accounting (not part of the paper's method; used to measure it).
  * Every kernel launch of a context is counted per kind together with its
  * algorithmic bytes (one read of each input and one write of each output).

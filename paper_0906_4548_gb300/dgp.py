@@ -21,7 +21,8 @@ C_OVER_H0 = 2997.92458
 
 EXPORTED = ["dgp_background", "dgp_init", "dgp_destroy", "dgp_strerror", "dgp_reset", "dgp_solve_phi",
             "dgp_solve_forces", "dgp_solve_history", "dgp_get_solution", "dgp_deposit", "pm_step", "pm_step_host", "power_spectrum", "bispectrum",
-            "dgp_profile", "dgp_profile_read", "dgp_kernel_name"]
+            "dgp_profile", "dgp_profile_read", "dgp_kernel_name", "dgp_power_spectrum_noalloc"]
+DGP_NOALLOC_MAX_N = 64
 DGP_KERNEL_KINDS = 10
 
 
@@ -85,6 +86,7 @@ def _load():
         "dgp_profile": (i, [vp, i]),
         "dgp_profile_read": (i, [vp, i, P(i64), P(d), P(i64), P(d), P(d)]),
         "dgp_kernel_name": (ctypes.c_char_p, [i]),
+        "dgp_power_spectrum_noalloc": (i, [vp, i, d, i, P(d), P(d), P(i64), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -230,3 +232,19 @@ def dgp_profile_read(ctx):
         out[lib.dgp_kernel_name(kind).decode()] = dict(launches=l.value, bytes=b.value, timed=t.value, ms=ms.value,
                                                        timed_bytes=tb.value)
     return out
+
+
+def dgp_power_spectrum_noalloc(delta, n, box, nbins, stream=None):
+    """P(k) of an FP32 n^3 device field without a context and without any device
+    allocation (n <= DGP_NOALLOC_MAX_N); same outputs as power_spectrum."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    k = np.zeros(nbins)
+    pk = np.zeros(nbins)
+    nm = np.zeros(nbins, dtype=np.int64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib.dgp_power_spectrum_noalloc(_ptr(delta), n, box, nbins, k.ctypes.data_as(dp), pk.ctypes.data_as(dp),
+                                          nm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ctypes.c_void_p(stream)),
+           "dgp_power_spectrum_noalloc")
+    return k, pk, nm

@@ -28,11 +28,53 @@ __host__ __device__ constexpr int bitrev_c(int i, int bits) {
   return r;
 }
 
+// cos(pi j / 16) for any integer j, from its values on [0, pi/2] (decimal
+// expansions of the exact constants) and the symmetries of cos.
+__host__ __device__ constexpr double cos_pi16(int j) {
+  j = ((j % 32) + 32) % 32;
+  if (j > 16) j = 32 - j;
+  if (j > 8) return -cos_pi16(16 - j);
+  return j == 0 ? 1.0
+       : j == 1 ? 0.98078528040323044913
+       : j == 2 ? 0.92387953251128675613
+       : j == 3 ? 0.83146961230254523708
+       : j == 4 ? 0.70710678118654752440
+       : j == 5 ? 0.55557023301960222474
+       : j == 6 ? 0.38268343236508977173
+       : j == 7 ? 0.19509032201612826785
+       : 0.0;
+}
+
+// W_32^j = exp(-2 pi i j / 32) = (cos(pi j / 16), -sin(pi j / 16)) in constant
+// memory; with a compile-time index the FMA reads it as a constant-bank operand.
+#define DGP_W32(j) {cos_pi16(j), -cos_pi16((j) - 8)}
+#define DGP_W32F(j) {(float)cos_pi16(j), (float)-cos_pi16((j) - 8)}
+static __constant__ double2 c_w32d[32] = {
+    DGP_W32(0),  DGP_W32(1),  DGP_W32(2),  DGP_W32(3),  DGP_W32(4),  DGP_W32(5),  DGP_W32(6),  DGP_W32(7),
+    DGP_W32(8),  DGP_W32(9),  DGP_W32(10), DGP_W32(11), DGP_W32(12), DGP_W32(13), DGP_W32(14), DGP_W32(15),
+    DGP_W32(16), DGP_W32(17), DGP_W32(18), DGP_W32(19), DGP_W32(20), DGP_W32(21), DGP_W32(22), DGP_W32(23),
+    DGP_W32(24), DGP_W32(25), DGP_W32(26), DGP_W32(27), DGP_W32(28), DGP_W32(29), DGP_W32(30), DGP_W32(31)};
+static __constant__ float2 c_w32f[32] = {
+    DGP_W32F(0),  DGP_W32F(1),  DGP_W32F(2),  DGP_W32F(3),  DGP_W32F(4),  DGP_W32F(5),  DGP_W32F(6),
+    DGP_W32F(7),  DGP_W32F(8),  DGP_W32F(9),  DGP_W32F(10), DGP_W32F(11), DGP_W32F(12), DGP_W32F(13),
+    DGP_W32F(14), DGP_W32F(15), DGP_W32F(16), DGP_W32F(17), DGP_W32F(18), DGP_W32F(19), DGP_W32F(20),
+    DGP_W32F(21), DGP_W32F(22), DGP_W32F(23), DGP_W32F(24), DGP_W32F(25), DGP_W32F(26), DGP_W32F(27),
+    DGP_W32F(28), DGP_W32F(29), DGP_W32F(30), DGP_W32F(31)};
+#undef DGP_W32
+#undef DGP_W32F
+
+// W_R^m for R dividing 32.
+template <typename V, int R>
+__device__ __forceinline__ V twiddle_c(int m) {
+  const int j = ((32 / R) * m) & 31;
+  if constexpr (sizeof(V) == 16) return c_w32d[j];
+  else return c_w32f[j];
+}
+
 // Forward DFT of the R values in v (natural order in and out), radix-2
-// decimation in time.  tw is the W_N table, TWS = N / R so that
-// W_R^m = tw[m * TWS].
+// decimation in time, R <= 32; the twiddles are compile-time constants.
 template <int R, int TWS, typename V>
-__device__ __forceinline__ void dft_regs(V (&v)[R], const V* __restrict__ tw) {
+__device__ __forceinline__ void dft_regs(V (&v)[R], const V* __restrict__ /*tw*/) {
   constexpr int L = Log2<R>::v;
 #pragma unroll
   for (int i = 0; i < R; ++i) {
@@ -52,8 +94,16 @@ __device__ __forceinline__ void dft_regs(V (&v)[R], const V* __restrict__ tw) {
       if (k != 0) {
         if (4 * k == len) {
           t = cmake<V>(t.y, -t.x);  // times W_4^1 = -i
+        } else if (8 * k == len) {
+          // times W_8^1 = (1 - i) / sqrt(2)
+          const auto c = (decltype(V::x))0.70710678118654752440;
+          t = cmake<V>((t.x + t.y) * c, (t.y - t.x) * c);
+        } else if (8 * k == 3 * len) {
+          // times W_8^3 = -(1 + i) / sqrt(2)
+          const auto c = (decltype(V::x))0.70710678118654752440;
+          t = cmake<V>((t.y - t.x) * c, -(t.x + t.y) * c);
         } else {
-          t = cmul(t, tw[k * (R / len) * TWS]);
+          t = cmul(t, twiddle_c<V, R>(k * (R / len)));
         }
       }
       v[i + k] = cadd(u, t);

@@ -13,7 +13,7 @@
 namespace dgp {
 
 template <typename T, int N, bool INV>
-__global__ void __launch_bounds__(256) k_fft_y(const __grid_constant__ FieldSet<T> f, int64_t npencils,
+__global__ void __launch_bounds__(256, 4) k_fft_y(const __grid_constant__ FieldSet<T> f, int64_t npencils,
                                               const vec2_t<T>* __restrict__ g_tw) {
   using V = vec2_t<T>;
   constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;

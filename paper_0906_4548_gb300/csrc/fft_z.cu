@@ -39,7 +39,7 @@ __device__ __forceinline__ void prologue_coeffs(const ZPrologue& pro, T* s_ss) {
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(ZGeom<T, N>::THREADS)
+__global__ void __launch_bounds__(ZGeom<T, N>::THREADS, 3)
 k_fft_z_r2c(const T* __restrict__ in, int64_t in_stride, vec2_t<T>* __restrict__ out, int64_t out_stride,
             ZPrologue pro, const vec2_t<T>* __restrict__ g_tw) {
   using V = vec2_t<T>;
@@ -99,7 +99,7 @@ k_fft_z_r2c(const T* __restrict__ in, int64_t in_stride, vec2_t<T>* __restrict__
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(ZGeom<T, N>::THREADS)
+__global__ void __launch_bounds__(ZGeom<T, N>::THREADS, 3)
 k_fft_z_c2r(const __grid_constant__ FieldSet<T> in, const __grid_constant__ FieldSet<T> outp,
             const vec2_t<T>* __restrict__ g_tw) {
   using V = vec2_t<T>;

@@ -254,7 +254,7 @@ __device__ __forceinline__ void pair_c2r(const vec2_t<T>* G, vec2_t<T>* s_T, con
 }
 
 template <typename T, int N, class AR>
-__global__ void __launch_bounds__(FGeom<T, N>::THREADS)
+__global__ void __launch_bounds__(FGeom<T, N>::THREADS, 2)
     k_fused_relax(const __grid_constant__ FusedArgs<T> args, const vec2_t<T>* __restrict__ g_tw) {
   using V = vec2_t<T>;
   using G_ = FGeom<T, N>;

@@ -58,6 +58,30 @@ def cic_deposit(pos, n, box, mass=None):
     return rho.reshape(n, n, n)
 
 
+def cell_index(pos, n, box):
+    """Cell of the lower CIC corner of each particle, (ix n + iy) n + iz with
+    i = floor(x / d) mod n per axis (the point that receives weight
+    (1 - fx)(1 - fy)(1 - fz) in Eq. CIC).  int64 array of length Np."""
+    (ix, _), (iy, _), (iz, _) = _cic_cells(np.asarray(pos, dtype=np.float64), n, box)
+    return (ix * n + iy) * n + iz
+
+
+def cell_sort(pos, n, box):
+    """Counting sort of particles by cell_index: (order, cell_start) with
+    order a stable permutation putting the keys in nondecreasing order and
+    cell_start[c] = number of particles with key < c, for c = 0 .. n^3."""
+    key = cell_index(pos, n, box)
+    counts = np.bincount(key, minlength=n ** 3)
+    start = np.zeros(n ** 3 + 1, dtype=np.int64)
+    start[1:] = np.cumsum(counts)
+    order = np.empty(key.size, dtype=np.int64)
+    cursor = start[:-1].copy()
+    for p in range(key.size):  # scatter in input order: stable
+        order[cursor[key[p]]] = p
+        cursor[key[p]] += 1
+    return order, start
+
+
 def density_contrast(rho):
     """delta = rho / rho_bar - 1 with rho_bar the mean of the mesh (Sec. III.A)."""
     return rho / float(np.mean(rho)) - 1.0

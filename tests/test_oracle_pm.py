@@ -58,6 +58,42 @@ def test_single_particle_brute_force_weights():
     assert np.max(np.abs(rho - want)) < 1e-14
 
 
+def test_cell_index_hand_values_and_wrap():
+    """Key = (ix n + iy) n + iz, i = floor(x / d) mod n, checked on values worked by hand (n = 4, d = 2)."""
+    n, box = 4, 8.0
+    pos = np.array([[3.0, -0.5, 8.0, 7.999, 0.0],
+                    [0.5, 2.0, 1.99, 4.0, 6.0],
+                    [7.9, 0.0, 3.0, 2.0, 5.5]])
+    want = [(1 * 4 + 0) * 4 + 3, (3 * 4 + 1) * 4 + 0, (0 * 4 + 0) * 4 + 1, (3 * 4 + 2) * 4 + 1, (0 * 4 + 3) * 4 + 2]
+    assert pm.cell_index(pos, n, box).tolist() == want
+
+
+def test_cell_index_is_the_full_weight_corner():
+    """The keyed point receives (1 - fx)(1 - fy)(1 - fz) of the particle in the deposit (Eq. CIC)."""
+    n, box = 8, 16.0
+    d = box / n
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        p = rng.uniform(0, box, (3, 1))
+        key = int(pm.cell_index(p, n, box)[0])
+        f = p[:, 0] / d - np.floor(p[:, 0] / d)
+        rho = pm.cic_deposit(p, n, box).reshape(-1)
+        assert abs(rho[key] - np.prod(1 - f)) < 1e-14
+
+
+def test_cell_sort_matches_a_stable_comparison_sort():
+    n, box = 6, 12.0
+    rng = np.random.default_rng(9)
+    pos = rng.uniform(0, box, (3, 900))
+    pos[:, 100:200] = pos[:, 0:1]  # a crowded cell
+    key = pm.cell_index(pos, n, box)
+    order, start = pm.cell_sort(pos, n, box)
+    assert order.tolist() == sorted(range(pos.shape[1]), key=lambda p: key[p])
+    assert start[0] == 0 and start[-1] == pos.shape[1]
+    for c in range(n ** 3):
+        assert start[c + 1] - start[c] == int(np.sum(key == c))
+
+
 @pytest.mark.parametrize("gravity,geff", [("grh", "GR"), ("nl", "local")])
 def test_linear_growth_of_low_amplitude_wave(gravity, geff):
     """A long plane wave of tiny amplitude grows like D+(a) (the linearised

@@ -41,6 +41,8 @@ UNIT = "steps/s"
 # Mean residual evaluations per solve of this workload as measured on GB300
 # (used by the oracle reference arm, which has no GPU run to read it from).
 E_PER_SOLVE_REF = 20.8
+# Cell sort cadence of the particles (pm_step sorts after every K-th drift; 0 = never).
+SORT_EVERY = 8
 
 
 PRECISION_DESC = {
@@ -51,12 +53,12 @@ PRECISION_DESC = {
 }
 
 
-def config(n_gpus, prec="mixed"):
+def config(n_gpus, prec="mixed", sort_every=SORT_EVERY):
     return {"workload": "dgp_pm_%dcube_box%g_ns%g_rms%g_a%g-%g_%dsteps_tol%g" % (
         WL["n"], WL["box"], WL["n_s"], WL["rms"], WL["a_start"], WL["a_end"], WL["run_steps"], WL["tol"]),
         "mesh": WL["n"], "particles": WL["n"] ** 3, "box_mpc_h": WL["box"], "rc_H0": WL["rc_H0"],
         "w": WL["w"], "tol": WL["tol"], "precision": PRECISION_DESC[prec],
-        "parallelism": "replicas" if n_gpus > 1 else "single",
+        "parallelism": "replicas" if n_gpus > 1 else "single", "cell_sort_every": sort_every,
         "l2": "inputs larger than L2 (particles 403 MB, fields 64 MB each); no flush"}
 
 
@@ -186,6 +188,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--precision", default="mixed", choices=sorted(PRECISION_DESC))
     ap.add_argument("--no-compare", action="store_true", help="skip the precision comparison runs")
+    ap.add_argument("--sort-every", type=int, default=SORT_EVERY,
+                    help="cell-sort the particles after every K-th drift (0: never)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -216,7 +220,7 @@ def main():
     parts = dgp.particles(*cur)
     pcode = {"mixed": dgp.DGP_MIXED_EFT, "mixed-fp64": dgp.DGP_MIXED, "fp32": dgp.DGP_FP32}
     ctx = dgp.dgp_init(box, n, WL["rc_H0"], WL["omega_m0"], w=WL["w"], precision=pcode[args.precision],
-                       max_iter=WL["max_iter"], tol=WL["tol"])
+                       max_iter=WL["max_iter"], tol=WL["tol"], sort_every=args.sort_every)
     dlna = math.log(WL["a_end"] / WL["a_start"]) / WL["run_steps"]
     sched = [WL["a_start"] * math.exp(i * dlna) for i in range(max(args.steps, args.warmup) + 1)]
 
@@ -285,7 +289,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"mixed": "f32+eft", "mixed-fp64": "f32+f64", "fp32": "f32"}[args.precision],
-            "data": "synthetic", "config": config(world, args.precision),
+            "data": "synthetic", "config": config(world, args.precision, args.sort_every),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": None, "kernel": dom,
                          "peak_source": peak_kind},
@@ -310,7 +314,7 @@ def main():
                 comp[name] = {"value": value, "evals_per_solve_mean": sum(evals) / len(evals)}
                 continue
             c2 = dgp.dgp_init(box, n, WL["rc_H0"], WL["omega_m0"], w=WL["w"], precision=pcode[name],
-                              max_iter=WL["max_iter"], tol=WL["tol"])
+                              max_iter=WL["max_iter"], tol=WL["tol"], sort_every=args.sort_every)
             for cc, s0 in zip(cur, ic):
                 cc.copy_(s0)
             infs = []

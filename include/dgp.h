@@ -80,6 +80,8 @@ typedef struct {
   int local_only;    /* nonzero: drop the sqrt(-lapbar) terms (Appendix Eq. FullDGP2simp) */
   int max_iter;      /* relaxation updates per solve before giving up, >= 0 */
   double tol;        /* normalised-residual tolerance used by pm_step (Eq. normres) */
+  int sort_every;    /* >= 0; nonzero: every sort_every-th pm_step call cell-sorts the
+                        particles after its drift (dgp_sort_particles); 0: never */
 } dgp_params;
 
 typedef struct {
@@ -161,13 +163,33 @@ int dgp_get_solution(dgp_ctx *c, void *D);
  * delta: device n^3 output.  Positions outside [0, box) are wrapped. */
 int dgp_deposit(dgp_ctx *c, const dgp_particles *parts, void *delta);
 
+/* Counting sort of the particles by mesh cell, in place (support for the CIC
+ * assignment of Sec. III.A; the paper deposits particles in storage order).
+ * The key of a particle is the cell of its lower CIC corner,
+ * (ix n + iy) n + iz with i = floor(x n / box) mod n per axis, the index the
+ * deposit and the gather use.  After the call the six arrays are permuted
+ * together so that keys are nondecreasing; the order of particles that share
+ * a cell is not specified (it can differ between calls).  Particles carry no
+ * identity in this interface, so the permutation is not returned.
+ *   parts:      device arrays of the context precision, n <= 2^31 - 1;
+ *   cell_start: NULL, or device int32[n^3 + 1] receiving the first slot of
+ *               each cell (cell c holds slots cell_start[c] .. cell_start[c+1]-1;
+ *               cell_start[n^3] = parts->n); synchronised on return when given.
+ * The first call, and any call with more particles than before, allocates
+ * 4 + 6 sizeof(real) bytes per particle and 12 n^3 bytes of workspace; the
+ * sort itself goes through those copies (the six arrays are copied back).
+ * DGP_E_INVALID for a bad argument, DGP_E_NOMEM, DGP_E_CUDA. */
+int dgp_sort_particles(dgp_ctx *c, dgp_particles *parts, int32_t *cell_start);
+
 /* One kick-drift-kick step from a to a + da, uniform in ln a (Sec. III.A):
  * p += g(x, a) K(a, a_h); x += p Dr(a, a + da); p += g(x', a + da) K(a_h, a + da)
  * with a_h the midpoint in ln a, K = int dlna / E and Dr = int dlna / (a^2 E).
  * The force at the start reuses the mesh force the previous call left when
  * that call ended at the same a with the same particle buffers; otherwise it
  * is computed first.  The solve uses params.tol and the warm start.  info
- * (host, may be NULL) describes the solve at a + da. */
+ * (host, may be NULL) describes the solve at a + da.  With params.sort_every
+ * = K > 0, every K-th call (counted since init or dgp_reset) reorders the
+ * particles by cell after the drift, as dgp_sort_particles does. */
 int pm_step(dgp_ctx *c, dgp_particles *parts, double a, double da, dgp_solve_info *info);
 
 /* pm_step on host particle arrays (pageable or pinned): copies them to the
@@ -227,7 +249,7 @@ int dgp_power_spectrum_noalloc(const float *delta, int n, double box, int nbins,
  * events and returns, for kind in [0, DGP_KERNEL_KINDS): launches and bytes
  * since the reset, and the timed launches, their summed duration (ms) and
  * their bytes.  Any output pointer may be NULL. */
-#define DGP_KERNEL_KINDS 10
+#define DGP_KERNEL_KINDS 11
 int dgp_profile(dgp_ctx *c, int timing);
 int dgp_profile_read(dgp_ctx *c, int kind, int64_t *launches, double *bytes, int64_t *timed, double *ms,
                      double *timed_bytes);

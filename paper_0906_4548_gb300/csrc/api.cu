@@ -121,10 +121,10 @@ static double time_integral(double a0, double a1, double om, double rc, int pw) 
 // when timing is on, each launch is bracketed by two events on the context's
 // stream and the durations are resolved when read.
 enum KernelKind { KK_Z_R2C = 0, KK_Z_C2R, KK_Y, KK_X_HESSIAN, KK_X_OTHER, KK_RELAX, KK_REDUCE, KK_DEPOSIT,
-                  KK_GATHER, KK_MISC, KK_COUNT };
+                  KK_GATHER, KK_MISC, KK_SORT, KK_COUNT };
 static const char* const kKernelNames[KK_COUNT] = {
     "fft_z_r2c", "fft_z_c2r", "fft_y", "fft_x_hessian", "fft_x_other", "relax", "reduce", "cic_deposit",
-    "cic_gather_kick", "misc"};
+    "cic_gather_kick", "misc", "cell_sort"};
 
 struct Profiler {
   bool timing = false;
@@ -189,6 +189,7 @@ class EngineBase {
   virtual int solve(double a, const void* delta, void* phi, void* gx, void* gy, void* gz, double tol,
                     dgp_solve_info* info) = 0;
   virtual int deposit(const dgp_particles* parts, void* delta) = 0;
+  virtual int sort(dgp_particles* parts, int* cell_start) = 0;
   virtual int step(dgp_particles* parts, double a, double da, dgp_solve_info* info) = 0;
   virtual int step_host(dgp_particles* parts, double a, double da, dgp_solve_info* info) = 0;
   virtual int pk(const void* delta, int nbins, double* k, double* pk, int64_t* nmodes) = 0;
@@ -241,6 +242,13 @@ class Engine : public EngineBase {
   int64_t force_np = -1;
   T* hp[6] = {};                // device copies for pm_step_host
   int64_t hp_n = 0;
+  // cell sort: key and permuted copies per particle, counts / starts / cursors per cell
+  int* srt_key = nullptr;
+  T* srt_tmp[6] = {};
+  int64_t srt_np = 0;
+  int* srt_cell = nullptr;      // [3][M]: count, start, cursor
+  int* srt_sums = nullptr;
+  int64_t nsteps = 0;           // pm_step calls since init / reset
 
  public:
   ~Engine() override {
@@ -253,6 +261,8 @@ class Engine : public EngineBase {
     cudaFree(sD); cudaFree(sD2); cudaFree(sDelta); cudaFree(tw);
     cudaFree(partials); cudaFree(d_rstats); cudaFree(d_misc);
     cudaFree(pk_partials); cudaFree(d_pk);
+    cudaFree(srt_key); cudaFree(srt_cell); cudaFree(srt_sums);
+    for (int i = 0; i < 6; ++i) cudaFree(srt_tmp[i]);
     cudaFreeHost(h_stats);
   }
 
@@ -304,6 +314,7 @@ class Engine : public EngineBase {
   void reset() override {
     wcur = -1;
     force_valid = false;
+    nsteps = 0;
   }
 
   int get_solution(void* D) override {
@@ -529,10 +540,47 @@ class Engine : public EngineBase {
     return pp->x && pp->y && pp->z && pp->px && pp->py && pp->pz;
   }
 
+  // Counting sort of the particles by the cell of their lower CIC corner,
+  // in place (through the context's copies); cell_start (device, M + 1) optional.
+  int sort_impl(const dgp_particles* pp, int* cell_start) {
+    const int64_t np = pp->n;
+    if (np > 0x7fffffff) return DGP_E_INVALID;
+    if (!srt_cell) {
+      if (cudaMalloc(&srt_cell, sizeof(int) * 3 * M) != cudaSuccess) return DGP_E_NOMEM;
+      if (cudaMalloc(&srt_sums, sizeof(int) * sort_scan_blocks(M)) != cudaSuccess) return DGP_E_NOMEM;
+    }
+    if (np > srt_np) {
+      DGP_CUDA(cudaStreamSynchronize(stream));
+      cudaFree(srt_key);
+      srt_key = nullptr;
+      for (int i = 0; i < 6; ++i) { cudaFree(srt_tmp[i]); srt_tmp[i] = nullptr; }
+      srt_np = 0;
+      if (cudaMalloc(&srt_key, sizeof(int) * np) != cudaSuccess) return DGP_E_NOMEM;
+      for (int i = 0; i < 6; ++i)
+        if (cudaMalloc(&srt_tmp[i], sizeof(T) * np) != cudaSuccess) return DGP_E_NOMEM;
+      srt_np = np;
+    }
+    ParticleSet<T> in{{(T*)pp->x, (T*)pp->y, (T*)pp->z, (T*)pp->px, (T*)pp->py, (T*)pp->pz}};
+    ParticleSet<T> out{{srt_tmp[0], srt_tmp[1], srt_tmp[2], srt_tmp[3], srt_tmp[4], srt_tmp[5]}};
+    const SortWork w{srt_key, srt_cell, srt_cell + M, srt_cell + 2 * M, srt_sums};
+    const double pb = sizeof(T) * 15.0 + 8.0;  // read x (3), key out/in, read 6, write 6
+    prof.run(KK_SORT, pb * np + 16.0 * M, stream, [&] { launch_cell_sort<T>(in, np, cic(), w, out, stream); });
+    DGP_CHECK_LAUNCH();
+    for (int i = 0; i < 6 && np > 0; ++i)
+      DGP_CUDA(cudaMemcpyAsync(in.p[i], out.p[i], sizeof(T) * np, cudaMemcpyDeviceToDevice, stream));
+    if (cell_start) {
+      const int total = (int)np;
+      DGP_CUDA(cudaMemcpyAsync(cell_start, w.start, sizeof(int) * M, cudaMemcpyDeviceToDevice, stream));
+      DGP_CUDA(cudaMemcpyAsync(cell_start + M, &total, sizeof(int), cudaMemcpyHostToDevice, stream));
+      DGP_CUDA(cudaStreamSynchronize(stream));
+    }
+    return DGP_OK;
+  }
+
   int forces_at(const dgp_particles* pp, double a, dgp_solve_info* info) {
     prof.run(KK_MISC, RB, stream, [&] { launch_fill<T>(rRho, M, (T)0, stream); });
     prof.run(KK_DEPOSIT, 3.0 * sizeof(T) * pp->n + RB, stream, [&] {
-      launch_cic_deposit<T>((const T*)pp->x, (const T*)pp->y, (const T*)pp->z, pp->n, rRho, cic(), stream);
+      launch_cic_deposit_warp<T>((const T*)pp->x, (const T*)pp->y, (const T*)pp->z, pp->n, rRho, cic(), stream);
     });
     DGP_CHECK_LAUNCH();
     const int rc = solve_impl(a, rRho, true, nullptr, rG[0], rG[1], rG[2], p.tol, info);
@@ -551,12 +599,17 @@ class Engine : public EngineBase {
     return solve_impl(a, (const T*)delta, false, (T*)phi, (T*)gx, (T*)gy, (T*)gz, tol, info);
   }
 
+  int sort(dgp_particles* pp, int* cell_start) override {
+    if (!valid_parts(pp)) return DGP_E_INVALID;
+    return sort_impl(pp, cell_start);
+  }
+
   int deposit(const dgp_particles* pp, void* delta) override {
     if (!valid_parts(pp) || !delta) return DGP_E_INVALID;
     if (pp->n == 0) return DGP_E_INVALID;
     prof.run(KK_MISC, RB, stream, [&] { launch_fill<T>(rRho, M, (T)0, stream); });
     prof.run(KK_DEPOSIT, 3.0 * sizeof(T) * pp->n + RB, stream, [&] {
-      launch_cic_deposit<T>((const T*)pp->x, (const T*)pp->y, (const T*)pp->z, pp->n, rRho, cic(), stream);
+      launch_cic_deposit_warp<T>((const T*)pp->x, (const T*)pp->y, (const T*)pp->z, pp->n, rRho, cic(), stream);
     });
     int rc;
     if ((rc = reduce_sum(rRho, false, d_misc + 0))) return rc;
@@ -581,6 +634,8 @@ class Engine : public EngineBase {
                             rG[1], rG[2], cp, k1, dr, 1, stream);
     });
     DGP_CHECK_LAUNCH();
+    ++nsteps;
+    if (p.sort_every > 0 && nsteps % p.sort_every == 0 && (rc = sort_impl(pp, nullptr))) return rc;
     if ((rc = forces_at(pp, a1, info))) return rc;
     const double k2 = time_integral(ah, a1, om, rc_, 0);
     prof.run(KK_GATHER, 9.0 * sizeof(T) * pp->n + 3 * RB, stream, [&] {
@@ -739,7 +794,7 @@ int dgp_init(dgp_ctx** out, const dgp_params* p, const dgp_cosmology* cosmo, voi
   const int n = p->n;
   if (n != 16 && n != 32 && n != 64 && n != 128 && n != 256 && n != 512) return DGP_E_INVALID;
   if (!(p->box > 0) || !(p->rc_H0 > 0) || !(p->w >= 0 && p->w < 1) || p->max_iter < 0 || !(p->tol >= 0) ||
-      !isfinite(p->tol))
+      !isfinite(p->tol) || p->sort_every < 0)
     return DGP_E_INVALID;
   if (p->precision < DGP_FP32 || p->precision > DGP_MIXED_EFT) return DGP_E_INVALID;
   if (p->gravity < DGP_GRAVITY_NL || p->gravity > DGP_GRAVITY_GRH) return DGP_E_INVALID;
@@ -828,6 +883,11 @@ const char* dgp_kernel_name(int kind) {
 int dgp_deposit(dgp_ctx* c, const dgp_particles* parts, void* delta) {
   if (!c) return DGP_E_INVALID;
   return c->eng->deposit(parts, delta);
+}
+
+int dgp_sort_particles(dgp_ctx* c, dgp_particles* parts, int32_t* cell_start) {
+  if (!c) return DGP_E_INVALID;
+  return c->eng->sort(parts, cell_start);
 }
 
 int pm_step(dgp_ctx* c, dgp_particles* parts, double a, double da, dgp_solve_info* info) {

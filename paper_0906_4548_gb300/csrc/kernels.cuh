@@ -119,13 +119,31 @@ struct CicParams {
 };
 
 template <typename T>
-void launch_cic_deposit(const T* x, const T* y, const T* z, int64_t np, T* rho, CicParams cp,
-                        cudaStream_t s);
-
-template <typename T>
 void launch_gather_kick(T* x, T* y, T* z, T* px, T* py, T* pz, int64_t np, const T* gx,
                         const T* gy, const T* gz, CicParams cp, double kick, double drift, int do_drift,
                         cudaStream_t s);
+
+// Counting sort of particles by CIC cell (sort_deposit.cu).
+template <typename T>
+struct ParticleSet {
+  T* p[6];  // x, y, z, px, py, pz
+};
+struct SortWork {
+  int* key;     // [np] cell of each particle
+  int* count;   // [N^3] particles per cell
+  int* start;   // [N^3] exclusive scan of count: first slot of each cell
+  int* cursor;  // [N^3] scatter cursors
+  int* sums;    // [sort_scan_blocks(N^3)] chunk sums of the scan
+};
+int sort_scan_blocks(int64_t m);
+// Writes the particles of parts, ordered by cell, into tmp (no copy back).
+template <typename T>
+void launch_cell_sort(const ParticleSet<T>& parts, int64_t np, CicParams cp, const SortWork& w,
+                      const ParticleSet<T>& tmp, cudaStream_t s);
+// CIC deposit with warp-aggregated atomics over lanes that share a cell.
+template <typename T>
+void launch_cic_deposit_warp(const T* x, const T* y, const T* z, int64_t np, T* rho, CicParams cp,
+                              cudaStream_t s);
 
 int num_sms();
 

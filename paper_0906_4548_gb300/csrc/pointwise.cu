@@ -7,6 +7,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "cic.cuh"
 
 namespace dgp {
 
@@ -167,63 +168,6 @@ DGP_INST_PW(double)
 // (1 - f, f) per axis, periodic.  In FP32 x/d is formed as an exact product
 // with N/box held as an unevaluated pair (hi + lo), so the fractional offset
 // carries no more error than the position itself.
-__device__ __forceinline__ void cic_axis(float x, const CicParams& cp, int& i0, int& i1, float& f) {
-  const float hi = x * cp.inv_d_hi;
-  const float lo = fmaf(x, cp.inv_d_hi, -hi) + x * cp.inv_d_lo;
-  float fl = floorf(hi);
-  f = (hi - fl) + lo;
-  if (f < 0.f) { f += 1.f; fl -= 1.f; }
-  else if (f >= 1.f) { f -= 1.f; fl += 1.f; }
-  int i = (int)fl % cp.n;
-  if (i < 0) i += cp.n;
-  i0 = i;
-  i1 = (i + 1 == cp.n) ? 0 : i + 1;
-}
-
-__device__ __forceinline__ void cic_axis(double x, const CicParams& cp, int& i0, int& i1, double& f) {
-  const double u = x * cp.inv_d;
-  const double fl = floor(u);
-  f = u - fl;
-  long long i = (long long)fl % cp.n;
-  if (i < 0) i += cp.n;
-  i0 = (int)i;
-  i1 = (i0 + 1 == cp.n) ? 0 : i0 + 1;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_cic_deposit(const T* __restrict__ x, const T* __restrict__ y,
-                                                     const T* __restrict__ z, int64_t np, T* __restrict__ rho,
-                                                     CicParams cp) {
-  const int64_t n = cp.n;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
-    int ix0, ix1, iy0, iy1, iz0, iz1;
-    T fx, fy, fz;
-    cic_axis(x[p], cp, ix0, ix1, fx);
-    cic_axis(y[p], cp, iy0, iy1, fy);
-    cic_axis(z[p], cp, iz0, iz1, fz);
-    const T gx = (T)1 - fx, gy = (T)1 - fy, gz = (T)1 - fz;
-    const int64_t r00 = (ix0 * n + iy0) * n, r01 = (ix0 * n + iy1) * n;
-    const int64_t r10 = (ix1 * n + iy0) * n, r11 = (ix1 * n + iy1) * n;
-    atomicAdd(rho + r00 + iz0, gx * gy * gz);
-    atomicAdd(rho + r00 + iz1, gx * gy * fz);
-    atomicAdd(rho + r01 + iz0, gx * fy * gz);
-    atomicAdd(rho + r01 + iz1, gx * fy * fz);
-    atomicAdd(rho + r10 + iz0, fx * gy * gz);
-    atomicAdd(rho + r10 + iz1, fx * gy * fz);
-    atomicAdd(rho + r11 + iz0, fx * fy * gz);
-    atomicAdd(rho + r11 + iz1, fx * fy * fz);
-  }
-}
-
-template <typename T>
-void launch_cic_deposit(const T* x, const T* y, const T* z, int64_t np, T* rho, CicParams cp, cudaStream_t s) {
-  if (np <= 0) return;
-  int64_t blocks = (np + 255) / 256;
-  const int64_t cap = (int64_t)num_sms() * 16;
-  if (blocks > cap) blocks = cap;
-  k_cic_deposit<T><<<(unsigned)blocks, 256, 0, s>>>(x, y, z, np, rho, cp);
-}
-
 template <typename T>
 __device__ __forceinline__ T wrap_periodic(T v, T box, T inv_box) {
   v -= box * floor(v * inv_box);
@@ -292,7 +236,6 @@ void launch_gather_kick(T* x, T* y, T* z, T* px, T* py, T* pz, int64_t np, const
 }
 
 #define DGP_INST_P(T)                                                                              \
-  template void launch_cic_deposit<T>(const T*, const T*, const T*, int64_t, T*, CicParams, cudaStream_t); \
   template void launch_gather_kick<T>(T*, T*, T*, T*, T*, T*, int64_t, const T*, const T*, const T*,  \
                                       CicParams, double, double, int, cudaStream_t);
 DGP_INST_P(float)

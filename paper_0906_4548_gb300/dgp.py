@@ -21,9 +21,10 @@ C_OVER_H0 = 2997.92458
 
 EXPORTED = ["dgp_background", "dgp_init", "dgp_destroy", "dgp_strerror", "dgp_reset", "dgp_solve_phi",
             "dgp_solve_forces", "dgp_solve_history", "dgp_get_solution", "dgp_deposit", "pm_step", "pm_step_host", "power_spectrum", "bispectrum",
-            "dgp_profile", "dgp_profile_read", "dgp_kernel_name", "dgp_power_spectrum_noalloc"]
+            "dgp_profile", "dgp_profile_read", "dgp_kernel_name", "dgp_power_spectrum_noalloc",
+            "dgp_sort_particles"]
 DGP_NOALLOC_MAX_N = 64
-DGP_KERNEL_KINDS = 10
+DGP_KERNEL_KINDS = 11
 
 
 class DgpError(RuntimeError):
@@ -39,7 +40,8 @@ class Cosmology(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("box", ctypes.c_double), ("n", ctypes.c_int), ("rc_H0", ctypes.c_double),
                 ("w", ctypes.c_double), ("precision", ctypes.c_int), ("gravity", ctypes.c_int),
-                ("local_only", ctypes.c_int), ("max_iter", ctypes.c_int), ("tol", ctypes.c_double)]
+                ("local_only", ctypes.c_int), ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
+                ("sort_every", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -87,6 +89,7 @@ def _load():
         "dgp_profile_read": (i, [vp, i, P(i64), P(d), P(i64), P(d), P(d)]),
         "dgp_kernel_name": (ctypes.c_char_p, [i]),
         "dgp_power_spectrum_noalloc": (i, [vp, i, d, i, P(d), P(d), P(i64), vp]),
+        "dgp_sort_particles": (i, [vp, P(Particles), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -130,13 +133,13 @@ def dgp_background(omega_m0, rc_H0, a, c_over_H0=C_OVER_H0):
 
 
 def dgp_init(box, n, rc_H0, omega_m0=0.27, w=1.0 / 3.0, precision=DGP_MIXED, gravity=DGP_GRAVITY_NL,
-             local_only=False, max_iter=100, tol=1e-6, stream=None, c_over_H0=C_OVER_H0):
+             local_only=False, max_iter=100, tol=1e-6, stream=None, c_over_H0=C_OVER_H0, sort_every=0):
     """Returns an opaque context handle (ctypes.c_void_p)."""
     if stream is None:
         import torch
         stream = torch.cuda.current_stream().cuda_stream
     ctx = ctypes.c_void_p()
-    p = Params(box, n, rc_H0, w, precision, gravity, 1 if local_only else 0, max_iter, tol)
+    p = Params(box, n, rc_H0, w, precision, gravity, 1 if local_only else 0, max_iter, tol, sort_every)
     _check(lib.dgp_init(ctypes.byref(ctx), ctypes.byref(p), ctypes.byref(Cosmology(omega_m0, c_over_H0)),
                         ctypes.c_void_p(stream)), "dgp_init")
     return ctx
@@ -183,6 +186,11 @@ def particles(x, y, z, px, py, pz):
 
 def dgp_deposit(ctx, parts, delta):
     _check(lib.dgp_deposit(ctx, ctypes.byref(parts), _ptr(delta)), "dgp_deposit")
+
+
+def dgp_sort_particles(ctx, parts, cell_start=None):
+    """Cell-sorts the particle arrays in place; cell_start: None or a device int32 tensor of n^3 + 1."""
+    _check(lib.dgp_sort_particles(ctx, ctypes.byref(parts), _ptr(cell_start)), "dgp_sort_particles")
 
 
 def pm_step(ctx, parts, a, da):

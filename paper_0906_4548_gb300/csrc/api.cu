@@ -4,6 +4,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <utility>
 #include <vector>
@@ -163,6 +164,11 @@ struct Profiler {
     used = 0;
     return DGP_OK;
   }
+  // bytes of work that launches already counted (with 0 bytes) turned out to do
+  void credit(int kind, double b) {
+    bytes[kind] += b;
+    if (timing) timed_bytes[kind] += b;
+  }
   template <class F>
   void run(int kind, double b, cudaStream_t s, F&& f) {
     launches[kind] += 1;
@@ -240,6 +246,12 @@ class Engine : public EngineBase {
   double force_a = 0.0;
   const void* force_x = nullptr;
   int64_t force_np = -1;
+  SolveCtl* d_ctl = nullptr;    // stop-rule state of the running solve
+  SolveCtl* h_ctl = nullptr;    // pinned host copy
+  double* d_hist = nullptr;     // [max_iter + 1] normalised residuals of the running solve
+  int last_stop_it = -1;        // last iteration examined by the previous solve
+  static constexpr int kPatience = 10;  // iterations without a new minimum before stopping
+  static constexpr int kChunk = 4;      // iterations enqueued per verdict after the first chunk
   T* hp[6] = {};                // device copies for pm_step_host
   int64_t hp_n = 0;
   // cell sort: key and permuted copies per particle, counts / starts / cursors per cell
@@ -262,6 +274,7 @@ class Engine : public EngineBase {
     cudaFree(partials); cudaFree(d_rstats); cudaFree(d_misc);
     cudaFree(pk_partials); cudaFree(d_pk);
     cudaFree(srt_key); cudaFree(srt_cell); cudaFree(srt_sums);
+    cudaFree(d_ctl); cudaFree(d_hist); cudaFreeHost(h_ctl);
     for (int i = 0; i < 6; ++i) cudaFree(srt_tmp[i]);
     cudaFreeHost(h_stats);
   }
@@ -286,6 +299,9 @@ class Engine : public EngineBase {
     if (cudaMalloc(&d_rstats, sizeof(double) * 12) != cudaSuccess) return DGP_E_NOMEM;
     if (cudaMalloc(&d_misc, sizeof(double) * 8) != cudaSuccess) return DGP_E_NOMEM;
     if (cudaMallocHost(&h_stats, sizeof(double) * 8) != cudaSuccess) return DGP_E_NOMEM;
+    if (cudaMalloc(&d_ctl, sizeof(SolveCtl)) != cudaSuccess) return DGP_E_NOMEM;
+    if (cudaMallocHost(&h_ctl, sizeof(SolveCtl)) != cudaSuccess) return DGP_E_NOMEM;
+    if (cudaMalloc(&d_hist, sizeof(double) * ((size_t)p.max_iter + 1)) != cudaSuccess) return DGP_E_NOMEM;
     pk_blocks = x_pass_blocks<T, N>();
     if (cudaMalloc(&pk_partials, sizeof(double) * 3 * (N / 2) * (size_t)pk_blocks) != cudaSuccess) return DGP_E_NOMEM;
     if (cudaMalloc(&d_pk, sizeof(double) * 3 * (N / 2)) != cudaSuccess) return DGP_E_NOMEM;
@@ -313,6 +329,7 @@ class Engine : public EngineBase {
 
   void reset() override {
     wcur = -1;
+    last_stop_it = -1;
     force_valid = false;
     nsteps = 0;
   }
@@ -413,18 +430,12 @@ class Engine : public EngineBase {
         launch_fft_x_op<T, N>(need_lin ? XOP_SOURCE_LIN : XOP_SOURCE, sDelta, nullptr, fs(s6, 2), 0, kp, nullptr, 0,
                               0, 0, tw, stream);
       });
-      int j0 = need_lin ? 0 : wcur;
+      const int j0 = need_lin ? 0 : wcur;
       T* outs[2] = {rS, rD[j0]};
       if ((rc = inverse_yz(s6, outs, need_lin ? 2 : 1))) return rc;
+      // eps = <|S|> (Eq. normres) is read by the controller at the first iteration
       if ((rc = reduce_sum(rS, true, d_misc + 1))) return rc;
       if (need_lin && (rc = reduce_sum(rD[j0], false, d_rstats + 4 * j0 + 1))) return rc;
-      if ((rc = fetch(d_misc + 1, 1))) return rc;
-      const double eps = h_stats[0] / (double)M;
-      if (!isfinite(eps)) return DGP_E_NONFINITE;
-      // Eq. normres divides by eps; a zero source (uniform density) has no
-      // scale, and the absolute mean residual is monitored instead.
-      const double rnorm = eps > 0.0 ? eps : 1.0;
-      inf.eps = eps;
 
       RelaxParams rp;
       rp.alpha = c.alpha; rp.w = p.w; rp.c2 = c.c2; rp.inv_m = 1.0 / (double)M;
@@ -436,59 +447,103 @@ class Engine : public EngineBase {
       rp.two_omw = (float)(2.0 * (1.0 - p.w));
       rp.alpha_f = (float)c.alpha;
       rp.bad_bp_f = (float)(-c.alpha * c.alpha / (4.0 * (1.0 - p.w)));
-      history.clear();
       const int arith = p.precision == DGP_FP32 ? ARITH_F32 : (p.precision == DGP_MIXED_EFT ? ARITH_EFT : ARITH_F64);
-      int cur = j0, best = -1, best_it = -1;
-      double rbest = INFINITY, rprev = INFINITY, prev_nbad = 0.0, last_bad = 0.0;
-      bool converged = false;
-      // sDc holds the z- and y-transformed current iterate; the fused pass writes
-      // the z-transformed next iterate into sDn.
-      V* sDc = sD;
-      V* sDn = sD2;
-      if ((rc = forward_zy(rD[cur], sDc, ZPrologue{nullptr, 0.0, 0}))) return rc;
-      for (int it = 0; it <= p.max_iter; ++it) {
-        prof.run(KK_X_HESSIAN, 7 * SB, stream, [&] {
-          launch_fft_x_op<T, N>(XOP_HESSIAN, sDc, nullptr, fs(s6, 6), 0, kp, nullptr, 0, 0, 0, tw, stream);
+
+      // Buffers: the starting iterate stays in rD[j0]; iteration it >= 1 reads
+      // the previous output, and the outputs alternate between the other two.
+      // The y-transformed spectrum of iteration it's input alternates sD / sD2.
+      int pb[2], npb = 0;
+      for (int b = 0; b < 3; ++b)
+        if (b != j0) pb[npb++] = b;
+      auto in_buf = [&](int it) { return it == 0 ? j0 : pb[(it - 1) & 1]; };
+      auto out_buf = [&](int it) { return pb[it & 1]; };
+      auto spec_in = [&](int it) { return (it & 1) ? sD2 : sD; };
+      auto spec_out = [&](int it) { return (it & 1) ? sD : sD2; };
+      const int* skip = &d_ctl->done;
+      // One iteration: Hessian spectra, inverse y, fused z pass + update,
+      // statistics, (stop rules), forward y of the new iterate.  With control,
+      // every kernel returns at entry once the controller has stopped the solve.
+      auto enqueue = [&](int it, bool control) -> int {
+        const int* sk = control ? skip : nullptr;
+        const int ib = in_buf(it), ob = out_buf(it);
+        prof.run(KK_X_HESSIAN, 0, stream, [&] {
+          launch_fft_x_op<T, N>(XOP_HESSIAN, spec_in(it), nullptr, fs(s6, 6), 0, kp, nullptr, 0, 0, 0, tw, stream,
+                                sk);
         });
-        prof.run(KK_Y, 12 * SB, stream, [&] { launch_fft_y<T, N>(fs(s6, 6), 6, true, tw, stream); });
-        int nxt = 0;
-        while (nxt == cur || nxt == best) ++nxt;
-        prof.run(KK_RELAX, 7 * SB + 3 * RB, stream, [&] {
-          launch_fused_relax<T, N>(arith, s6, rD[cur], d_rstats + 4 * cur + 1, rS, rD[nxt], sDn, rp, partials,
-                                   tw, stream);
+        prof.run(KK_Y, 0, stream, [&] { launch_fft_y<T, N>(fs(s6, 6), 6, true, tw, stream, sk); });
+        prof.run(KK_RELAX, 0, stream, [&] {
+          launch_fused_relax<T, N>(arith, s6, rD[ib], d_rstats + 4 * ib + 1, rS, rD[ob], spec_out(it), rp, partials,
+                                   tw, stream, sk);
         });
-        prof.run(KK_REDUCE, 32.0 * fblocks, stream,
-                 [&] { launch_finalize(partials, fblocks, 4, d_rstats + 4 * nxt, stream); });
+        prof.run(KK_REDUCE, 0, stream,
+                 [&] { launch_finalize(partials, fblocks, 4, d_rstats + 4 * ob, stream, sk); });
+        if (control)
+          prof.run(KK_REDUCE, 0, stream, [&] {
+            launch_relax_control(d_ctl, d_rstats + 4 * ob, d_misc + 1, d_hist, it, p.max_iter, kPatience, tol,
+                                 1.0 / (double)M, stream);
+          });
+        prof.run(KK_Y, 0, stream, [&] {
+          V* o[1] = {spec_out(it)};
+          launch_fft_y<T, N>(fs(o, 1), 1, false, tw, stream, sk);
+        });
         DGP_CHECK_LAUNCH();
-        if ((rc = fetch(d_rstats + 4 * nxt, 4))) return rc;
-        const double r = h_stats[0] / (double)M / rnorm;
-        history.push_back(r);
-        const double nbad = h_stats[2];
-        last_bad = nbad;
-        if (h_stats[3] > 0.0 || !isfinite(r)) return DGP_E_NONFINITE;
-        if (r < rbest) { rbest = r; best = cur; best_it = it; }
-        if (r < tol) { converged = true; break; }
-        if (it == p.max_iter) break;
-        if (it > 0 && prev_nbad > 0.0 && r > rprev) break;
-        if (it - best_it >= 10) break;
-        rprev = r;
-        prev_nbad = nbad;
-        prof.run(KK_Y, 2 * SB, stream, [&] {
-          V* o[1] = {sDn};
-          launch_fft_y<T, N>(fs(o, 1), 1, false, tw, stream);
-        });
-        V* t = sDc; sDc = sDn; sDn = t;
-        cur = nxt;
+        return DGP_OK;
+      };
+      auto credit = [&](int iters, int yfwd) {
+        prof.credit(KK_X_HESSIAN, 7 * SB * iters);
+        prof.credit(KK_Y, 12 * SB * iters + 2 * SB * yfwd);
+        prof.credit(KK_RELAX, (7 * SB + 3 * RB) * iters);
+        prof.credit(KK_REDUCE, 32.0 * fblocks * iters);
+      };
+
+      if ((rc = forward_zy(rD[j0], sD, ZPrologue{nullptr, 0.0, 0}))) return rc;
+      DGP_CUDA(cudaMemsetAsync(d_ctl, 0, sizeof(SolveCtl), stream));
+      // Iterations are enqueued in chunks and the controller's verdict is read
+      // once per chunk; the first chunk covers the previous solve's length.
+      int it = 0;
+      int chunk = last_stop_it >= 0 ? last_stop_it + 2 : 4;
+      while (true) {
+        const int end = std::min(it + chunk, p.max_iter + 1);
+        for (; it < end; ++it)
+          if ((rc = enqueue(it, true))) return rc;
+        DGP_CUDA(cudaMemcpyAsync(h_ctl, d_ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, stream));
+        DGP_CUDA(cudaStreamSynchronize(stream));
+        if (h_ctl->done || it > p.max_iter) break;
+        chunk = kChunk;
       }
-      // sDc holds the spectrum of rD[cur]; the accepted iterate may be an earlier one
-      if (best != cur && (rc = forward_zy(rD[best], sDc, ZPrologue{nullptr, 0.0, 0}))) return rc;
-      sDphi = sDc;
-      accepted = best;
+      const SolveCtl st = *h_ctl;
+      if (!st.done) return DGP_E_STATE;  // the controller stops at it = max_iter at the latest
+      const int s_it = st.stop_it;
+      credit(s_it + 1, s_it);
+      history.assign(s_it + 1, 0.0);
+      DGP_CUDA(cudaMemcpyAsync(history.data(), d_hist, sizeof(double) * (s_it + 1), cudaMemcpyDeviceToHost, stream));
+      DGP_CUDA(cudaStreamSynchronize(stream));
+      if (st.status == CTL_NONFINITE) return DGP_E_NONFINITE;
+      last_stop_it = s_it;
+      inf.eps = st.eps;
+      const int best_it = st.best_it;
+      if (best_it == s_it) {
+        // the input of the last examined iteration: its buffer and spectrum are intact
+        accepted = in_buf(s_it);
+        sDphi = spec_in(s_it);
+      } else {
+        // an earlier iterate: the start is intact; a later one is regenerated by
+        // replaying the (deterministic) iterations that produced it
+        if (best_it > 0) {
+          if ((rc = forward_zy(rD[j0], sD, ZPrologue{nullptr, 0.0, 0}))) return rc;
+          for (int k = 0; k < best_it; ++k)
+            if ((rc = enqueue(k, false))) return rc;
+          credit(best_it, best_it);
+        }
+        accepted = in_buf(best_it);
+        if ((rc = forward_zy(rD[accepted], sD, ZPrologue{nullptr, 0.0, 0}))) return rc;
+        sDphi = sD;
+      }
       inf.iters = best_it;
-      inf.norm_res = rbest;
-      inf.min_norm_res = rbest;
-      inf.bad_fraction = last_bad / (double)M;
-      status = converged ? DGP_OK : DGP_E_NOT_CONVERGED;
+      inf.norm_res = st.rbest;
+      inf.min_norm_res = st.rbest;
+      inf.bad_fraction = st.last_bad / (double)M;
+      status = st.status == CTL_CONVERGED ? DGP_OK : DGP_E_NOT_CONVERGED;
       inf.status = status;
       wcur = accepted;
     }

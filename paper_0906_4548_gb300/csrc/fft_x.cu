@@ -45,6 +45,7 @@ template <typename T> struct XArgs {
   double* pk_partials;
   int nbins;
   double shell_lo, shell_hi;
+  const int* skip;
 };
 
 template <typename T, int N>
@@ -111,6 +112,7 @@ __device__ __forceinline__ double geff_dev(const KParams& kp, double kmag) {
 template <typename T, int N, int OP>
 __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
     k_fft_x(const __grid_constant__ XArgs<T> args, const vec2_t<T>* __restrict__ g_tw) {
+  if (args.skip && *args.skip) return;
   using V = vec2_t<T>;
   constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, TY = XGeom<T, N>::TY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -265,8 +267,9 @@ static void launch_x(const XArgs<T>& a, const vec2_t<T>* tw, cudaStream_t s) {
 template <typename T, int N>
 void launch_fft_x_op(int op, const vec2_t<T>* in0, const vec2_t<T>* in1, const FieldSet<T>& out, int nout_mask,
                      const KParams& kp, double* pk_partials, int nbins, double shell_lo, double shell_hi,
-                     const vec2_t<T>* tw, cudaStream_t s) {
+                     const vec2_t<T>* tw, cudaStream_t s, const int* skip) {
   XArgs<T> a;
+  a.skip = skip;
   a.in0 = in0; a.in1 = in1; a.out = out; a.nout_mask = nout_mask; a.kp = kp;
   a.pk_partials = pk_partials; a.nbins = nbins; a.shell_lo = shell_lo; a.shell_hi = shell_hi;
   switch (op) {
@@ -283,7 +286,7 @@ void launch_fft_x_op(int op, const vec2_t<T>* in0, const vec2_t<T>* in1, const F
 #define DGP_INST_X(T, N)                                                                            \
   template void launch_fft_x_op<T, N>(int, const vec2_t<T>*, const vec2_t<T>*, const FieldSet<T>&, int, \
                                       const KParams&, double*, int, double, double, const vec2_t<T>*,   \
-                                      cudaStream_t);
+                                      cudaStream_t, const int*);
 #define DGP_INST_X_ALL(T) DGP_INST_X(T, 16) DGP_INST_X(T, 32) DGP_INST_X(T, 64) DGP_INST_X(T, 128) \
   DGP_INST_X(T, 256) DGP_INST_X(T, 512)
 DGP_INST_X_ALL(float)

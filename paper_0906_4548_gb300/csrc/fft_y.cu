@@ -14,7 +14,8 @@ namespace dgp {
 
 template <typename T, int N, bool INV>
 __global__ void __launch_bounds__(256, 4) k_fft_y(const __grid_constant__ FieldSet<T> f, int64_t npencils,
-                                              const vec2_t<T>* __restrict__ g_tw) {
+                                              const vec2_t<T>* __restrict__ g_tw, const int* __restrict__ skip) {
+  if (skip && *skip) return;
   using V = vec2_t<T>;
   constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
   constexpr int P = 256 / N1;
@@ -52,7 +53,8 @@ __global__ void __launch_bounds__(256, 4) k_fft_y(const __grid_constant__ FieldS
 }
 
 template <typename T, int N>
-void launch_fft_y(const FieldSet<T>& f, int nfields, bool inverse, const vec2_t<T>* tw, cudaStream_t s) {
+void launch_fft_y(const FieldSet<T>& f, int nfields, bool inverse, const vec2_t<T>* tw, cudaStream_t s,
+                  const int* skip) {
   using V = vec2_t<T>;
   constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
   constexpr int P = 256 / N1;
@@ -61,15 +63,15 @@ void launch_fft_y(const FieldSet<T>& f, int nfields, bool inverse, const vec2_t<
   dim3 grid((unsigned)((npencils + P - 1) / P), (unsigned)nfields);
   if (inverse) {
     cudaFuncSetAttribute(k_fft_y<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_fft_y<T, N, true><<<grid, 256, smem, s>>>(f, npencils, tw);
+    k_fft_y<T, N, true><<<grid, 256, smem, s>>>(f, npencils, tw, skip);
   } else {
     cudaFuncSetAttribute(k_fft_y<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_fft_y<T, N, false><<<grid, 256, smem, s>>>(f, npencils, tw);
+    k_fft_y<T, N, false><<<grid, 256, smem, s>>>(f, npencils, tw, skip);
   }
 }
 
 #define DGP_INST_Y(T, N) \
-  template void launch_fft_y<T, N>(const FieldSet<T>&, int, bool, const vec2_t<T>*, cudaStream_t);
+  template void launch_fft_y<T, N>(const FieldSet<T>&, int, bool, const vec2_t<T>*, cudaStream_t, const int*);
 #define DGP_INST_Y_ALL(T) DGP_INST_Y(T, 16) DGP_INST_Y(T, 32) DGP_INST_Y(T, 64) DGP_INST_Y(T, 128) \
   DGP_INST_Y(T, 256) DGP_INST_Y(T, 512)
 DGP_INST_Y_ALL(float)

@@ -174,6 +174,11 @@ template <typename T, int N> struct FGeom {
   static constexpr int GSZ = 2 * NK * (TY + 1);         // one field pair's half-spectrum tile
   static constexpr int TSZ = TY * N1 * (N2 + 1);        // four-step transpose
   static constexpr int P = TY / 2;                       // row pairs in the forward transform
+  // G1 is reused after the second pair: D_new rows (TY x N) then the prefetched
+  // S rows (TY x SS, padded when it fits so two rows of a warp use other banks)
+  static constexpr int SS_PAD = N + 16;
+  static constexpr bool PAD_FITS = (2 * TY * N + TY * 16) * sizeof(T) <= GSZ * 2 * sizeof(T);
+  static constexpr int SS = PAD_FITS ? SS_PAD : N;
 };
 
 template <typename T> struct FusedArgs {
@@ -185,6 +190,7 @@ template <typename T> struct FusedArgs {
   vec2_t<T>* Snew;           // z-transformed next iterate, layout S[kz][x][y]
   double* partials;          // [blocks][4]
   RelaxParams rp;
+  const int* skip;
 };
 
 // Start copying the TY-row tile of spectra A and B into G (layout
@@ -202,6 +208,18 @@ __device__ __forceinline__ void issue_pair(const vec2_t<T>* __restrict__ A, cons
     vec2_t<T>* dst = G + f * NK * (TY + 1) + kz * (TY + 1) + yl;
     if constexpr (sizeof(T) == 8) cp_async_16(dst, src);
     else cp_async_8(dst, src);
+  }
+  cp_commit();
+}
+
+// Start copying the TY rows of the source S (16-byte pieces) into s_S with row stride SS.
+template <typename T, int N>
+__device__ __forceinline__ void issue_source(const T* __restrict__ S, int64_t rbase0, T* s_S) {
+  constexpr int TY = FGeom<T, N>::TY, SS = FGeom<T, N>::SS;
+  constexpr int PER = 16 / sizeof(T);  // elements per 16-byte copy
+  for (int item = threadIdx.x; item < TY * N / PER; item += blockDim.x) {
+    const int r = item / (N / PER), c = (item % (N / PER)) * PER;
+    cp_async_16(s_S + r * SS + c, S + rbase0 + (int64_t)r * N + c);
   }
   cp_commit();
 }
@@ -256,6 +274,7 @@ __device__ __forceinline__ void pair_c2r(const vec2_t<T>* G, vec2_t<T>* s_T, con
 template <typename T, int N, class AR>
 __global__ void __launch_bounds__(FGeom<T, N>::THREADS, 2)
     k_fused_relax(const __grid_constant__ FusedArgs<T> args, const vec2_t<T>* __restrict__ g_tw) {
+  if (args.skip && *args.skip) return;
   using V = vec2_t<T>;
   using G_ = FGeom<T, N>;
   using Acc = typename AR::Acc;
@@ -294,11 +313,12 @@ __global__ void __launch_bounds__(FGeom<T, N>::THREADS, 2)
   T ra[N2], rb[N2];
 #pragma unroll 1
   for (int pr = 0; pr < 3; ++pr) {
-    if (pr < 2) cp_wait<1>();
-    else cp_wait<0>();
+    cp_wait<1>();  // groups: pair 0, pair 1, pair 2 (issued at pr 0), S (issued at pr 1)
     __syncthreads();  // tile pr visible; s_T free
     pair_c2r<T, N>((pr & 1) ? G1 : G0, s_T, s_tw, ra, rb);
-    if (pr == 0) issue_pair<T, N>(args.spec[4], args.spec[5], x, y0, G0);  // G0 read by phase 1 already
+    // pair_c2r's barrier follows its last read of the tile, so the buffer is free
+    if (pr == 0) issue_pair<T, N>(args.spec[4], args.spec[5], x, y0, G0);
+    if (pr == 1) issue_source<T, N>(args.S, ((int64_t)x * N + y0) * N, reinterpret_cast<T*>(G1) + TY * N);
     if (pr == 0) {
       // a = H_xx, b = H_yy:  q = a^2 + a b + b^2 - (a + b) d
 #pragma unroll
@@ -330,6 +350,9 @@ __global__ void __launch_bounds__(FGeom<T, N>::THREADS, 2)
     bad_bp = rp.bad_bp_f;
   }
   T* s_dn = reinterpret_cast<T*>(G1);  // TY rows of D_new (G1 is free: pair 1 is done)
+  const T* s_S = s_dn + TY * N;
+  cp_wait<0>();
+  __syncthreads();  // S rows visible
   Acc acc_r;
   AR::q_init(acc_r);
   // the sum of D_new sets the mean removed next iteration: double for double data
@@ -339,7 +362,7 @@ __global__ void __launch_bounds__(FGeom<T, N>::THREADS, 2)
   for (int k2 = 0; k2 < N2; ++k2) {
     const int z = lane + N1 * k2;
     const int64_t idx = rbase + z;
-    const Acc R = AR::residual(q[k2], d[k2], rb[k2], args.S[idx], rp);
+    const Acc R = AR::residual(q[k2], d[k2], rb[k2], s_S[row * G_::SS + z], rp);
     T bpt = (T)AR::bprime(d[k2], R, rp);
     bool neg;
     T dt = (T)AR::disc(d[k2], R, rp, neg);
@@ -425,8 +448,10 @@ static void launch_f(const FusedArgs<T>& a, const vec2_t<T>* tw, cudaStream_t s)
 
 template <typename T, int N>
 void launch_fused_relax(int arith, vec2_t<T>* const* spec6, const T* D, const double* dsum, const T* S, T* Dnew,
-                        vec2_t<T>* Snew, RelaxParams rp, double* partials, const vec2_t<T>* tw, cudaStream_t s) {
+                        vec2_t<T>* Snew, RelaxParams rp, double* partials, const vec2_t<T>* tw, cudaStream_t s,
+                        const int* skip) {
   FusedArgs<T> a;
+  a.skip = skip;
   for (int i = 0; i < 6; ++i) a.spec[i] = spec6[i];
   a.D = D; a.dsum = dsum; a.S = S; a.Dnew = Dnew; a.Snew = Snew; a.partials = partials; a.rp = rp;
   if constexpr (sizeof(T) == 8) {
@@ -440,7 +465,8 @@ void launch_fused_relax(int arith, vec2_t<T>* const* spec6, const T* D, const do
 
 #define DGP_INST_F(T, N)                                                                                    \
   template void launch_fused_relax<T, N>(int, vec2_t<T>* const*, const T*, const double*, const T*, T*,       \
-                                         vec2_t<T>*, RelaxParams, double*, const vec2_t<T>*, cudaStream_t); \
+                                         vec2_t<T>*, RelaxParams, double*, const vec2_t<T>*, cudaStream_t,  \
+                                         const int*);                                                       \
   template int fused_relax_blocks<T, N>();
 #define DGP_INST_F_ALL(T) DGP_INST_F(T, 16) DGP_INST_F(T, 32) DGP_INST_F(T, 64) DGP_INST_F(T, 128) \
   DGP_INST_F(T, 256) DGP_INST_F(T, 512)

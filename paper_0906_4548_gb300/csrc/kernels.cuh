@@ -44,8 +44,12 @@ struct KParams {
 enum XOp { XOP_HESSIAN = 0, XOP_SOURCE = 1, XOP_SOURCE_LIN = 2, XOP_PHI_FORCE = 3, XOP_PK = 4,
            XOP_SHELL = 5 };
 
+// Every launcher of a kernel that can run inside a relaxation iteration takes
+// skip: NULL, or a device flag read at kernel entry; when it is nonzero the
+// whole grid returns at once (iterations enqueued past the solver's stop).
 template <typename T, int N>
-void launch_fft_y(const FieldSet<T>& f, int nfields, bool inverse, const vec2_t<T>* tw, cudaStream_t s);
+void launch_fft_y(const FieldSet<T>& f, int nfields, bool inverse, const vec2_t<T>* tw, cudaStream_t s,
+                  const int* skip = nullptr);
 
 template <typename T, int N>
 void launch_fft_z_r2c(const T* in, int64_t in_stride, vec2_t<T>* out, int64_t out_stride, int nfields,
@@ -63,7 +67,7 @@ void launch_fft_z_c2r(const FieldSet<T>& in, T* const* out, int nfields, const v
 template <typename T, int N>
 void launch_fft_x_op(int op, const vec2_t<T>* in0, const vec2_t<T>* in1, const FieldSet<T>& out,
                      int nout_mask, const KParams& kp, double* pk_partials, int nbins, double shell_lo,
-                     double shell_hi, const vec2_t<T>* tw, cudaStream_t s);
+                     double shell_hi, const vec2_t<T>* tw, cudaStream_t s, const int* skip = nullptr);
 
 template <typename T, int N> int x_pass_blocks();
 
@@ -86,11 +90,29 @@ struct RelaxParams {
 enum { ARITH_F32 = 0, ARITH_EFT = 1, ARITH_F64 = 2 };
 template <typename T, int N>
 void launch_fused_relax(int arith, vec2_t<T>* const* spec6, const T* D, const double* dsum, const T* S, T* Dnew,
-                        vec2_t<T>* Snew, RelaxParams rp, double* partials, const vec2_t<T>* tw, cudaStream_t s);
+                        vec2_t<T>* Snew, RelaxParams rp, double* partials, const vec2_t<T>* tw, cudaStream_t s,
+                        const int* skip = nullptr);
 template <typename T, int N> int fused_relax_blocks();
 
 // partials[nblocks][ncomp] -> out[ncomp], fixed summation order.
-void launch_finalize(const double* partials, int nblocks, int ncomp, double* out, cudaStream_t s);
+void launch_finalize(const double* partials, int nblocks, int ncomp, double* out, cudaStream_t s,
+                     const int* skip = nullptr);
+
+// Stop rules of the relaxation (Eq. normres, Sec. III.C), applied on the device
+// after each iteration so the host need not wait for every residual.
+enum { CTL_RUNNING = 0, CTL_CONVERGED = 1, CTL_STOPPED = 2, CTL_NONFINITE = 3 };
+struct SolveCtl {
+  int done;      // nonzero once a rule has stopped the solve (the skip flag)
+  int status;    // CTL_*
+  int stop_it;   // last iteration whose residual was examined
+  int best_it;   // iteration whose incoming iterate has the smallest residual
+  double rbest, rprev, prev_nbad, last_bad;
+  double eps, rnorm;  // <|S|> and the normalisation of the residual
+};
+// stats: [sum |R|, sum D_new, bad points, non-finite R] of iteration it;
+// abs_src_sum: sum |S| (read at it = 0); hist[it] receives <|R|> / rnorm.
+void launch_relax_control(SolveCtl* ctl, const double* stats, const double* abs_src_sum, double* hist, int it,
+                          int max_iter, int patience, double tol, double inv_m, cudaStream_t s);
 
 template <typename T>
 void launch_sum(const T* a, int64_t m, bool absval, double* partials, int nblocks, cudaStream_t s);

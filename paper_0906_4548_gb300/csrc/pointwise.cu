@@ -51,7 +51,8 @@ __device__ __forceinline__ void block_sum(double (&v)[NC]) {
 
 // --------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ partials, int nblocks, int ncomp,
-                                                  double* __restrict__ out) {
+                                                  double* __restrict__ out, const int* __restrict__ skip) {
+  if (skip && *skip) return;
   if (ncomp == 4) {  // the relaxation statistics: one pass over the partials
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
@@ -75,17 +76,95 @@ __global__ void __launch_bounds__(256) k_finalize(const double* __restrict__ par
   }
 }
 
-void launch_finalize(const double* partials, int nblocks, int ncomp, double* out, cudaStream_t s) {
-  k_finalize<<<1, 256, 0, s>>>(partials, nblocks, ncomp, out);
+void launch_finalize(const double* partials, int nblocks, int ncomp, double* out, cudaStream_t s,
+                     const int* skip) {
+  k_finalize<<<1, 256, 0, s>>>(partials, nblocks, ncomp, out, skip);
 }
 
+// One thread applies the stop rules of the relaxation to iteration it (the
+// same rules, in the same order, as a host loop would): normalised residual
+// r = <|R|> / eps (absolute when eps = 0) below tol: converged; it = max_iter,
+// a residual rise while bad points were present, or no new minimum for
+// `patience` iterations: stopped with the minimum-residual iterate; a
+// non-finite R or eps: failed.
+__global__ void k_relax_control(SolveCtl* __restrict__ c, const double* __restrict__ stats,
+                                const double* __restrict__ abs_src_sum, double* __restrict__ hist, int it,
+                                int max_iter, int patience, double tol, double inv_m) {
+  if (threadIdx.x != 0 || c->done) return;
+  if (it == 0) {
+    const double eps = abs_src_sum[0] * inv_m;
+    c->eps = eps;
+    c->rnorm = eps > 0.0 ? eps : 1.0;
+    c->rbest = INFINITY;
+    c->rprev = INFINITY;
+    c->prev_nbad = 0.0;
+    c->best_it = -1;
+    if (!isfinite(eps)) {
+      c->status = CTL_NONFINITE;
+      c->stop_it = 0;
+      c->done = 1;
+      return;
+    }
+  }
+  const double r = stats[0] * inv_m / c->rnorm;
+  const double nbad = stats[2];
+  hist[it] = r;
+  c->last_bad = nbad;
+  c->stop_it = it;
+  if (stats[3] > 0.0 || !isfinite(r)) {
+    c->status = CTL_NONFINITE;
+    c->done = 1;
+    return;
+  }
+  if (r < c->rbest) {
+    c->rbest = r;
+    c->best_it = it;
+  }
+  if (r < tol) {
+    c->status = CTL_CONVERGED;
+    c->done = 1;
+    return;
+  }
+  if (it == max_iter || (it > 0 && c->prev_nbad > 0.0 && r > c->rprev) || it - c->best_it >= patience) {
+    c->status = CTL_STOPPED;
+    c->done = 1;
+    return;
+  }
+  c->rprev = r;
+  c->prev_nbad = nbad;
+}
+
+void launch_relax_control(SolveCtl* ctl, const double* stats, const double* abs_src_sum, double* hist, int it,
+                          int max_iter, int patience, double tol, double inv_m, cudaStream_t s) {
+  k_relax_control<<<1, 32, 0, s>>>(ctl, stats, abs_src_sum, hist, it, max_iter, patience, tol, inv_m);
+}
+
+// Per-thread sums of FP32 data run on the FP32 pipe as an unevaluated pair:
+// Knuth's TwoSum keeps every rounding error of the running sum s in c, so
+// s + c is the thread's sum to about 2^-44 relative; the cross-thread and
+// cross-block stages are FP64.  (Per-element FP64 conversion and addition
+// would make the pass FP64-pipe bound on GB300.)
 template <typename T>
 __global__ void __launch_bounds__(256) k_sum(const T* __restrict__ a, int64_t m, int absval,
                                              double* __restrict__ partials) {
   double acc = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = (double)a[i];
-    acc += absval ? fabs(v) : v;
+  if constexpr (sizeof(T) == 4) {
+    float s = 0.f, c = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const float v = absval ? fabsf(a[i]) : a[i];
+      const float t = s + v;
+      const float bb = t - s;
+      c += (s - (t - bb)) + (v - bb);
+      s = t;
+    }
+    acc = (double)s + (double)c;
+  } else {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const double v = (double)a[i];
+      acc += absval ? fabs(v) : v;
+    }
   }
   double v[1] = {acc};
   block_sum<1>(v);
@@ -117,12 +196,29 @@ void launch_product3_sum(const T* a, const T* b, const T* c, int64_t m, double* 
   k_product3<T><<<nblocks, 256, 0, s>>>(a, b, c, m, partials);
 }
 
+// delta = rho / mean - 1; FP32 data use 1 / mean as a float pair (hi + lo),
+// formed once per block, so the per-element work stays on the FP32 pipe.
 template <typename T>
 __global__ void k_density_contrast(const T* __restrict__ rho, T* __restrict__ delta, int64_t m,
                                    const double* __restrict__ sum) {
-  const double inv_mean = (double)m / sum[0];
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
-    delta[i] = (T)((double)rho[i] * inv_mean - 1.0);
+  if constexpr (sizeof(T) == 4) {
+    __shared__ float s_inv[2];
+    if (threadIdx.x == 0) {
+      const double inv = (double)m / sum[0];
+      s_inv[0] = (float)inv;
+      s_inv[1] = (float)(inv - (double)s_inv[0]);
+    }
+    __syncthreads();
+    const float hi = s_inv[0], lo = s_inv[1];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+      delta[i] = fmaf(rho[i], hi, fmaf(rho[i], lo, -1.f));
+  } else {
+    const double inv_mean = (double)m / sum[0];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+      delta[i] = (T)((double)rho[i] * inv_mean - 1.0);
+  }
 }
 
 template <typename T>
@@ -143,9 +239,24 @@ void launch_fill(T* a, int64_t m, T v, cudaStream_t s) {
 
 template <typename T>
 __global__ void k_sub_mean(const T* __restrict__ in, T* __restrict__ out, int64_t m, const double* __restrict__ sum) {
-  const double mean = sum[0] / (double)m;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = (T)((double)in[i] - mean);
+  if constexpr (sizeof(T) == 4) {
+    __shared__ float s_mean[2];
+    if (threadIdx.x == 0) {
+      const double mean = sum[0] / (double)m;
+      s_mean[0] = (float)mean;
+      s_mean[1] = (float)(mean - (double)s_mean[0]);
+    }
+    __syncthreads();
+    const float hi = s_mean[0], lo = s_mean[1];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+      out[i] = (in[i] - hi) - lo;
+  } else {
+    const double mean = sum[0] / (double)m;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+      out[i] = (T)((double)in[i] - mean);
+  }
 }
 
 template <typename T>

@@ -213,6 +213,37 @@ def test_not_converged_reports_best_iterate(dgp, torch_dev):
     assert abs(info["norm_res"] / oinfo["norm_res"] - 1) < 1e-3
 
 
+def test_stop_on_bad_point_divergence_returns_earlier_iterate(dgp, torch_dev):
+    """A strongly nonlinear field (rms 1) gives bad points and a residual rise
+    (Sec. III.C): the solve stops one iteration after its minimum-residual
+    iterate, which the GPU path must hand back (D, phi) exactly as the oracle."""
+    torch, dev = torch_dev
+    n, box, a = 32, 100.0, 0.15
+    d, _ = inputs.linear_field(n, box, -1.5, 1.0, seed=5)
+    phi_o, _, D_o, oinfo = ofield.solve_phi(d, a, box, OM, 1.0, tol=1e-12, max_iter=60)
+    assert not oinfo["converged"] and 0 < oinfo["iters"] < len(oinfo["history"]) - 1
+    ctx = dgp.dgp_init(box, n, 1.0, OM, precision=dgp.DGP_FP64, max_iter=60)
+    try:
+        dd = to_dev(torch_dev, d, torch.float64)
+        phi = torch.empty_like(dd)
+        st, info = dgp.dgp_solve_phi(ctx, a, dd, phi, 1e-12)
+        hist = dgp.dgp_solve_history(ctx)
+        Dt = torch.empty_like(dd)
+        dgp.dgp_get_solution(ctx, Dt)
+        # the next solve starts from the accepted iterate (warm start)
+        st2, info2 = dgp.dgp_solve_phi(ctx, a, dd, None, 1e-12)
+        hist2 = dgp.dgp_solve_history(ctx)
+    finally:
+        dgp.dgp_destroy(ctx)
+    assert st == dgp.DGP_E_NOT_CONVERGED and info["iters"] == oinfo["iters"]
+    assert len(hist) == len(oinfo["history"])
+    assert np.allclose(hist, oinfo["history"], rtol=1e-9, atol=0)
+    assert abs(info["norm_res"] / oinfo["norm_res"] - 1) < 1e-9
+    assert rel_l2(Dt.cpu().numpy(), D_o - D_o.mean()) < 1e-9
+    assert rel_l2(phi.cpu().numpy(), phi_o) < 1e-9
+    assert abs(hist2[0] / info["norm_res"] - 1) < 1e-9
+
+
 def test_pm_run_fp64_matches_oracle(dgp, torch_dev):
     """32^3, 100 Mpc/h, FP64: one solve to 1e-10 at a = 0.05, then 10 KDK steps to a = 0.1."""
     torch, dev = torch_dev

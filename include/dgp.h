@@ -251,6 +251,10 @@ int dgp_power_spectrum_noalloc(const float *delta, int n, double box, int nbins,
  * their bytes.  Any output pointer may be NULL. */
 #define DGP_KERNEL_KINDS 11
 int dgp_profile(dgp_ctx *c, int timing);
+/* As dgp_profile, but only launches of the kinds whose bit is set in
+ * kind_mask (bit k for kind k) are bracketed by events, so the timing of the
+ * others is not perturbed by event records. */
+int dgp_profile_kinds(dgp_ctx *c, unsigned kind_mask);
 int dgp_profile_read(dgp_ctx *c, int kind, int64_t *launches, double *bytes, int64_t *timed, double *ms,
                      double *timed_bytes);
 /* Name of a kernel kind ("fft_z_r2c", "fft_y", "relax", ...), NULL if out of range. */

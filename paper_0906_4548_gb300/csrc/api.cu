@@ -128,7 +128,7 @@ static const char* const kKernelNames[KK_COUNT] = {
     "cic_gather_kick", "misc", "cell_sort"};
 
 struct Profiler {
-  bool timing = false;
+  unsigned timing = 0;  // bit k: launches of kind k are bracketed by events
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
   std::vector<std::pair<int, double>> pending;  // (kind, bytes) per event pair
@@ -138,7 +138,7 @@ struct Profiler {
   int64_t timed[KK_COUNT] = {};
   double timed_bytes[KK_COUNT] = {};
 
-  void reset(bool t) {
+  void reset(unsigned t) {
     resolve();
     timing = t;
     for (int k = 0; k < KK_COUNT; ++k) { launches[k] = 0; bytes[k] = 0; ms[k] = 0; timed[k] = 0; timed_bytes[k] = 0; }
@@ -167,13 +167,13 @@ struct Profiler {
   // bytes of work that launches already counted (with 0 bytes) turned out to do
   void credit(int kind, double b) {
     bytes[kind] += b;
-    if (timing) timed_bytes[kind] += b;
+    if ((timing >> kind) & 1u) timed_bytes[kind] += b;
   }
   template <class F>
   void run(int kind, double b, cudaStream_t s, F&& f) {
     launches[kind] += 1;
     bytes[kind] += b;
-    if (!timing) { f(); return; }
+    if (!((timing >> kind) & 1u)) { f(); return; }
     if (pending.size() >= 8192) resolve();
     cudaEventRecord(ev(), s);
     f();
@@ -912,7 +912,13 @@ int dgp_solve_history(dgp_ctx* c, double* out, int max_n) {
 
 int dgp_profile(dgp_ctx* c, int timing) {
   if (!c) return DGP_E_INVALID;
-  c->eng->prof.reset(timing != 0);
+  c->eng->prof.reset(timing != 0 ? (1u << dgp::KK_COUNT) - 1u : 0u);
+  return DGP_OK;
+}
+
+int dgp_profile_kinds(dgp_ctx* c, unsigned kind_mask) {
+  if (!c) return DGP_E_INVALID;
+  c->eng->prof.reset(kind_mask & ((1u << dgp::KK_COUNT) - 1u));
   return DGP_OK;
 }
 

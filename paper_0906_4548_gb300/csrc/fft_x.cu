@@ -167,6 +167,7 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
   }
 
   constexpr int NT = XGeom<T, N>::THREADS;
+  const T inv_m = kc<T>(kp.inv_m, kp.inv_m_f);
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) {
     const int nx = signed_index(lane + N1 * k2, N);
@@ -176,8 +177,43 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
       inv = (T)1 / (T)n2;
       if (!kp.local_only) ikb = (T)1 / (kc<T>(kp.kbar_fac * 2.0 * M_PI / kp.box, kp.kbkf_f) * sqrt((T)n2));
     }
-    s_inv[k2 * NT + threadIdx.x] = inv;
+    // the Hessian outputs use 1 / (|n|^2 N^3) directly
+    s_inv[k2 * NT + threadIdx.x] = OP == XOP_HESSIAN ? inv * inv_m : inv;
     s_ikb[k2 * NT + threadIdx.x] = ikb;
+  }
+
+  if (OP == XOP_HESSIAN) {
+    // H_ab(k) = (n_a n_b / |n|^2) D(k) for (a, b) = xx, yy, xy, xz, yz with the
+    // absolute value where a component of an off-diagonal pair is on its Nyquist
+    // index (on the diagonal the product is a square anyway), then N = -D / kbar.
+    // The pair of each output is chosen once per output; per element the
+    // multiplier is branch-free.
+    const T fy = (T)ny, fz = (T)nz;
+#pragma unroll 1
+    for (int o = 0; o < 5; ++o) {
+      const bool a_is_x = o == 0 || o == 2 || o == 3;       // first component x, else y
+      const int b_sel = o == 0 ? 0 : (o == 1 || o == 2 ? 1 : 2);  // second: x, y or z
+      const T fb_fixed = b_sel == 1 ? fy : fz;
+      const bool nyq_fixed = (!a_is_x && nyq_y) || (b_sel == 1 && nyq_y) || (b_sel == 2 && nyq_z);
+      V Y[N2];
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        const int kx = lane + N1 * k2;
+        const T fx = (T)signed_index(kx, N);
+        const T fa = a_is_x ? fx : fy;
+        const T fb = b_sel == 0 ? fx : fb_fixed;
+        T prod = fa * fb;
+        const bool nyq = nyq_fixed || ((a_is_x || b_sel == 0) && kx == N / 2);
+        if (nyq) prod = fabs(prod);
+        Y[k2] = cscale(X0[k2], prod * s_inv[k2 * NT + threadIdx.x]);
+      }
+      x_inverse<T, N>(Y, args.out.p[o], kz, ky0, lane, yl, s_T, s_tw);
+    }
+    V Y[N2];
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) Y[k2] = cscale(X0[k2], -s_ikb[k2 * NT + threadIdx.x] * inv_m);
+    x_inverse<T, N>(Y, args.out.p[5], kz, ky0, lane, yl, s_T, s_tw);
+    return;
   }
 
   int nout;
@@ -185,7 +221,6 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
   else if (OP == XOP_SOURCE) nout = 1;
   else if (OP == XOP_SOURCE_LIN || OP == XOP_SHELL) nout = 2;
   else nout = 4;
-  const T inv_m = kc<T>(kp.inv_m, kp.inv_m_f);
   for (int o = 0; o < nout; ++o) {
     if (OP == XOP_PHI_FORCE && !((args.nout_mask >> o) & 1)) continue;
     V Y[N2];

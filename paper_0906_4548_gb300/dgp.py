@@ -22,7 +22,7 @@ C_OVER_H0 = 2997.92458
 EXPORTED = ["dgp_background", "dgp_init", "dgp_destroy", "dgp_strerror", "dgp_reset", "dgp_solve_phi",
             "dgp_solve_forces", "dgp_solve_history", "dgp_get_solution", "dgp_deposit", "pm_step", "pm_step_host", "power_spectrum", "bispectrum",
             "dgp_profile", "dgp_profile_read", "dgp_kernel_name", "dgp_power_spectrum_noalloc",
-            "dgp_sort_particles"]
+            "dgp_sort_particles", "dgp_profile_kinds"]
 DGP_NOALLOC_MAX_N = 64
 DGP_KERNEL_KINDS = 11
 
@@ -86,6 +86,7 @@ def _load():
         "power_spectrum": (i, [vp, vp, i, P(d), P(d), P(i64)]),
         "bispectrum": (i, [vp, vp, d, d, i, P(d), d, P(d), P(d)]),
         "dgp_profile": (i, [vp, i]),
+        "dgp_profile_kinds": (i, [vp, ctypes.c_uint]),
         "dgp_profile_read": (i, [vp, i, P(i64), P(d), P(i64), P(d), P(d)]),
         "dgp_kernel_name": (ctypes.c_char_p, [i]),
         "dgp_power_spectrum_noalloc": (i, [vp, i, d, i, P(d), P(d), P(i64), vp]),
@@ -225,8 +226,17 @@ def bispectrum(ctx, delta, k1, k2, thetas, dk=0.0):
     return b, q
 
 
-def dgp_profile(ctx, timing):
-    _check(lib.dgp_profile(ctx, 1 if timing else 0), "dgp_profile")
+def dgp_profile(ctx, timing, kinds=None):
+    """Reset the kernel counters; time every kind (timing true), none, or only
+    the kinds named in `kinds` (kernel names as returned by dgp_profile_read)."""
+    if kinds is None:
+        _check(lib.dgp_profile(ctx, 1 if timing else 0), "dgp_profile")
+        return
+    names = [lib.dgp_kernel_name(k).decode() for k in range(DGP_KERNEL_KINDS)]
+    mask = 0
+    for kname in kinds:
+        mask |= 1 << names.index(kname)
+    _check(lib.dgp_profile_kinds(ctx, mask), "dgp_profile_kinds")
 
 
 def dgp_profile_read(ctx):

@@ -26,6 +26,8 @@
 // to shared memory with cp.async while the current pair is transformed.
 #include <math.h>
 
+#include <type_traits>
+
 #include "fft_core.cuh"
 #include "kernels.cuh"
 
@@ -54,6 +56,9 @@ __device__ __forceinline__ void fp_acc(FP& s, FP t) {
   s.hi = u.hi;
   s.lo += u.lo + t.lo;
 }
+
+__device__ __forceinline__ FP pair_of(float x) { return FP{x, 0.f}; }
+__device__ __forceinline__ FP pair_of(FP x) { return x; }
 
 // Arithmetic policies.  d is the mean-free D at a point; q accumulates
 // sum_{i<j} (H_ij^2 - H_ii H_jj); R, B', Delta as in the file header.
@@ -199,15 +204,22 @@ template <typename T, int N>
 __device__ __forceinline__ void issue_pair(const vec2_t<T>* __restrict__ A, const vec2_t<T>* __restrict__ B, int x,
                                            int y0, vec2_t<T>* G) {
   using G_ = FGeom<T, N>;
-  constexpr int TY = G_::TY, NK = G_::NK;
-  for (int item = threadIdx.x; item < 2 * NK * TY; item += blockDim.x) {
-    const int f = item / (NK * TY);
-    const int rem = item - f * NK * TY;
-    const int kz = rem / TY, yl = rem % TY;
-    const vec2_t<T>* src = (f == 0 ? A : B) + ((int64_t)kz * N + x) * N + y0 + yl;
-    vec2_t<T>* dst = G + f * NK * (TY + 1) + kz * (TY + 1) + yl;
-    if constexpr (sizeof(T) == 8) cp_async_16(dst, src);
-    else cp_async_8(dst, src);
+  constexpr int TY = G_::TY, NK = G_::NK, THREADS = G_::THREADS;
+  static_assert(THREADS % TY == 0, "each thread copies one column of the tile");
+  constexpr int KZS = THREADS / TY;               // kz rows per round
+  constexpr int ROUNDS = (NK + KZS - 1) / KZS;
+  const int yl = threadIdx.x % TY, kz0 = threadIdx.x / TY;
+#pragma unroll
+  for (int f = 0; f < 2; ++f) {
+    const vec2_t<T>* src = (f == 0 ? A : B) + ((int64_t)kz0 * N + x) * N + y0 + yl;
+    vec2_t<T>* dst = G + f * NK * (TY + 1) + kz0 * (TY + 1) + yl;
+#pragma unroll
+    for (int i = 0; i < ROUNDS; ++i) {
+      if (i < ROUNDS - 1 || kz0 + i * KZS < NK) {
+        if constexpr (sizeof(T) == 8) cp_async_16(dst + i * KZS * (TY + 1), src + (int64_t)i * KZS * N * N);
+        else cp_async_8(dst + i * KZS * (TY + 1), src + (int64_t)i * KZS * N * N);
+      }
+    }
   }
   cp_commit();
 }
@@ -244,7 +256,15 @@ __device__ __forceinline__ void pair_c2r(const vec2_t<T>* G, vec2_t<T>* s_T, con
     for (int j1 = 0; j1 < N1; ++j1) {
       const int k = N2 * j1 + lane;
       V A, B;
-      if (k <= N / 2) {
+      // j1 is a compile-time index: whole blocks of k below or above N/2 need no test
+      if (N2 * j1 + N2 - 1 < N / 2) {
+        A = GA[k * (TY + 1) + row];
+        B = GB[k * (TY + 1) + row];
+        if (j1 == 0 && lane == 0) { A.y = 0; B.y = 0; }
+      } else if (N2 * j1 > N / 2) {
+        A = cconj(GA[(N - k) * (TY + 1) + row]);
+        B = cconj(GB[(N - k) * (TY + 1) + row]);
+      } else if (k <= N / 2) {
         A = GA[k * (TY + 1) + row];
         B = GB[k * (TY + 1) + row];
         if (k == 0 || k == N / 2) { A.y = 0; B.y = 0; }
@@ -406,25 +426,52 @@ __global__ void __launch_bounds__(FGeom<T, N>::THREADS, 2)
     for (int k2 = 0; k2 < N2; ++k2) s_Zf[(fl + N1 * k2) * (P + 1) + fp] = u[k2];
   }
   __syncthreads();
-  for (int item = threadIdx.x; item < NK * TY; item += blockDim.x) {
-    const int kz = item / TY, yl = item % TY;
-    const int p = yl >> 1;
-    const V zk = s_Zf[kz * (P + 1) + p];
-    const V zm = s_Zf[((N - kz) & (N - 1)) * (P + 1) + p];
-    V r;
-    if ((yl & 1) == 0) r = cmake<V>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
-    else r = cmake<V>((T)0.5 * (zk.y + zm.y), (T)-0.5 * (zk.x - zm.x));
-    args.Snew[((int64_t)kz * N + x) * N + y0 + yl] = r;
+  {
+    // thread (kz0, yl) writes kz = kz0, kz0 + KZS, ... of column yl
+    constexpr int THREADS = G_::THREADS, KZS = THREADS / TY, ROUNDS = (NK + KZS - 1) / KZS;
+    const int yl = threadIdx.x % TY, kz0 = threadIdx.x / TY, p = yl >> 1;
+    const bool odd = yl & 1;
+    V* dst = args.Snew + ((int64_t)kz0 * N + x) * N + y0 + yl;
+#pragma unroll
+    for (int i = 0; i < ROUNDS; ++i) {
+      const int kz = kz0 + i * KZS;
+      if (i < ROUNDS - 1 || kz < NK) {
+        const V zk = s_Zf[kz * (P + 1) + p];
+        const V zm = s_Zf[((N - kz) & (N - 1)) * (P + 1) + p];
+        V r;
+        if (!odd) r = cmake<V>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
+        else r = cmake<V>((T)0.5 * (zk.y + zm.y), (T)-0.5 * (zk.x - zm.x));
+        dst[(int64_t)i * KZS * N * N] = r;
+      }
+    }
   }
-  // block statistics (FP64)
+  // block statistics: FP64 across warps; within a warp FP64 for FP64
+  // accumulators, otherwise float pairs (TwoSum) and integer counts
   __shared__ double s_part[4][32];
-  double v4[4] = {AR::to_d(acc_r), (double)acc_d, (double)nbad, (double)nonfin};
   const int wl = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if constexpr (std::is_same<Acc, double>::value || sizeof(T) == 8) {
+    double v4[4] = {AR::to_d(acc_r), (double)acc_d, (double)nbad, (double)nonfin};
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < 4; ++c) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v4[c] += __shfl_xor_sync(0xffffffffu, v4[c], o);
-    if (wl == 0) s_part[c][wid] = v4[c];
+      for (int o = 16; o > 0; o >>= 1) v4[c] += __shfl_xor_sync(0xffffffffu, v4[c], o);
+      if (wl == 0) s_part[c][wid] = v4[c];
+    }
+  } else {
+    FP r2 = pair_of(acc_r), d2{(float)acc_d, 0.f};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      fp_acc(r2, FP{__shfl_xor_sync(0xffffffffu, r2.hi, o), __shfl_xor_sync(0xffffffffu, r2.lo, o)});
+      fp_acc(d2, FP{__shfl_xor_sync(0xffffffffu, d2.hi, o), __shfl_xor_sync(0xffffffffu, d2.lo, o)});
+    }
+    const unsigned nb = __reduce_add_sync(0xffffffffu, (unsigned)nbad);
+    const unsigned nf = __reduce_add_sync(0xffffffffu, (unsigned)nonfin);
+    if (wl == 0) {
+      s_part[0][wid] = (double)r2.hi + (double)r2.lo;
+      s_part[1][wid] = (double)d2.hi + (double)d2.lo;
+      s_part[2][wid] = (double)nb;
+      s_part[3][wid] = (double)nf;
+    }
   }
   __syncthreads();
   if (threadIdx.x < 4) {

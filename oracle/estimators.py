@@ -22,6 +22,7 @@ closed forms tested (a field with known cross-shell content).
 
 import numpy as np
 
+from . import background as bg
 from .fft import fft3, ifft3_real
 from .field import KGrid
 
@@ -43,6 +44,37 @@ def power_spectrum(delta, box, nbins=None):
     ps = np.bincount(bs, weights=p[sel], minlength=nb)
     with np.errstate(invalid="ignore", divide="ignore"):
         return ks / cnt, ps / cnt, cnt
+
+
+def brane_spectra(D, a, box, omega_m0, rc_H0, nbins=None):
+    """Spectra of the brane-bending mode from D = lapbar^2 C (Sec. IV):
+    P_c of the normalised mode c = alpha eta / (3 (eta - 1)) D (Eq. cdef),
+    P_C of C itself, C(k) = -D(k) / kbar^2 with kbar = C_H |k| / (a E), and the
+    dimensionless spectrum of g_4i = grad_i C, Delta(k) = 4 pi k^5 P_C(k)
+    (Eq. DGradC, k the shell's mean |k| in h/Mpc, C dimensionless).  Shells and
+    normalisation as power_spectrum.  Returns (k_mean, P_c, P_C, Delta, n_modes)."""
+    n = D.shape[0]
+    m = n ** 3
+    nb = n // 2 if nbins is None else nbins
+    coef = bg.coefficients(a, omega_m0, rc_H0)
+    grid = KGrid(n, box)
+    kf = 2.0 * np.pi / box
+    Dk = fft3(D)
+    kbar = bg.C_H * np.where(grid.zero, 1.0, grid.kmag) / (a * coef["E"])
+    fac_c = coef["alpha"] * coef["eta"] / (3.0 * (coef["eta"] - 1.0))
+    pc = box ** 3 * np.abs(fac_c * Dk / m) ** 2
+    pC = box ** 3 * np.abs(Dk / kbar ** 2 / m) ** 2
+    b = np.floor(grid.kmag / kf + 0.5).astype(np.int64) * np.ones((n, n, n), np.int64)
+    sel = (b >= 1) & (b <= nb)
+    bs = b[sel] - 1
+    cnt = np.bincount(bs, minlength=nb)
+    ks = np.bincount(bs, weights=(grid.kmag * np.ones((n, n, n)))[sel], minlength=nb)
+    sc = np.bincount(bs, weights=pc[sel], minlength=nb)
+    sC = np.bincount(bs, weights=pC[sel], minlength=nb)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        kmean = ks / cnt
+        PC = sC / cnt
+        return kmean, sc / cnt, PC, 4.0 * np.pi * kmean ** 5 * PC, cnt
 
 
 def _shell(grid, k, dk):

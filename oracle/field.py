@@ -191,6 +191,20 @@ def solve_brane_bending(delta, a, box, omega_m0, rc_H0, w=1.0 / 3.0, tol=1e-12,
     return D, info
 
 
+def spherical_D(delta_k, grid, coef, local_only=False):
+    """Spherical approximation of Eq. FullDGP2 (Sec. IV, Eq. FullDGP2sph): the
+    w = 1/3 relaxation update from C = 0.  There every H_ij and N vanish, so
+    B' = S and the '+' root is D = (-alpha + sqrt(alpha^2 + (8/3) S)) / (4/3)
+    (bad points, Delta < 0, take Delta = 0); S = s (1 - beta/kbar) delta keeps
+    its nonlocal factor.  Returns (D mean-free, D_k, number of bad points)."""
+    S = ifft3_real(source_spectrum(delta_k, grid, coef, local_only))
+    z = np.zeros_like(S)
+    D, nbad = relax_update(z, {p: z for p in PAIRS}, z, S, coef, 1.0 / 3.0)
+    D_k = fft3(D)
+    D_k[grid.zero] = 0.0
+    return ifft3_real(D_k), D_k, nbad
+
+
 def phi_spectrum(delta_k, D_k, grid, coef, local_only=False, gravity="nl"):
     """phi(k) in code units from Eq. FullDGP1 (Sec. II) given delta(k), D(k).
 
@@ -243,6 +257,14 @@ def solve_phi(delta, a, box, omega_m0, rc_H0, w=1.0 / 3.0, tol=1e-12, max_iter=5
                                       D_init, local_only)
         D_k = info["D_k"]
         grid, coef, delta_k = info["grid"], info["coef"], info["delta_k"]
+    elif gravity == "sph":
+        grid = KGrid(delta.shape[0], box)
+        coef = bg.coefficients(a, omega_m0, rc_H0)
+        delta_k = fft3(delta)
+        delta_k[grid.zero] = 0.0
+        D, D_k, nbad = spherical_D(delta_k, grid, coef, local_only)
+        info = dict(iters=1, converged=True, bad=[nbad])
+        gravity = "nl"  # Eq. FullDGP1 with the spherical D
     else:
         grid = KGrid(delta.shape[0], box)
         coef = bg.coefficients(a, omega_m0, rc_H0)

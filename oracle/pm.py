@@ -110,7 +110,7 @@ class PMState:
     """Particle state of the oracle run plus the carried solver state."""
 
     def __init__(self, pos, mom, a, n, box, omega_m0, rc_H0, w=1.0 / 3.0, tol=1e-12,
-                 max_iter=500, gravity="nl", local_only=False):
+                 max_iter=500, gravity="nl", local_only=False, a_nonlinear=0.0):
         self.pos = np.array(pos, dtype=np.float64) % box
         self.mom = np.array(mom, dtype=np.float64)
         self.a = float(a)
@@ -118,6 +118,8 @@ class PMState:
         self.omega_m0, self.rc_H0 = omega_m0, rc_H0
         self.w, self.tol, self.max_iter = w, tol, max_iter
         self.gravity, self.local_only = gravity, local_only
+        # Sec. III.D: the linearised DGP equation before a_nonlinear, the full one after
+        self.a_nonlinear = a_nonlinear
         self.D = None          # warm start: last accepted nonlinear solution
         self.g_part = None     # force at the particles at self.a
         self.solves = []       # info of each field solve
@@ -125,9 +127,10 @@ class PMState:
     def forces_at_particles(self):
         """Deposit -> delta -> field solve -> g = -grad(phi) on the mesh -> CIC gather."""
         delta = density_contrast(cic_deposit(self.pos, self.n, self.box))
+        gravity = "ldgp" if (self.gravity == "nl" and self.a < self.a_nonlinear) else self.gravity
         _, g, D, info = field.solve_phi(delta, self.a, self.box, self.omega_m0, self.rc_H0,
                                         self.w, self.tol, self.max_iter, self.D,
-                                        self.local_only, self.gravity)
+                                        self.local_only, gravity)
         if D is not None:
             self.D = D
         self.solves.append(dict(a=self.a, iters=info.get("iters", 0),

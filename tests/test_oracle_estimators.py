@@ -3,7 +3,9 @@ import itertools
 
 import numpy as np
 
+from oracle import background as bg
 from oracle import estimators as est
+from oracle import field
 from oracle.field import KGrid
 from paper_0906_4548_gb300 import inputs
 
@@ -55,3 +57,39 @@ def test_bispectrum_matches_brute_force_triangle_average():
     assert cnt > 0
     want = box ** 6 / n ** 9 * acc / cnt
     assert abs(B[0] - want) < 1e-10 * abs(want)
+
+
+def test_brane_spectra_of_a_plane_wave():
+    """P_c, P_C and Delta of D = A cos(2 k_f x) from their definitions (Eqs. cdef,
+    DGradC): only the +-k modes of shell 2 carry power."""
+    n, box, a, A = 16, 80.0, 0.5, 0.7
+    x = np.arange(n) * box / n
+    D = A * np.cos(2 * 2 * np.pi / box * x)[:, None, None] * np.ones((n, n, n))
+    k, Pc, PC, Dl, cnt = est.brane_spectra(D, a, box, 0.27, 1.0)
+    coef = bg.coefficients(a, 0.27, 1.0)
+    kk = 2 * 2 * np.pi / box
+    kbar = bg.C_H * kk / (a * coef["E"])
+    fac = coef["alpha"] * coef["eta"] / (3 * (coef["eta"] - 1))
+    # |D_k / M|^2 = A^2 / 4 at each of the two modes
+    assert np.isclose(Pc[1], box ** 3 * fac ** 2 * A ** 2 / 2 / cnt[1], rtol=1e-12)
+    assert np.isclose(PC[1], box ** 3 * (A / kbar ** 2) ** 2 / 2 / cnt[1], rtol=1e-12)
+    assert np.isclose(Dl[1], 4 * np.pi * k[1] ** 5 * PC[1], rtol=1e-12)
+    assert np.all(Pc[np.arange(len(Pc)) != 1] < 1e-25)
+
+
+def test_brane_spectrum_linear_theory_ratio():
+    """In linear theory c_k / delta_k = alpha (1 - beta/kbar) / (alpha - c2/kbar)
+    (Sec. IV: P_c / P_m -> 1 once kbar >> 1), here for a plane wave delta."""
+    from oracle.fft import fft3, ifft3_real
+    n, box, a = 16, 60.0, 0.6
+    grid = KGrid(n, box)
+    coef = bg.coefficients(a, 0.27, 1.0)
+    kk = 3 * 2 * np.pi / box
+    x = np.arange(n) * box / n
+    d = 0.1 * np.cos(kk * x)[None, :, None] * np.ones((n, n, n))
+    D = ifft3_real(field.linear_D_spectrum(field.source_spectrum(fft3(d), grid, coef), grid, coef))
+    k, Pc, PC, Dl, cnt = est.brane_spectra(D, a, box, 0.27, 1.0)
+    _, Pd, _ = est.power_spectrum(d, box)
+    kbar = bg.C_H * kk / (a * coef["E"])
+    ratio = (coef["alpha"] * (1 - coef["beta"] / kbar) / (coef["alpha"] - coef["c2"] / kbar)) ** 2
+    assert abs(Pc[2] / Pd[2] - ratio) < 1e-12 * ratio

@@ -8,6 +8,7 @@ import pytest
 from oracle import background as bg
 from oracle import field
 from oracle.fft import fft3, ifft3_real
+from paper_0906_4548_gb300 import inputs
 
 OM = 0.27
 
@@ -234,3 +235,38 @@ def test_force_is_minus_gradient_of_phi_single_mode():
     want = amp * k * np.sin(k * y)[None, :, None] * np.ones((n, n, n))  # -d/dy
     assert np.max(np.abs(g[1] - want)) < 1e-12 * abs(amp * k)
     assert np.max(np.abs(g[0])) < 1e-14 and np.max(np.abs(g[2])) < 1e-14
+
+
+def test_spherical_mode_local_is_sphpoi():
+    """Sec. IV: with the nonlocal terms dropped, phi of the spherical mode obeys
+    Eq. SphPoi pointwise (for the mean-free density the solver sees)."""
+    n, box, a = 16, 50.0, 0.4
+    rng = np.random.default_rng(3)
+    d = rng.uniform(0.0, 1.6, (n, n, n))  # delta - mean >= -1: no bad points for w = 1/3 (Sec. III.C)
+    phi, g, D, info = field.solve_phi(d, a, box, OM, 1.0, local_only=True, gravity="sph")
+    coef = bg.coefficients(a, OM, 1.0)
+    eta, alpha, E = coef["eta"], coef["alpha"], coef["E"]
+    assert info["bad"] == [0]
+    dm = d - d.mean()
+    sph = 1.5 * (eta - 1) / eta * dm - (1 / (2 * eta)) * (3 * alpha / 4) * (
+        np.sqrt(1 + 8 / alpha ** 2 * (eta - 1) / eta * dm) - 1)
+    grid = field.KGrid(n, box)
+    lap = -grid.k2 * fft3(phi) / (a * E) ** 2   # = FFT of lapbar^2 phi in these units
+    want = fft3(sph)
+    want[grid.zero] = 0.0
+    assert np.max(np.abs(lap - want)) < 1e-10 * np.max(np.abs(want))
+
+
+def test_spherical_mode_is_first_w13_update_with_nonlocal_source():
+    """Sec. IV: including the nonlocal terms, the spherical D is the first
+    iterate of the full w = 1/3 FFT-relaxation started from C = 0."""
+    n, box, a = 16, 50.0, 0.3
+    d, _ = inputs.linear_field(n, box, -1.5, 0.2, seed=4)  # min delta > -1: no bad points
+    coef = bg.coefficients(a, OM, 1.0)
+    grid = field.KGrid(n, box)
+    dk = fft3(d)
+    dk[grid.zero] = 0
+    Dsph, _, nbad = field.spherical_D(dk, grid, coef)
+    D1, info = field.solve_brane_bending(d, a, box, OM, 1.0, D_init=np.zeros_like(d), max_iter=1, tol=0.0)
+    assert nbad == 0 and info["iters"] == 1  # the update lowered the residual of C = 0
+    assert np.max(np.abs(D1 - Dsph)) < 1e-13 * np.max(np.abs(Dsph))

@@ -117,3 +117,23 @@ def test_linear_growth_of_low_amplitude_wave(gravity, geff):
     disp = ((st.pos[0] - qx.reshape(-1) + box / 2) % box) - box / 2
     growth_sim = np.sum(disp * np.sin(k * qx.reshape(-1))) / np.sum(psi.reshape(-1) * np.sin(k * qx.reshape(-1)))
     assert abs(growth_sim / (D1 / D0) - 1) < 5e-3, (growth_sim, D1 / D0)
+
+
+def test_linear_switch_epoch():
+    """Sec. III.D: before a_nonlinear the linearised DGP equation is used; a
+    switch after the run's end reproduces the lDGP run, a switch at a = 0 the
+    nonlinear run, and a switch inside it solves nonlinearly only from there."""
+    n, box = 16, 60.0
+    pos, mom = inputs.lattice_particles(n, box)
+    rng = np.random.default_rng(3)
+    pos = (pos + rng.normal(0, 1.0, pos.shape)) % box
+    kw = dict(tol=1e-10, max_iter=200)
+    late = pm.run(pos, mom, 0.1, 0.2, 3, n, box, OM, 1.0, a_nonlinear=1.0, **kw)
+    ldgp = pm.run(pos, mom, 0.1, 0.2, 3, n, box, OM, 1.0, gravity="ldgp", **kw)
+    assert np.array_equal(late.pos, ldgp.pos) and np.array_equal(late.mom, ldgp.mom)
+    early = pm.run(pos, mom, 0.1, 0.2, 3, n, box, OM, 1.0, a_nonlinear=0.0, **kw)
+    nl = pm.run(pos, mom, 0.1, 0.2, 3, n, box, OM, 1.0, **kw)
+    assert np.array_equal(early.pos, nl.pos)
+    mid = pm.run(pos, mom, 0.1, 0.2, 3, n, box, OM, 1.0, a_nonlinear=0.15, **kw)
+    assert [s["a"] < 0.15 for s in mid.solves] == [s["iters"] == 0 for s in mid.solves]
+    assert not np.array_equal(mid.pos, nl.pos) and not np.array_equal(mid.pos, ldgp.pos)

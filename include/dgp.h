@@ -61,7 +61,12 @@ typedef enum {
  *                 floats with error-free transformations (TwoSum, FMA TwoProd),
  *                 ~48 significant bits, without the FP64 pipe. */
 enum { DGP_FP32 = 0, DGP_MIXED = 1, DGP_FP64 = 2, DGP_MIXED_EFT = 3 };
-enum { DGP_GRAVITY_NL = 0, DGP_GRAVITY_LDGP = 1, DGP_GRAVITY_GRH = 2 };
+/* Gravity modes: the full nonlinear DGP equations (Eqs. FullDGP1-2), the
+ * linearised DGP Poisson equation (Eq. LinearDGP), GR with the DGP expansion
+ * (Eq. GRPoisson), and the spherical approximation of Sec. IV: Eq. FullDGP2sph
+ * solved by one w = 1/3 relaxation update from C = 0 (Eq. SphPoi locally;
+ * the nonlocal factor of the source is kept, N[C = 0] = 0), then Eq. FullDGP1. */
+enum { DGP_GRAVITY_NL = 0, DGP_GRAVITY_LDGP = 1, DGP_GRAVITY_GRH = 2, DGP_GRAVITY_SPH = 3 };
 
 typedef struct dgp_ctx dgp_ctx;
 
@@ -76,12 +81,15 @@ typedef struct {
   double rc_H0;      /* crossover scale r_c in units of c/H0, > 0 (Sec. II) */
   double w;          /* splitting parameter of Eq. FullDGP2wpara, 0 <= w < 1 */
   int precision;     /* DGP_FP32, DGP_MIXED, DGP_FP64 or DGP_MIXED_EFT */
-  int gravity;       /* DGP_GRAVITY_NL (Eqs. FullDGP1-2), _LDGP (Eq. LinearDGP), _GRH (Eq. GRPoisson) */
+  int gravity;       /* DGP_GRAVITY_NL (Eqs. FullDGP1-2), _LDGP (Eq. LinearDGP), _GRH (Eq. GRPoisson),
+                        _SPH (spherical approximation, Sec. IV) */
   int local_only;    /* nonzero: drop the sqrt(-lapbar) terms (Appendix Eq. FullDGP2simp) */
   int max_iter;      /* relaxation updates per solve before giving up, >= 0 */
   double tol;        /* normalised-residual tolerance used by pm_step (Eq. normres) */
   int sort_every;    /* >= 0; nonzero: every sort_every-th pm_step call cell-sorts the
                         particles after its drift (dgp_sort_particles); 0: never */
+  double a_nonlinear; /* >= 0; with DGP_GRAVITY_NL, solves at a < a_nonlinear use the
+                        linearised equation (Sec. III.D switches at a ~ 0.1); 0: never */
 } dgp_params;
 
 typedef struct {
@@ -162,6 +170,18 @@ int dgp_get_solution(dgp_ctx *c, void *D);
  * contrast delta = rho / rho_bar - 1 (rho_bar: FP64 mean of the mesh).
  * delta: device n^3 output.  Positions outside [0, box) are wrapped. */
 int dgp_deposit(dgp_ctx *c, const dgp_particles *parts, void *delta);
+
+/* Spectra of the brane-bending mode C of the context's accepted nonlinear
+ * solution D = lapbar^2 C, at the scale factor of that solve (Sec. IV):
+ *   pc[b]:  P_c of c = alpha eta / (3 (eta - 1)) D (Eq. cdef; P_c / P_m -> 1 on
+ *           linear scales, suppressed by the Vainshtein mechanism);
+ *   pC[b]:  P_C of C, C(k) = -D(k) / kbar^2 with kbar = (c/H0) |k| / (a E);
+ *   delta_gradc[b]: 4 pi k^5 P_C(k) (Eq. DGradC; C dimensionless, k the
+ *           shell's mean |k| in h/Mpc).
+ * Shells, k[b] and nmodes[b] as power_spectrum (host outputs, 1 <= nbins <= n/2).
+ * DGP_E_STATE if no nonlinear solve has been accepted since init/reset. */
+int dgp_brane_spectra(dgp_ctx *c, int nbins, double *k, double *pc, double *pC, double *delta_gradc,
+                      int64_t *nmodes);
 
 /* Counting sort of the particles by mesh cell, in place (support for the CIC
  * assignment of Sec. III.A; the paper deposits particles in storage order).

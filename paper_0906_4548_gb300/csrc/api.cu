@@ -196,6 +196,7 @@ class EngineBase {
                     dgp_solve_info* info) = 0;
   virtual int deposit(const dgp_particles* parts, void* delta) = 0;
   virtual int sort(dgp_particles* parts, int* cell_start) = 0;
+  virtual int brane(int nbins, double* k, double* pc, double* pC, double* dgc, int64_t* nmodes) = 0;
   virtual int step(dgp_particles* parts, double a, double da, dgp_solve_info* info) = 0;
   virtual int step_host(dgp_particles* parts, double a, double da, dgp_solve_info* info) = 0;
   virtual int pk(const void* delta, int nbins, double* k, double* pk, int64_t* nmodes) = 0;
@@ -250,6 +251,7 @@ class Engine : public EngineBase {
   SolveCtl* h_ctl = nullptr;    // pinned host copy
   double* d_hist = nullptr;     // [max_iter + 1] normalised residuals of the running solve
   int last_stop_it = -1;        // last iteration examined by the previous solve
+  double last_nl_a = -1.0;      // scale factor of the last nonlinear solve
   static constexpr int kPatience = 10;  // iterations without a new minimum before stopping
   static constexpr int kChunk = 4;      // iterations enqueued per verdict after the first chunk
   T* hp[6] = {};                // device copies for pm_step_host
@@ -303,8 +305,8 @@ class Engine : public EngineBase {
     if (cudaMallocHost(&h_ctl, sizeof(SolveCtl)) != cudaSuccess) return DGP_E_NOMEM;
     if (cudaMalloc(&d_hist, sizeof(double) * ((size_t)p.max_iter + 1)) != cudaSuccess) return DGP_E_NOMEM;
     pk_blocks = x_pass_blocks<T, N>();
-    if (cudaMalloc(&pk_partials, sizeof(double) * 3 * (N / 2) * (size_t)pk_blocks) != cudaSuccess) return DGP_E_NOMEM;
-    if (cudaMalloc(&d_pk, sizeof(double) * 3 * (N / 2)) != cudaSuccess) return DGP_E_NOMEM;
+    if (cudaMalloc(&pk_partials, sizeof(double) * 4 * (N / 2) * (size_t)pk_blocks) != cudaSuccess) return DGP_E_NOMEM;
+    if (cudaMalloc(&d_pk, sizeof(double) * 4 * (N / 2)) != cudaSuccess) return DGP_E_NOMEM;
     // twiddles W_N^t = exp(-2 pi i t / N), computed in FP64 and rounded once
     // and the two phase tables of the four-step split N = N1 * N2 (see fft_core.cuh)
     constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
@@ -329,6 +331,7 @@ class Engine : public EngineBase {
 
   void reset() override {
     wcur = -1;
+    last_nl_a = -1.0;
     last_stop_it = -1;
     force_valid = false;
     nsteps = 0;
@@ -345,7 +348,7 @@ class Engine : public EngineBase {
   }
 
  private:
-  KParams kparams(const Coef& c) const {
+  KParams kparams(const Coef& c, int gravity) const {
     KParams kp;
     kp.box = p.box;
     kp.inv_m = 1.0 / (double)M;
@@ -353,7 +356,9 @@ class Engine : public EngineBase {
     kp.local_only = p.local_only;
     kp.eta = c.eta; kp.alpha = c.alpha; kp.beta = c.beta; kp.s = c.s; kp.c2 = c.c2; kp.c3 = c.c3;
     kp.aE = c.a * c.E; kp.q = c.q; kp.rc_H0 = p.rc_H0; kp.a = c.a;
-    kp.gravity = p.gravity;
+    // the phi operation takes the nonlinear form (with a D spectrum) for the
+    // nonlinear and the spherical modes
+    kp.gravity = gravity == DGP_GRAVITY_SPH ? DGP_GRAVITY_NL : gravity;
     const double kf = 2.0 * M_PI / p.box;
     kp.kf_f = (float)kf;
     kp.inv_m_f = (float)kp.inv_m;
@@ -409,8 +414,10 @@ class Engine : public EngineBase {
   int solve_impl(double a, const T* src, bool from_rho, T* phi, T* g0, T* g1, T* g2, double tol,
                  dgp_solve_info* info) {
     int rc;
+    // Sec. III.D: the linearised DGP equation before a_nonlinear
+    const int grav = (p.gravity == DGP_GRAVITY_NL && a < p.a_nonlinear) ? DGP_GRAVITY_LDGP : p.gravity;
     const Coef c = coefficients(a, cosmo.omega_m0, p.rc_H0);
-    const KParams kp = kparams(c);
+    const KParams kp = kparams(c, grav);
     ZPrologue pro{nullptr, 1.0 / (double)M, 0};
     if (from_rho) {
       if ((rc = reduce_sum(src, false, d_misc + 0))) return rc;
@@ -424,7 +431,27 @@ class Engine : public EngineBase {
     int accepted = -1;
     int status = DGP_OK;
 
-    if (p.gravity == DGP_GRAVITY_NL) {
+    if (grav == DGP_GRAVITY_SPH) {
+      // one w = 1/3 update from C = 0 (Eq. FullDGP2sph): source, pointwise root
+      prof.run(KK_X_OTHER, SB * 2, stream, [&] {
+        launch_fft_x_op<T, N>(XOP_SOURCE, sDelta, nullptr, fs(s6, 1), 0, kp, nullptr, 0, 0, 0, tw, stream);
+      });
+      T* outs[1] = {rS};
+      if ((rc = inverse_yz(s6, outs, 1))) return rc;
+      prof.run(KK_RELAX, 2 * RB, stream,
+               [&] { launch_sph_update<T>(rS, rH[0], M, c.alpha, partials, nblocks, stream); });
+      prof.run(KK_REDUCE, 8.0 * nblocks, stream, [&] { launch_finalize(partials, nblocks, 1, d_misc + 3, stream); });
+      DGP_CHECK_LAUNCH();
+      if ((rc = forward_zy(rH[0], sD, ZPrologue{nullptr, 0.0, 0}))) return rc;
+      if ((rc = fetch(d_misc + 3, 1))) return rc;
+      sDphi = sD;
+      inf.iters = 1;
+      inf.bad_fraction = h_stats[0] / (double)M;
+      inf.status = DGP_OK;
+    }
+
+    if (grav == DGP_GRAVITY_NL) {
+      last_nl_a = a;
       const bool need_lin = wcur < 0;
       prof.run(KK_X_OTHER, SB * (need_lin ? 3 : 2), stream, [&] {
         launch_fft_x_op<T, N>(need_lin ? XOP_SOURCE_LIN : XOP_SOURCE, sDelta, nullptr, fs(s6, 2), 0, kp, nullptr, 0,
@@ -554,7 +581,7 @@ class Engine : public EngineBase {
     if (phi) mask |= 1;
     if (g0) mask |= 14;
     if (mask) {
-      const int nin = p.gravity == DGP_GRAVITY_NL ? 2 : 1;
+      const int nin = (grav == DGP_GRAVITY_NL || grav == DGP_GRAVITY_SPH) ? 2 : 1;
       prof.run(KK_X_OTHER, SB * (nin + __builtin_popcount(mask)), stream, [&] {
         launch_fft_x_op<T, N>(XOP_PHI_FORCE, sDelta, sDphi, fs(outs, 4), mask, kp, nullptr, 0, 0, 0, tw, stream);
       });
@@ -727,7 +754,7 @@ class Engine : public EngineBase {
     int rc;
     if ((rc = forward_zy((const T*)delta, s6[0], ZPrologue{nullptr, 0.0, 0}))) return rc;
     const Coef c = coefficients(1.0, cosmo.omega_m0, p.rc_H0);
-    KParams kp = kparams(c);
+    KParams kp = kparams(c, p.gravity);
     prof.run(KK_X_OTHER, SB, stream, [&] {
       launch_fft_x_op<T, N>(XOP_PK, s6[0], nullptr, fs(s6, 0), 0, kp, pk_partials, nbins, 0, 0, tw, stream);
     });
@@ -746,6 +773,39 @@ class Engine : public EngineBase {
     return DGP_OK;
   }
 
+  // Spectra of the brane-bending mode of the accepted solution (Sec. IV):
+  // P_c of c = alpha eta / (3 (eta - 1)) D, P_C of C = -D / kbar^2 and
+  // Delta = 4 pi k^5 P_C, at the scale factor of the last nonlinear solve.
+  int brane(int nbins, double* k, double* pc, double* pC, double* dgc, int64_t* nmodes) override {
+    if (nbins < 1 || nbins > N / 2 || !k || !pc || !pC || !dgc || !nmodes) return DGP_E_INVALID;
+    if (wcur < 0 || !(last_nl_a > 0.0)) return DGP_E_STATE;
+    int rc;
+    if ((rc = forward_zy(rD[wcur], s6[0], ZPrologue{nullptr, 0.0, 0}))) return rc;
+    const Coef c = coefficients(last_nl_a, cosmo.omega_m0, p.rc_H0);
+    const KParams kp = kparams(c, p.gravity);
+    prof.run(KK_X_OTHER, SB, stream, [&] {
+      launch_fft_x_op<T, N>(XOP_PK_BRANE, s6[0], nullptr, fs(s6, 0), 0, kp, pk_partials, nbins, 0, 0, tw, stream);
+    });
+    prof.run(KK_REDUCE, 32.0 * nbins * pk_blocks, stream,
+             [&] { launch_finalize(pk_partials, pk_blocks, 4 * nbins, d_pk, stream); });
+    DGP_CHECK_LAUNCH();
+    double hb[4 * 256];
+    DGP_CUDA(cudaMemcpyAsync(hb, d_pk, sizeof(double) * 4 * nbins, cudaMemcpyDeviceToHost, stream));
+    DGP_CUDA(cudaStreamSynchronize(stream));
+    const double fac_c = c.alpha * c.eta / (3.0 * (c.eta - 1.0));
+    const double kbf = cosmo.c_over_H0 / (c.a * c.E) * 2.0 * M_PI / p.box;  // kbar = kbf |n|
+    const double kbf4 = kbf * kbf * kbf * kbf;
+    for (int b = 0; b < nbins; ++b) {
+      const double cnt = hb[b];
+      nmodes[b] = (int64_t)llround(cnt);
+      k[b] = cnt > 0 ? hb[nbins + b] / cnt : NAN;
+      pc[b] = cnt > 0 ? fac_c * fac_c * hb[2 * nbins + b] / cnt : NAN;
+      pC[b] = cnt > 0 ? hb[3 * nbins + b] / cnt / kbf4 : NAN;
+      dgc[b] = cnt > 0 ? 4.0 * M_PI * pow(k[b], 5) * pC[b] : NAN;
+    }
+    return DGP_OK;
+  }
+
   int bispec(const void* delta, double k1, double k2, int ntheta, const double* theta, double dk, double* b,
              double* q) override {
     if (!delta || ntheta < 0 || (ntheta > 0 && (!theta || !b || !q)) || !(k1 > 0) || !(k2 > 0))
@@ -756,7 +816,7 @@ class Engine : public EngineBase {
     // delta's S2 in s6[5]; each shell uses s6[0..1] and two real fields
     if ((rc = forward_zy((const T*)delta, s6[5], ZPrologue{nullptr, 0.0, 0}))) return rc;
     const Coef c = coefficients(1.0, cosmo.omega_m0, p.rc_H0);
-    const KParams kp = kparams(c);
+    const KParams kp = kparams(c, p.gravity);
     auto shell = [&](double kc, T* d, T* ind) -> int {
       prof.run(KK_X_OTHER, 3 * SB, stream, [&] {
         launch_fft_x_op<T, N>(XOP_SHELL, s6[5], nullptr, fs(s6, 2), 0, kp, nullptr, 0, (kc - 0.5 * dk) / kf,
@@ -852,7 +912,8 @@ int dgp_init(dgp_ctx** out, const dgp_params* p, const dgp_cosmology* cosmo, voi
       !isfinite(p->tol) || p->sort_every < 0)
     return DGP_E_INVALID;
   if (p->precision < DGP_FP32 || p->precision > DGP_MIXED_EFT) return DGP_E_INVALID;
-  if (p->gravity < DGP_GRAVITY_NL || p->gravity > DGP_GRAVITY_GRH) return DGP_E_INVALID;
+  if (p->gravity < DGP_GRAVITY_NL || p->gravity > DGP_GRAVITY_SPH) return DGP_E_INVALID;
+  if (!(p->a_nonlinear >= 0.0) || !isfinite(p->a_nonlinear)) return DGP_E_INVALID;
   if (!(cosmo->omega_m0 > 0) || !(cosmo->c_over_H0 > 0)) return DGP_E_INVALID;
   dgp::EngineBase* e = p->precision == DGP_FP64 ? dgp::make_engine<double>(n) : dgp::make_engine<float>(n);
   if (!e) return DGP_E_NOMEM;
@@ -944,6 +1005,12 @@ const char* dgp_kernel_name(int kind) {
 int dgp_deposit(dgp_ctx* c, const dgp_particles* parts, void* delta) {
   if (!c) return DGP_E_INVALID;
   return c->eng->deposit(parts, delta);
+}
+
+int dgp_brane_spectra(dgp_ctx* c, int nbins, double* k, double* pc, double* pC, double* delta_gradc,
+                      int64_t* nmodes) {
+  if (!c) return DGP_E_INVALID;
+  return c->eng->brane(nbins, k, pc, pC, delta_gradc, nmodes);
 }
 
 int dgp_sort_particles(dgp_ctx* c, dgp_particles* parts, int32_t* cell_start) {

@@ -124,8 +124,9 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
   T* s_ikb = s_inv + N2 * XGeom<T, N>::THREADS;                // N2 * THREADS
   double* s_bins = reinterpret_cast<double*>(s_ikb + N2 * XGeom<T, N>::THREADS);
   load_twiddles(s_tw, g_tw, N);
-  if (OP == XOP_PK)
-    for (int i = threadIdx.x; i < 3 * args.nbins; i += blockDim.x) s_bins[i] = 0.0;
+  constexpr int NBS = OP == XOP_PK_BRANE ? 4 : 3;  // sums per shell
+  if (OP == XOP_PK || OP == XOP_PK_BRANE)
+    for (int i = threadIdx.x; i < NBS * args.nbins; i += blockDim.x) s_bins[i] = 0.0;
   const int yl = threadIdx.x % TY;
   const int lane = threadIdx.x / TY;
   const int kz = blockIdx.y;
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
   x_forward<T, N>(args.in0, kz, ky0, lane, yl, s_T, s_tw, X0);
   if (OP == XOP_PHI_FORCE && kp.gravity == 0) x_forward<T, N>(args.in1, kz, ky0, lane, yl, s_T, s_tw, X1);
 
-  if (OP == XOP_PK) {
+  if (OP == XOP_PK || OP == XOP_PK_BRANE) {
     const double norm = kp.box * kp.box * kp.box * kp.inv_m * kp.inv_m;
     const double w = (kz == 0 || kz == N / 2) ? 1.0 : 2.0;
 #pragma unroll
@@ -157,12 +158,13 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
         atomicAdd(&s_bins[b - 1], w);
         atomicAdd(&s_bins[args.nbins + b - 1], w * nm * (2.0 * M_PI / kp.box));
         atomicAdd(&s_bins[2 * args.nbins + b - 1], w * p);
+        if (OP == XOP_PK_BRANE) atomicAdd(&s_bins[3 * args.nbins + b - 1], w * p / ((double)n2 * (double)n2));
       }
     }
     __syncthreads();
     const int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
-    for (int i = threadIdx.x; i < 3 * args.nbins; i += blockDim.x)
-      args.pk_partials[blk * 3 * args.nbins + i] = s_bins[i];
+    for (int i = threadIdx.x; i < NBS * args.nbins; i += blockDim.x)
+      args.pk_partials[blk * NBS * args.nbins + i] = s_bins[i];
     return;
   }
 
@@ -293,7 +295,8 @@ template <typename T, int N, int OP>
 static void launch_x(const XArgs<T>& a, const vec2_t<T>* tw, cudaStream_t s) {
   using G = XGeom<T, N>;
   const size_t smem = sizeof(vec2_t<T>) * (kTwiddleTables * N + (size_t)N * G::TY) +
-                      sizeof(T) * 2 * Split<N>::N2 * G::THREADS + (OP == XOP_PK ? sizeof(double) * 3 * a.nbins : 0);
+                      sizeof(T) * 2 * Split<N>::N2 * G::THREADS + (OP == XOP_PK ? sizeof(double) * 3 * a.nbins : 0) +
+                      (OP == XOP_PK_BRANE ? sizeof(double) * 4 * a.nbins : 0);
   cudaFuncSetAttribute(k_fft_x<T, N, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid(N / G::TY, N / 2 + 1);
   k_fft_x<T, N, OP><<<grid, G::THREADS, smem, s>>>(a, tw);
@@ -313,6 +316,7 @@ void launch_fft_x_op(int op, const vec2_t<T>* in0, const vec2_t<T>* in1, const F
     case XOP_SOURCE_LIN: launch_x<T, N, XOP_SOURCE_LIN>(a, tw, s); break;
     case XOP_PHI_FORCE: launch_x<T, N, XOP_PHI_FORCE>(a, tw, s); break;
     case XOP_PK: launch_x<T, N, XOP_PK>(a, tw, s); break;
+    case XOP_PK_BRANE: launch_x<T, N, XOP_PK_BRANE>(a, tw, s); break;
     case XOP_SHELL: launch_x<T, N, XOP_SHELL>(a, tw, s); break;
     default: break;
   }

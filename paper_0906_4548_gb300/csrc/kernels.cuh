@@ -42,7 +42,7 @@ struct KParams {
 };
 
 enum XOp { XOP_HESSIAN = 0, XOP_SOURCE = 1, XOP_SOURCE_LIN = 2, XOP_PHI_FORCE = 3, XOP_PK = 4,
-           XOP_SHELL = 5 };
+           XOP_SHELL = 5, XOP_PK_BRANE = 6 };
 
 // Every launcher of a kernel that can run inside a relaxation iteration takes
 // skip: NULL, or a device flag read at kernel entry; when it is nonzero the
@@ -61,7 +61,9 @@ void launch_fft_z_c2r(const FieldSet<T>& in, T* const* out, int nfields, const v
 
 // x-pass: forward x transform of nin input spectra, op, inverse x transform of
 // each of the op's outputs.  For XOP_PK, outputs are the per-block bin
-// partials (pk_partials, 3 * nbins doubles per block).  For XOP_SHELL the
+// partials (pk_partials, 3 * nbins doubles per block: modes, sum |k|,
+// sum |X|^2 box^3 / N^6); XOP_PK_BRANE adds sum |X|^2 box^3 / N^6 / |n|^4
+// (4 * nbins per block).  For XOP_SHELL the
 // op is a shell indicator on |k| (shell_lo <= |k|/k_f < shell_hi) applied to
 // input 0 (out 0) and the indicator itself (out 1).
 template <typename T, int N>
@@ -93,6 +95,12 @@ void launch_fused_relax(int arith, vec2_t<T>* const* spec6, const T* D, const do
                         vec2_t<T>* Snew, RelaxParams rp, double* partials, const vec2_t<T>* tw, cudaStream_t s,
                         const int* skip = nullptr);
 template <typename T, int N> int fused_relax_blocks();
+
+// Spherical approximation (Eq. FullDGP2sph): the w = 1/3 update from C = 0,
+// D = 2 S / (alpha + sqrt(alpha^2 + (8/3) S)), bad points (Delta < 0) take
+// D = -3 alpha / 4.  partials[b] = bad points of block b (nblocks blocks).
+template <typename T>
+void launch_sph_update(const T* S, T* D, int64_t m, double alpha, double* partials, int nblocks, cudaStream_t s);
 
 // partials[nblocks][ncomp] -> out[ncomp], fixed summation order.
 void launch_finalize(const double* partials, int nblocks, int ncomp, double* out, cudaStream_t s,

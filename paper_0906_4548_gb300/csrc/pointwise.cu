@@ -264,7 +264,33 @@ void launch_sub_mean(const T* in, T* out, int64_t m, const double* sum, cudaStre
   k_sub_mean<T><<<num_sms() * 4, 256, 0, s>>>(in, out, m, sum);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_sph_update(const T* __restrict__ S, T* __restrict__ D, int64_t m, T alpha,
+                                                    T alpha2, double* __restrict__ partials) {
+  const T eight_thirds = (T)8 / (T)3, bad_d = (T)-0.75 * alpha;
+  double nbad = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const T s = S[i];
+    const T disc = alpha2 + eight_thirds * s;
+    if (disc < (T)0) {
+      D[i] = bad_d;
+      nbad += 1.0;
+    } else {
+      D[i] = (T)2 * s / (alpha + sqrt(disc));
+    }
+  }
+  double v[1] = {nbad};
+  block_sum<1>(v);
+  if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
+}
+
+template <typename T>
+void launch_sph_update(const T* S, T* D, int64_t m, double alpha, double* partials, int nblocks, cudaStream_t s) {
+  k_sph_update<T><<<nblocks, 256, 0, s>>>(S, D, m, (T)alpha, (T)(alpha * alpha), partials);
+}
+
 #define DGP_INST_PW(T)                                                                         \
+  template void launch_sph_update<T>(const T*, T*, int64_t, double, double*, int, cudaStream_t); \
   template void launch_sum<T>(const T*, int64_t, bool, double*, int, cudaStream_t);            \
   template void launch_product3_sum<T>(const T*, const T*, const T*, int64_t, double*, int,    \
                                        cudaStream_t);                                          \

@@ -16,13 +16,13 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 DGP_OK, DGP_E_INVALID, DGP_E_CUDA, DGP_E_NOMEM, DGP_E_NONFINITE = 0, 1, 2, 3, 4
 DGP_E_NOT_CONVERGED, DGP_E_BAD_POINTS, DGP_E_TIMEOUT, DGP_E_STATE = 5, 6, 7, 8
 DGP_FP32, DGP_MIXED, DGP_FP64, DGP_MIXED_EFT = 0, 1, 2, 3
-DGP_GRAVITY_NL, DGP_GRAVITY_LDGP, DGP_GRAVITY_GRH = 0, 1, 2
+DGP_GRAVITY_NL, DGP_GRAVITY_LDGP, DGP_GRAVITY_GRH, DGP_GRAVITY_SPH = 0, 1, 2, 3
 C_OVER_H0 = 2997.92458
 
 EXPORTED = ["dgp_background", "dgp_init", "dgp_destroy", "dgp_strerror", "dgp_reset", "dgp_solve_phi",
             "dgp_solve_forces", "dgp_solve_history", "dgp_get_solution", "dgp_deposit", "pm_step", "pm_step_host", "power_spectrum", "bispectrum",
             "dgp_profile", "dgp_profile_read", "dgp_kernel_name", "dgp_power_spectrum_noalloc",
-            "dgp_sort_particles", "dgp_profile_kinds"]
+            "dgp_sort_particles", "dgp_profile_kinds", "dgp_brane_spectra"]
 DGP_NOALLOC_MAX_N = 64
 DGP_KERNEL_KINDS = 11
 
@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
     _fields_ = [("box", ctypes.c_double), ("n", ctypes.c_int), ("rc_H0", ctypes.c_double),
                 ("w", ctypes.c_double), ("precision", ctypes.c_int), ("gravity", ctypes.c_int),
                 ("local_only", ctypes.c_int), ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
-                ("sort_every", ctypes.c_int)]
+                ("sort_every", ctypes.c_int), ("a_nonlinear", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -91,6 +91,7 @@ def _load():
         "dgp_kernel_name": (ctypes.c_char_p, [i]),
         "dgp_power_spectrum_noalloc": (i, [vp, i, d, i, P(d), P(d), P(i64), vp]),
         "dgp_sort_particles": (i, [vp, P(Particles), vp]),
+        "dgp_brane_spectra": (i, [vp, i, P(d), P(d), P(d), P(d), P(i64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -134,13 +135,15 @@ def dgp_background(omega_m0, rc_H0, a, c_over_H0=C_OVER_H0):
 
 
 def dgp_init(box, n, rc_H0, omega_m0=0.27, w=1.0 / 3.0, precision=DGP_MIXED, gravity=DGP_GRAVITY_NL,
-             local_only=False, max_iter=100, tol=1e-6, stream=None, c_over_H0=C_OVER_H0, sort_every=0):
+             local_only=False, max_iter=100, tol=1e-6, stream=None, c_over_H0=C_OVER_H0, sort_every=0,
+             a_nonlinear=0.0):
     """Returns an opaque context handle (ctypes.c_void_p)."""
     if stream is None:
         import torch
         stream = torch.cuda.current_stream().cuda_stream
     ctx = ctypes.c_void_p()
-    p = Params(box, n, rc_H0, w, precision, gravity, 1 if local_only else 0, max_iter, tol, sort_every)
+    p = Params(box, n, rc_H0, w, precision, gravity, 1 if local_only else 0, max_iter, tol, sort_every,
+               a_nonlinear)
     _check(lib.dgp_init(ctypes.byref(ctx), ctypes.byref(p), ctypes.byref(Cosmology(omega_m0, c_over_H0)),
                         ctypes.c_void_p(stream)), "dgp_init")
     return ctx
@@ -214,6 +217,16 @@ def power_spectrum(ctx, delta, nbins):
     _check(lib.power_spectrum(ctx, _ptr(delta), nbins, k.ctypes.data_as(dp), pk.ctypes.data_as(dp),
                               nm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))), "power_spectrum")
     return k, pk, nm
+
+
+def dgp_brane_spectra(ctx, nbins):
+    """(k, P_c, P_C, Delta_gradC, nmodes) of the accepted nonlinear solution."""
+    out = [np.zeros(nbins) for _ in range(4)]
+    nm = np.zeros(nbins, dtype=np.int64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib.dgp_brane_spectra(ctx, nbins, *[o.ctypes.data_as(dp) for o in out],
+                                 nm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))), "dgp_brane_spectra")
+    return (*out, nm)
 
 
 def bispectrum(ctx, delta, k1, k2, thetas, dk=0.0):

@@ -43,6 +43,31 @@ UNIT = "steps/s"
 E_PER_SOLVE_REF = 20.8
 # Cell sort cadence of the particles (pm_step sorts after every K-th drift; 0 = never).
 SORT_EVERY = 8
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
+# kernel kind from one ncu capture (summarised under profiles/), with the
+# SHA-256 of the sources the captured kernel was built from: when they have
+# changed since, the traffic is reported as null.
+NCU_TRAFFIC = {
+    "relax": {"bytes": 655.3e6, "sources": ["fused_relax.cu", "fft_core.cuh", "kernels.cuh", "common.cuh"],
+              "sha256": "9cdf07663074520a2f1be376a18b4385679970ba79e8aa76abc25e82954eeb5c",
+              "profile": "profiles/k_fused_relax_256cube.md"},
+}
+
+
+def sources_sha256(names):
+    import hashlib
+    h = hashlib.sha256()
+    for nm in names:
+        with open(os.path.join(ROOT, "paper_0906_4548_gb300", "csrc", nm), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kind):
+    rec = NCU_TRAFFIC.get(kind)
+    if not rec or rec["bytes"] is None or rec["sha256"] != sources_sha256(rec["sources"]):
+        return None
+    return rec["bytes"]
 
 
 PRECISION_DESC = {
@@ -297,7 +322,9 @@ def main():
             "vs_baseline": None, "dtype": {"mixed": "f32+eft", "mixed-fp64": "f32+f64", "fp32": "f32"}[args.precision],
             "data": "synthetic", "config": config(world, args.precision, args.sort_every),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": None, "kernel": dom,
+                         "frac": round(achieved / peak, 4), "traffic": recorded_traffic(dom), "kernel": dom,
+                         "algorithmic_bytes_per_launch": round(d["timed_bytes"] / max(d["timed"], 1)),
+                         "traffic_unit": "bytes per launch (ncu DRAM read + write)",
                          "peak_source": peak_kind},
             "e2e": e2e, "gpu_launches": int(sum(v["launches"] for v in prof.values())),
             "clocks": clk.summary(),

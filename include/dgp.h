@@ -77,7 +77,7 @@ typedef struct {
 
 typedef struct {
   double box;        /* side of the periodic box, Mpc/h, > 0 */
-  int n;             /* mesh points per side: 16, 32, 64, 128, 256 or 512 */
+  int n;             /* mesh points per side: 16, 32, 48, 64, 96, 128, 256 or 512 */
   double rc_H0;      /* crossover scale r_c in units of c/H0, > 0 (Sec. II) */
   double w;          /* splitting parameter of Eq. FullDGP2wpara, 0 <= w < 1 */
   int precision;     /* DGP_FP32, DGP_MIXED, DGP_FP64 or DGP_MIXED_EFT */

@@ -865,6 +865,8 @@ static EngineBase* make_engine(int n) {
     case 128: return new (std::nothrow) Engine<T, 128>();
     case 256: return new (std::nothrow) Engine<T, 256>();
     case 512: return new (std::nothrow) Engine<T, 512>();
+    case 48: return new (std::nothrow) Engine<T, 48>();
+    case 96: return new (std::nothrow) Engine<T, 96>();
     default: return nullptr;
   }
 }
@@ -907,7 +909,8 @@ int dgp_init(dgp_ctx** out, const dgp_params* p, const dgp_cosmology* cosmo, voi
   *out = nullptr;
   if (!p || !cosmo) return DGP_E_INVALID;
   const int n = p->n;
-  if (n != 16 && n != 32 && n != 64 && n != 128 && n != 256 && n != 512) return DGP_E_INVALID;
+  if (n != 16 && n != 32 && n != 48 && n != 64 && n != 96 && n != 128 && n != 256 && n != 512)
+    return DGP_E_INVALID;
   if (!(p->box > 0) || !(p->rc_H0 > 0) || !(p->w >= 0 && p->w < 1) || p->max_iter < 0 || !(p->tol >= 0) ||
       !isfinite(p->tol) || p->sort_every < 0)
     return DGP_E_INVALID;

@@ -30,9 +30,13 @@ __device__ __forceinline__ int signed_index(int i, int n) { return i < n / 2 ? i
 
 // Launch geometry of the two-level pencil FFT: N = N1 * N2, N1 >= N2.
 template <int N> struct Split;
+// N = N1 * N2 with N1 a power of two (the lane count of a pencil) and N2 <= N1
+// a power of two, 3 or 6 (meshes of 2^a 3^b points).
 template <> struct Split<16> { static constexpr int N1 = 4, N2 = 4; };
 template <> struct Split<32> { static constexpr int N1 = 8, N2 = 4; };
+template <> struct Split<48> { static constexpr int N1 = 16, N2 = 3; };
 template <> struct Split<64> { static constexpr int N1 = 8, N2 = 8; };
+template <> struct Split<96> { static constexpr int N1 = 16, N2 = 6; };
 template <> struct Split<128> { static constexpr int N1 = 16, N2 = 8; };
 template <> struct Split<256> { static constexpr int N1 = 16, N2 = 16; };
 template <> struct Split<512> { static constexpr int N1 = 32, N2 = 16; };

@@ -71,10 +71,9 @@ __device__ __forceinline__ V twiddle_c(int m) {
   else return c_w32f[j];
 }
 
-// Forward DFT of the R values in v (natural order in and out), radix-2
-// decimation in time, R <= 32; the twiddles are compile-time constants.
-template <int R, int TWS, typename V>
-__device__ __forceinline__ void dft_regs(V (&v)[R], const V* __restrict__ /*tw*/) {
+// Radix-2 decimation in time, natural order in and out, R a power of two <= 32.
+template <int R, typename V>
+__device__ __forceinline__ void dft_regs_pow2(V (&v)[R]) {
   constexpr int L = Log2<R>::v;
 #pragma unroll
   for (int i = 0; i < R; ++i) {
@@ -110,6 +109,48 @@ __device__ __forceinline__ void dft_regs(V (&v)[R], const V* __restrict__ /*tw*/
       v[i + k + half] = csub(u, t);
     }
   }
+}
+
+// 3-point DFT in place: with W_3 = -1/2 - i h, h = sqrt(3)/2,
+// X0 = a + s, X1 = t - i h d, X2 = t + i h d, where s = b + c, d = b - c,
+// t = a - s/2.
+template <typename V>
+__device__ __forceinline__ void dft3(V& a, V& b, V& c) {
+  using S = decltype(V::x);
+  const S h = (S)0.86602540378443864676;  // sqrt(3) / 2
+  const V s = cadd(b, c), d = csub(b, c);
+  const V t = cmake<V>(a.x - (S)0.5 * s.x, a.y - (S)0.5 * s.y);
+  a = cadd(a, s);
+  b = cmake<V>(t.x + h * d.y, t.y - h * d.x);
+  c = cmake<V>(t.x - h * d.y, t.y + h * d.x);
+}
+
+// Forward DFT of the R values in v (natural order in and out): R = 3 directly,
+// R = 6 as two 3-point DFTs of the even and odd elements combined with
+// W_6^k = 1/2 - i h, -1/2 - i h (decimation in time), otherwise radix-2
+// decimation in time for R <= 32 with compile-time twiddle constants.
+template <int R, int TWS, typename V>
+__device__ __forceinline__ void dft_regs(V (&v)[R], const V* __restrict__ tw) {
+  if constexpr (R == 3) {
+    dft3(v[0], v[1], v[2]);
+  } else if constexpr (R == 6) {
+    using S = decltype(V::x);
+    const S h = (S)0.86602540378443864676, half = (S)0.5;
+    V e0 = v[0], e1 = v[2], e2 = v[4], o0 = v[1], o1 = v[3], o2 = v[5];
+    dft3(e0, e1, e2);
+    dft3(o0, o1, o2);
+    const V t1 = cmake<V>(half * o1.x + h * o1.y, half * o1.y - h * o1.x);    // W_6^1 o1
+    const V t2 = cmake<V>(-half * o2.x + h * o2.y, -half * o2.y - h * o2.x);  // W_6^2 o2
+    v[0] = cadd(e0, o0);
+    v[3] = csub(e0, o0);
+    v[1] = cadd(e1, t1);
+    v[4] = csub(e1, t1);
+    v[2] = cadd(e2, t2);
+    v[5] = csub(e2, t2);
+  } else {
+    dft_regs_pow2<R>(v);
+  }
+  (void)tw;
 }
 
 template <int R, typename V>

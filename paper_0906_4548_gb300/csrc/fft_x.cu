@@ -327,12 +327,13 @@ void launch_fft_x_op(int op, const vec2_t<T>* in0, const vec2_t<T>* in1, const F
                                       const KParams&, double*, int, double, double, const vec2_t<T>*,   \
                                       cudaStream_t, const int*);
 #define DGP_INST_X_ALL(T) DGP_INST_X(T, 16) DGP_INST_X(T, 32) DGP_INST_X(T, 64) DGP_INST_X(T, 128) \
-  DGP_INST_X(T, 256) DGP_INST_X(T, 512)
+  DGP_INST_X(T, 256) DGP_INST_X(T, 512) DGP_INST_X(T, 48) DGP_INST_X(T, 96)
 DGP_INST_X_ALL(float)
 DGP_INST_X_ALL(double)
 #define DGP_INST_XB(T) template int x_pass_blocks<T, 16>(); template int x_pass_blocks<T, 32>(); \
   template int x_pass_blocks<T, 64>(); template int x_pass_blocks<T, 128>(); \
-  template int x_pass_blocks<T, 256>(); template int x_pass_blocks<T, 512>();
+  template int x_pass_blocks<T, 256>(); template int x_pass_blocks<T, 512>(); \
+  template int x_pass_blocks<T, 48>(); template int x_pass_blocks<T, 96>();
 DGP_INST_XB(float)
 DGP_INST_XB(double)
 

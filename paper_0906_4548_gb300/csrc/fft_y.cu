@@ -73,7 +73,7 @@ void launch_fft_y(const FieldSet<T>& f, int nfields, bool inverse, const vec2_t<
 #define DGP_INST_Y(T, N) \
   template void launch_fft_y<T, N>(const FieldSet<T>&, int, bool, const vec2_t<T>*, cudaStream_t, const int*);
 #define DGP_INST_Y_ALL(T) DGP_INST_Y(T, 16) DGP_INST_Y(T, 32) DGP_INST_Y(T, 64) DGP_INST_Y(T, 128) \
-  DGP_INST_Y(T, 256) DGP_INST_Y(T, 512)
+  DGP_INST_Y(T, 256) DGP_INST_Y(T, 512) DGP_INST_Y(T, 48) DGP_INST_Y(T, 96)
 DGP_INST_Y_ALL(float)
 DGP_INST_Y_ALL(double)
 

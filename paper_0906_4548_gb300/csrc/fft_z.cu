@@ -15,7 +15,8 @@ namespace dgp {
 
 template <typename T, int N> struct ZGeom {
   static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
-  static constexpr int TYW = (sizeof(T) == 8 || N >= 512) ? 16 : 32;
+  static constexpr int TYW0 = (sizeof(T) == 8 || N >= 512) ? 16 : 32;
+  static constexpr int TYW = N % TYW0 == 0 ? TYW0 : 16;  // rows per CTA divide N
   static constexpr int TY = TYW < N ? TYW : N;
   static constexpr int P = TY / 2;
   static constexpr int THREADS = P * N1;
@@ -90,7 +91,7 @@ k_fft_z_r2c(const T* __restrict__ in, int64_t in_stride, vec2_t<T>* __restrict__
     const int kz = item / TY, yl = item % TY;
     const int p = yl >> 1;
     const V zk = s_Z[kz * (P + 1) + p];
-    const V zm = s_Z[((N - kz) & (N - 1)) * (P + 1) + p];
+    const V zm = s_Z[((N - kz) % N) * (P + 1) + p];
     V r;
     if ((yl & 1) == 0) r = cmake<V>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
     else r = cmake<V>((T)0.5 * (zk.y + zm.y), (T)-0.5 * (zk.x - zm.x));
@@ -204,7 +205,7 @@ void launch_fft_z_c2r(const FieldSet<T>& in, T* const* out, int nfields, const v
                                        const vec2_t<T>*, cudaStream_t);                            \
   template void launch_fft_z_c2r<T, N>(const FieldSet<T>&, T* const*, int, const vec2_t<T>*, cudaStream_t);
 #define DGP_INST_Z_ALL(T) DGP_INST_Z(T, 16) DGP_INST_Z(T, 32) DGP_INST_Z(T, 64) DGP_INST_Z(T, 128) \
-  DGP_INST_Z(T, 256) DGP_INST_Z(T, 512)
+  DGP_INST_Z(T, 256) DGP_INST_Z(T, 512) DGP_INST_Z(T, 48) DGP_INST_Z(T, 96)
 DGP_INST_Z_ALL(float)
 DGP_INST_Z_ALL(double)
 

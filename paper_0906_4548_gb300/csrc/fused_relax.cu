@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(FGeom<T, N>::THREADS, 2)
       const int kz = kz0 + i * KZS;
       if (i < ROUNDS - 1 || kz < NK) {
         const V zk = s_Zf[kz * (P + 1) + p];
-        const V zm = s_Zf[((N - kz) & (N - 1)) * (P + 1) + p];
+        const V zm = s_Zf[((N - kz) % N) * (P + 1) + p];
         V r;
         if (!odd) r = cmake<V>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
         else r = cmake<V>((T)0.5 * (zk.y + zm.y), (T)-0.5 * (zk.x - zm.x));
@@ -516,7 +516,7 @@ void launch_fused_relax(int arith, vec2_t<T>* const* spec6, const T* D, const do
                                          const int*);                                                       \
   template int fused_relax_blocks<T, N>();
 #define DGP_INST_F_ALL(T) DGP_INST_F(T, 16) DGP_INST_F(T, 32) DGP_INST_F(T, 64) DGP_INST_F(T, 128) \
-  DGP_INST_F(T, 256) DGP_INST_F(T, 512)
+  DGP_INST_F(T, 256) DGP_INST_F(T, 512) DGP_INST_F(T, 48) DGP_INST_F(T, 96)
 DGP_INST_F_ALL(float)
 DGP_INST_F_ALL(double)
 

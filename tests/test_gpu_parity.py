@@ -55,7 +55,7 @@ def np_dtype(prec, dgp):
     return np.float64 if prec == dgp.DGP_FP64 else np.float32
 
 
-@pytest.mark.parametrize("n,prec", [(16, 0), (32, 1), (64, 0), (32, 2)])
+@pytest.mark.parametrize("n,prec", [(16, 0), (32, 1), (64, 0), (32, 2), (48, 1), (96, 0), (48, 2)])
 def test_power_spectrum_parity(dgp, torch_dev, n, prec):
     torch, _ = torch_dev
     box = 150.0
@@ -72,7 +72,7 @@ def test_power_spectrum_parity(dgp, torch_dev, n, prec):
     assert np.max(np.abs(P / Po - 1)) < tol
 
 
-@pytest.mark.parametrize("n,prec", [(32, 1), (64, 0), (32, 2)])
+@pytest.mark.parametrize("n,prec", [(32, 1), (64, 0), (32, 2), (48, 1), (96, 2)])
 def test_deposit_parity_ragged(dgp, torch_dev, n, prec):
     torch, _ = torch_dev
     box = 100.0
@@ -131,6 +131,10 @@ def _solve_both(dgp, torch_dev, n, box, a, prec, tol_gpu, seed=5, w=1 / 3, local
     (128, 200.0, 0.5, 1, 1e-6, 1e-5),
     (64, 200.0, 0.5, 3, 1e-6, 1e-5),       # mixed, residual by error-free FP32 transformations
     (128, 200.0, 1.0, 3, 1e-6, 1e-5),
+    (48, 150.0, 0.5, 2, 1e-10, 1e-9),      # radix-3 meshes (N = 16 x 3, 16 x 6)
+    (48, 150.0, 0.5, 3, 1e-6, 1e-5),
+    (96, 200.0, 0.7, 3, 1e-6, 1e-5),
+    (96, 200.0, 0.7, 0, 1e-6, 1e-5),
 ])
 def test_solve_phi_and_forces_parity(dgp, torch_dev, n, box, a, prec, tol_gpu, tol_phi):
     got, want = _solve_both(dgp, torch_dev, n, box, a, prec, tol_gpu)
@@ -211,6 +215,32 @@ def test_not_converged_reports_best_iterate(dgp, torch_dev):
     assert st == dgp.DGP_E_NOT_CONVERGED and info["status"] == dgp.DGP_E_NOT_CONVERGED
     assert info["iters"] == oinfo["iters"] == 2
     assert abs(info["norm_res"] / oinfo["norm_res"] - 1) < 1e-3
+
+
+def test_pm_run_radix3_fp64_matches_oracle(dgp, torch_dev):
+    """48^3 (16 x 3 split) FP64, 4 steps: positions and momenta match the oracle run."""
+    torch, dev = torch_dev
+    n, box, a0, a1, ns = 48, 150.0, 0.1, 0.15, 4
+    pos, mom, _ = zel(n, box, a0, -1.5, 0.5, 7)
+    st = opm.run(pos, mom, a0, a1, ns, n, box, OM, 1.0, tol=1e-10, max_iter=300)
+    ctx = dgp.dgp_init(box, n, 1.0, OM, precision=dgp.DGP_FP64, tol=1e-10, max_iter=300, sort_every=2)
+    try:
+        t = [to_dev(torch_dev, v, torch.float64) for v in (*pos, *mom)]
+        parts = dgp.particles(*t)
+        a = a0
+        dl = (math.log(a1) - math.log(a0)) / ns
+        for i in range(ns):
+            a_next = a0 * math.exp((i + 1) * dl)
+            dgp.pm_step(ctx, parts, a, a_next - a)
+            a = a_next
+        x = np.stack([v.cpu().numpy() for v in t[:3]])
+        p = np.stack([v.cpu().numpy() for v in t[3:]])
+    finally:
+        dgp.dgp_destroy(ctx)
+    # the cell sort permutes the particles: compare after ordering both by position
+    o_g = np.lexsort(x[::-1])
+    o_o = np.lexsort(st.pos[::-1])
+    assert rel_l2(x[:, o_g], st.pos[:, o_o]) < 1e-12 and rel_l2(p[:, o_g], st.mom[:, o_o]) < 1e-9
 
 
 def test_stop_on_bad_point_divergence_returns_earlier_iterate(dgp, torch_dev):

@@ -203,6 +203,119 @@ def run_reference(args):
     return 0
 
 
+# Batched workload: independent realisations of uneven meshes stepped together.
+WB = dict(sizes=[48] * 16 + [64] * 16 + [96] * 16, box_range=(50.0, 200.0), rc_range=(0.5, 2.0), n_s=-1.5,
+          rms=0.5, seed=100, a_start=0.02, a_end=1.0, run_steps=50, omega_m0=0.27, tol=1e-6, max_iter=100)
+
+
+def run_batched(args):
+    """48 realisations (16 x 48^3, 16 x 64^3, 16 x 96^3, particles = mesh cells), boxes and r_c H0
+    drawn uniformly, distinct seeds, FP32, 50 steps each: the batch path (one context and stream per
+    realisation, all stepped together) and the plain path (the same realisations stepped one after
+    another on one stream).  value = realisation-steps per second of the batch path."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_0906_4548_gb300 import dgp, inputs
+    rng = np.random.default_rng(WB["seed"])
+    nr = len(WB["sizes"])
+    boxes = rng.uniform(*WB["box_range"], nr)
+    rcs = rng.uniform(*WB["rc_range"], nr)
+    dev = torch.device("cuda", 0)
+    ics = []
+    for i, n in enumerate(WB["sizes"]):
+        bgi = dgp.dgp_background(WB["omega_m0"], rcs[i], WB["a_start"])
+        vf = WB["a_start"] ** 2 * bgi["E"] * bgi["growth_f"]
+        pos, mom, _ = inputs.zeldovich_particles(n, boxes[i], WB["n_s"], WB["rms"], WB["seed"] + i, vf)
+        ics.append([torch.tensor(v.astype(np.float32), device=dev) for v in (*pos, *mom)])
+    cur = [[t.clone() for t in ic] for ic in ics]
+    parts = [dgp.particles(*c) for c in cur]
+    prec = dgp.DGP_FP32
+    plist = [dgp.params(boxes[i], n, rcs[i], precision=prec, tol=WB["tol"], max_iter=WB["max_iter"],
+                        sort_every=SORT_EVERY) for i, n in enumerate(WB["sizes"])]
+    dlna = math.log(WB["a_end"] / WB["a_start"]) / WB["run_steps"]
+    sched = [WB["a_start"] * math.exp(i * dlna) for i in range(WB["run_steps"] + 1)]
+    steps = min(args.steps, WB["run_steps"])
+
+    def restart(ctxs):
+        for c, ic in zip(cur, ics):
+            for x, y in zip(c, ic):
+                x.copy_(y)
+        for c in ctxs:
+            dgp.dgp_reset(c)
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    b, ctxs = dgp.dgp_batch_create(plist, WB["omega_m0"])
+    infos = []
+    try:
+        restart(ctxs)
+        for i in range(args.warmup):
+            dgp.dgp_batch_step(b, parts, [sched[i]] * nr, [sched[i + 1] - sched[i]] * nr)
+        restart(ctxs)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            time.sleep(0.3)
+            e0.record(stream)
+            t0 = time.perf_counter()
+            for i in range(steps):
+                infos.append(dgp.dgp_batch_step(b, parts, [sched[i]] * nr, [sched[i + 1] - sched[i]] * nr))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        ms = e0.elapsed_time(e1)
+        pk_batch = []
+        for k in (0, 16, 32):
+            dl = torch.empty((WB["sizes"][k],) * 3, dtype=torch.float32, device=dev)
+            dgp.dgp_deposit(ctxs[k], parts[k], dl)
+            pk_batch.append(dgp.power_spectrum(ctxs[k], dl, WB["sizes"][k] // 2)[1])
+    finally:
+        dgp.dgp_batch_destroy(b)
+    # plain path: the same realisations, one context at a time on the current stream
+    seq = [dgp.dgp_init(boxes[i], n, rcs[i], WB["omega_m0"], precision=prec, tol=WB["tol"],
+                        max_iter=WB["max_iter"], sort_every=SORT_EVERY) for i, n in enumerate(WB["sizes"])]
+    try:
+        restart(seq)
+        for i in range(args.warmup):
+            for k in range(nr):
+                dgp.pm_step(seq[k], parts[k], sched[i], sched[i + 1] - sched[i])
+        restart(seq)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for i in range(steps):
+            for k in range(nr):
+                dgp.pm_step(seq[k], parts[k], sched[i], sched[i + 1] - sched[i])
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms_seq = f0.elapsed_time(f1)
+        diffs = []
+        for j, k in enumerate((0, 16, 32)):
+            dl = torch.empty((WB["sizes"][k],) * 3, dtype=torch.float32, device=dev)
+            dgp.dgp_deposit(seq[k], parts[k], dl)
+            pk = dgp.power_spectrum(seq[k], dl, WB["sizes"][k] // 2)[1]
+            diffs.append(float(np.max(np.abs(pk_batch[j] / pk - 1))))
+    finally:
+        for c in seq:
+            dgp.dgp_destroy(c)
+    evals = [i["iters"] + 1 for step in infos for i in step]
+    line = {"metric": "PM realisation-steps/s, 48 realisations (16 x 48^3, 16 x 64^3, 16 x 96^3) incl. "
+                      "converged DGP phi solves", "value": nr * steps / (ms / 1000.0), "unit": "realisation-steps/s",
+            "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": ms / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "dgp_pm_batched_48x(48,64,96)cube_box50-200_rc0.5-2_a0.02-1_50steps_tol1e-6",
+                       "realisations": nr, "precision": PRECISION_DESC["fp32"], "cell_sort_every": SORT_EVERY,
+                       "l2": "realisations' fields and particles (about 1.5 GB in total) exceed L2; no flush"},
+            "wall_s": wall, "clocks": clk.summary(),
+            "plain_path": {"value": nr * steps / (ms_seq / 1000.0), "ms_per_step": ms_seq / steps,
+                           "how": "the same 48 contexts stepped one after another on one stream"},
+            "end_pk_max_rel_diff_batch_vs_plain": max(diffs),
+            "solver": {"evals_per_solve_mean": sum(evals) / len(evals), "max_evals": max(evals),
+                       "not_converged": sum(1 for step in infos for i in step if i["status"] != 0)}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -213,11 +326,15 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--precision", default="mixed", choices=sorted(PRECISION_DESC))
     ap.add_argument("--no-compare", action="store_true", help="skip the precision comparison runs")
+    ap.add_argument("--workload", default="pm256", choices=["pm256", "batched"],
+                    help="pm256: the 256^3 PM run (default); batched: 48 small realisations")
     ap.add_argument("--sort-every", type=int, default=SORT_EVERY,
                     help="cell-sort the particles after every K-th drift (0: never)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
 
     import numpy as np
     import torch

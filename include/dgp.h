@@ -171,6 +171,35 @@ int dgp_get_solution(dgp_ctx *c, void *D);
  * delta: device n^3 output.  Positions outside [0, box) are wrapped. */
 int dgp_deposit(dgp_ctx *c, const dgp_particles *parts, void *delta);
 
+/* Host waits of the context (the relaxation's stop-rule verdicts, host outputs)
+ * block on an event and yield the CPU (on != 0) instead of spinning (0, the
+ * default).  For callers that drive many contexts from many host threads. */
+int dgp_set_blocking_sync(dgp_ctx *c, int on);
+
+/* ---- Batches of independent realisations --------------------------------
+ * Not part of the paper's method: many small boxes (e.g. 48 realisations of
+ * 48^3, 64^3 and 96^3 meshes with different boxes and r_c) stepped together
+ * so the GPU overlaps their small kernels.  Each realisation is a context on
+ * its own non-blocking stream, stepped by its own host worker thread; the
+ * contexts use blocking host waits.
+ *   dgp_batch_create: count contexts from params[count] (sizes may differ)
+ *     and one cosmology; DGP_E_INVALID, DGP_E_NOMEM or DGP_E_CUDA on failure,
+ *     *out = NULL then.
+ *   dgp_batch_context: the i-th context (for deposit, P(k), reset, ...); the
+ *     batch keeps ownership (do not destroy it).
+ *   dgp_batch_step: pm_step of every realisation i with parts[i], a[i], da[i]
+ *     (info[i] filled when info != NULL).  The batch streams first wait for
+ *     the work enqueued so far on cuda_stream (may be NULL); the call returns
+ *     when every realisation's step has completed on the device.  Returns
+ *     the first non-OK status of a realisation (the others still step).
+ * Calls on one batch must not overlap. */
+typedef struct dgp_batch dgp_batch;
+int dgp_batch_create(dgp_batch **out, int count, const dgp_params *params, const dgp_cosmology *cosmo);
+int dgp_batch_context(dgp_batch *b, int i, dgp_ctx **out);
+int dgp_batch_step(dgp_batch *b, dgp_particles *parts, const double *a, const double *da, dgp_solve_info *info,
+                   void *cuda_stream);
+void dgp_batch_destroy(dgp_batch *b);
+
 /* Spectra of the brane-bending mode C of the context's accepted nonlinear
  * solution D = lapbar^2 C, at the scale factor of that solve (Sec. IV):
  *   pc[b]:  P_c of c = alpha eta / (3 (eta - 1)) D (Eq. cdef; P_c / P_m -> 1 on

@@ -206,6 +206,26 @@ class EngineBase {
   virtual int get_solution(void* D) = 0;
   Profiler prof;
   std::vector<double> history;  // normalised residual of each iterate of the last solve
+  cudaEvent_t sync_event = nullptr;  // set: host waits block on this event instead of spinning
+
+  // Host wait for the work enqueued so far on the context's stream.
+  cudaError_t wait_stream() {
+    if (!sync_event) return cudaStreamSynchronize(stream);
+    const cudaError_t e = cudaEventRecord(sync_event, stream);
+    return e != cudaSuccess ? e : cudaEventSynchronize(sync_event);
+  }
+  int set_blocking(bool on) {
+    if (on && !sync_event) {
+      if (cudaEventCreateWithFlags(&sync_event, cudaEventBlockingSync | cudaEventDisableTiming) != cudaSuccess) {
+        sync_event = nullptr;
+        return DGP_E_CUDA;
+      }
+    } else if (!on && sync_event) {
+      cudaEventDestroy(sync_event);
+      sync_event = nullptr;
+    }
+    return DGP_OK;
+  }
 };
 
 #define DGP_CUDA(call)                          \
@@ -277,6 +297,7 @@ class Engine : public EngineBase {
     cudaFree(pk_partials); cudaFree(d_pk);
     cudaFree(srt_key); cudaFree(srt_cell); cudaFree(srt_sums);
     cudaFree(d_ctl); cudaFree(d_hist); cudaFreeHost(h_ctl);
+    set_blocking(false);
     for (int i = 0; i < 6; ++i) cudaFree(srt_tmp[i]);
     cudaFreeHost(h_stats);
   }
@@ -404,7 +425,7 @@ class Engine : public EngineBase {
 
   int fetch(const double* dsrc, int n) {
     DGP_CUDA(cudaMemcpyAsync(h_stats, dsrc, sizeof(double) * n, cudaMemcpyDeviceToHost, stream));
-    DGP_CUDA(cudaStreamSynchronize(stream));
+    DGP_CUDA(wait_stream());
     return DGP_OK;
   }
 
@@ -534,7 +555,7 @@ class Engine : public EngineBase {
         for (; it < end; ++it)
           if ((rc = enqueue(it, true))) return rc;
         DGP_CUDA(cudaMemcpyAsync(h_ctl, d_ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, stream));
-        DGP_CUDA(cudaStreamSynchronize(stream));
+        DGP_CUDA(wait_stream());
         if (h_ctl->done || it > p.max_iter) break;
         chunk = kChunk;
       }
@@ -544,7 +565,7 @@ class Engine : public EngineBase {
       credit(s_it + 1, s_it);
       history.assign(s_it + 1, 0.0);
       DGP_CUDA(cudaMemcpyAsync(history.data(), d_hist, sizeof(double) * (s_it + 1), cudaMemcpyDeviceToHost, stream));
-      DGP_CUDA(cudaStreamSynchronize(stream));
+      DGP_CUDA(wait_stream());
       if (st.status == CTL_NONFINITE) return DGP_E_NONFINITE;
       last_stop_it = s_it;
       inf.eps = st.eps;
@@ -598,7 +619,7 @@ class Engine : public EngineBase {
     }
     if (info) {
       *info = inf;
-      DGP_CUDA(cudaStreamSynchronize(stream));
+      DGP_CUDA(wait_stream());
     }
     return status;
   }
@@ -632,7 +653,7 @@ class Engine : public EngineBase {
       if (cudaMalloc(&srt_sums, sizeof(int) * sort_scan_blocks(M)) != cudaSuccess) return DGP_E_NOMEM;
     }
     if (np > srt_np) {
-      DGP_CUDA(cudaStreamSynchronize(stream));
+      DGP_CUDA(wait_stream());
       cudaFree(srt_key);
       srt_key = nullptr;
       for (int i = 0; i < 6; ++i) { cudaFree(srt_tmp[i]); srt_tmp[i] = nullptr; }
@@ -654,7 +675,7 @@ class Engine : public EngineBase {
       const int total = (int)np;
       DGP_CUDA(cudaMemcpyAsync(cell_start, w.start, sizeof(int) * M, cudaMemcpyDeviceToDevice, stream));
       DGP_CUDA(cudaMemcpyAsync(cell_start + M, &total, sizeof(int), cudaMemcpyHostToDevice, stream));
-      DGP_CUDA(cudaStreamSynchronize(stream));
+      DGP_CUDA(wait_stream());
     }
     return DGP_OK;
   }
@@ -745,7 +766,7 @@ class Engine : public EngineBase {
     const int rc = step(&dp, a, da, info);
     if (rc != DGP_OK) return rc;
     for (int i = 0; i < 6; ++i) DGP_CUDA(cudaMemcpyAsync(src[i], hp[i], bytes, cudaMemcpyDeviceToHost, stream));
-    DGP_CUDA(cudaStreamSynchronize(stream));
+    DGP_CUDA(wait_stream());
     return DGP_OK;
   }
 
@@ -763,7 +784,7 @@ class Engine : public EngineBase {
     DGP_CHECK_LAUNCH();
     double hb[3 * 256];
     DGP_CUDA(cudaMemcpyAsync(hb, d_pk, sizeof(double) * 3 * nbins, cudaMemcpyDeviceToHost, stream));
-    DGP_CUDA(cudaStreamSynchronize(stream));
+    DGP_CUDA(wait_stream());
     for (int b = 0; b < nbins; ++b) {
       const double cnt = hb[b];
       nmodes[b] = (int64_t)llround(cnt);
@@ -791,7 +812,7 @@ class Engine : public EngineBase {
     DGP_CHECK_LAUNCH();
     double hb[4 * 256];
     DGP_CUDA(cudaMemcpyAsync(hb, d_pk, sizeof(double) * 4 * nbins, cudaMemcpyDeviceToHost, stream));
-    DGP_CUDA(cudaStreamSynchronize(stream));
+    DGP_CUDA(wait_stream());
     const double fac_c = c.alpha * c.eta / (3.0 * (c.eta - 1.0));
     const double kbf = cosmo.c_over_H0 / (c.a * c.E) * 2.0 * M_PI / p.box;  // kbar = kbf |n|
     const double kbf4 = kbf * kbf * kbf * kbf;
@@ -1008,6 +1029,11 @@ const char* dgp_kernel_name(int kind) {
 int dgp_deposit(dgp_ctx* c, const dgp_particles* parts, void* delta) {
   if (!c) return DGP_E_INVALID;
   return c->eng->deposit(parts, delta);
+}
+
+int dgp_set_blocking_sync(dgp_ctx* c, int on) {
+  if (!c) return DGP_E_INVALID;
+  return c->eng->set_blocking(on != 0);
 }
 
 int dgp_brane_spectra(dgp_ctx* c, int nbins, double* k, double* pc, double* pC, double* delta_gradc,

@@ -22,7 +22,8 @@ C_OVER_H0 = 2997.92458
 EXPORTED = ["dgp_background", "dgp_init", "dgp_destroy", "dgp_strerror", "dgp_reset", "dgp_solve_phi",
             "dgp_solve_forces", "dgp_solve_history", "dgp_get_solution", "dgp_deposit", "pm_step", "pm_step_host", "power_spectrum", "bispectrum",
             "dgp_profile", "dgp_profile_read", "dgp_kernel_name", "dgp_power_spectrum_noalloc",
-            "dgp_sort_particles", "dgp_profile_kinds", "dgp_brane_spectra"]
+            "dgp_sort_particles", "dgp_profile_kinds", "dgp_brane_spectra", "dgp_set_blocking_sync",
+            "dgp_batch_create", "dgp_batch_context", "dgp_batch_step", "dgp_batch_destroy"]
 DGP_NOALLOC_MAX_N = 64
 DGP_KERNEL_KINDS = 11
 
@@ -92,6 +93,11 @@ def _load():
         "dgp_power_spectrum_noalloc": (i, [vp, i, d, i, P(d), P(d), P(i64), vp]),
         "dgp_sort_particles": (i, [vp, P(Particles), vp]),
         "dgp_brane_spectra": (i, [vp, i, P(d), P(d), P(d), P(d), P(i64)]),
+        "dgp_set_blocking_sync": (i, [vp, i]),
+        "dgp_batch_create": (i, [P(vp), i, P(Params), P(Cosmology)]),
+        "dgp_batch_context": (i, [vp, i, P(vp)]),
+        "dgp_batch_step": (i, [vp, P(Particles), P(d), P(d), P(SolveInfo), vp]),
+        "dgp_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -147,6 +153,46 @@ def dgp_init(box, n, rc_H0, omega_m0=0.27, w=1.0 / 3.0, precision=DGP_MIXED, gra
     _check(lib.dgp_init(ctypes.byref(ctx), ctypes.byref(p), ctypes.byref(Cosmology(omega_m0, c_over_H0)),
                         ctypes.c_void_p(stream)), "dgp_init")
     return ctx
+
+
+def params(box, n, rc_H0, w=1.0 / 3.0, precision=DGP_MIXED, gravity=DGP_GRAVITY_NL, local_only=False,
+           max_iter=100, tol=1e-6, sort_every=0, a_nonlinear=0.0):
+    return Params(box, n, rc_H0, w, precision, gravity, 1 if local_only else 0, max_iter, tol, sort_every,
+                  a_nonlinear)
+
+
+def dgp_batch_create(param_list, omega_m0=0.27, c_over_H0=C_OVER_H0):
+    """A batch of len(param_list) contexts (see params()); returns (handle, [contexts])."""
+    arr = (Params * len(param_list))(*param_list)
+    b = ctypes.c_void_p()
+    _check(lib.dgp_batch_create(ctypes.byref(b), len(param_list), arr, ctypes.byref(Cosmology(omega_m0, c_over_H0))),
+           "dgp_batch_create")
+    ctxs = []
+    for i in range(len(param_list)):
+        c = ctypes.c_void_p()
+        _check(lib.dgp_batch_context(b, i, ctypes.byref(c)), "dgp_batch_context")
+        ctxs.append(c)
+    return b, ctxs
+
+
+def dgp_batch_step(batch, parts_list, a, da, stream=None):
+    """pm_step of every realisation; returns the list of solve infos."""
+    import torch
+    n = len(parts_list)
+    parts = (Particles * n)(*parts_list)
+    av = np.ascontiguousarray(a, dtype=np.float64)
+    dv = np.ascontiguousarray(da, dtype=np.float64)
+    infos = (SolveInfo * n)()
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib.dgp_batch_step(batch, parts, av.ctypes.data_as(dp), dv.ctypes.data_as(dp), infos,
+                              ctypes.c_void_p(stream)), "dgp_batch_step")
+    return [x.as_dict() for x in infos]
+
+
+def dgp_batch_destroy(batch):
+    lib.dgp_batch_destroy(batch)
 
 
 def dgp_destroy(ctx):

@@ -53,7 +53,7 @@ def test_host_only_calls_without_gpu(lib):
 
 
 def test_init_rejects_bad_parameters_before_touching_the_gpu(lib):
-    for kw in (dict(n=48), dict(n=0), dict(w=1.0), dict(rc_H0=0.0), dict(precision=7), dict(precision=-1),
+    for kw in (dict(n=40), dict(n=24), dict(n=0), dict(w=1.0), dict(rc_H0=0.0), dict(precision=7), dict(precision=-1),
                dict(sort_every=-1), dict(gravity=4), dict(a_nonlinear=-0.5)):
         args = dict(box=100.0, n=32, rc_H0=1.0, precision=lib.DGP_MIXED)
         args.update(kw)

@@ -1,0 +1,84 @@
+"""Batches of independent realisations (dgp_batch_*): every realisation of a
+mixed-size batch steps exactly as the same realisation stepped alone."""
+import math
+
+import numpy as np
+import pytest
+
+from test_gpu_parity import OM, rel_l2, to_dev, zel  # noqa: F401
+from test_gpu_parity import dgp, torch_dev  # noqa: F401  (fixtures)
+
+pytestmark = pytest.mark.gpu
+
+CASES = [(32, 80.0, 1.0, 1), (48, 120.0, 0.6, 2), (64, 200.0, 1.7, 3), (32, 60.0, 1.2, 4), (96, 150.0, 0.9, 5)]
+
+
+def _ics(n, box, rc, seed, a0):
+    pos, mom, _ = zel(n, box, a0, -1.5, 0.5, seed, rc)
+    return pos, mom
+
+
+@pytest.mark.parametrize("prec,tol,sort_every", [(2, 1e-11, 2), (3, 2e-5, 0)])
+def test_batch_matches_individual_contexts(dgp, torch_dev, prec, tol, sort_every):
+    """FP64 with the cell sort: compared after ordering by position.  FP32 runs
+    differ at the 1e-6 level (float atomics), where ordering by position would
+    pair up different particles, so that case keeps the input order."""
+    torch, dev = torch_dev
+    td = torch.float64 if prec == dgp.DGP_FP64 else torch.float32
+    a0, a1, ns = 0.2, 0.3, 3
+    dl = (math.log(a1) - math.log(a0)) / ns
+    sched = [a0 * math.exp(i * dl) for i in range(ns + 1)]
+    ics = [_ics(n, box, rc, seed, a0) for n, box, rc, seed in CASES]
+    plist = [dgp.params(box, n, rc, precision=prec, tol=1e-9 if prec == 2 else 1e-6, max_iter=200,
+                        sort_every=sort_every) for n, box, rc, _ in CASES]
+    # batch
+    b, ctxs = dgp.dgp_batch_create(plist, OM)
+    try:
+        tb = [[to_dev(torch_dev, v, td) for v in (*p, *m)] for p, m in ics]
+        parts = [dgp.particles(*t) for t in tb]
+        binfo = []
+        for i in range(ns):
+            binfo.append(dgp.dgp_batch_step(b, parts, [sched[i]] * len(CASES),
+                                            [sched[i + 1] - sched[i]] * len(CASES)))
+        got = [np.stack([v.cpu().numpy() for v in t]) for t in tb]
+    finally:
+        dgp.dgp_batch_destroy(b)
+    # the same realisations, one context at a time
+    for k, ((n, box, rc, _), (p, m)) in enumerate(zip(CASES, ics)):
+        ctx = dgp.dgp_init(box, n, rc, OM, precision=prec, tol=1e-9 if prec == 2 else 1e-6, max_iter=200,
+                           sort_every=sort_every)
+        try:
+            t = [to_dev(torch_dev, v, td) for v in (*p, *m)]
+            pp = dgp.particles(*t)
+            for i in range(ns):
+                inf = dgp.pm_step(ctx, pp, sched[i], sched[i + 1] - sched[i])
+                assert inf["iters"] == binfo[i][k]["iters"] or prec != dgp.DGP_FP64
+            want = np.stack([v.cpu().numpy() for v in t])
+        finally:
+            dgp.dgp_destroy(ctx)
+        if sort_every:
+            # the cell sort orders particles within a cell arbitrarily: compare sorted by position
+            og = np.lexsort(got[k][:3][::-1])
+            ow = np.lexsort(want[:3][::-1])
+            assert rel_l2(got[k][:, og], want[:, ow]) < tol, k
+        else:
+            assert rel_l2(got[k], want) < tol, k
+
+
+def test_batch_reports_a_failing_realisation(dgp, torch_dev):
+    torch, dev = torch_dev
+    plist = [dgp.params(60.0, 32, 1.0), dgp.params(60.0, 48, 1.0)]
+    b, ctxs = dgp.dgp_batch_create(plist, OM)
+    try:
+        p, m = _ics(32, 60.0, 1.0, 3, 0.2)
+        t = [to_dev(torch_dev, v, torch.float32) for v in (*p, *m)]
+        empty = [torch.empty(0, dtype=torch.float32, device=dev) for _ in range(6)]
+        x0 = t[0].clone()
+        with pytest.raises(dgp.DgpError) as e:
+            dgp.dgp_batch_step(b, [dgp.particles(*t), dgp.particles(*empty)], [0.2, 0.2], [0.01, 0.01])
+        assert e.value.status == dgp.DGP_E_INVALID
+        assert not torch.equal(t[0], x0)  # the valid realisation stepped
+        with pytest.raises(dgp.DgpError):
+            dgp.dgp_batch_create([dgp.params(60.0, 40, 1.0)], OM)  # invalid size: nothing leaks
+    finally:
+        dgp.dgp_batch_destroy(b)

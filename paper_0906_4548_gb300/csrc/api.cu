@@ -164,13 +164,16 @@ struct Profiler {
     used = 0;
     return DGP_OK;
   }
+  void count(int kind, int64_t n) { launches[kind] += n; }
   // bytes of work that launches already counted (with 0 bytes) turned out to do
   void credit(int kind, double b) {
     bytes[kind] += b;
     if ((timing >> kind) & 1u) timed_bytes[kind] += b;
   }
+  bool capturing = false;  // launches recorded into a graph are counted when the graph runs
   template <class F>
   void run(int kind, double b, cudaStream_t s, F&& f) {
+    if (capturing) { f(); return; }
     launches[kind] += 1;
     bytes[kind] += b;
     if (!((timing >> kind) & 1u)) { f(); return; }
@@ -274,6 +277,9 @@ class Engine : public EngineBase {
   double last_nl_a = -1.0;      // scale factor of the last nonlinear solve
   static constexpr int kPatience = 10;  // iterations without a new minimum before stopping
   static constexpr int kChunk = 4;      // iterations enqueued per verdict after the first chunk
+  // CUDA graph of two consecutive iterations (it odd, it + 1), one per buffer
+  // holding the starting iterate; updated with each solve's parameters
+  cudaGraphExec_t pair_exec[3] = {nullptr, nullptr, nullptr};
   T* hp[6] = {};                // device copies for pm_step_host
   int64_t hp_n = 0;
   // cell sort: key and permuted copies per particle, counts / starts / cursors per cell
@@ -297,6 +303,8 @@ class Engine : public EngineBase {
     cudaFree(pk_partials); cudaFree(d_pk);
     cudaFree(srt_key); cudaFree(srt_cell); cudaFree(srt_sums);
     cudaFree(d_ctl); cudaFree(d_hist); cudaFreeHost(h_ctl);
+    for (int i = 0; i < 3; ++i)
+      if (pair_exec[i]) cudaGraphExecDestroy(pair_exec[i]);
     set_blocking(false);
     for (int i = 0; i < 6; ++i) cudaFree(srt_tmp[i]);
     cudaFreeHost(h_stats);
@@ -527,7 +535,7 @@ class Engine : public EngineBase {
                  [&] { launch_finalize(partials, fblocks, 4, d_rstats + 4 * ob, stream, sk); });
         if (control)
           prof.run(KK_REDUCE, 0, stream, [&] {
-            launch_relax_control(d_ctl, d_rstats + 4 * ob, d_misc + 1, d_hist, it, p.max_iter, kPatience, tol,
+            launch_relax_control(d_ctl, d_rstats + 4 * ob, d_misc + 1, d_hist, p.max_iter, kPatience, tol,
                                  1.0 / (double)M, stream);
           });
         prof.run(KK_Y, 0, stream, [&] {
@@ -546,14 +554,62 @@ class Engine : public EngineBase {
 
       if ((rc = forward_zy(rD[j0], sD, ZPrologue{nullptr, 0.0, 0}))) return rc;
       DGP_CUDA(cudaMemsetAsync(d_ctl, 0, sizeof(SolveCtl), stream));
+      // Iterations after the first run as a CUDA graph of two iterations (the
+      // buffers alternate with period two) unless launches are being timed.
+      // (Stream capture is not available on the legacy default stream; a
+      // capture that fails leaves the iterations to direct launches.)
+      bool graphs = prof.timing == 0 && stream != nullptr && stream != cudaStreamLegacy &&
+                    stream != cudaStreamPerThread;
+      if (graphs) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+          cudaGetLastError();
+          graphs = false;
+        } else {
+          prof.capturing = true;
+          const int r1 = enqueue(1, true), r2 = r1 ? r1 : enqueue(2, true);
+          prof.capturing = false;
+          const cudaError_t e = cudaStreamEndCapture(stream, &g);
+          cudaGraphExec_t& ex = pair_exec[j0];
+          if (r1 || r2 || e != cudaSuccess || !g) {
+            graphs = false;
+          } else {
+            if (ex) {
+              cudaGraphExecUpdateResultInfo ui;
+              if (cudaGraphExecUpdate(ex, g, &ui) != cudaSuccess) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(ex);
+                ex = nullptr;
+              }
+            }
+            if (!ex && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+              ex = nullptr;
+              graphs = false;
+            }
+          }
+          if (g) cudaGraphDestroy(g);
+          if (!graphs) cudaGetLastError();
+        }
+      }
       // Iterations are enqueued in chunks and the controller's verdict is read
       // once per chunk; the first chunk covers the previous solve's length.
       int it = 0;
       int chunk = last_stop_it >= 0 ? last_stop_it + 2 : 4;
       while (true) {
         const int end = std::min(it + chunk, p.max_iter + 1);
-        for (; it < end; ++it)
-          if ((rc = enqueue(it, true))) return rc;
+        while (it < end) {
+          if (graphs && it > 0 && (it & 1)) {
+            DGP_CUDA(cudaGraphLaunch(pair_exec[j0], stream));
+            prof.count(KK_X_HESSIAN, 2);
+            prof.count(KK_Y, 4);
+            prof.count(KK_RELAX, 2);
+            prof.count(KK_REDUCE, 4);
+            it += 2;
+          } else {
+            if ((rc = enqueue(it, true))) return rc;
+            ++it;
+          }
+        }
         DGP_CUDA(cudaMemcpyAsync(h_ctl, d_ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, stream));
         DGP_CUDA(wait_stream());
         if (h_ctl->done || it > p.max_iter) break;

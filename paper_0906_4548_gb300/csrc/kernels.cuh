@@ -111,15 +111,18 @@ void launch_finalize(const double* partials, int nblocks, int ncomp, double* out
 enum { CTL_RUNNING = 0, CTL_CONVERGED = 1, CTL_STOPPED = 2, CTL_NONFINITE = 3 };
 struct SolveCtl {
   int done;      // nonzero once a rule has stopped the solve (the skip flag)
+  int next_it;   // index of the iteration the controller examines next
   int status;    // CTL_*
   int stop_it;   // last iteration whose residual was examined
   int best_it;   // iteration whose incoming iterate has the smallest residual
   double rbest, rprev, prev_nbad, last_bad;
   double eps, rnorm;  // <|S|> and the normalisation of the residual
 };
-// stats: [sum |R|, sum D_new, bad points, non-finite R] of iteration it;
-// abs_src_sum: sum |S| (read at it = 0); hist[it] receives <|R|> / rnorm.
-void launch_relax_control(SolveCtl* ctl, const double* stats, const double* abs_src_sum, double* hist, int it,
+// stats: [sum |R|, sum D_new, bad points, non-finite R] of the iteration
+// it = ctl->next_it (counted on the device, so the same launch serves every
+// iteration of a captured graph); abs_src_sum: sum |S| (read at it = 0);
+// hist[it] receives <|R|> / rnorm.
+void launch_relax_control(SolveCtl* ctl, const double* stats, const double* abs_src_sum, double* hist,
                           int max_iter, int patience, double tol, double inv_m, cudaStream_t s);
 
 template <typename T>

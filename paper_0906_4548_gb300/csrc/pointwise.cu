@@ -88,9 +88,11 @@ void launch_finalize(const double* partials, int nblocks, int ncomp, double* out
 // `patience` iterations: stopped with the minimum-residual iterate; a
 // non-finite R or eps: failed.
 __global__ void k_relax_control(SolveCtl* __restrict__ c, const double* __restrict__ stats,
-                                const double* __restrict__ abs_src_sum, double* __restrict__ hist, int it,
+                                const double* __restrict__ abs_src_sum, double* __restrict__ hist,
                                 int max_iter, int patience, double tol, double inv_m) {
   if (threadIdx.x != 0 || c->done) return;
+  const int it = c->next_it;
+  c->next_it = it + 1;
   if (it == 0) {
     const double eps = abs_src_sum[0] * inv_m;
     c->eps = eps;
@@ -134,9 +136,9 @@ __global__ void k_relax_control(SolveCtl* __restrict__ c, const double* __restri
   c->prev_nbad = nbad;
 }
 
-void launch_relax_control(SolveCtl* ctl, const double* stats, const double* abs_src_sum, double* hist, int it,
+void launch_relax_control(SolveCtl* ctl, const double* stats, const double* abs_src_sum, double* hist,
                           int max_iter, int patience, double tol, double inv_m, cudaStream_t s) {
-  k_relax_control<<<1, 32, 0, s>>>(ctl, stats, abs_src_sum, hist, it, max_iter, patience, tol, inv_m);
+  k_relax_control<<<1, 32, 0, s>>>(ctl, stats, abs_src_sum, hist, max_iter, patience, tol, inv_m);
 }
 
 // Per-thread sums of FP32 data run on the FP32 pipe as an unevaluated pair:

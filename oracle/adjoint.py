@@ -1,0 +1,125 @@
+"""Adjoint of the converged field solve (delta -> phi) in the oracle.
+
+Test infrastructure: see ``oracle/__init__.py``.
+
+The forward solve (Secs. III.B-C) defines D implicitly by R(D, delta) = 0 on
+mean-free fields, with
+    R(D, delta) = D^2 + alpha D - sum_ij H_ij(D)^2 + c2 N[D] - S[delta]  (Eq. FullDGP2),
+and phi = A delta + B D from Eq. FullDGP1, A and B real even Fourier
+multipliers (phi_spectrum with D = 0, resp. delta = 0).  For a cotangent
+phibar of phi (gradient of a scalar L = <phibar, phi>, <.,.> the sum over
+mesh points), the implicit function theorem gives
+    Dbar = B phibar,   J^T lam = Dbar,   deltabar = A phibar + S lam,
+with J = dR/dD and S = -dR/ddelta the source multiplier s (1 - beta/kbar).
+H_ij, N, A, B and S are real even multipliers, hence symmetric, so
+    J^T lam = (2 D + alpha) lam - 2 sum_ij H_ij[H_ij(D) lam] + c2 N[lam]
+(the sum over all nine i, j).  J^T lam = g is solved by the w-splitting the
+forward solve uses (Sec. III.C): the diagonal (2 (1 - w) D + alpha) lam is
+taken implicitly and the rest from the previous iterate,
+    lam_new = (g - 2 w D lam + 2 sum_ij H_ij[H_ij(D) lam] - c2 N[lam] + c) / (2 (1 - w) D + alpha).
+The solve lives on mean-free fields: J maps them to mean-free fields (the
+nonlinear terms' mean vanishes since sum_ij (k_i k_j / k^2)^2 = 1), so the
+system is P J^T lam = P g with P the mean projection and lam mean-free; the
+constant c (the free mean of J^T lam - g) is the one that makes lam_new
+mean-free.  At a converged D the divisor equals sqrt(Delta) of Eq. nabla^2Cwpara.
+
+A cotangent of the forces g_i = -d_i phi enters as phibar = sum_i d_i gbar_i
+(i k_i in Fourier space, the Nyquist component set to zero), the transpose of
+the force multiplier -i k_i.
+
+Parity pins (tests/test_oracle_adjoint.py): central finite differences of
+<phibar, phi(delta)> through the oracle's own nonlinear solve; the identity
+<u, J v> = <J^T u, v> with J v taken by finite differences of the forward
+residual; and the D = 0 limit, where J^T = alpha + c2 N is diagonal in k.
+"""
+
+import numpy as np
+
+from . import field
+from .fft import fft3, ifft3_real
+
+_ALL_PAIRS = [(i, j) for i in range(3) for j in range(3)]
+
+
+def _mult(grid, coef, local_only):
+    """Real even multipliers of Eq. FullDGP1 and Eq. FullDGP2: A, B (phi = A delta + B D),
+    S (source), the N operator n(k) = -1/kbar."""
+    a, E, eta = coef["a"], coef["E"], coef["eta"]
+    ikb = field._kbar_inv(grid, coef, local_only)
+    pref = -(a * E) ** 2 / grid.k2_safe
+    den = 1.0 + ikb / eta
+    A = np.where(grid.zero, 0.0, pref * 1.5 * (eta - 1.0) / eta / den)
+    B = np.where(grid.zero, 0.0, pref * (-1.0 / (2.0 * eta) + coef["c3"] * ikb) / den)
+    S = np.where(grid.zero, 0.0, coef["s"] * (1.0 - coef["beta"] * ikb))
+    Nm = -ikb
+    return A, B, S, Nm
+
+
+def _apply(mult, f):
+    return ifft3_real(mult * fft3(f))
+
+
+def _mean_free(f):
+    return f - np.mean(f)
+
+
+def jt_apply(lam, D, H, grid, coef, local_only=False):
+    """J^T lam for the converged D with Hessian fields H (dict over field.PAIRS)."""
+    _, _, _, Nm = _mult(grid, coef, local_only)
+    out = (2.0 * D + coef["alpha"]) * lam + coef["c2"] * _apply(Nm, lam)
+    for (i, j) in _ALL_PAIRS:
+        p = (min(i, j), max(i, j))
+        out -= 2.0 * _apply(grid.hessian_multiplier(i, j), H[p] * lam)
+    return out
+
+
+def solve_adjoint(D, H, g, grid, coef, w=1.0 / 3.0, tol=1e-12, max_iter=500, local_only=False):
+    """Solve J^T lam = g (mean-free g) by the w-split iteration; returns (lam, info)."""
+    _, _, _, Nm = _mult(grid, coef, local_only)
+    diag = 2.0 * (1.0 - w) * D + coef["alpha"]
+    if np.any(diag <= 0.0):
+        raise ValueError("2 (1 - w) D + alpha must be positive (no bad points at the solution)")
+    gn = float(np.mean(np.abs(g)))
+    scale = gn if gn > 0 else 1.0
+    inv_diag_mean = float(np.mean(1.0 / diag))
+
+    def update(rhs):  # rhs = g - rest; the constant making the result mean-free
+        c = -float(np.mean(rhs / diag)) / inv_diag_mean
+        return (rhs + c) / diag
+
+    lam = update(g)
+    history = []
+    for it in range(max_iter + 1):
+        r = float(np.mean(np.abs(_mean_free(jt_apply(lam, D, H, grid, coef, local_only) - g)))) / scale
+        history.append(r)
+        if r < tol or it == max_iter:
+            break
+        rest = 2.0 * w * D * lam + coef["c2"] * _apply(Nm, lam)
+        for (i, j) in _ALL_PAIRS:
+            p = (min(i, j), max(i, j))
+            rest -= 2.0 * _apply(grid.hessian_multiplier(i, j), H[p] * lam)
+        lam = update(g - rest)
+    return lam, dict(iters=len(history) - 1, history=history, converged=history[-1] < tol)
+
+
+def phibar_from_forces(gbar, grid):
+    """phibar = sum_i d_i gbar_i: the transpose of g_i = -d_i phi (Nyquist component zero)."""
+    out = np.zeros_like(gbar[0])
+    for i in range(3):
+        out += ifft3_real(grid.gradient_multiplier(i) * fft3(gbar[i]))
+    return out
+
+
+def phi_vjp(delta, a, box, omega_m0, rc_H0, phibar, w=1.0 / 3.0, tol=1e-13, adj_tol=1e-12,
+            max_iter=500, local_only=False):
+    """deltabar = d<phibar, phi(delta)>/d delta through the converged nonlinear solve.
+    Returns (deltabar, info) with the forward solve's D and the adjoint's lam."""
+    D, finfo = field.solve_brane_bending(delta, a, box, omega_m0, rc_H0, w, tol, max_iter,
+                                         local_only=local_only)
+    grid, coef = finfo["grid"], finfo["coef"]
+    _, H, _ = field.derived_fields(finfo["D_k"], grid, coef, local_only)
+    A, B, S, _ = _mult(grid, coef, local_only)
+    Dbar = _apply(B, phibar)
+    lam, ainfo = solve_adjoint(D, H, Dbar, grid, coef, w, adj_tol, max_iter, local_only)
+    deltabar = _apply(A, phibar) + _apply(S, lam)
+    return deltabar, dict(D=D, lam=lam, forward=finfo, adjoint=ainfo)

@@ -1,0 +1,95 @@
+"""Pins of the oracle's adjoint of the field solve (oracle/adjoint.py): finite
+differences through the nonlinear solve, the transpose identity against a
+finite-difference Jacobian of the forward residual, and the D = 0 limit."""
+import numpy as np
+
+from oracle import adjoint as adj
+from oracle import background as bg
+from oracle import field
+from oracle.fft import fft3, ifft3_real
+from paper_0906_4548_gb300 import inputs
+
+OM = 0.27
+
+
+def _mean_free(f):
+    return f - f.mean()
+
+
+def _converged(n, box, a, rms, seed):
+    d, _ = inputs.linear_field(n, box, -1.5, rms, seed=seed)
+    D, info = field.solve_brane_bending(d, a, box, OM, 1.0, tol=1e-13)  # no bad points at rms 0.25
+    assert info["converged"]
+    _, H, _ = field.derived_fields(info["D_k"], info["grid"], info["coef"])
+    return d, D, H, info
+
+
+def test_jt_is_the_transpose_of_the_residual_jacobian():
+    """R is quadratic in D, so the central difference (R(D + e v) - R(D - e v)) / 2e is J v exactly
+    (up to rounding); <u, J v> must equal <J^T u, v>."""
+    n, box, a = 16, 60.0, 0.6
+    d, D, H, info = _converged(n, box, a, 0.25, 3)
+    grid, coef = info["grid"], info["coef"]
+    S = info["S"]
+    rng = np.random.default_rng(1)
+    u, v = _mean_free(rng.standard_normal((n, n, n))), _mean_free(rng.standard_normal((n, n, n)))
+
+    def R(Dx):
+        Dm, Hx, Nx = field.derived_fields(fft3(Dx), grid, coef)
+        return field.residual(Dm, Hx, Nx, S, coef)
+
+    e = 1e-3 * np.max(np.abs(D))
+    Jv = (R(D + e * v) - R(D - e * v)) / (2 * e)
+    lhs = np.sum(u * Jv)
+    rhs = np.sum(adj.jt_apply(u, D, H, grid, coef) * v)
+    assert abs(lhs - rhs) < 1e-9 * (np.sum(np.abs(u * Jv)))
+
+
+def test_adjoint_solve_at_zero_D_is_diagonal_in_k():
+    """At D = 0 (every H_ij = 0), J^T = alpha + c2 N, i.e. lam(k) = g(k) / (alpha - c2 / kbar)."""
+    n, box, a = 16, 40.0, 0.4
+    grid = field.KGrid(n, box)
+    coef = bg.coefficients(a, OM, 1.0)
+    z = np.zeros((n, n, n))
+    H = {p: z for p in field.PAIRS}
+    g = _mean_free(np.random.default_rng(2).standard_normal((n, n, n)))
+    lam, info = adj.solve_adjoint(z, H, g, grid, coef, tol=1e-14)
+    assert info["converged"]
+    ikb = field._kbar_inv(grid, coef, False)
+    want = ifft3_real(np.where(grid.zero, 0.0, fft3(g) / (coef["alpha"] - coef["c2"] * ikb)))
+    assert np.max(np.abs(lam - want)) < 1e-12 * np.max(np.abs(want))
+
+
+def test_phi_vjp_matches_central_differences():
+    n, box, a = 16, 60.0, 0.6
+    d, _ = inputs.linear_field(n, box, -1.5, 0.25, seed=4)
+    rng = np.random.default_rng(5)
+    phibar = rng.standard_normal((n, n, n))
+    dbar, info = adj.phi_vjp(d, a, box, OM, 1.0, phibar)
+    assert info["adjoint"]["converged"]
+    for seed in (6, 7):
+        u = _mean_free(np.random.default_rng(seed).standard_normal((n, n, n)))
+        e = 1e-4
+        lp = np.sum(phibar * field.solve_phi(d + e * u, a, box, OM, 1.0, tol=1e-13)[0])
+        lm = np.sum(phibar * field.solve_phi(d - e * u, a, box, OM, 1.0, tol=1e-13)[0])
+        fd = (lp - lm) / (2 * e)
+        assert abs(fd - np.sum(dbar * u)) < 1e-6 * abs(fd)
+
+
+def test_force_cotangent_through_finite_differences():
+    """L = sum_i <gbar_i, g_i(delta)>: phibar from the forces' transpose, then the solve's VJP."""
+    n, box, a = 16, 60.0, 0.6
+    d, _ = inputs.linear_field(n, box, -1.5, 0.25, seed=8)
+    rng = np.random.default_rng(9)
+    gbar = [rng.standard_normal((n, n, n)) for _ in range(3)]
+    grid = field.KGrid(n, box)
+    dbar, _ = adj.phi_vjp(d, a, box, OM, 1.0, adj.phibar_from_forces(gbar, grid))
+    u = _mean_free(rng.standard_normal((n, n, n)))
+    e = 1e-4
+
+    def L(x):
+        g = field.solve_phi(x, a, box, OM, 1.0, tol=1e-13)[1]
+        return sum(np.sum(gbar[i] * g[i]) for i in range(3))
+
+    fd = (L(d + e * u) - L(d - e * u)) / (2 * e)
+    assert abs(fd - np.sum(dbar * u)) < 1e-6 * abs(fd)

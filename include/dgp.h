@@ -171,6 +171,27 @@ int dgp_get_solution(dgp_ctx *c, void *D);
  * delta: device n^3 output.  Positions outside [0, box) are wrapped. */
 int dgp_deposit(dgp_ctx *c, const dgp_particles *parts, void *delta);
 
+/* Adjoint of the context's last accepted nonlinear solve (gravity NL), for
+ * gradients through the field solve (the differentiation pattern of the
+ * method; the paper has no adjoint).  With delta -> D defined by R(D, delta) = 0
+ * (Eq. FullDGP2) on mean-free fields and phi = A delta + B D (Eq. FullDGP1),
+ * a cotangent phibar of phi (and/or gbar_i of the forces g_i = -d_i phi, which
+ * add sum_i d_i gbar_i to phibar) gives
+ *   deltabar = A phibar + S lam,  J^T lam = B phibar,
+ * J the Jacobian of R in D (J^T lam = (2D + alpha) lam - 2 sum_ij H_ij[H_ij(D) lam]
+ * + c2 N[lam]) and S the source multiplier s (1 - beta/kbar).  J^T lam = B phibar
+ * is solved by the relaxation's w-splitting (Sec. III.C) to <|P(J^T lam - g)|> /
+ * <|g|> < tol, P the mean projection, at most params.max_iter updates.
+ *   phibar, gbar_x, gbar_y, gbar_z: device n^3 fields (phibar may be NULL; the
+ *     three gbar all NULL or all set); deltabar: device n^3 output.
+ * info (host, may be NULL): iters = updates, norm_res = last residual, eps =
+ * <|B phibar|>.  Returns DGP_OK, DGP_E_NOT_CONVERGED (deltabar from the last
+ * iterate), DGP_E_STATE (no nonlinear solve accepted since init/reset),
+ * DGP_E_BAD_POINTS (2(1-w)D + alpha <= 0 somewhere: the splitting is not
+ * defined), DGP_E_INVALID (bad arguments or a gravity mode other than NL). */
+int dgp_solve_adjoint(dgp_ctx *c, const void *phibar, const void *gbar_x, const void *gbar_y,
+                      const void *gbar_z, void *deltabar, double tol, dgp_solve_info *info);
+
 /* Host waits of the context (the relaxation's stop-rule verdicts, host outputs)
  * block on an event and yield the CPU (on != 0) instead of spinning (0, the
  * default).  For callers that drive many contexts from many host threads. */

@@ -200,6 +200,8 @@ class EngineBase {
   virtual int deposit(const dgp_particles* parts, void* delta) = 0;
   virtual int sort(dgp_particles* parts, int* cell_start) = 0;
   virtual int brane(int nbins, double* k, double* pc, double* pC, double* dgc, int64_t* nmodes) = 0;
+  virtual int adjoint(const void* phibar, const void* const* gbar, void* deltabar, double tol,
+                      dgp_solve_info* info) = 0;
   virtual int step(dgp_particles* parts, double a, double da, dgp_solve_info* info) = 0;
   virtual int step_host(dgp_particles* parts, double a, double da, dgp_solve_info* info) = 0;
   virtual int pk(const void* delta, int nbins, double* k, double* pk, int64_t* nmodes) = 0;
@@ -289,6 +291,11 @@ class Engine : public EngineBase {
   int* srt_cell = nullptr;      // [3][M]: count, start, cursor
   int* srt_sums = nullptr;
   int64_t nsteps = 0;           // pm_step calls since init / reset
+  // adjoint workspace (allocated on the first dgp_solve_adjoint)
+  T* aP = nullptr;              // [7][M]: H_f(D) lam for six pairs, then lam
+  T* aF = nullptr;              // [4][M]: u, Q, Dbar, A phibar
+  V* aS = nullptr;              // [7][SPEC]
+  double* d_adj = nullptr;      // [8]: sum u, sum r, sum 1/diag, nonpositive diag, sum |res|, sum |g|
 
  public:
   ~Engine() override {
@@ -302,6 +309,7 @@ class Engine : public EngineBase {
     cudaFree(partials); cudaFree(d_rstats); cudaFree(d_misc);
     cudaFree(pk_partials); cudaFree(d_pk);
     cudaFree(srt_key); cudaFree(srt_cell); cudaFree(srt_sums);
+    cudaFree(aP); cudaFree(aF); cudaFree(aS); cudaFree(d_adj);
     cudaFree(d_ctl); cudaFree(d_hist); cudaFreeHost(h_ctl);
     for (int i = 0; i < 3; ++i)
       if (pair_exec[i]) cudaGraphExecDestroy(pair_exec[i]);
@@ -883,6 +891,129 @@ class Engine : public EngineBase {
     return DGP_OK;
   }
 
+  // Adjoint of the last accepted nonlinear solve (see dgp_solve_adjoint).
+  int adjoint(const void* phibar, const void* const* gbar, void* deltabar, double tol,
+              dgp_solve_info* info) override {
+    if (!deltabar || !(tol >= 0) || (!phibar && !gbar[0] && !gbar[1] && !gbar[2])) return DGP_E_INVALID;
+    if ((gbar[0] != nullptr) != (gbar[1] != nullptr) || (gbar[0] != nullptr) != (gbar[2] != nullptr))
+      return DGP_E_INVALID;
+    if (p.gravity != DGP_GRAVITY_NL) return DGP_E_INVALID;
+    if (wcur < 0 || !(last_nl_a > 0.0)) return DGP_E_STATE;
+    if (!aP) {
+      if (cudaMalloc(&aP, sizeof(T) * 7 * M) != cudaSuccess) return DGP_E_NOMEM;
+      if (cudaMalloc(&aF, sizeof(T) * 4 * M) != cudaSuccess) return DGP_E_NOMEM;
+      if (cudaMalloc(&aS, sizeof(V) * 7 * SPEC) != cudaSuccess) return DGP_E_NOMEM;
+      if (cudaMalloc(&d_adj, sizeof(double) * 8) != cudaSuccess) return DGP_E_NOMEM;
+    }
+    int rc;
+    T* const lam = aP + 6 * M;
+    T* const aU = aF;
+    T* const aQ = aF + M;
+    T* const aG = aF + 2 * M;
+    T* const aA = aF + 3 * M;
+    const Coef c = coefficients(last_nl_a, cosmo.omega_m0, p.rc_H0);
+    const KParams kp = kparams(c, DGP_GRAVITY_NL);
+    const ZPrologue none{nullptr, 0.0, 0};
+    // cotangent spectra -> Dbar = B phibar_tot and A phibar_tot (real fields)
+    FieldSet<T> in;
+    for (int i = 0; i < kMaxFields; ++i) in.p[i] = i < 7 ? aS + i * SPEC : nullptr;
+    int mask = 0;
+    if (phibar) {
+      if ((rc = forward_zy((const T*)phibar, in.p[0], none))) return rc;
+      mask |= 1;
+    }
+    for (int i = 0; i < 3; ++i)
+      if (gbar[i]) {
+        if ((rc = forward_zy((const T*)gbar[i], in.p[1 + i], none))) return rc;
+        mask |= 2 << i;
+      }
+    prof.run(KK_X_OTHER, SB * (__builtin_popcount(mask) + 2), stream,
+             [&] { launch_fft_x_adj<T, N>(XOP_ADJ_PHI, in, mask, fs(s6, 2), kp, tw, stream); });
+    T* ga[2] = {aG, aA};
+    if ((rc = inverse_yz(s6, ga, 2))) return rc;
+    // real Hessian fields of the accepted D: H_xx, H_yy, H_xy, H_xz, H_yz (and N)
+    if ((rc = forward_zy(rD[wcur], sD2, none))) return rc;
+    prof.run(KK_X_HESSIAN, 7 * SB, stream, [&] {
+      launch_fft_x_op<T, N>(XOP_HESSIAN, sD2, nullptr, fs(s6, 6), 0, kp, nullptr, 0, 0, 0, tw, stream);
+    });
+    if ((rc = inverse_yz(s6, rH, 6))) return rc;
+    const double* dsum = d_rstats + 4 * wcur + 1;
+    const double alpha = c.alpha, w = p.w;
+    prof.run(KK_REDUCE, RB, stream,
+             [&] { launch_adj_inv_diag<T>(rD[wcur], dsum, M, alpha, w, partials, nblocks, stream); });
+    prof.run(KK_REDUCE, 16.0 * nblocks, stream, [&] { launch_finalize(partials, nblocks, 2, d_adj + 2, stream); });
+    if ((rc = reduce_sum(aG, true, d_adj + 5))) return rc;
+    double hs[8];
+    DGP_CUDA(cudaMemcpyAsync(hs, d_adj, sizeof(double) * 8, cudaMemcpyDeviceToHost, stream));
+    DGP_CUDA(wait_stream());
+    if (hs[3] > 0.0) return DGP_E_BAD_POINTS;  // the w-split diagonal must be positive
+    const double gnorm = hs[5] > 0.0 ? hs[5] : 1.0;
+    // lam_0 from rest = 0, then the w-split iteration
+    DGP_CUDA(cudaMemsetAsync(lam, 0, sizeof(T) * M, stream));
+    DGP_CUDA(cudaMemsetAsync(aQ, 0, sizeof(T) * M, stream));
+    auto update = [&]() -> int {
+      prof.run(KK_RELAX, 6 * RB, stream, [&] {
+        launch_adj_update_a<T>(lam, rD[wcur], dsum, aG, aQ, aU, M, alpha, w, partials, nblocks, stream);
+      });
+      prof.run(KK_REDUCE, 16.0 * nblocks, stream, [&] { launch_finalize(partials, nblocks, 2, d_adj, stream); });
+      prof.run(KK_RELAX, 4 * RB, stream, [&] {
+        launch_adj_update_b<T>(lam, rD[wcur], dsum, aU, M, alpha, w, d_adj, partials, nblocks, stream);
+      });
+      prof.run(KK_REDUCE, 8.0 * nblocks, stream, [&] { launch_finalize(partials, nblocks, 1, d_adj + 4, stream); });
+      DGP_CHECK_LAUNCH();
+      return DGP_OK;
+    };
+    if ((rc = update())) return rc;
+    history.clear();
+    dgp_solve_info inf;
+    memset(&inf, 0, sizeof(inf));
+    inf.eps = hs[5] / (double)M;
+    bool converged = false;
+    T* h5[5] = {rH[0], rH[1], rH[2], rH[3], rH[4]};
+    FieldSet<T> aspec;
+    for (int i = 0; i < kMaxFields; ++i) aspec.p[i] = i < 7 ? aS + i * SPEC : nullptr;
+    int it = 0;
+    for (; it <= p.max_iter; ++it) {
+      prof.run(KK_MISC, 7 * RB, stream,
+               [&] { launch_adj_products<T>(lam, rD[wcur], dsum, h5, aP, M, stream); });
+      prof.run(KK_Z_R2C, 7 * (RB + SB), stream,
+               [&] { launch_fft_z_r2c<T, N>(aP, M, aS, SPEC, 7, none, tw, stream); });
+      prof.run(KK_Y, 14 * SB, stream, [&] { launch_fft_y<T, N>(aspec, 7, false, tw, stream); });
+      prof.run(KK_X_OTHER, 8 * SB, stream,
+               [&] { launch_fft_x_adj<T, N>(XOP_ADJ_COMBINE, aspec, 0x7f, fs(s6, 1), kp, tw, stream); });
+      T* qo[1] = {aQ};
+      if ((rc = inverse_yz(s6, qo, 1))) return rc;
+      if ((rc = update())) return rc;
+      DGP_CUDA(cudaMemcpyAsync(hs, d_adj + 4, sizeof(double), cudaMemcpyDeviceToHost, stream));
+      DGP_CUDA(wait_stream());
+      const double r = hs[0] / gnorm;  // projected residual of the iterate before this update
+      history.push_back(r);
+      if (!isfinite(r)) return DGP_E_NONFINITE;
+      if (r < tol) {
+        converged = true;
+        break;
+      }
+    }
+    // deltabar = A phibar_tot + S lam
+    if ((rc = forward_zy(lam, s6[0], none))) return rc;
+    prof.run(KK_X_OTHER, 2 * SB, stream, [&] {
+      launch_fft_x_op<T, N>(XOP_SOURCE, s6[0], nullptr, fs(s6 + 1, 1), 0, kp, nullptr, 0, 0, 0, tw, stream);
+    });
+    T* so[1] = {aU};
+    if ((rc = inverse_yz(s6 + 1, so, 1))) return rc;
+    prof.run(KK_MISC, 3 * RB, stream, [&] { launch_axpy<T>(aA, aU, (T*)deltabar, M, stream); });
+    DGP_CHECK_LAUNCH();
+    inf.iters = (int)history.size();
+    inf.norm_res = history.empty() ? 0.0 : history.back();
+    inf.min_norm_res = inf.norm_res;
+    inf.status = converged ? DGP_OK : DGP_E_NOT_CONVERGED;
+    if (info) {
+      *info = inf;
+      DGP_CUDA(wait_stream());
+    }
+    return inf.status;
+  }
+
   int bispec(const void* delta, double k1, double k2, int ntheta, const double* theta, double dk, double* b,
              double* q) override {
     if (!delta || ntheta < 0 || (ntheta > 0 && (!theta || !b || !q)) || !(k1 > 0) || !(k2 > 0))
@@ -1085,6 +1216,13 @@ const char* dgp_kernel_name(int kind) {
 int dgp_deposit(dgp_ctx* c, const dgp_particles* parts, void* delta) {
   if (!c) return DGP_E_INVALID;
   return c->eng->deposit(parts, delta);
+}
+
+int dgp_solve_adjoint(dgp_ctx* c, const void* phibar, const void* gbar_x, const void* gbar_y, const void* gbar_z,
+                      void* deltabar, double tol, dgp_solve_info* info) {
+  if (!c) return DGP_E_INVALID;
+  const void* g[3] = {gbar_x, gbar_y, gbar_z};
+  return c->eng->adjoint(phibar, g, deltabar, tol, info);
 }
 
 int dgp_set_blocking_sync(dgp_ctx* c, int on) {

@@ -46,6 +46,8 @@ template <typename T> struct XArgs {
   int nbins;
   double shell_lo, shell_hi;
   const int* skip;
+  FieldSet<T> in;  // adjoint ops: input spectra
+  int in_mask;
 };
 
 template <typename T, int N>
@@ -140,7 +142,8 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
   __syncthreads();
 
   V X0[N2], X1[N2];
-  x_forward<T, N>(args.in0, kz, ky0, lane, yl, s_T, s_tw, X0);
+  constexpr bool ADJ = OP == XOP_ADJ_PHI || OP == XOP_ADJ_COMBINE;
+  if (!ADJ) x_forward<T, N>(args.in0, kz, ky0, lane, yl, s_T, s_tw, X0);
   if (OP == XOP_PHI_FORCE && kp.gravity == 0) x_forward<T, N>(args.in1, kz, ky0, lane, yl, s_T, s_tw, X1);
 
   if (OP == XOP_PK || OP == XOP_PK_BRANE) {
@@ -182,6 +185,91 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
     // the Hessian outputs use 1 / (|n|^2 N^3) directly
     s_inv[k2 * NT + threadIdx.x] = OP == XOP_HESSIAN ? inv * inv_m : inv;
     s_ikb[k2 * NT + threadIdx.x] = ikb;
+  }
+
+  if (OP == XOP_ADJ_PHI) {
+    const T inv_m = kc<T>(kp.inv_m, kp.inv_m_f);
+    V acc[N2];
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) acc[k2] = cmake<V>((T)0, (T)0);
+#pragma unroll 1
+    for (int f = 0; f < 4; ++f) {
+      if (!((args.in_mask >> f) & 1)) continue;  // uniform over the block
+      x_forward<T, N>(args.in.p[f], kz, ky0, lane, yl, s_T, s_tw, X0);
+      const int nfix = f == 2 ? ny : nz;            // component of axis f - 1 when it is y or z
+      const bool nyq_fix = f == 2 ? nyq_y : nyq_z;
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        if (f == 0) {
+          acc[k2] = cadd(acc[k2], X0[k2]);
+        } else {
+          const int kx = lane + N1 * k2;
+          const bool nyq = f == 1 ? kx == N / 2 : nyq_fix;
+          const T ki = kf * (T)(f == 1 ? signed_index(kx, N) : nfix);
+          if (!nyq) acc[k2] = cadd(acc[k2], cmake<V>(-ki * X0[k2].y, ki * X0[k2].x));  // i k_i X
+        }
+      }
+    }
+    const T om15 = kc<T>(1.5 * (kp.eta - 1.0) / kp.eta, kp.om15_f);
+#pragma unroll 1
+    for (int o = 0; o < 2; ++o) {
+      V Y[N2];
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        const int nx = signed_index(lane + N1 * k2, N);
+        const int n2 = nx * nx + ny * ny + nz * nz;
+        Y[k2] = cmake<V>((T)0, (T)0);
+        if (n2 != 0) {
+          const T ikb = s_ikb[k2 * NT + threadIdx.x];
+          const T kmag = kf * sqrt((T)n2);
+          const T pref = -kc<T>(kp.aE * kp.aE, kp.aE2_f) / (kmag * kmag);
+          const T den = (T)1 + ikb * kc<T>(1.0 / kp.eta, kp.inv_eta_f);
+          const T cd = -kc<T>(0.5 / kp.eta, kp.half_inv_eta_f) + kc<T>(kp.c3, kp.c3_f) * ikb;
+          const T m = (o == 0 ? cd : om15) * pref / den;
+          Y[k2] = cscale(acc[k2], m * inv_m);
+        }
+      }
+      x_inverse<T, N>(Y, args.out.p[o], kz, ky0, lane, yl, s_T, s_tw);
+    }
+    return;
+  }
+
+  if (OP == XOP_ADJ_COMBINE) {
+    const T inv_m = kc<T>(kp.inv_m, kp.inv_m_f);
+    const T fy = (T)ny, fz = (T)nz;
+    V acc[N2];
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) acc[k2] = cmake<V>((T)0, (T)0);
+#pragma unroll 1
+    for (int f = 0; f < 7; ++f) {
+      x_forward<T, N>(args.in.p[f], kz, ky0, lane, yl, s_T, s_tw, X0);
+      // pair (a, b) of input f: xx, yy, zz, xy, xz, yz; weight -2 (diagonal) or -4 (twice off-diagonal)
+      const int ca = f == 0 || f == 3 || f == 4 ? 0 : (f == 1 || f == 5 ? 1 : 2);
+      const int cb = f == 0 ? 0 : (f == 1 || f == 3 ? 1 : 2);
+      const T wgt = f < 3 ? (T)-2 : (T)-4;
+      const T fa_fix = ca == 1 ? fy : fz, fb_fix = cb == 1 ? fy : fz;
+      const bool nyq_fix = (ca != 0 && (ca == 1 ? nyq_y : nyq_z)) || (cb != 0 && (cb == 1 ? nyq_y : nyq_z));
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        const int kx = lane + N1 * k2;
+        const T fx = (T)signed_index(kx, N);
+        const T inv_n2 = s_inv[k2 * NT + threadIdx.x];
+        T m;
+        if (f == 6) {
+          m = -kc<T>(kp.c2, kp.c2_f) * s_ikb[k2 * NT + threadIdx.x];  // c2 N = c2 (-1/kbar)
+        } else {
+          T prod = (ca == 0 ? fx : fa_fix) * (cb == 0 ? fx : fb_fix);
+          if (ca != cb && (nyq_fix || ((ca == 0 || cb == 0) && kx == N / 2))) prod = fabs(prod);
+          m = wgt * prod * inv_n2;
+        }
+        acc[k2] = cadd(acc[k2], cscale(X0[k2], m));
+      }
+    }
+    V Y[N2];
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) Y[k2] = cscale(acc[k2], inv_m);
+    x_inverse<T, N>(Y, args.out.p[0], kz, ky0, lane, yl, s_T, s_tw);
+    return;
   }
 
   if (OP == XOP_HESSIAN) {
@@ -310,6 +398,8 @@ void launch_fft_x_op(int op, const vec2_t<T>* in0, const vec2_t<T>* in1, const F
   a.skip = skip;
   a.in0 = in0; a.in1 = in1; a.out = out; a.nout_mask = nout_mask; a.kp = kp;
   a.pk_partials = pk_partials; a.nbins = nbins; a.shell_lo = shell_lo; a.shell_hi = shell_hi;
+  a.in_mask = 0;
+  for (int i = 0; i < kMaxFields; ++i) a.in.p[i] = nullptr;
   switch (op) {
     case XOP_HESSIAN: launch_x<T, N, XOP_HESSIAN>(a, tw, s); break;
     case XOP_SOURCE: launch_x<T, N, XOP_SOURCE>(a, tw, s); break;
@@ -322,10 +412,24 @@ void launch_fft_x_op(int op, const vec2_t<T>* in0, const vec2_t<T>* in1, const F
   }
 }
 
+template <typename T, int N>
+void launch_fft_x_adj(int op, const FieldSet<T>& in, int in_mask, const FieldSet<T>& out, const KParams& kp,
+                      const vec2_t<T>* tw, cudaStream_t s) {
+  XArgs<T> a;
+  a.skip = nullptr;
+  a.in0 = nullptr; a.in1 = nullptr; a.out = out; a.nout_mask = 0; a.kp = kp;
+  a.pk_partials = nullptr; a.nbins = 0; a.shell_lo = 0; a.shell_hi = 0;
+  a.in = in; a.in_mask = in_mask;
+  if (op == XOP_ADJ_PHI) launch_x<T, N, XOP_ADJ_PHI>(a, tw, s);
+  else if (op == XOP_ADJ_COMBINE) launch_x<T, N, XOP_ADJ_COMBINE>(a, tw, s);
+}
+
 #define DGP_INST_X(T, N)                                                                            \
   template void launch_fft_x_op<T, N>(int, const vec2_t<T>*, const vec2_t<T>*, const FieldSet<T>&, int, \
                                       const KParams&, double*, int, double, double, const vec2_t<T>*,   \
-                                      cudaStream_t, const int*);
+                                      cudaStream_t, const int*);                                        \
+  template void launch_fft_x_adj<T, N>(int, const FieldSet<T>&, int, const FieldSet<T>&, const KParams&,  \
+                                       const vec2_t<T>*, cudaStream_t);
 #define DGP_INST_X_ALL(T) DGP_INST_X(T, 16) DGP_INST_X(T, 32) DGP_INST_X(T, 64) DGP_INST_X(T, 128) \
   DGP_INST_X(T, 256) DGP_INST_X(T, 512) DGP_INST_X(T, 48) DGP_INST_X(T, 96)
 DGP_INST_X_ALL(float)

@@ -42,7 +42,7 @@ struct KParams {
 };
 
 enum XOp { XOP_HESSIAN = 0, XOP_SOURCE = 1, XOP_SOURCE_LIN = 2, XOP_PHI_FORCE = 3, XOP_PK = 4,
-           XOP_SHELL = 5, XOP_PK_BRANE = 6 };
+           XOP_SHELL = 5, XOP_PK_BRANE = 6, XOP_ADJ_PHI = 7, XOP_ADJ_COMBINE = 8 };
 
 // Every launcher of a kernel that can run inside a relaxation iteration takes
 // skip: NULL, or a device flag read at kernel entry; when it is nonzero the
@@ -70,6 +70,18 @@ template <typename T, int N>
 void launch_fft_x_op(int op, const vec2_t<T>* in0, const vec2_t<T>* in1, const FieldSet<T>& out,
                      int nout_mask, const KParams& kp, double* pk_partials, int nbins, double shell_lo,
                      double shell_hi, const vec2_t<T>* tw, cudaStream_t s, const int* skip = nullptr);
+
+// Adjoint x-passes (several y-transformed input spectra):
+//  XOP_ADJ_PHI: inputs (mask bit f) phibar, gbar_x, gbar_y, gbar_z; with
+//    phibar_tot = phibar + sum_i i k_i gbar_i (the transpose of g_i = -i k_i phi,
+//    Nyquist component zero), out0 = B phibar_tot and out1 = A phibar_tot, where
+//    phi = A delta + B D is Eq. FullDGP1.
+//  XOP_ADJ_COMBINE: inputs P_xx, P_yy, P_zz, P_xy, P_xz, P_yz (spectra of
+//    H_ij(D) lam) and lam; out0 = -2 sum_ij h_ij P_ij + c2 (-1/kbar) lam over all
+//    nine i, j (off-diagonals twice), h_ij the Hessian multipliers.
+template <typename T, int N>
+void launch_fft_x_adj(int op, const FieldSet<T>& in, int in_mask, const FieldSet<T>& out, const KParams& kp,
+                      const vec2_t<T>* tw, cudaStream_t s);
 
 template <typename T, int N> int x_pass_blocks();
 
@@ -101,6 +113,29 @@ template <typename T, int N> int fused_relax_blocks();
 // D = -3 alpha / 4.  partials[b] = bad points of block b (nblocks blocks).
 template <typename T>
 void launch_sph_update(const T* S, T* D, int64_t m, double alpha, double* partials, int nblocks, cudaStream_t s);
+
+// Adjoint relaxation (J^T lam = g on mean-free fields, w-split as the forward
+// iteration).  d = D - mean(D) (mean = dsum / m), diag = 2 (1 - w) d + alpha.
+//  products: P[f m + i] = H_f lam for f = xx, yy, zz (= d - xx - yy), xy, xz, yz.
+//  update_a: u = (g - 2 w d lam - Q) / diag; partials[b][2] = (sum u, sum diag (lam - u)).
+//  update_b: sums = [sum u, sum diag (lam - u), sum 1/diag]; lam <- u + c / diag with
+//    c = -mean(u) / mean(1/diag) (lam stays mean-free); partials[b] = sum |diag (lam_old - u)
+//    - mean| (the projected residual of the previous lam).
+//  inv_diag: partials[b][2] = (sum 1/diag, number of points with diag <= 0).
+template <typename T>
+void launch_adj_products(const T* lam, const T* D, const double* dsum, T* const* H5, T* P, int64_t m,
+                         cudaStream_t s);
+template <typename T>
+void launch_adj_update_a(const T* lam, const T* D, const double* dsum, const T* g, const T* Q, T* u, int64_t m,
+                         double alpha, double w, double* partials, int nblocks, cudaStream_t s);
+template <typename T>
+void launch_adj_update_b(T* lam, const T* D, const double* dsum, const T* u, int64_t m, double alpha, double w,
+                         const double* sums, double* partials, int nblocks, cudaStream_t s);
+template <typename T>
+void launch_adj_inv_diag(const T* D, const double* dsum, int64_t m, double alpha, double w, double* partials,
+                         int nblocks, cudaStream_t s);
+template <typename T>
+void launch_axpy(const T* x, const T* y, T* out, int64_t m, cudaStream_t s);  // out = x + y
 
 // partials[nblocks][ncomp] -> out[ncomp], fixed summation order.
 void launch_finalize(const double* partials, int nblocks, int ncomp, double* out, cudaStream_t s,

@@ -291,7 +291,135 @@ void launch_sph_update(const T* S, T* D, int64_t m, double alpha, double* partia
   k_sph_update<T><<<nblocks, 256, 0, s>>>(S, D, m, (T)alpha, (T)(alpha * alpha), partials);
 }
 
+// ---- adjoint relaxation (see kernels.cuh)
+template <typename T>
+__device__ __forceinline__ T block_mean_d(const double* dsum, int64_t m) {
+  __shared__ T s_mean;
+  if (threadIdx.x == 0) s_mean = (T)(dsum[0] / (double)m);
+  __syncthreads();
+  return s_mean;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_products(const T* __restrict__ lam, const T* __restrict__ D,
+                                                      const double* __restrict__ dsum, const T* __restrict__ hxx,
+                                                      const T* __restrict__ hyy, const T* __restrict__ hxy,
+                                                      const T* __restrict__ hxz, const T* __restrict__ hyz,
+                                                      T* __restrict__ P, int64_t m) {
+  const T mean = block_mean_d<T>(dsum, m);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const T l = lam[i], a = hxx[i], b = hyy[i];
+    P[i] = a * l;
+    P[m + i] = b * l;
+    P[2 * m + i] = ((D[i] - mean) - a - b) * l;
+    P[3 * m + i] = hxy[i] * l;
+    P[4 * m + i] = hxz[i] * l;
+    P[5 * m + i] = hyz[i] * l;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_update_a(const T* __restrict__ lam, const T* __restrict__ D,
+                                                      const double* __restrict__ dsum, const T* __restrict__ g,
+                                                      const T* __restrict__ Q, T* __restrict__ u, int64_t m,
+                                                      T alpha, T w, double* __restrict__ partials) {
+  const T mean = block_mean_d<T>(dsum, m);
+  double su = 0.0, sr = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const T d = D[i] - mean, l = lam[i];
+    const T diag = (T)2 * ((T)1 - w) * d + alpha;
+    const T ui = (g[i] - (T)2 * w * d * l - Q[i]) / diag;
+    u[i] = ui;
+    su += (double)ui;
+    sr += (double)(diag * (l - ui));
+  }
+  double v[2] = {su, sr};
+  block_sum<2>(v);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = v[0];
+    partials[2 * blockIdx.x + 1] = v[1];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_update_b(T* __restrict__ lam, const T* __restrict__ D,
+                                                      const double* __restrict__ dsum, const T* __restrict__ u,
+                                                      int64_t m, T alpha, T w, const double* __restrict__ sums,
+                                                      double* __restrict__ partials) {
+  const T mean = block_mean_d<T>(dsum, m);
+  const T c = (T)(-(sums[0] / (double)m) / (sums[2] / (double)m));
+  const T rmean = (T)(sums[1] / (double)m);
+  double sa = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const T d = D[i] - mean;
+    const T diag = (T)2 * ((T)1 - w) * d + alpha;
+    const T ui = u[i];
+    sa += (double)fabs(diag * (lam[i] - ui) - rmean);
+    lam[i] = ui + c / diag;
+  }
+  double v[1] = {sa};
+  block_sum<1>(v);
+  if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_inv_diag(const T* __restrict__ D, const double* __restrict__ dsum,
+                                                      int64_t m, T alpha, T w, double* __restrict__ partials) {
+  const T mean = block_mean_d<T>(dsum, m);
+  double s = 0.0, nbad = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const T diag = (T)2 * ((T)1 - w) * (D[i] - mean) + alpha;
+    if (diag > (T)0) s += 1.0 / (double)diag;
+    else nbad += 1.0;
+  }
+  double v[2] = {s, nbad};
+  block_sum<2>(v);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = v[0];
+    partials[2 * blockIdx.x + 1] = v[1];
+  }
+}
+
+template <typename T>
+__global__ void k_axpy(const T* __restrict__ x, const T* __restrict__ y, T* __restrict__ out, int64_t m) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = x[i] + y[i];
+}
+
+template <typename T>
+void launch_adj_products(const T* lam, const T* D, const double* dsum, T* const* H5, T* P, int64_t m,
+                         cudaStream_t s) {
+  k_adj_products<T><<<num_sms() * 4, 256, 0, s>>>(lam, D, dsum, H5[0], H5[1], H5[2], H5[3], H5[4], P, m);
+}
+template <typename T>
+void launch_adj_update_a(const T* lam, const T* D, const double* dsum, const T* g, const T* Q, T* u, int64_t m,
+                         double alpha, double w, double* partials, int nblocks, cudaStream_t s) {
+  k_adj_update_a<T><<<nblocks, 256, 0, s>>>(lam, D, dsum, g, Q, u, m, (T)alpha, (T)w, partials);
+}
+template <typename T>
+void launch_adj_update_b(T* lam, const T* D, const double* dsum, const T* u, int64_t m, double alpha, double w,
+                         const double* sums, double* partials, int nblocks, cudaStream_t s) {
+  k_adj_update_b<T><<<nblocks, 256, 0, s>>>(lam, D, dsum, u, m, (T)alpha, (T)w, sums, partials);
+}
+template <typename T>
+void launch_adj_inv_diag(const T* D, const double* dsum, int64_t m, double alpha, double w, double* partials,
+                         int nblocks, cudaStream_t s) {
+  k_adj_inv_diag<T><<<nblocks, 256, 0, s>>>(D, dsum, m, (T)alpha, (T)w, partials);
+}
+template <typename T>
+void launch_axpy(const T* x, const T* y, T* out, int64_t m, cudaStream_t s) {
+  k_axpy<T><<<num_sms() * 4, 256, 0, s>>>(x, y, out, m);
+}
+
 #define DGP_INST_PW(T)                                                                         \
+  template void launch_adj_products<T>(const T*, const T*, const double*, T* const*, T*, int64_t, cudaStream_t); \
+  template void launch_adj_update_a<T>(const T*, const T*, const double*, const T*, const T*, T*, int64_t,     \
+                                       double, double, double*, int, cudaStream_t);                           \
+  template void launch_adj_update_b<T>(T*, const T*, const double*, const T*, int64_t, double, double,         \
+                                       const double*, double*, int, cudaStream_t);                            \
+  template void launch_adj_inv_diag<T>(const T*, const double*, int64_t, double, double, double*, int,         \
+                                       cudaStream_t);                                                          \
+  template void launch_axpy<T>(const T*, const T*, T*, int64_t, cudaStream_t);                                 \
   template void launch_sph_update<T>(const T*, T*, int64_t, double, double*, int, cudaStream_t); \
   template void launch_sum<T>(const T*, int64_t, bool, double*, int, cudaStream_t);            \
   template void launch_product3_sum<T>(const T*, const T*, const T*, int64_t, double*, int,    \

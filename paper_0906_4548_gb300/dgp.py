@@ -23,7 +23,8 @@ EXPORTED = ["dgp_background", "dgp_init", "dgp_destroy", "dgp_strerror", "dgp_re
             "dgp_solve_forces", "dgp_solve_history", "dgp_get_solution", "dgp_deposit", "pm_step", "pm_step_host", "power_spectrum", "bispectrum",
             "dgp_profile", "dgp_profile_read", "dgp_kernel_name", "dgp_power_spectrum_noalloc",
             "dgp_sort_particles", "dgp_profile_kinds", "dgp_brane_spectra", "dgp_set_blocking_sync",
-            "dgp_batch_create", "dgp_batch_context", "dgp_batch_step", "dgp_batch_destroy"]
+            "dgp_batch_create", "dgp_batch_context", "dgp_batch_step", "dgp_batch_destroy",
+            "dgp_solve_adjoint"]
 DGP_NOALLOC_MAX_N = 64
 DGP_KERNEL_KINDS = 11
 
@@ -94,6 +95,7 @@ def _load():
         "dgp_sort_particles": (i, [vp, P(Particles), vp]),
         "dgp_brane_spectra": (i, [vp, i, P(d), P(d), P(d), P(d), P(i64)]),
         "dgp_set_blocking_sync": (i, [vp, i]),
+        "dgp_solve_adjoint": (i, [vp, vp, vp, vp, vp, vp, d, P(SolveInfo)]),
         "dgp_batch_create": (i, [P(vp), i, P(Params), P(Cosmology)]),
         "dgp_batch_context": (i, [vp, i, P(vp)]),
         "dgp_batch_step": (i, [vp, P(Particles), P(d), P(d), P(SolveInfo), vp]),
@@ -224,6 +226,15 @@ def dgp_solve_history(ctx):
     out = np.zeros(n)
     lib.dgp_solve_history(ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n)
     return out
+
+
+def dgp_solve_adjoint(ctx, phibar, deltabar, tol, gbar=None):
+    """deltabar for a cotangent phibar (and/or gbar = (gx, gy, gz)) of the last accepted solve."""
+    info = SolveInfo()
+    g = gbar if gbar is not None else (None, None, None)
+    st = _check(lib.dgp_solve_adjoint(ctx, _ptr(phibar), _ptr(g[0]), _ptr(g[1]), _ptr(g[2]), _ptr(deltabar), tol,
+                                      ctypes.byref(info)), "dgp_solve_adjoint", (DGP_OK, DGP_E_NOT_CONVERGED))
+    return st, info.as_dict()
 
 
 def dgp_get_solution(ctx, D):

@@ -1,0 +1,101 @@
+"""Adjoint of the converged field solve on the GPU (dgp_solve_adjoint) against
+the oracle's (oracle/adjoint.py) and against central differences of GPU solves."""
+import numpy as np
+import pytest
+
+from oracle import adjoint as oadj
+from oracle import field as ofield
+from paper_0906_4548_gb300 import inputs
+
+from test_gpu_parity import OM, rel_l2, to_dev  # noqa: F401
+from test_gpu_parity import dgp, torch_dev  # noqa: F401  (fixtures)
+
+pytestmark = pytest.mark.gpu
+
+
+def _field(n, box, rms, seed):
+    d, _ = inputs.linear_field(n, box, -1.5, rms, seed=seed)  # min delta > -1: no bad points
+    return d
+
+
+@pytest.mark.parametrize("n,prec,tol,use_forces", [(32, 2, 1e-9, False), (32, 2, 1e-9, True), (48, 2, 1e-9, False),
+                                                   (64, 3, 1e-4, False), (64, 0, 1e-4, True)])
+def test_adjoint_matches_oracle(dgp, torch_dev, n, prec, tol, use_forces):
+    torch, dev = torch_dev
+    box, a = 100.0, 0.6
+    td = torch.float64 if prec == dgp.DGP_FP64 else torch.float32
+    d = _field(n, box, 0.25, 4)
+    rng = np.random.default_rng(5)
+    if use_forces:
+        gbar = [rng.standard_normal((n, n, n)) for _ in range(3)]
+        phibar = oadj.phibar_from_forces(gbar, ofield.KGrid(n, box))
+    else:
+        phibar = rng.standard_normal((n, n, n))
+    want, oinfo = oadj.phi_vjp(d, a, box, OM, 1.0, phibar)
+    assert oinfo["adjoint"]["converged"]
+    ctx = dgp.dgp_init(box, n, 1.0, OM, precision=prec, tol=1e-12 if prec == 2 else 1e-6, max_iter=200)
+    try:
+        dd = to_dev(torch_dev, d, td)
+        dgp.dgp_solve_phi(ctx, a, dd, None, 1e-12 if prec == 2 else 1e-6)
+        out = torch.empty_like(dd)
+        if use_forces:
+            st, info = dgp.dgp_solve_adjoint(ctx, None, out, 1e-12 if prec == 2 else 1e-6,
+                                             gbar=[to_dev(torch_dev, g, td) for g in gbar])
+        else:
+            st, info = dgp.dgp_solve_adjoint(ctx, to_dev(torch_dev, phibar, td), out, 1e-12 if prec == 2 else 1e-6)
+        got = out.double().cpu().numpy()
+    finally:
+        dgp.dgp_destroy(ctx)
+    assert st == dgp.DGP_OK and info["iters"] >= 1
+    assert rel_l2(got, want) < tol
+
+
+def test_adjoint_directional_derivative_of_gpu_solves(dgp, torch_dev):
+    """<deltabar, u> against (L(delta + e u) - L(delta - e u)) / 2e with L = <phibar, phi> from GPU solves (FP64)."""
+    torch, dev = torch_dev
+    n, box, a = 32, 100.0, 0.6
+    d = _field(n, box, 0.25, 6)
+    rng = np.random.default_rng(7)
+    phibar = rng.standard_normal((n, n, n))
+    u = rng.standard_normal((n, n, n))
+    u -= u.mean()
+    ctx = dgp.dgp_init(box, n, 1.0, OM, precision=dgp.DGP_FP64, tol=1e-13, max_iter=300)
+    try:
+        pb = to_dev(torch_dev, phibar, torch.float64)
+        phi = torch.empty((n, n, n), dtype=torch.float64, device=dev)
+
+        def L(x):
+            dgp.dgp_reset(ctx)
+            dgp.dgp_solve_phi(ctx, a, to_dev(torch_dev, x, torch.float64), phi, 1e-13)
+            return float((phi * pb).sum())
+
+        e = 1e-4
+        fd = (L(d + e * u) - L(d - e * u)) / (2 * e)
+        dgp.dgp_reset(ctx)
+        dgp.dgp_solve_phi(ctx, a, to_dev(torch_dev, d, torch.float64), None, 1e-13)
+        out = torch.empty_like(phi)
+        st, info = dgp.dgp_solve_adjoint(ctx, pb, out, 1e-12)
+        ad = float((out * to_dev(torch_dev, u, torch.float64)).sum())
+    finally:
+        dgp.dgp_destroy(ctx)
+    assert abs(fd - ad) < 1e-6 * abs(fd)
+
+
+def test_adjoint_states_and_arguments(dgp, torch_dev):
+    torch, dev = torch_dev
+    n, box = 16, 50.0
+    ctx = dgp.dgp_init(box, n, 1.0, OM, precision=dgp.DGP_MIXED)
+    try:
+        z = torch.zeros((n, n, n), dtype=torch.float32, device=dev)
+        out = torch.empty_like(z)
+        with pytest.raises(dgp.DgpError) as e:
+            dgp.dgp_solve_adjoint(ctx, z, out, 1e-6)
+        assert e.value.status == dgp.DGP_E_STATE
+        dgp.dgp_solve_phi(ctx, 0.5, to_dev(torch_dev, _field(n, box, 0.2, 1), torch.float32), None, 1e-6)
+        with pytest.raises(dgp.DgpError) as e:
+            dgp.dgp_solve_adjoint(ctx, None, out, 1e-6)
+        assert e.value.status == dgp.DGP_E_INVALID
+        st, info = dgp.dgp_solve_adjoint(ctx, z, out, 1e-6)  # zero cotangent: zero gradient
+        assert float(out.abs().max()) == 0.0
+    finally:
+        dgp.dgp_destroy(ctx)

@@ -27,14 +27,19 @@ A cotangent of the forces g_i = -d_i phi enters as phibar = sum_i d_i gbar_i
 (i k_i in Fourier space, the Nyquist component set to zero), the transpose of
 the force multiplier -i k_i.
 
+The particle side (deposit, force interpolation, the kick-drift-kick step)
+is differentiated below by hand from the CIC weights' derivatives.
+
 Parity pins (tests/test_oracle_adjoint.py): central finite differences of
 <phibar, phi(delta)> through the oracle's own nonlinear solve; the identity
 <u, J v> = <J^T u, v> with J v taken by finite differences of the forward
-residual; and the D = 0 limit, where J^T = alpha + c2 N is diagonal in k.
+residual; the D = 0 limit, where J^T = alpha + c2 N is diagonal in k; and
+central differences of the deposit, the particle forces and a whole step.
 """
 
 import numpy as np
 
+from . import background as bg
 from . import field
 from .fft import fft3, ifft3_real
 
@@ -123,3 +128,88 @@ def phi_vjp(delta, a, box, omega_m0, rc_H0, phibar, w=1.0 / 3.0, tol=1e-13, adj_
     lam, ainfo = solve_adjoint(D, H, Dbar, grid, coef, w, adj_tol, max_iter, local_only)
     deltabar = _apply(A, phibar) + _apply(S, lam)
     return deltabar, dict(D=D, lam=lam, forward=finfo, adjoint=ainfo)
+
+
+# ---------------------------------------------------------------- particles
+# CIC (Eq. CIC) is piecewise linear in the positions: for the corner c of a
+# particle the weight is W = w_x w_y w_z with w = 1 - f or f per axis, and
+# dW/dx_a = (+-1/d) times the other two factors (- for the lower corner).
+
+def _corner_terms(pos, n, box):
+    """Yield (flat corner index, W, dW/dx, dW/dy, dW/dz) for the 8 corners of every particle."""
+    from . import pm
+    d = box / n
+    (ix, fx), (iy, fy), (iz, fz) = pm._cic_cells(np.asarray(pos, float), n, box)
+    for dx in (0, 1):
+        wx, sx, jx = (fx, 1.0 / d, (ix + 1) % n) if dx else (1.0 - fx, -1.0 / d, ix)
+        for dy in (0, 1):
+            wy, sy, jy = (fy, 1.0 / d, (iy + 1) % n) if dy else (1.0 - fy, -1.0 / d, iy)
+            for dz in (0, 1):
+                wz, sz, jz = (fz, 1.0 / d, (iz + 1) % n) if dz else (1.0 - fz, -1.0 / d, iz)
+                yield (jx * n + jy) * n + jz, wx * wy * wz, sx * wy * wz, wx * sy * wz, wx * wy * sz
+
+
+def deposit_vjp(pos, n, box, rhobar):
+    """Transpose of the Jacobian of rho(x) = sum_p W(x - x_p) in the positions:
+    xbar_p = sum_c grad W(x_p - c) rhobar_c, shape (3, Np)."""
+    flat = np.asarray(rhobar, float).reshape(-1)
+    out = np.zeros((3, np.asarray(pos).shape[1]))
+    for idx, _, gx, gy, gz in _corner_terms(pos, n, box):
+        v = flat[idx]
+        out[0] += gx * v
+        out[1] += gy * v
+        out[2] += gz * v
+    return out
+
+
+def gather_vjp(grids, pos, box, fbar):
+    """F_p,i = sum_c W(x_p - c) G_i(c) (the force interpolation of Sec. III.A): for the
+    particle cotangents fbar (3, Np) returns (Gbar, xbar): Gbar_i = sum_p W fbar_i,p (the
+    deposit of fbar) and xbar_p = sum_c grad W(x_p - c) (G(c) . fbar_p)."""
+    from . import pm
+    n = grids[0].shape[0]
+    Gbar = [pm.cic_deposit(pos, n, box, mass=fbar[i]) for i in range(3)]
+    flats = [np.asarray(g, float).reshape(-1) for g in grids]
+    xbar = np.zeros((3, np.asarray(pos).shape[1]))
+    for idx, _, gx, gy, gz in _corner_terms(pos, n, box):
+        v = flats[0][idx] * fbar[0] + flats[1][idx] * fbar[1] + flats[2][idx] * fbar[2]
+        xbar[0] += gx * v
+        xbar[1] += gy * v
+        xbar[2] += gz * v
+    return Gbar, xbar
+
+
+def force_vjp(pos, a, n, box, omega_m0, rc_H0, fbar, w=1.0 / 3.0, tol=1e-13, adj_tol=1e-12):
+    """xbar for the particle forces F(x) = gather(g(delta(x)), x) of Sec. III.A: the
+    direct term of the gather, plus deposit of fbar -> force cotangent grids -> the solve's
+    adjoint -> deltabar -> rhobar = deltabar M / Np (delta = rho M / Np - 1, the particle
+    count being conserved) -> the deposit's transpose."""
+    from . import pm
+    pos = np.asarray(pos, float) % box
+    npart = pos.shape[1]
+    delta = pm.density_contrast(pm.cic_deposit(pos, n, box))
+    _, g, _, _ = field.solve_phi(delta, a, box, omega_m0, rc_H0, w, tol)
+    Gbar, xbar = gather_vjp(g, pos, box, fbar)
+    grid = field.KGrid(n, box)
+    dbar, _ = phi_vjp(delta, a, box, omega_m0, rc_H0, phibar_from_forces(Gbar, grid), w, tol, adj_tol)
+    return xbar + deposit_vjp(pos, n, box, dbar * (n ** 3 / npart))
+
+
+def step_vjp(pos0, mom0, a, da, xbar1, pbar1, n, box, omega_m0, rc_H0, w=1.0 / 3.0, tol=1e-13):
+    """Transpose of the Jacobian of one kick-drift-kick step (Sec. III.A, as PMState.step):
+    p_h = p0 + K1 F(x0), x1 = x0 + Dr p_h (mod box), p1 = p_h + K2 F(x1).
+    Returns (xbar0, pbar0) for the cotangents (xbar1, pbar1) of (x1, p1)."""
+    a1 = a + da
+    ah = np.exp(0.5 * (np.log(a) + np.log(a1)))
+    k1 = bg.kick_factor(a, ah, omega_m0, rc_H0)
+    k2 = bg.kick_factor(ah, a1, omega_m0, rc_H0)
+    dr = bg.drift_factor(a, a1, omega_m0, rc_H0)
+    from . import pm
+    st = pm.PMState(pos0, mom0, a, n, box, omega_m0, rc_H0, w=w, tol=tol)
+    f0 = st.forces_at_particles()
+    ph = st.mom + k1 * f0
+    x1 = (st.pos + dr * ph) % box
+    xbar = xbar1 + force_vjp(x1, a1, n, box, omega_m0, rc_H0, k2 * pbar1, w, tol)
+    phbar = pbar1 + dr * xbar
+    xbar0 = xbar + force_vjp(st.pos, a, n, box, omega_m0, rc_H0, k1 * phbar, w, tol)
+    return xbar0, phbar

@@ -93,3 +93,84 @@ def test_force_cotangent_through_finite_differences():
 
     fd = (L(d + e * u) - L(d - e * u)) / (2 * e)
     assert abs(fd - np.sum(dbar * u)) < 1e-6 * abs(fd)
+
+
+# ---------------------------------------------------------------- particle side
+from oracle import pm  # noqa: E402
+
+
+def _particles(n, box, sig, seed):
+    pos, mom = inputs.lattice_particles(n, box)
+    rng = np.random.default_rng(seed)
+    pos = (pos + rng.normal(0, sig * box / n, pos.shape)) % box
+    mom = rng.normal(0, 0.5, pos.shape)
+    return pos, mom
+
+
+def test_deposit_vjp_central_differences():
+    n, box = 8, 16.0
+    pos, _ = _particles(n, box, 0.3, 1)
+    rng = np.random.default_rng(2)
+    rbar = rng.standard_normal((n, n, n))
+    u = rng.standard_normal(pos.shape)
+    e = 1e-7
+    fd = (np.sum(rbar * pm.cic_deposit(pos + e * u, n, box)) - np.sum(rbar * pm.cic_deposit(pos - e * u, n, box))) / (2 * e)
+    assert abs(fd - np.sum(adj.deposit_vjp(pos, n, box, rbar) * u)) < 1e-7 * abs(fd)
+
+
+def test_gather_vjp_central_differences():
+    n, box = 8, 16.0
+    pos, _ = _particles(n, box, 0.3, 3)
+    rng = np.random.default_rng(4)
+    grids = [rng.standard_normal((n, n, n)) for _ in range(3)]
+    fbar = rng.standard_normal(pos.shape)
+    u = rng.standard_normal(pos.shape)
+    dg = [rng.standard_normal((n, n, n)) for _ in range(3)]
+
+    def L(x, gs):
+        return sum(np.sum(fbar[i] * pm.cic_interpolate(gs[i], x, box)) for i in range(3))
+
+    Gbar, xbar = adj.gather_vjp(grids, pos, box, fbar)
+    e = 1e-7
+    fd_x = (L(pos + e * u, grids) - L(pos - e * u, grids)) / (2 * e)
+    assert abs(fd_x - np.sum(xbar * u)) < 1e-7 * abs(fd_x)
+    fd_g = (L(pos, [g + e * h for g, h in zip(grids, dg)]) - L(pos, [g - e * h for g, h in zip(grids, dg)])) / (2 * e)
+    assert abs(fd_g - sum(np.sum(Gbar[i] * dg[i]) for i in range(3))) < 1e-7 * abs(fd_g)
+
+
+def test_force_vjp_central_differences():
+    """Particle forces through deposit, density contrast, the nonlinear solve and the gather."""
+    n, box, a = 16, 80.0, 0.5
+    pos, _ = _particles(n, box, 0.25, 5)
+    rng = np.random.default_rng(6)
+    fbar = rng.standard_normal(pos.shape)
+    u = rng.standard_normal(pos.shape)
+
+    def L(x):
+        st = pm.PMState(x, np.zeros_like(x), a, n, box, OM, 1.0, tol=1e-13)
+        return np.sum(fbar * st.forces_at_particles())
+
+    e = 1e-5
+    fd = (L(pos + e * u) - L(pos - e * u)) / (2 * e)
+    got = np.sum(adj.force_vjp(pos, a, n, box, OM, 1.0, fbar) * u)
+    assert abs(fd - got) < 1e-6 * abs(fd)
+
+
+def test_step_vjp_central_differences():
+    n, box, a, da = 16, 80.0, 0.5, 0.02
+    pos, mom = _particles(n, box, 0.25, 7)
+    rng = np.random.default_rng(8)
+    xb1, pb1 = rng.standard_normal(pos.shape), rng.standard_normal(pos.shape)
+    u, v = rng.standard_normal(pos.shape), rng.standard_normal(pos.shape)
+
+    def L(x, p):
+        st = pm.PMState(x, p, a, n, box, OM, 1.0, tol=1e-13)
+        st.step(da)
+        # positions enter through their increments (x1 - x0 is smooth; the wrap is not)
+        return np.sum(xb1 * ((st.pos - x + box / 2) % box)) + np.sum(pb1 * st.mom)
+
+    xb0, pb0 = adj.step_vjp(pos, mom, a, da, xb1, pb1, n, box, OM, 1.0)
+    e = 1e-5
+    fd = (L(pos + e * u, mom + e * v) - L(pos - e * u, mom - e * v)) / (2 * e)
+    got = np.sum((xb0 - xb1) * u) + np.sum(pb0 * v)
+    assert abs(fd - got) < 1e-6 * abs(fd)

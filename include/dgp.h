@@ -192,6 +192,24 @@ int dgp_deposit(dgp_ctx *c, const dgp_particles *parts, void *delta);
 int dgp_solve_adjoint(dgp_ctx *c, const void *phibar, const void *gbar_x, const void *gbar_y,
                       const void *gbar_z, void *deltabar, double tol, dgp_solve_info *info);
 
+/* Transpose of the Jacobian of one pm_step (gravity NL): for cotangents
+ * (xbar1, pbar1) of the positions and momenta after the step from a to a + da,
+ * returns those of the state before it, given that state in `start` (device
+ * arrays, unchanged).  cot holds (xbar1, pbar1) on entry (x, y, z, px, py, pz
+ * members, device arrays of n values) and (xbar0, pbar0) on return.  The step
+ * is recomputed from `start`; with p_h = p0 + K1 F(x0), x1 = x0 + Dr p_h and
+ * p1 = p_h + K2 F(x1):
+ *   xbar = xbar1 + F'(x1)^T (K2 pbar1),  pbar0 = pbar1 + Dr xbar,
+ *   xbar0 = xbar + F'(x0)^T (K1 pbar0),
+ * where F'(x)^T fbar is the force VJP: the gather's transpose with the CIC
+ * weights' derivatives, plus the deposit of fbar -> dgp_solve_adjoint (force
+ * cotangents) -> the density contrast's cotangent -> the deposit's transpose.
+ * Three nonlinear solves (x0, x1, x0) and two adjoint solves at params.tol.
+ * The periodic wrap is the identity on the cotangents (positions differ by
+ * lattice vectors only).  The context's warm start and force cache are
+ * replaced.  DGP_E_INVALID for bad arguments or a gravity mode other than NL. */
+int pm_step_adjoint(dgp_ctx *c, const dgp_particles *start, double a, double da, dgp_particles *cot);
+
 /* Host waits of the context (the relaxation's stop-rule verdicts, host outputs)
  * block on an event and yield the CPU (on != 0) instead of spinning (0, the
  * default).  For callers that drive many contexts from many host threads. */

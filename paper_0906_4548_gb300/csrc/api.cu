@@ -202,6 +202,7 @@ class EngineBase {
   virtual int brane(int nbins, double* k, double* pc, double* pC, double* dgc, int64_t* nmodes) = 0;
   virtual int adjoint(const void* phibar, const void* const* gbar, void* deltabar, double tol,
                       dgp_solve_info* info) = 0;
+  virtual int step_adjoint(const dgp_particles* start, double a, double da, dgp_particles* cot) = 0;
   virtual int step(dgp_particles* parts, double a, double da, dgp_solve_info* info) = 0;
   virtual int step_host(dgp_particles* parts, double a, double da, dgp_solve_info* info) = 0;
   virtual int pk(const void* delta, int nbins, double* k, double* pk, int64_t* nmodes) = 0;
@@ -296,6 +297,9 @@ class Engine : public EngineBase {
   T* aF = nullptr;              // [4][M]: u, Q, Dbar, A phibar
   V* aS = nullptr;              // [7][SPEC]
   double* d_adj = nullptr;      // [8]: sum u, sum r, sum 1/diag, nonpositive diag, sum |res|, sum |g|
+  T* ap[6] = {};                // step adjoint: the recomputed particle state
+  int64_t ap_n = 0;
+  T* aFb = nullptr;             // [3][M] force-cotangent grids
 
  public:
   ~Engine() override {
@@ -309,7 +313,8 @@ class Engine : public EngineBase {
     cudaFree(partials); cudaFree(d_rstats); cudaFree(d_misc);
     cudaFree(pk_partials); cudaFree(d_pk);
     cudaFree(srt_key); cudaFree(srt_cell); cudaFree(srt_sums);
-    cudaFree(aP); cudaFree(aF); cudaFree(aS); cudaFree(d_adj);
+    cudaFree(aP); cudaFree(aF); cudaFree(aS); cudaFree(d_adj); cudaFree(aFb);
+    for (int i = 0; i < 6; ++i) cudaFree(ap[i]);
     cudaFree(d_ctl); cudaFree(d_hist); cudaFreeHost(h_ctl);
     for (int i = 0; i < 3; ++i)
       if (pair_exec[i]) cudaGraphExecDestroy(pair_exec[i]);
@@ -1014,6 +1019,77 @@ class Engine : public EngineBase {
     return inf.status;
   }
 
+  // VJP of the particle forces at the positions xs.p[0..2] for the cotangent
+  // scale * xs.p[3..5]; accumulates into xb.p[0..2].  Solves at a first, so the
+  // context's accepted D is the one the adjoint needs.
+  int force_vjp(const ParticleSet<T>& xs, int64_t np, double scale, double a, const ParticleSet<T>& xb) {
+    int rc;
+    dgp_particles dp{xs.p[0], xs.p[1], xs.p[2], xs.p[0], xs.p[1], xs.p[2], np};
+    if ((rc = forces_at(&dp, a, nullptr))) return rc;
+    const CicParams cp = cic();
+    T* fb[3] = {aFb, aFb + M, aFb + 2 * M};
+    prof.run(KK_MISC, 3 * RB, stream, [&] { launch_fill<T>(aFb, 3 * M, (T)0, stream); });
+    prof.run(KK_DEPOSIT, 6.0 * sizeof(T) * np + 3 * RB, stream,
+             [&] { launch_deposit_vec<T>(xs, scale, np, fb, cp, stream); });
+    DGP_CHECK_LAUNCH();
+    const void* gb[3] = {fb[0], fb[1], fb[2]};
+    rc = adjoint(nullptr, gb, rRho, p.tol, nullptr);
+    if (rc != DGP_OK && rc != DGP_E_NOT_CONVERGED) return rc;
+    prof.run(KK_GATHER, 9.0 * sizeof(T) * np + 4 * RB, stream, [&] {
+      launch_force_vjp_gather<T>(xs, scale, np, rG, rRho, (double)M / (double)np, xb, cp, stream);
+    });
+    DGP_CHECK_LAUNCH();
+    return DGP_OK;
+  }
+
+  // Transpose of one kick-drift-kick step (see pm_step_adjoint).
+  int step_adjoint(const dgp_particles* st, double a, double da, dgp_particles* cot) override {
+    if (!valid_parts(st) || !valid_parts(cot) || st->n == 0 || cot->n != st->n) return DGP_E_INVALID;
+    if (!(a > 0.0) || !(da > 0.0) || !isfinite(a + da)) return DGP_E_INVALID;
+    if (p.gravity != DGP_GRAVITY_NL) return DGP_E_INVALID;
+    const int64_t np = st->n;
+    if (ap_n < np) {
+      for (int i = 0; i < 6; ++i) {
+        cudaFree(ap[i]);
+        ap[i] = nullptr;
+        if (cudaMalloc(&ap[i], sizeof(T) * np) != cudaSuccess) { ap_n = 0; return DGP_E_NOMEM; }
+      }
+      ap_n = np;
+    }
+    if (!aFb && cudaMalloc(&aFb, sizeof(T) * 3 * M) != cudaSuccess) return DGP_E_NOMEM;
+    const double a1 = a + da;
+    const double ah = exp(0.5 * (log(a) + log(a1)));
+    const double om = cosmo.omega_m0, rc_ = p.rc_H0;
+    const double k1 = time_integral(a, ah, om, rc_, 0), dr = time_integral(a, a1, om, rc_, 2);
+    const double k2 = time_integral(ah, a1, om, rc_, 0);
+    int rc;
+    // recompute x1 (and p_h) from the start state on the context's copies
+    const void* src[6] = {st->x, st->y, st->z, st->px, st->py, st->pz};
+    for (int i = 0; i < 6; ++i)
+      DGP_CUDA(cudaMemcpyAsync(ap[i], src[i], sizeof(T) * np, cudaMemcpyDeviceToDevice, stream));
+    dgp_particles sp{ap[0], ap[1], ap[2], ap[3], ap[4], ap[5], np};
+    if ((rc = forces_at(&sp, a, nullptr))) return rc;
+    const CicParams cp = cic();
+    prof.run(KK_GATHER, 12.0 * sizeof(T) * np + 3 * RB, stream, [&] {
+      launch_gather_kick<T>(ap[0], ap[1], ap[2], ap[3], ap[4], ap[5], np, rG[0], rG[1], rG[2], cp, k1, dr, 1,
+                            stream);
+    });
+    DGP_CHECK_LAUNCH();
+    T* const cv[6] = {(T*)cot->x, (T*)cot->y, (T*)cot->z, (T*)cot->px, (T*)cot->py, (T*)cot->pz};
+    const ParticleSet<T> xb{{cv[0], cv[1], cv[2], cv[0], cv[1], cv[2]}};
+    const ParticleSet<T> pb{{cv[3], cv[4], cv[5], cv[3], cv[4], cv[5]}};
+    // x1: fbar = k2 pbar1
+    if ((rc = force_vjp(ParticleSet<T>{{ap[0], ap[1], ap[2], cv[3], cv[4], cv[5]}}, np, k2, a1, xb))) return rc;
+    // pbar_h = pbar1 + Dr xbar
+    prof.run(KK_MISC, 9.0 * sizeof(T) * np, stream, [&] { launch_particle_axpy<T>(xb, dr, np, pb, stream); });
+    DGP_CHECK_LAUNCH();
+    // x0: fbar = k1 pbar_h
+    const ParticleSet<T> at0{{(T*)st->x, (T*)st->y, (T*)st->z, cv[3], cv[4], cv[5]}};
+    if ((rc = force_vjp(at0, np, k1, a, xb))) return rc;
+    force_valid = false;
+    return DGP_OK;
+  }
+
   int bispec(const void* delta, double k1, double k2, int ntheta, const double* theta, double dk, double* b,
              double* q) override {
     if (!delta || ntheta < 0 || (ntheta > 0 && (!theta || !b || !q)) || !(k1 > 0) || !(k2 > 0))
@@ -1216,6 +1292,11 @@ const char* dgp_kernel_name(int kind) {
 int dgp_deposit(dgp_ctx* c, const dgp_particles* parts, void* delta) {
   if (!c) return DGP_E_INVALID;
   return c->eng->deposit(parts, delta);
+}
+
+int pm_step_adjoint(dgp_ctx* c, const dgp_particles* start, double a, double da, dgp_particles* cot) {
+  if (!c) return DGP_E_INVALID;
+  return c->eng->step_adjoint(start, a, da, cot);
 }
 
 int dgp_solve_adjoint(dgp_ctx* c, const void* phibar, const void* gbar_x, const void* gbar_y, const void* gbar_z,

@@ -213,6 +213,21 @@ template <typename T>
 void launch_cic_deposit_warp(const T* x, const T* y, const T* z, int64_t np, T* rho, CicParams cp,
                               cudaStream_t s);
 
+// Particle side of the step adjoint (particle_adjoint.cu); pp.p[0..2] positions,
+// pp.p[3..5] a per-particle 3-vector c, scaled by `scale`:
+//  deposit_vec: g_i += sum_p W scale c_i,p;
+//  force_vjp_gather: xb_p += sum_c grad W (G(c) . scale c_p + rscale rbar(c));
+//  particle_axpy: out[0..2] += a in[0..2].
+template <typename T>
+void launch_deposit_vec(const ParticleSet<T>& pp, double scale, int64_t np, T* const* g, CicParams cp,
+                        cudaStream_t s);
+template <typename T>
+void launch_force_vjp_gather(const ParticleSet<T>& pp, double scale, int64_t np, T* const* G, const T* rbar,
+                             double rscale, const ParticleSet<T>& xb, CicParams cp, cudaStream_t s);
+template <typename T>
+void launch_particle_axpy(const ParticleSet<T>& in, double a, int64_t np, const ParticleSet<T>& out,
+                          cudaStream_t s);
+
 int num_sms();
 
 }  // namespace dgp

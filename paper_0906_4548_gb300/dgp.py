@@ -24,7 +24,7 @@ EXPORTED = ["dgp_background", "dgp_init", "dgp_destroy", "dgp_strerror", "dgp_re
             "dgp_profile", "dgp_profile_read", "dgp_kernel_name", "dgp_power_spectrum_noalloc",
             "dgp_sort_particles", "dgp_profile_kinds", "dgp_brane_spectra", "dgp_set_blocking_sync",
             "dgp_batch_create", "dgp_batch_context", "dgp_batch_step", "dgp_batch_destroy",
-            "dgp_solve_adjoint"]
+            "dgp_solve_adjoint", "pm_step_adjoint"]
 DGP_NOALLOC_MAX_N = 64
 DGP_KERNEL_KINDS = 11
 
@@ -96,6 +96,7 @@ def _load():
         "dgp_brane_spectra": (i, [vp, i, P(d), P(d), P(d), P(d), P(i64)]),
         "dgp_set_blocking_sync": (i, [vp, i]),
         "dgp_solve_adjoint": (i, [vp, vp, vp, vp, vp, vp, d, P(SolveInfo)]),
+        "pm_step_adjoint": (i, [vp, P(Particles), d, d, P(Particles)]),
         "dgp_batch_create": (i, [P(vp), i, P(Params), P(Cosmology)]),
         "dgp_batch_context": (i, [vp, i, P(vp)]),
         "dgp_batch_step": (i, [vp, P(Particles), P(d), P(d), P(SolveInfo), vp]),
@@ -235,6 +236,11 @@ def dgp_solve_adjoint(ctx, phibar, deltabar, tol, gbar=None):
     st = _check(lib.dgp_solve_adjoint(ctx, _ptr(phibar), _ptr(g[0]), _ptr(g[1]), _ptr(g[2]), _ptr(deltabar), tol,
                                       ctypes.byref(info)), "dgp_solve_adjoint", (DGP_OK, DGP_E_NOT_CONVERGED))
     return st, info.as_dict()
+
+
+def pm_step_adjoint(ctx, start, a, da, cot):
+    """cot (Particles of cotangents (xbar1, pbar1)) <- (xbar0, pbar0) for the step from `start` at a."""
+    _check(lib.pm_step_adjoint(ctx, ctypes.byref(start), a, da, ctypes.byref(cot)), "pm_step_adjoint")
 
 
 def dgp_get_solution(ctx, D):

@@ -99,3 +99,34 @@ def test_adjoint_states_and_arguments(dgp, torch_dev):
         assert float(out.abs().max()) == 0.0
     finally:
         dgp.dgp_destroy(ctx)
+
+
+def _particles(n, box, sig, seed):
+    pos, _ = inputs.lattice_particles(n, box)
+    rng = np.random.default_rng(seed)
+    pos = (pos + rng.normal(0, sig * box / n, pos.shape)) % box
+    mom = rng.normal(0, 0.5, pos.shape)
+    return pos, mom
+
+
+@pytest.mark.parametrize("n,prec,tol", [(16, 2, 1e-8), (32, 2, 1e-8), (32, 3, 2e-3)])
+def test_step_adjoint_matches_oracle(dgp, torch_dev, n, prec, tol):
+    torch, dev = torch_dev
+    box, a, da = 80.0 * n / 16, 0.5, 0.02
+    pos, mom = _particles(n, box, 0.25, 7)
+    rng = np.random.default_rng(8)
+    xb1, pb1 = rng.standard_normal(pos.shape), rng.standard_normal(pos.shape)
+    xb0, pb0 = oadj.step_vjp(pos, mom, a, da, xb1, pb1, n, box, OM, 1.0)
+    td = torch.float64 if prec == dgp.DGP_FP64 else torch.float32
+    ctx = dgp.dgp_init(box, n, 1.0, OM, precision=prec, tol=1e-12 if prec == 2 else 1e-6, max_iter=300)
+    try:
+        st = [to_dev(torch_dev, v, td) for v in (*pos, *mom)]
+        cot = [to_dev(torch_dev, v, td) for v in (*xb1, *pb1)]
+        dgp.pm_step_adjoint(ctx, dgp.particles(*st), a, da, dgp.particles(*cot))
+        got = np.stack([v.double().cpu().numpy() for v in cot])
+        unchanged = np.stack([v.double().cpu().numpy() for v in st])
+    finally:
+        dgp.dgp_destroy(ctx)
+    assert np.array_equal(unchanged, np.concatenate([pos, mom]).astype(unchanged.dtype) if prec == 2 else
+                          np.concatenate([pos, mom]).astype(np.float32).astype(np.float64))
+    assert rel_l2(got[:3], xb0) < tol and rel_l2(got[3:], pb0) < tol

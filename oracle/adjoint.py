@@ -213,3 +213,36 @@ def step_vjp(pos0, mom0, a, da, xbar1, pbar1, n, box, omega_m0, rc_H0, w=1.0 / 3
     phbar = pbar1 + dr * xbar
     xbar0 = xbar + force_vjp(st.pos, a, n, box, omega_m0, rc_H0, k1 * phbar, w, tol)
     return xbar0, phbar
+
+
+# ---------------------------------------------------------------- estimator and initial conditions
+def pk_vjp(delta, box, nbins, dldp):
+    """deltabar for L(P) with the P(k) estimator of Sec. IV (estimators.power_spectrum):
+    P_b = box^3 / (M^2 n_b) sum_{k in b} |delta_k|^2, so dL/ddelta(x) =
+    2 sum_k c(k) Re(delta_k e^{i k x}) with c(k) = dL/dP_b box^3 / (M^2 n_b) on shell b."""
+    from .estimators import power_spectrum
+    n = delta.shape[0]
+    m = n ** 3
+    grid = field.KGrid(n, box)
+    kf = 2.0 * np.pi / box
+    _, _, cnt = power_spectrum(delta, box, nbins)
+    b = np.floor(grid.kmag / kf + 0.5).astype(np.int64) * np.ones((n, n, n), np.int64)
+    c = np.zeros((n, n, n))
+    sel = (b >= 1) & (b <= nbins)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        cb = np.where(cnt > 0, np.asarray(dldp, float) * box ** 3 / (m * m * np.maximum(cnt, 1)), 0.0)
+    c[sel] = cb[b[sel] - 1]
+    return 2.0 * m * ifft3_real(c * fft3(delta))
+
+
+def zeldovich_vjp(xbar, pbar, n, box, vel_factor):
+    """deltaL_bar for (pos, mom) = (q + Psi, vel_factor Psi), Psi_j = IFFT(i k_j / k^2 delta_L(k))
+    (Nyquist component of k_j dropped): sum_j Psi_j^T (xbar_j + vel_factor pbar_j), the transpose of
+    the multiplier i k_j / k^2 being -i k_j / k^2."""
+    grid = field.KGrid(n, box)
+    out = np.zeros((n, n, n))
+    for j in range(3):
+        psibar = (np.asarray(xbar[j]) + vel_factor * np.asarray(pbar[j])).reshape(n, n, n)
+        mult = np.where(grid.zero, 0.0, -grid.gradient_multiplier(j) / grid.k2_safe)
+        out += ifft3_real(mult * fft3(psibar))
+    return out

@@ -96,6 +96,18 @@ def zeldovich_particles(n, box, n_s, rms, seed, vel_factor):
     Returns (pos, mom, A): pos and mom float64 arrays of shape (3, n^3) in
     lattice order (x index slowest), positions wrapped into [0, box)."""
     dk, A = linear_field_k(n, box, n_s, rms, seed)
+    pos, mom = _zeldovich(dk, n, box, vel_factor)
+    return pos, mom, A
+
+
+def zeldovich_from_field(delta_l, box, vel_factor):
+    """The same map from a real linear field delta_L (n^3): Psi = IFFT(i k / k^2 delta_L(k)),
+    the Nyquist component of each k_j dropped; pos = q + Psi (wrapped), mom = vel_factor Psi."""
+    n = delta_l.shape[0]
+    return _zeldovich(np.fft.fftn(delta_l), n, box, vel_factor)
+
+
+def _zeldovich(dk, n, box, vel_factor):
     k1, _ = _kvec(n, box)
     k1z = np.where(np.arange(n) == n // 2, 0.0, k1)  # i k_j is odd: drop Nyquist
     kx, ky, kz = np.meshgrid(k1, k1, k1, indexing="ij")
@@ -108,7 +120,7 @@ def zeldovich_particles(n, box, n_s, rms, seed, vel_factor):
     psi = [np.fft.ifftn(1j * g * dk / k2s).real for g in grads]
     pos = np.stack([(qq + p).reshape(-1) for qq, p in zip((qx, qy, qz), psi)]) % box
     mom = vel_factor * np.stack([p.reshape(-1) for p in psi])
-    return pos, mom, A
+    return pos, mom
 
 
 def lattice_particles(n, box):

@@ -174,3 +174,39 @@ def test_step_vjp_central_differences():
     fd = (L(pos + e * u, mom + e * v) - L(pos - e * u, mom - e * v)) / (2 * e)
     got = np.sum((xb0 - xb1) * u) + np.sum(pb0 * v)
     assert abs(fd - got) < 1e-6 * abs(fd)
+
+
+def test_pk_vjp_central_differences():
+    from oracle import estimators as est
+    n, box, nb = 16, 60.0, 8
+    d, _ = inputs.linear_field(n, box, -1.5, 0.5, seed=11)
+    rng = np.random.default_rng(12)
+    w, target = rng.uniform(0.5, 1.5, nb), rng.uniform(0.5, 1.5, nb) * est.power_spectrum(d, box, nb)[1]
+
+    def L(x):
+        P = est.power_spectrum(x, box, nb)[1]
+        return np.sum(w * (P - target) ** 2)
+
+    P = est.power_spectrum(d, box, nb)[1]
+    dbar = adj.pk_vjp(d, box, nb, 2 * w * (P - target))
+    u = rng.standard_normal((n, n, n))
+    e = 1e-5
+    fd = (L(d + e * u) - L(d - e * u)) / (2 * e)
+    assert abs(fd - np.sum(dbar * u)) < 1e-7 * abs(fd)
+
+
+def test_zeldovich_vjp_central_differences():
+    n, box, vf = 16, 60.0, 0.7
+    d, _ = inputs.linear_field(n, box, -1.5, 0.3, seed=13)
+    rng = np.random.default_rng(14)
+    xb, pb = rng.standard_normal((3, n ** 3)), rng.standard_normal((3, n ** 3))
+    u = rng.standard_normal((n, n, n))
+    e = 1e-6
+
+    def L(x):
+        pos, mom = inputs.zeldovich_from_field(x, box, vf)
+        q, _ = inputs.lattice_particles(n, box)
+        return np.sum(xb * ((pos - q + box / 2) % box)) + np.sum(pb * mom)
+
+    fd = (L(d + e * u) - L(d - e * u)) / (2 * e)
+    assert abs(fd - np.sum(adj.zeldovich_vjp(xb, pb, n, box, vf) * u)) < 1e-7 * abs(fd)

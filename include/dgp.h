@@ -210,6 +210,25 @@ int dgp_solve_adjoint(dgp_ctx *c, const void *phibar, const void *gbar_x, const 
  * replaced.  DGP_E_INVALID for bad arguments or a gravity mode other than NL. */
 int pm_step_adjoint(dgp_ctx *c, const dgp_particles *start, double a, double da, dgp_particles *cot);
 
+/* Zel'dovich initial conditions from a device n^3 linear field delta_L (Sec. III.A
+ * uses 2LPT; this is the first-order map the synthetic inputs use): one particle
+ * per mesh cell in lattice order (x index slowest), Psi_j = IFFT(i k_j / k^2
+ * delta_L(k)) with the Nyquist component of k_j dropped, pos = q + Psi wrapped
+ * into [0, box), mom = vel_factor Psi.  out->n must be n^3. */
+int dgp_zeldovich(dgp_ctx *c, const void *delta_l, double vel_factor, dgp_particles *out);
+
+/* Transpose of dgp_zeldovich: delta_l_bar = sum_j (-i k_j / k^2)[xbar_j + vel_factor pbar_j]
+ * for the cotangents in cot (lattice order, n^3 particles). */
+int dgp_zeldovich_adjoint(dgp_ctx *c, const dgp_particles *cot, double vel_factor, void *delta_l_bar);
+
+/* Transpose of particles -> CIC deposit -> density contrast -> power_spectrum for
+ * the host gradient dl_dp[nbins] = dL/dP_b: the density contrast's cotangent is
+ * 2 sum_k c(k) delta_k e^{ikx}, c = dL/dP_b box^3 / (n^6 n_b) on shell b, and its
+ * transpose through the deposit is added to the position cotangents of cot
+ * (its momentum members are not touched). */
+int dgp_power_spectrum_adjoint(dgp_ctx *c, const dgp_particles *parts, int nbins, const double *dl_dp,
+                               dgp_particles *cot);
+
 /* Host waits of the context (the relaxation's stop-rule verdicts, host outputs)
  * block on an event and yield the CPU (on != 0) instead of spinning (0, the
  * default).  For callers that drive many contexts from many host threads. */

@@ -203,6 +203,9 @@ class EngineBase {
   virtual int adjoint(const void* phibar, const void* const* gbar, void* deltabar, double tol,
                       dgp_solve_info* info) = 0;
   virtual int step_adjoint(const dgp_particles* start, double a, double da, dgp_particles* cot) = 0;
+  virtual int zeldovich(const void* dl, double vf, dgp_particles* out) = 0;
+  virtual int zeldovich_adjoint(const dgp_particles* cot, double vf, void* dlbar) = 0;
+  virtual int pk_adjoint(const dgp_particles* pp, int nbins, const double* dldp, dgp_particles* cot) = 0;
   virtual int step(dgp_particles* parts, double a, double da, dgp_solve_info* info) = 0;
   virtual int step_host(dgp_particles* parts, double a, double da, dgp_solve_info* info) = 0;
   virtual int pk(const void* delta, int nbins, double* k, double* pk, int64_t* nmodes) = 0;
@@ -1090,6 +1093,79 @@ class Engine : public EngineBase {
     return DGP_OK;
   }
 
+  // Zel'dovich particles from a linear field (lattice order) and the map's transpose.
+  int zeldovich(const void* dl, double vf, dgp_particles* out) override {
+    if (!dl || !valid_parts(out) || out->n != M) return DGP_E_INVALID;
+    int rc;
+    if ((rc = forward_zy((const T*)dl, s6[0], ZPrologue{nullptr, 0.0, 0}))) return rc;
+    const Coef c = coefficients(1.0, cosmo.omega_m0, p.rc_H0);
+    const KParams kp = kparams(c, p.gravity);
+    prof.run(KK_X_OTHER, 4 * SB, stream, [&] {
+      launch_fft_x_op<T, N>(XOP_ZEL, s6[0], nullptr, fs(s6 + 1, 3), 0, kp, nullptr, 0, 0, 0, tw, stream);
+    });
+    if ((rc = inverse_yz(s6 + 1, rG, 3))) return rc;
+    T* o[6] = {(T*)out->x, (T*)out->y, (T*)out->z, (T*)out->px, (T*)out->py, (T*)out->pz};
+    prof.run(KK_MISC, 9 * RB, stream, [&] { launch_zel_particles<T>(rG, vf, cic(), o, stream); });
+    DGP_CHECK_LAUNCH();
+    force_valid = false;
+    return DGP_OK;
+  }
+
+  int zeldovich_adjoint(const dgp_particles* cot, double vf, void* dlbar) override {
+    if (!dlbar || !valid_parts(cot) || cot->n != M) return DGP_E_INVALID;
+    int rc;
+    T* cv[6] = {(T*)cot->x, (T*)cot->y, (T*)cot->z, (T*)cot->px, (T*)cot->py, (T*)cot->pz};
+    prof.run(KK_MISC, 9 * RB, stream, [&] { launch_zel_cot<T>(cv, vf, M, rG, stream); });
+    for (int j = 0; j < 3; ++j)
+      if ((rc = forward_zy(rG[j], s6[1 + j], ZPrologue{nullptr, 0.0, 0}))) return rc;
+    const Coef c = coefficients(1.0, cosmo.omega_m0, p.rc_H0);
+    const KParams kp = kparams(c, p.gravity);
+    FieldSet<T> in = fs(s6, 4);
+    prof.run(KK_X_OTHER, 4 * SB, stream,
+             [&] { launch_fft_x_adj<T, N>(XOP_ZEL_ADJ, in, 0xe, fs(s6, 1), kp, tw, stream); });
+    T* o[1] = {(T*)dlbar};
+    if ((rc = inverse_yz(s6, o, 1))) return rc;
+    force_valid = false;
+    return DGP_OK;
+  }
+
+  // Transpose of particles -> deposit -> delta -> P(k) for dL/dP_b (see dgp_power_spectrum_adjoint).
+  int pk_adjoint(const dgp_particles* pp, int nbins, const double* dldp, dgp_particles* cot) override {
+    if (!valid_parts(pp) || !valid_parts(cot) || pp->n == 0 || cot->n != pp->n || !dldp || nbins < 1 ||
+        nbins > N / 2)
+      return DGP_E_INVALID;
+    int rc;
+    T* delta = rH[0];
+    if ((rc = deposit(pp, delta))) return rc;
+    double k[256], pk[256];
+    int64_t cnt[256];
+    if ((rc = this->pk(delta, nbins, k, pk, cnt))) return rc;
+    double hc[256];
+    const double l3 = p.box * p.box * p.box;
+    for (int b = 0; b < nbins; ++b)
+      hc[b] = cnt[b] > 0 ? dldp[b] * l3 / ((double)M * (double)M * (double)cnt[b]) : 0.0;
+    DGP_CUDA(cudaMemcpyAsync(d_pk, hc, sizeof(double) * nbins, cudaMemcpyHostToDevice, stream));
+    if ((rc = forward_zy(delta, s6[0], ZPrologue{nullptr, 0.0, 0}))) return rc;
+    const Coef c = coefficients(1.0, cosmo.omega_m0, p.rc_H0);
+    const KParams kp = kparams(c, p.gravity);
+    prof.run(KK_X_OTHER, 2 * SB, stream, [&] {
+      launch_fft_x_op<T, N>(XOP_PK_ADJ, s6[0], nullptr, fs(s6 + 1, 1), 0, kp, d_pk, nbins, 0, 0, tw, stream);
+    });
+    T* o[1] = {rRho};
+    if ((rc = inverse_yz(s6 + 1, o, 1))) return rc;
+    // the deposit's transpose (the force term is absent: scale 0 on finite fields)
+    T* const g3[3] = {rRho, rRho, rRho};
+    const ParticleSet<T> xs{{(T*)pp->x, (T*)pp->y, (T*)pp->z, (T*)pp->x, (T*)pp->y, (T*)pp->z}};
+    const ParticleSet<T> xb{{(T*)cot->x, (T*)cot->y, (T*)cot->z, (T*)cot->x, (T*)cot->y, (T*)cot->z}};
+    prof.run(KK_GATHER, 6.0 * sizeof(T) * pp->n + RB, stream, [&] {
+      launch_force_vjp_gather<T>(xs, 0.0, pp->n, g3, rRho, (double)M / (double)pp->n, xb, cic(), stream);
+    });
+    DGP_CHECK_LAUNCH();
+    DGP_CUDA(wait_stream());  // hc is read by the copy above
+    force_valid = false;
+    return DGP_OK;
+  }
+
   int bispec(const void* delta, double k1, double k2, int ntheta, const double* theta, double dk, double* b,
              double* q) override {
     if (!delta || ntheta < 0 || (ntheta > 0 && (!theta || !b || !q)) || !(k1 > 0) || !(k2 > 0))
@@ -1292,6 +1368,22 @@ const char* dgp_kernel_name(int kind) {
 int dgp_deposit(dgp_ctx* c, const dgp_particles* parts, void* delta) {
   if (!c) return DGP_E_INVALID;
   return c->eng->deposit(parts, delta);
+}
+
+int dgp_zeldovich(dgp_ctx* c, const void* delta_l, double vel_factor, dgp_particles* out) {
+  if (!c) return DGP_E_INVALID;
+  return c->eng->zeldovich(delta_l, vel_factor, out);
+}
+
+int dgp_zeldovich_adjoint(dgp_ctx* c, const dgp_particles* cot, double vel_factor, void* delta_l_bar) {
+  if (!c) return DGP_E_INVALID;
+  return c->eng->zeldovich_adjoint(cot, vel_factor, delta_l_bar);
+}
+
+int dgp_power_spectrum_adjoint(dgp_ctx* c, const dgp_particles* parts, int nbins, const double* dl_dp,
+                               dgp_particles* cot) {
+  if (!c) return DGP_E_INVALID;
+  return c->eng->pk_adjoint(parts, nbins, dl_dp, cot);
 }
 
 int pm_step_adjoint(dgp_ctx* c, const dgp_particles* start, double a, double da, dgp_particles* cot) {

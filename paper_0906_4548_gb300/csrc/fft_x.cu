@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
   __syncthreads();
 
   V X0[N2], X1[N2];
-  constexpr bool ADJ = OP == XOP_ADJ_PHI || OP == XOP_ADJ_COMBINE;
+  constexpr bool ADJ = OP == XOP_ADJ_PHI || OP == XOP_ADJ_COMBINE || OP == XOP_ZEL_ADJ;
   if (!ADJ) x_forward<T, N>(args.in0, kz, ky0, lane, yl, s_T, s_tw, X0);
   if (OP == XOP_PHI_FORCE && kp.gravity == 0) x_forward<T, N>(args.in1, kz, ky0, lane, yl, s_T, s_tw, X1);
 
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
     s_ikb[k2 * NT + threadIdx.x] = ikb;
   }
 
-  if (OP == XOP_ADJ_PHI) {
+  if (OP == XOP_ADJ_PHI || OP == XOP_ZEL_ADJ) {
     const T inv_m = kc<T>(kp.inv_m, kp.inv_m_f);
     V acc[N2];
 #pragma unroll
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
     }
     const T om15 = kc<T>(1.5 * (kp.eta - 1.0) / kp.eta, kp.om15_f);
 #pragma unroll 1
-    for (int o = 0; o < 2; ++o) {
+    for (int o = 0; o < (OP == XOP_ZEL_ADJ ? 1 : 2); ++o) {
       V Y[N2];
 #pragma unroll
       for (int k2 = 0; k2 < N2; ++k2) {
@@ -220,12 +220,17 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
         const int n2 = nx * nx + ny * ny + nz * nz;
         Y[k2] = cmake<V>((T)0, (T)0);
         if (n2 != 0) {
-          const T ikb = s_ikb[k2 * NT + threadIdx.x];
           const T kmag = kf * sqrt((T)n2);
-          const T pref = -kc<T>(kp.aE * kp.aE, kp.aE2_f) / (kmag * kmag);
-          const T den = (T)1 + ikb * kc<T>(1.0 / kp.eta, kp.inv_eta_f);
-          const T cd = -kc<T>(0.5 / kp.eta, kp.half_inv_eta_f) + kc<T>(kp.c3, kp.c3_f) * ikb;
-          const T m = (o == 0 ? cd : om15) * pref / den;
+          T m;
+          if (OP == XOP_ZEL_ADJ) {
+            m = (T)-1 / (kmag * kmag);
+          } else {
+            const T ikb = s_ikb[k2 * NT + threadIdx.x];
+            const T pref = -kc<T>(kp.aE * kp.aE, kp.aE2_f) / (kmag * kmag);
+            const T den = (T)1 + ikb * kc<T>(1.0 / kp.eta, kp.inv_eta_f);
+            const T cd = -kc<T>(0.5 / kp.eta, kp.half_inv_eta_f) + kc<T>(kp.c3, kp.c3_f) * ikb;
+            m = (o == 0 ? cd : om15) * pref / den;
+          }
           Y[k2] = cscale(acc[k2], m * inv_m);
         }
       }
@@ -303,6 +308,46 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) Y[k2] = cscale(X0[k2], -s_ikb[k2 * NT + threadIdx.x] * inv_m);
     x_inverse<T, N>(Y, args.out.p[5], kz, ky0, lane, yl, s_T, s_tw);
+    return;
+  }
+
+  if (OP == XOP_PK_ADJ) {
+    V Y[N2];
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+      const int nx = signed_index(lane + N1 * k2, N);
+      const int n2 = nx * nx + ny * ny + nz * nz;
+      Y[k2] = cmake<V>((T)0, (T)0);
+      if (n2 != 0) {
+        const int b = (int)floor(sqrt((double)n2) + 0.5);  // the shell of the P(k) estimator
+        if (b >= 1 && b <= args.nbins) Y[k2] = cscale(X0[k2], (T)(2.0 * args.pk_partials[b - 1]));
+      }
+    }
+    x_inverse<T, N>(Y, args.out.p[0], kz, ky0, lane, yl, s_T, s_tw);
+    return;
+  }
+  if (OP == XOP_ZEL) {
+    const T inv_m = kc<T>(kp.inv_m, kp.inv_m_f);
+#pragma unroll 1
+    for (int o = 0; o < 3; ++o) {
+      const int nfix = o == 1 ? ny : nz;
+      const bool nyq_fix = o == 1 ? nyq_y : nyq_z;
+      V Y[N2];
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        const int kx = lane + N1 * k2;
+        const int nx = signed_index(kx, N);
+        const int n2 = nx * nx + ny * ny + nz * nz;
+        const bool nyq = o == 0 ? kx == N / 2 : nyq_fix;
+        Y[k2] = cmake<V>((T)0, (T)0);
+        if (n2 != 0 && !nyq) {
+          const T ki = kf * (T)(o == 0 ? nx : nfix);
+          const T m = ki / (kf * kf * (T)n2) * inv_m;
+          Y[k2] = cmake<V>(-m * X0[k2].y, m * X0[k2].x);  // (i k_j / k^2) X
+        }
+      }
+      x_inverse<T, N>(Y, args.out.p[o], kz, ky0, lane, yl, s_T, s_tw);
+    }
     return;
   }
 
@@ -407,6 +452,8 @@ void launch_fft_x_op(int op, const vec2_t<T>* in0, const vec2_t<T>* in1, const F
     case XOP_PHI_FORCE: launch_x<T, N, XOP_PHI_FORCE>(a, tw, s); break;
     case XOP_PK: launch_x<T, N, XOP_PK>(a, tw, s); break;
     case XOP_PK_BRANE: launch_x<T, N, XOP_PK_BRANE>(a, tw, s); break;
+    case XOP_ZEL: launch_x<T, N, XOP_ZEL>(a, tw, s); break;
+    case XOP_PK_ADJ: launch_x<T, N, XOP_PK_ADJ>(a, tw, s); break;
     case XOP_SHELL: launch_x<T, N, XOP_SHELL>(a, tw, s); break;
     default: break;
   }
@@ -422,6 +469,7 @@ void launch_fft_x_adj(int op, const FieldSet<T>& in, int in_mask, const FieldSet
   a.in = in; a.in_mask = in_mask;
   if (op == XOP_ADJ_PHI) launch_x<T, N, XOP_ADJ_PHI>(a, tw, s);
   else if (op == XOP_ADJ_COMBINE) launch_x<T, N, XOP_ADJ_COMBINE>(a, tw, s);
+  else if (op == XOP_ZEL_ADJ) launch_x<T, N, XOP_ZEL_ADJ>(a, tw, s);
 }
 
 #define DGP_INST_X(T, N)                                                                            \

@@ -42,7 +42,12 @@ struct KParams {
 };
 
 enum XOp { XOP_HESSIAN = 0, XOP_SOURCE = 1, XOP_SOURCE_LIN = 2, XOP_PHI_FORCE = 3, XOP_PK = 4,
-           XOP_SHELL = 5, XOP_PK_BRANE = 6, XOP_ADJ_PHI = 7, XOP_ADJ_COMBINE = 8 };
+           XOP_SHELL = 5, XOP_PK_BRANE = 6, XOP_ADJ_PHI = 7, XOP_ADJ_COMBINE = 8, XOP_ZEL = 9, XOP_ZEL_ADJ = 10,
+           XOP_PK_ADJ = 11 };
+// XOP_ZEL: the Zel'dovich displacements Psi_j = (i k_j / k^2) delta_L (Nyquist component of
+//   k_j zero), three outputs.  XOP_PK_ADJ: out0 = 2 c_b delta(k) on shell b (the P(k)
+//   estimator's transpose; c = pk_partials[b - 1], nbins shells); the inverse
+//   transforms' 1/N^3 is not applied, so the real output is 2 sum_k c delta_k e^{ikx}.
 
 // Every launcher of a kernel that can run inside a relaxation iteration takes
 // skip: NULL, or a device flag read at kernel entry; when it is nonzero the
@@ -76,6 +81,8 @@ void launch_fft_x_op(int op, const vec2_t<T>* in0, const vec2_t<T>* in1, const F
 //    phibar_tot = phibar + sum_i i k_i gbar_i (the transpose of g_i = -i k_i phi,
 //    Nyquist component zero), out0 = B phibar_tot and out1 = A phibar_tot, where
 //    phi = A delta + B D is Eq. FullDGP1.
+//  XOP_ZEL_ADJ: inputs (mask bits 1..3) Psibar_x, Psibar_y, Psibar_z; out0 =
+//    -(1/k^2) sum_j i k_j Psibar_j, the transpose of the Zel'dovich multiplier.
 //  XOP_ADJ_COMBINE: inputs P_xx, P_yy, P_zz, P_xy, P_xz, P_yz (spectra of
 //    H_ij(D) lam) and lam; out0 = -2 sum_ij h_ij P_ij + c2 (-1/kbar) lam over all
 //    nine i, j (off-diagonals twice), h_ij the Hessian multipliers.
@@ -227,6 +234,13 @@ void launch_force_vjp_gather(const ParticleSet<T>& pp, double scale, int64_t np,
 template <typename T>
 void launch_particle_axpy(const ParticleSet<T>& in, double a, int64_t np, const ParticleSet<T>& out,
                           cudaStream_t s);
+
+// Zel'dovich particles on the lattice (x index slowest): pos = (q + Psi) wrapped,
+// mom = vf Psi; and the transpose: psibar_j = xbar_j + vf pbar_j as n^3 fields.
+template <typename T>
+void launch_zel_particles(T* const* psi, double vf, CicParams cp, T* const* out, cudaStream_t s);
+template <typename T>
+void launch_zel_cot(T* const* cot, double vf, int64_t m, T* const* psibar, cudaStream_t s);
 
 int num_sms();
 

@@ -502,7 +502,56 @@ void launch_gather_kick(T* x, T* y, T* z, T* px, T* py, T* pz, int64_t np, const
                                                     do_drift);
 }
 
+template <typename T>
+__global__ void k_zel_particles(const T* __restrict__ p0, const T* __restrict__ p1, const T* __restrict__ p2, T vf,
+                                CicParams cp, T* __restrict__ x, T* __restrict__ y, T* __restrict__ z,
+                                T* __restrict__ px, T* __restrict__ py, T* __restrict__ pz) {
+  const int64_t n = cp.n, m = n * n * n;
+  T box, inv_box;
+  if constexpr (sizeof(T) == 8) {
+    box = cp.box;
+    inv_box = 1.0 / cp.box;
+  } else {
+    box = cp.box_f;
+    inv_box = cp.inv_box_f;
+  }
+  const T d = box / (T)n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ix = i / (n * n), iy = (i / n) % n, iz = i % n;
+    x[i] = wrap_periodic((T)ix * d + p0[i], box, inv_box);
+    y[i] = wrap_periodic((T)iy * d + p1[i], box, inv_box);
+    z[i] = wrap_periodic((T)iz * d + p2[i], box, inv_box);
+    px[i] = vf * p0[i];
+    py[i] = vf * p1[i];
+    pz[i] = vf * p2[i];
+  }
+}
+
+template <typename T>
+__global__ void k_zel_cot(const T* __restrict__ xb, const T* __restrict__ yb, const T* __restrict__ zb,
+                          const T* __restrict__ pxb, const T* __restrict__ pyb, const T* __restrict__ pzb, T vf,
+                          int64_t m, T* __restrict__ o0, T* __restrict__ o1, T* __restrict__ o2) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    o0[i] = xb[i] + vf * pxb[i];
+    o1[i] = yb[i] + vf * pyb[i];
+    o2[i] = zb[i] + vf * pzb[i];
+  }
+}
+
+template <typename T>
+void launch_zel_particles(T* const* psi, double vf, CicParams cp, T* const* out, cudaStream_t s) {
+  k_zel_particles<T><<<num_sms() * 4, 256, 0, s>>>(psi[0], psi[1], psi[2], (T)vf, cp, out[0], out[1], out[2],
+                                                   out[3], out[4], out[5]);
+}
+template <typename T>
+void launch_zel_cot(T* const* cot, double vf, int64_t m, T* const* psibar, cudaStream_t s) {
+  k_zel_cot<T><<<num_sms() * 4, 256, 0, s>>>(cot[0], cot[1], cot[2], cot[3], cot[4], cot[5], (T)vf, m, psibar[0],
+                                             psibar[1], psibar[2]);
+}
+
 #define DGP_INST_P(T)                                                                              \
+  template void launch_zel_particles<T>(T* const*, double, CicParams, T* const*, cudaStream_t);     \
+  template void launch_zel_cot<T>(T* const*, double, int64_t, T* const*, cudaStream_t);            \
   template void launch_gather_kick<T>(T*, T*, T*, T*, T*, T*, int64_t, const T*, const T*, const T*,  \
                                       CicParams, double, double, int, cudaStream_t);
 DGP_INST_P(float)

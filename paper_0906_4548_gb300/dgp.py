@@ -24,7 +24,8 @@ EXPORTED = ["dgp_background", "dgp_init", "dgp_destroy", "dgp_strerror", "dgp_re
             "dgp_profile", "dgp_profile_read", "dgp_kernel_name", "dgp_power_spectrum_noalloc",
             "dgp_sort_particles", "dgp_profile_kinds", "dgp_brane_spectra", "dgp_set_blocking_sync",
             "dgp_batch_create", "dgp_batch_context", "dgp_batch_step", "dgp_batch_destroy",
-            "dgp_solve_adjoint", "pm_step_adjoint"]
+            "dgp_solve_adjoint", "pm_step_adjoint", "dgp_zeldovich", "dgp_zeldovich_adjoint",
+            "dgp_power_spectrum_adjoint"]
 DGP_NOALLOC_MAX_N = 64
 DGP_KERNEL_KINDS = 11
 
@@ -97,6 +98,9 @@ def _load():
         "dgp_set_blocking_sync": (i, [vp, i]),
         "dgp_solve_adjoint": (i, [vp, vp, vp, vp, vp, vp, d, P(SolveInfo)]),
         "pm_step_adjoint": (i, [vp, P(Particles), d, d, P(Particles)]),
+        "dgp_zeldovich": (i, [vp, vp, d, P(Particles)]),
+        "dgp_zeldovich_adjoint": (i, [vp, P(Particles), d, vp]),
+        "dgp_power_spectrum_adjoint": (i, [vp, P(Particles), i, P(d), P(Particles)]),
         "dgp_batch_create": (i, [P(vp), i, P(Params), P(Cosmology)]),
         "dgp_batch_context": (i, [vp, i, P(vp)]),
         "dgp_batch_step": (i, [vp, P(Particles), P(d), P(d), P(SolveInfo), vp]),
@@ -241,6 +245,21 @@ def dgp_solve_adjoint(ctx, phibar, deltabar, tol, gbar=None):
 def pm_step_adjoint(ctx, start, a, da, cot):
     """cot (Particles of cotangents (xbar1, pbar1)) <- (xbar0, pbar0) for the step from `start` at a."""
     _check(lib.pm_step_adjoint(ctx, ctypes.byref(start), a, da, ctypes.byref(cot)), "pm_step_adjoint")
+
+
+def dgp_zeldovich(ctx, delta_l, vel_factor, out):
+    _check(lib.dgp_zeldovich(ctx, _ptr(delta_l), vel_factor, ctypes.byref(out)), "dgp_zeldovich")
+
+
+def dgp_zeldovich_adjoint(ctx, cot, vel_factor, delta_l_bar):
+    _check(lib.dgp_zeldovich_adjoint(ctx, ctypes.byref(cot), vel_factor, _ptr(delta_l_bar)), "dgp_zeldovich_adjoint")
+
+
+def dgp_power_spectrum_adjoint(ctx, parts, dl_dp, cot):
+    g = np.ascontiguousarray(dl_dp, dtype=np.float64)
+    _check(lib.dgp_power_spectrum_adjoint(ctx, ctypes.byref(parts), g.size,
+                                          g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(cot)),
+           "dgp_power_spectrum_adjoint")
 
 
 def dgp_get_solution(ctx, D):

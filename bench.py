@@ -316,6 +316,121 @@ def run_batched(args):
     return 0
 
 
+# Gradient workload: a P(k) loss after a 128^3 run, differentiated with respect to the linear field.
+WA = dict(n=128, box=200.0, n_s=-1.5, rms=0.5, seed=3, target_seed=4, a_start=0.02, a_end=1.0, run_steps=100,
+          every=10, omega_m0=0.27, rc_H0=1.0, tol=1e-6, max_iter=100)
+
+
+def run_adjoint(args):
+    """128^3 mesh and particles, FP32, 100 steps from a = 0.02 to 1 with a checkpoint every 10 steps:
+    L = sum_k [P(k) - P_target(k)]^2 (target from a second seed), its gradient with respect to the
+    128^3 linear field (initial Fourier modes) by the adjoint kernels, timed, and checked against
+    central differences of the loss along --fd-modes random single Fourier modes."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_0906_4548_gb300 import autodiff, dgp, inputs
+    n, box = WA["n"], WA["box"]
+    dev = torch.device("cuda", 0)
+    bgi = dgp.dgp_background(WA["omega_m0"], WA["rc_H0"], WA["a_start"])
+    vf = WA["a_start"] ** 2 * bgi["E"] * bgi["growth_f"]
+    dl = torch.tensor(inputs.linear_field(n, box, WA["n_s"], WA["rms"], WA["seed"])[0], dtype=torch.float32,
+                      device=dev)
+    dl_t = torch.tensor(inputs.linear_field(n, box, WA["n_s"], WA["rms"], WA["target_seed"])[0],
+                        dtype=torch.float32, device=dev)
+    dlna = math.log(WA["a_end"] / WA["a_start"]) / WA["run_steps"]
+    nsteps = args.adjoint_steps if args.adjoint_steps else WA["run_steps"]
+    sched = [WA["a_start"] * math.exp(i * dlna) for i in range(nsteps + 1)]
+    nb = n // 2
+    fd64 = args.fd_precision == "fp64"
+    ctx = dgp.dgp_init(box, n, WA["rc_H0"], WA["omega_m0"], precision=dgp.DGP_FP32, tol=WA["tol"],
+                       max_iter=WA["max_iter"], sort_every=0)
+    stream = torch.cuda.current_stream()
+    try:
+        def final_pk(field):
+            x, p = autodiff.ZeldovichIC.apply(field, ctx, vf)
+            dgp.dgp_reset(ctx)
+            x, p = autodiff.PMRun.apply(x, p, ctx, sched, WA["every"])
+            delta = torch.empty((n, n, n), dtype=field.dtype, device=dev)
+            xc = x.detach().contiguous()
+            dgp.dgp_deposit(ctx, dgp.particles(xc[0], xc[1], xc[2], xc[0], xc[1], xc[2]), delta)
+            return dgp.power_spectrum(ctx, delta, nb)[1]
+
+        target = final_pk(dl_t)
+        w = np.ones(nb)
+
+        def loss(field, grad):
+            d = field.clone().requires_grad_(grad)
+            x, p = autodiff.ZeldovichIC.apply(d, ctx, vf)
+            dgp.dgp_reset(ctx)
+            x, p = autodiff.PMRun.apply(x, p, ctx, sched, WA["every"])
+            return autodiff.PkLoss.apply(x, ctx, n, target, w), d
+
+        for _ in range(max(1, min(args.warmup, 1))):   # one untimed forward + backward
+            L, d = loss(dl, True)
+            L.backward()
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        with ClockSampler(0) as clk:
+            time.sleep(0.3)
+            e0.record(stream)
+            L, d = loss(dl, True)
+            e1.record(stream)
+            L.backward()
+            e2.record(stream)
+            torch.cuda.synchronize()
+        ms_fwd, ms_bwd = e0.elapsed_time(e1), e1.elapsed_time(e2)
+        loss_value = float(L.detach())
+        grad = d.grad.detach().double().cpu().numpy()
+        if fd64:
+            # the accuracy check in FP64 (tolerance 1e-10): FP32 rounding and a 1e-6 solver
+            # tolerance, amplified over 100 steps, swamp small central differences
+            dgp.dgp_destroy(ctx)
+            ctx = dgp.dgp_init(box, n, WA["rc_H0"], WA["omega_m0"], precision=dgp.DGP_FP64, tol=1e-10,
+                               max_iter=300, sort_every=0)
+            dl, dl_t = dl.double(), dl_t.double()
+            target = final_pk(dl_t)
+            L64, d64 = loss(dl, True)
+            L64.backward()
+            grad = d64.grad.detach().cpu().numpy()
+        # central differences along random single modes of the linear field
+        rng = np.random.default_rng(0)
+        xg = np.arange(n) * box / n
+        fd = []
+        for t in range(args.fd_modes):
+            k = rng.integers(1, n // 4, 3)
+            u = np.cos(2 * np.pi / box * (k[0] * xg[:, None, None] + k[1] * xg[None, :, None]
+                                          + k[2] * xg[None, None, :]) + rng.uniform(0, 2 * np.pi))
+            e = (1e-4 if fd64 else 2e-3) * WA["rms"]
+            ut = torch.tensor(u, dtype=dl.dtype, device=dev)
+            lp = float(loss(dl + e * ut, False)[0])
+            lm = float(loss(dl - e * ut, False)[0])
+            f = (lp - lm) / (2 * e)
+            a_ = float(np.sum(grad * u))
+            fd.append({"mode": [int(v) for v in k], "central_difference": f, "adjoint": a_,
+                       "rel_diff": abs(f - a_) / max(abs(f), 1e-300)})
+    finally:
+        dgp.dgp_destroy(ctx)
+    rel = [x["rel_diff"] for x in fd]
+    line = {"metric": "gradient evaluations/s of a P(k) loss after a 128^3, 100-step DGP PM run (adjoint kernels, "
+                      "checkpoint every 10 steps)", "value": 1000.0 / (ms_fwd + ms_bwd),
+            "unit": "gradients/s", "n_gpus": 1, "steps": nsteps, "warmup": 1,
+            "ms_per_step": (ms_fwd + ms_bwd) / nsteps, "final_a": sched[-1], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "dgp_pm_adjoint_128cube_box200_ns-1.5_a0.02-1_100steps_every10_tol1e-6",
+                       "gradient_wrt": "the 128^3 linear field delta_L (initial Fourier modes)",
+                       "rc_gradient": None, "rc_gradient_note": "not formed: r_c is a constant of the context",
+                       "l2": "particles (25 MB per array) and fields (8 MB each) partly fit L2; no flush"},
+            "forward_ms": ms_fwd, "backward_ms": ms_bwd, "backward_over_forward": ms_bwd / ms_fwd,
+            "loss": loss_value, "clocks": clk.summary(),
+            "fd_check": {"modes": len(fd), "precision": "fp64, tol 1e-10" if fd64 else "fp32, tol 1e-6",
+                         "max_rel_diff": max(rel) if rel else None,
+                         "median_rel_diff": float(np.median(rel)) if rel else None, "cases": fd}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -326,8 +441,14 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--precision", default="mixed", choices=sorted(PRECISION_DESC))
     ap.add_argument("--no-compare", action="store_true", help="skip the precision comparison runs")
-    ap.add_argument("--workload", default="pm256", choices=["pm256", "batched"],
-                    help="pm256: the 256^3 PM run (default); batched: 48 small realisations")
+    ap.add_argument("--workload", default="pm256", choices=["pm256", "batched", "adjoint"],
+                    help="pm256: the 256^3 PM run (default); batched: 48 small realisations; adjoint: the "
+                         "gradient of a P(k) loss after a 128^3 run")
+    ap.add_argument("--fd-modes", type=int, default=20, help="adjoint workload: central-difference checks")
+    ap.add_argument("--adjoint-steps", type=int, default=0,
+                    help="adjoint workload: run only the first K of the 100 steps (0: all)")
+    ap.add_argument("--fd-precision", default="fp32", choices=["fp32", "fp64"],
+                    help="adjoint workload: precision of the gradient and differences that are compared")
     ap.add_argument("--sort-every", type=int, default=SORT_EVERY,
                     help="cell-sort the particles after every K-th drift (0: never)")
     args = ap.parse_args()
@@ -335,6 +456,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
 
     import numpy as np
     import torch

@@ -301,8 +301,9 @@ int pm_step(dgp_ctx *c, dgp_particles *parts, double a, double da, dgp_solve_inf
 
 /* pm_step on host particle arrays (pageable or pinned): copies them to the
  * context's device buffers, steps, and copies them back before returning.
- * The host arrays are float or double per the context precision, n <= the
- * n^3 particles of the mesh. */
+ * The positions are final after the drift, so their copy back runs on a
+ * second stream during the field solve (overlapped when the host arrays are
+ * pinned).  The host arrays are float or double per the context precision. */
 int pm_step_host(dgp_ctx *c, dgp_particles *host_parts, double a, double da, dgp_solve_info *info);
 
 /* Power spectrum of a device n^3 field (Sec. IV):

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <new>
 #include <utility>
 #include <vector>
@@ -286,6 +287,8 @@ class Engine : public EngineBase {
   // CUDA graph of two consecutive iterations (it odd, it + 1), one per buffer
   // holding the starting iterate; updated with each solve's parameters
   cudaGraphExec_t pair_exec[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t copy_stream = nullptr;  // pm_step_host: positions back to the host during the solve
+  cudaEvent_t drift_ev = nullptr;
   T* hp[6] = {};                // device copies for pm_step_host
   int64_t hp_n = 0;
   // cell sort: key and permuted copies per particle, counts / starts / cursors per cell
@@ -319,6 +322,8 @@ class Engine : public EngineBase {
     cudaFree(aP); cudaFree(aF); cudaFree(aS); cudaFree(d_adj); cudaFree(aFb);
     for (int i = 0; i < 6; ++i) cudaFree(ap[i]);
     cudaFree(d_ctl); cudaFree(d_hist); cudaFreeHost(h_ctl);
+    if (copy_stream) cudaStreamDestroy(copy_stream);
+    if (drift_ev) cudaEventDestroy(drift_ev);
     for (int i = 0; i < 3; ++i)
       if (pair_exec[i]) cudaGraphExecDestroy(pair_exec[i]);
     set_blocking(false);
@@ -794,6 +799,13 @@ class Engine : public EngineBase {
   }
 
   int step(dgp_particles* pp, double a, double da, dgp_solve_info* info) override {
+    return step_impl(pp, a, da, info, nullptr);
+  }
+
+  // after_drift (may be null) runs once the positions are final for the step
+  // (after the drift and the cell sort), before the field solve at a + da.
+  int step_impl(dgp_particles* pp, double a, double da, dgp_solve_info* info,
+                const std::function<int()>* after_drift) {
     if (!valid_parts(pp) || pp->n == 0) return DGP_E_INVALID;
     if (!(a > 0.0) || !(da > 0.0) || !isfinite(a + da)) return DGP_E_INVALID;
     const double a1 = a + da;
@@ -811,6 +823,7 @@ class Engine : public EngineBase {
     DGP_CHECK_LAUNCH();
     ++nsteps;
     if (p.sort_every > 0 && nsteps % p.sort_every == 0 && (rc = sort_impl(pp, nullptr))) return rc;
+    if (after_drift && (rc = (*after_drift)())) return rc;
     if ((rc = forces_at(pp, a1, info))) return rc;
     const double k2 = time_integral(ah, a1, om, rc_, 0);
     prof.run(KK_GATHER, 9.0 * sizeof(T) * pp->n + 3 * RB, stream, [&] {
@@ -831,13 +844,29 @@ class Engine : public EngineBase {
       }
       hp_n = hpp->n;
     }
+    if (!copy_stream) {
+      DGP_CUDA(cudaStreamCreateWithFlags(&copy_stream, cudaStreamNonBlocking));
+      DGP_CUDA(cudaEventCreateWithFlags(&drift_ev, cudaEventDisableTiming));
+    }
     void* src[6] = {hpp->x, hpp->y, hpp->z, hpp->px, hpp->py, hpp->pz};
     const size_t bytes = sizeof(T) * hpp->n;
     for (int i = 0; i < 6; ++i) DGP_CUDA(cudaMemcpyAsync(hp[i], src[i], bytes, cudaMemcpyHostToDevice, stream));
     dgp_particles dp{hp[0], hp[1], hp[2], hp[3], hp[4], hp[5], hpp->n};
-    const int rc = step(&dp, a, da, info);
-    if (rc != DGP_OK) return rc;
-    for (int i = 0; i < 6; ++i) DGP_CUDA(cudaMemcpyAsync(src[i], hp[i], bytes, cudaMemcpyDeviceToHost, stream));
+    // the positions are final after the drift: copy them back while the field solve runs
+    const std::function<int()> positions_out = [&]() -> int {
+      DGP_CUDA(cudaEventRecord(drift_ev, stream));
+      DGP_CUDA(cudaStreamWaitEvent(copy_stream, drift_ev, 0));
+      for (int i = 0; i < 3; ++i)
+        DGP_CUDA(cudaMemcpyAsync(src[i], hp[i], bytes, cudaMemcpyDeviceToHost, copy_stream));
+      return DGP_OK;
+    };
+    const int rc = step_impl(&dp, a, da, info, &positions_out);
+    if (rc != DGP_OK) {
+      cudaStreamSynchronize(copy_stream);
+      return rc;
+    }
+    for (int i = 3; i < 6; ++i) DGP_CUDA(cudaMemcpyAsync(src[i], hp[i], bytes, cudaMemcpyDeviceToHost, stream));
+    DGP_CUDA(cudaStreamSynchronize(copy_stream));
     DGP_CUDA(wait_stream());
     return DGP_OK;
   }

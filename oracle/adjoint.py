@@ -30,6 +30,13 @@ the force multiplier -i k_i.
 The particle side (deposit, force interpolation, the kick-drift-kick step)
 is differentiated below by hand from the CIC weights' derivatives.
 
+The crossover scale r_c H0 enters the converged solve through the scalar
+coefficients and E(a) (in 1/kbar and the prefactor (a E)^2 / k^2).  With D, lam
+and delta held at the solution, its explicit derivative is
+    rcbar = <phibar, A' delta + B' D> - <lam, dR/d(r_c H0)>,
+    dR/d(r_c H0) = alpha' D + c2' N[D] + c2 N'[D] - S' delta,
+(' = d/d(r_c H0)); a step adds the derivatives of its kick and drift factors.
+
 Parity pins (tests/test_oracle_adjoint.py): central finite differences of
 <phibar, phi(delta)> through the oracle's own nonlinear solve; the identity
 <u, J v> = <J^T u, v> with J v taken by finite differences of the forward
@@ -58,6 +65,34 @@ def _mult(grid, coef, local_only):
     S = np.where(grid.zero, 0.0, coef["s"] * (1.0 - coef["beta"] * ikb))
     Nm = -ikb
     return A, B, S, Nm
+
+
+def _mult_drc(grid, coef, dcoef, local_only):
+    """d/d(r_c H0) of the multipliers of _mult (dcoef from background.coefficient_derivatives)."""
+    a, E, eta = coef["a"], coef["E"], coef["eta"]
+    dE, deta = dcoef["E"], dcoef["eta"]
+    ikb = field._kbar_inv(grid, coef, local_only)
+    dikb = ikb * dE / E                                  # 1/kbar = a E / (C_H |k|)
+    pref = -(a * E) ** 2 / grid.k2_safe
+    dpref = 2.0 * pref * dE / E
+    den = 1.0 + ikb / eta
+    dden = dikb / eta - ikb * deta / (eta * eta)
+    om, dom = (eta - 1.0) / eta, deta / (eta * eta)
+    dA = 1.5 * (dpref * om / den + pref * dom / den - pref * om * dden / (den * den))
+    b = -1.0 / (2.0 * eta) + coef["c3"] * ikb
+    db = deta / (2.0 * eta * eta) + dcoef["c3"] * ikb + coef["c3"] * dikb
+    dB = dpref * b / den + pref * db / den - pref * b * dden / (den * den)
+    dS = dcoef["s"] * (1.0 - coef["beta"] * ikb) - coef["s"] * (dcoef["beta"] * ikb + coef["beta"] * dikb)
+    z = grid.zero
+    return (np.where(z, 0.0, dA), np.where(z, 0.0, dB), np.where(z, 0.0, dS), np.where(z, 0.0, -dikb))
+
+
+def rc_bar_solve(phibar, lam, delta, D, grid, coef, dcoef, local_only=False):
+    """Explicit d<phibar, phi>/d(r_c H0) of a converged solve (module docstring)."""
+    _, _, _, Nm = _mult(grid, coef, local_only)
+    dA, dB, dS, dN = _mult_drc(grid, coef, dcoef, local_only)
+    dR = dcoef["alpha"] * D + dcoef["c2"] * _apply(Nm, D) + coef["c2"] * _apply(dN, D) - _apply(dS, delta)
+    return float(np.sum(phibar * (_apply(dA, delta) + _apply(dB, D))) - np.sum(lam * dR))
 
 
 def _apply(mult, f):
@@ -127,7 +162,9 @@ def phi_vjp(delta, a, box, omega_m0, rc_H0, phibar, w=1.0 / 3.0, tol=1e-13, adj_
     Dbar = _apply(B, phibar)
     lam, ainfo = solve_adjoint(D, H, Dbar, grid, coef, w, adj_tol, max_iter, local_only)
     deltabar = _apply(A, phibar) + _apply(S, lam)
-    return deltabar, dict(D=D, lam=lam, forward=finfo, adjoint=ainfo)
+    dcoef = bg.coefficient_derivatives(a, omega_m0, rc_H0)
+    rcbar = rc_bar_solve(phibar, lam, delta, D, grid, coef, dcoef, local_only)
+    return deltabar, dict(D=D, lam=lam, forward=finfo, adjoint=ainfo, rcbar=rcbar)
 
 
 # ---------------------------------------------------------------- particles
@@ -179,11 +216,13 @@ def gather_vjp(grids, pos, box, fbar):
     return Gbar, xbar
 
 
-def force_vjp(pos, a, n, box, omega_m0, rc_H0, fbar, w=1.0 / 3.0, tol=1e-13, adj_tol=1e-12):
+def force_vjp(pos, a, n, box, omega_m0, rc_H0, fbar, w=1.0 / 3.0, tol=1e-13, adj_tol=1e-12,
+              with_rc=False):
     """xbar for the particle forces F(x) = gather(g(delta(x)), x) of Sec. III.A: the
     direct term of the gather, plus deposit of fbar -> force cotangent grids -> the solve's
     adjoint -> deltabar -> rhobar = deltabar M / Np (delta = rho M / Np - 1, the particle
-    count being conserved) -> the deposit's transpose."""
+    count being conserved) -> the deposit's transpose.  with_rc: returns (xbar, rcbar,
+    <fbar, F>), rcbar the explicit d<fbar, F>/d(r_c H0) of the solve."""
     from . import pm
     pos = np.asarray(pos, float) % box
     npart = pos.shape[1]
@@ -191,14 +230,25 @@ def force_vjp(pos, a, n, box, omega_m0, rc_H0, fbar, w=1.0 / 3.0, tol=1e-13, adj
     _, g, _, _ = field.solve_phi(delta, a, box, omega_m0, rc_H0, w, tol)
     Gbar, xbar = gather_vjp(g, pos, box, fbar)
     grid = field.KGrid(n, box)
-    dbar, _ = phi_vjp(delta, a, box, omega_m0, rc_H0, phibar_from_forces(Gbar, grid), w, tol, adj_tol)
-    return xbar + deposit_vjp(pos, n, box, dbar * (n ** 3 / npart))
+    dbar, info = phi_vjp(delta, a, box, omega_m0, rc_H0, phibar_from_forces(Gbar, grid), w, tol, adj_tol)
+    xbar = xbar + deposit_vjp(pos, n, box, dbar * (n ** 3 / npart))
+    if not with_rc:
+        return xbar
+    F = np.stack([pm.cic_interpolate(g[i], pos, box) for i in range(3)])
+    return xbar, info["rcbar"], float(np.sum(np.asarray(fbar) * F))
 
 
-def step_vjp(pos0, mom0, a, da, xbar1, pbar1, n, box, omega_m0, rc_H0, w=1.0 / 3.0, tol=1e-13):
+def step_vjp(pos0, mom0, a, da, xbar1, pbar1, n, box, omega_m0, rc_H0, w=1.0 / 3.0, tol=1e-13,
+             with_rc=False):
     """Transpose of the Jacobian of one kick-drift-kick step (Sec. III.A, as PMState.step):
     p_h = p0 + K1 F(x0), x1 = x0 + Dr p_h (mod box), p1 = p_h + K2 F(x1).
-    Returns (xbar0, pbar0) for the cotangents (xbar1, pbar1) of (x1, p1)."""
+    Returns (xbar0, pbar0) for the cotangents (xbar1, pbar1) of (x1, p1); with_rc also
+    the step's explicit derivative in r_c H0 (xbar0, pbar0, rcbar):
+        K2' <pbar1, F(x1)> + rcbar_solve(x1) + Dr' <xbar1_tot, p_h>
+        + K1' <pbar_h, F(x0)> + rcbar_solve(x0),
+    xbar1_tot the cotangent of x1 after the second kick's transpose."""
+    if with_rc:
+        return _step_vjp_rc(pos0, mom0, a, da, xbar1, pbar1, n, box, omega_m0, rc_H0, w, tol)
     a1 = a + da
     ah = np.exp(0.5 * (np.log(a) + np.log(a1)))
     k1 = bg.kick_factor(a, ah, omega_m0, rc_H0)
@@ -213,6 +263,29 @@ def step_vjp(pos0, mom0, a, da, xbar1, pbar1, n, box, omega_m0, rc_H0, w=1.0 / 3
     phbar = pbar1 + dr * xbar
     xbar0 = xbar + force_vjp(st.pos, a, n, box, omega_m0, rc_H0, k1 * phbar, w, tol)
     return xbar0, phbar
+
+
+def _step_vjp_rc(pos0, mom0, a, da, xbar1, pbar1, n, box, omega_m0, rc_H0, w, tol):
+    from . import pm
+    a1 = a + da
+    ah = np.exp(0.5 * (np.log(a) + np.log(a1)))
+    k1 = bg.kick_factor(a, ah, omega_m0, rc_H0)
+    k2 = bg.kick_factor(ah, a1, omega_m0, rc_H0)
+    dr = bg.drift_factor(a, a1, omega_m0, rc_H0)
+    dk1 = bg.kick_factor_drc(a, ah, omega_m0, rc_H0)
+    dk2 = bg.kick_factor_drc(ah, a1, omega_m0, rc_H0)
+    ddr = bg.drift_factor_drc(a, a1, omega_m0, rc_H0)
+    st = pm.PMState(pos0, mom0, a, n, box, omega_m0, rc_H0, w=w, tol=tol)
+    f0 = st.forces_at_particles()
+    ph = st.mom + k1 * f0
+    x1 = (st.pos + dr * ph) % box
+    pbar1 = np.asarray(pbar1, float)
+    xb, rc1, pf1 = force_vjp(x1, a1, n, box, omega_m0, rc_H0, k2 * pbar1, w, tol, with_rc=True)
+    xbar = np.asarray(xbar1, float) + xb
+    phbar = pbar1 + dr * xbar
+    xb0, rc0, pf0 = force_vjp(st.pos, a, n, box, omega_m0, rc_H0, k1 * phbar, w, tol, with_rc=True)
+    rcbar = dk2 * pf1 / k2 + rc1 + ddr * float(np.sum(xbar * ph)) + dk1 * pf0 / k1 + rc0
+    return xbar + xb0, phbar, rcbar
 
 
 # ---------------------------------------------------------------- estimator and initial conditions
@@ -246,3 +319,18 @@ def zeldovich_vjp(xbar, pbar, n, box, vel_factor):
         mult = np.where(grid.zero, 0.0, -grid.gradient_multiplier(j) / grid.k2_safe)
         out += ifft3_real(mult * fft3(psibar))
     return out
+
+
+def zeldovich_displacement(delta_l, box):
+    """Psi_j = IFFT(i k_j / k^2 delta_L(k)), the Nyquist component of k_j dropped (three n^3 fields)."""
+    n = delta_l.shape[0]
+    grid = field.KGrid(n, box)
+    dk = fft3(np.asarray(delta_l, float))
+    return [ifft3_real(np.where(grid.zero, 0.0, grid.gradient_multiplier(j) / grid.k2_safe) * dk)
+            for j in range(3)]
+
+
+def zeldovich_vf_bar(pbar, delta_l, box):
+    """Cotangent of vel_factor in mom = vel_factor Psi: sum_j <pbar_j, Psi_j>."""
+    psi = zeldovich_displacement(delta_l, box)
+    return float(sum(np.sum(np.asarray(pbar[j]).reshape(psi[j].shape) * psi[j]) for j in range(3)))

@@ -157,3 +157,106 @@ def drift_factor(a0, a1, omega_m0, rc_H0):
     return _gauss_legendre(
         lambda x: 1.0 / (math.exp(2 * x) * float(hubble_E(math.exp(x), omega_m0, rc_H0))),
         math.log(a0), math.log(a1))
+
+
+# ---------------------------------------------------------------- derivatives in r_c H0
+# d/d(r_c H0) of the quantities above, written out by the chain rule (the
+# gradient of a loss with respect to the crossover scale goes through E(a),
+# eta = r_c H and every coefficient of Eqs. FullDGP1-2).
+
+def hubble_E_drc(a, omega_m0, rc_H0):
+    """dE/d(r_c H0): differentiating E^2 - eps E - Om a^-3 = 0 with eps = 1/(r_c H0)
+    gives (2E - eps) dE = E d eps, d eps = -d(r_c H0) / (r_c H0)^2."""
+    E = float(hubble_E(a, omega_m0, rc_H0))
+    eps = 1.0 / rc_H0
+    return -E / (rc_H0 * rc_H0 * (2.0 * E - eps))
+
+
+def coefficient_derivatives(a, omega_m0, rc_H0):
+    """d/d(r_c H0) of E, eta, alpha, beta, s, c2, c3, q and Omega_m(a), as a dict
+    with the same keys as coefficients()."""
+    c = coefficients(a, omega_m0, rc_H0)
+    E, eta, beta = c["E"], c["eta"], c["beta"]
+    dE = hubble_E_drc(a, omega_m0, rc_H0)
+    deta = E + rc_H0 * dE
+    den = 2.0 * eta * eta - eta            # eta (2 eta - 1)
+    dden = 4.0 * eta - 1.0
+    a_num, b_num = 2.0 * eta * eta - 2.0 * eta + 1.0, 2.0 * eta * eta - 2.0 * eta - 1.0
+    dalpha = 3.0 * ((4.0 * eta - 2.0) * den - a_num * dden) / (den * den)
+    dbeta = ((4.0 * eta - 2.0) * den - b_num * dden) / (den * den)
+    ds = 3.0 / (eta * eta)
+    t = 2.0 * eta - 1.0
+    dc2 = 3.0 * (dbeta * (eta - 1.0) / t + beta / (t * t))
+    c3_num, c3_den = 3.0 * eta * eta - 5.0 * eta + 1.0, 4.0 * eta ** 3 - 2.0 * eta * eta
+    dc3 = ((6.0 * eta - 5.0) * c3_den - c3_num * (12.0 * eta * eta - 4.0 * eta)) / (c3_den * c3_den)
+    dq = -3.0 / (t * t)
+    out = dict(E=dE, eta=deta, alpha=dalpha * deta, beta=dbeta * deta, s=ds * deta, c2=dc2 * deta,
+               c3=dc3 * deta, q=dq * deta, omega_m=-2.0 * c["omega_m"] * dE / E)
+    return out
+
+
+def kick_factor_drc(a0, a1, omega_m0, rc_H0):
+    """d/d(r_c H0) of kick_factor: the same 8-point rule applied to -E'/E^2."""
+    def fn(x):
+        a = math.exp(x)
+        E = float(hubble_E(a, omega_m0, rc_H0))
+        return -hubble_E_drc(a, omega_m0, rc_H0) / (E * E)
+    return _gauss_legendre(fn, math.log(a0), math.log(a1))
+
+
+def drift_factor_drc(a0, a1, omega_m0, rc_H0):
+    """d/d(r_c H0) of drift_factor: the same 8-point rule applied to -E'/(a^2 E^2)."""
+    def fn(x):
+        a = math.exp(x)
+        E = float(hubble_E(a, omega_m0, rc_H0))
+        return -hubble_E_drc(a, omega_m0, rc_H0) / (a * a * E * E)
+    return _gauss_legendre(fn, math.log(a0), math.log(a1))
+
+
+def growth_drc(a_out, omega_m0, rc_H0, a_start=1e-5, steps_per_efold=400):
+    """(D+, f, dD+/d(r_c H0), df/d(r_c H0)) with the local G_eff: the growth ODE of
+    growth() integrated together with its sensitivity equations
+        z' = (dF/dy) z + dF/d(r_c H0),  z = dy/d(r_c H0),  z(a_start) = 0,
+    by the same classical RK4 steps (forward-mode differentiation of the RK4 map)."""
+    eps = 1.0 / rc_H0
+
+    def rhs(lna, y):
+        a = math.exp(lna)
+        c = coefficients(a, omega_m0, rc_H0)
+        dc = coefficient_derivatives(a, omega_m0, rc_H0)
+        E, eta, q = c["E"], c["eta"], c["q"]
+        G = (2.0 * E - eps) * E
+        dG = (2.0 * dc["E"] + eps * eps) * E + (2.0 * E - eps) * dc["E"]   # d eps = -eps^2
+        L = -3.0 * omega_m0 * a ** -3 / G
+        dL = 3.0 * omega_m0 * a ** -3 * dG / (G * G)
+        u = 2.0 * eta * (2.0 + q)
+        du = 2.0 * dc["eta"] * (2.0 + q) + 2.0 * eta * dc["q"]
+        g = (u - 4.0) / (u - 3.0)
+        dg = du / ((u - 3.0) ** 2)
+        src = 1.5 * c["omega_m"] * g
+        dsrc = 1.5 * (dc["omega_m"] * g + c["omega_m"] * dg)
+        D, dD, zD, zdD = y
+        return np.array([dD, -(2.0 + L) * dD + src * D,
+                         zdD, -(2.0 + L) * zdD - dL * dD + src * zD + dsrc * D])
+
+    x0, x1 = math.log(a_start), math.log(a_out)
+    n = max(1, int(math.ceil((x1 - x0) * steps_per_efold)))
+    h = (x1 - x0) / n
+    y = np.array([a_start, a_start, 0.0, 0.0])
+    x = x0
+    for _ in range(n):
+        k1 = rhs(x, y)
+        k2 = rhs(x + 0.5 * h, y + 0.5 * h * k1)
+        k3 = rhs(x + 0.5 * h, y + 0.5 * h * k2)
+        k4 = rhs(x + h, y + h * k3)
+        y = y + (h / 6.0) * (k1 + 2 * k2 + 2 * k3 + k4)
+        x += h
+    D, dD, zD, zdD = (float(v) for v in y)
+    return D, dD / D, zD, (zdD * D - dD * zD) / (D * D)
+
+
+def zeldovich_velocity_factor_drc(a, omega_m0, rc_H0):
+    """(vf, dvf/d(r_c H0)) for vf = a^2 E f (local G_eff)."""
+    _, f, _, df = growth_drc(a, omega_m0, rc_H0)
+    E = float(hubble_E(a, omega_m0, rc_H0))
+    return a * a * E * f, a * a * (hubble_E_drc(a, omega_m0, rc_H0) * f + E * df)

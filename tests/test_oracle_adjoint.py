@@ -210,3 +210,71 @@ def test_zeldovich_vjp_central_differences():
 
     fd = (L(d + e * u) - L(d - e * u)) / (2 * e)
     assert abs(fd - np.sum(adj.zeldovich_vjp(xb, pb, n, box, vf) * u)) < 1e-7 * abs(fd)
+
+
+# ---------------------------------------------------------------- r_c H0
+def test_background_derivatives_central_differences():
+    """Chain-rule derivatives in r_c H0 against central differences of the pinned background."""
+    for a, rc in ((0.5, 1.2), (0.05, 0.8), (1.0, 2.5)):
+        d = bg.coefficient_derivatives(a, OM, rc)
+        h = 1e-6 * rc
+        cp, cm = bg.coefficients(a, OM, rc + h), bg.coefficients(a, OM, rc - h)
+        for k in ("E", "eta", "alpha", "beta", "s", "c2", "c3", "q", "omega_m"):
+            fd = (cp[k] - cm[k]) / (2 * h)
+            assert abs(d[k] - fd) < 1e-7 * abs(fd) + 1e-12, k
+        for f, df in ((bg.kick_factor, bg.kick_factor_drc), (bg.drift_factor, bg.drift_factor_drc)):
+            fd = (f(a * 0.9, a, OM, rc + h) - f(a * 0.9, a, OM, rc - h)) / (2 * h)
+            assert abs(df(a * 0.9, a, OM, rc) - fd) < 1e-7 * abs(fd)
+
+
+def test_velocity_factor_derivative_central_differences():
+    """d(a^2 E f)/d(r_c H0) from the RK4 sensitivity equations against differences of the
+    growth ODE itself; the value matches zeldovich_velocity_factor."""
+    for a, rc in ((0.02, 1.0), (0.5, 0.7)):
+        vf, dvf = bg.zeldovich_velocity_factor_drc(a, OM, rc)
+        assert abs(vf - bg.zeldovich_velocity_factor(a, OM, rc)) < 1e-14 * vf
+        h = 1e-4 * rc
+        fd = (bg.zeldovich_velocity_factor(a, OM, rc + h) - bg.zeldovich_velocity_factor(a, OM, rc - h)) / (2 * h)
+        assert abs(dvf - fd) < 1e-6 * abs(fd)
+
+
+def test_phi_vjp_rc_central_differences():
+    """d<phibar, phi>/d(r_c H0) through the converged nonlinear solve (delta fixed)."""
+    n, box, a, rc = 16, 60.0, 0.6, 1.0
+    d, _ = inputs.linear_field(n, box, -1.5, 0.25, seed=4)
+    phibar = np.random.default_rng(15).standard_normal((n, n, n))
+    _, info = adj.phi_vjp(d, a, box, OM, rc, phibar)
+    h = 1e-5
+    lp = np.sum(phibar * field.solve_phi(d, a, box, OM, rc + h, tol=1e-13)[0])
+    lm = np.sum(phibar * field.solve_phi(d, a, box, OM, rc - h, tol=1e-13)[0])
+    fd = (lp - lm) / (2 * h)
+    assert abs(fd - info["rcbar"]) < 1e-6 * abs(fd)
+
+
+def test_step_vjp_rc_central_differences():
+    n, box, a, da, rc = 16, 80.0, 0.5, 0.02, 1.0
+    pos, mom = _particles(n, box, 0.25, 7)
+    rng = np.random.default_rng(16)
+    xb1, pb1 = rng.standard_normal(pos.shape), rng.standard_normal(pos.shape)
+
+    def L(r):
+        st = pm.PMState(pos, mom, a, n, box, OM, r, tol=1e-13)
+        st.step(da)
+        return np.sum(xb1 * ((st.pos - pos + box / 2) % box)) + np.sum(pb1 * st.mom)
+
+    xb0, pb0, rcbar = adj.step_vjp(pos, mom, a, da, xb1, pb1, n, box, OM, rc, with_rc=True)
+    xr, pr = adj.step_vjp(pos, mom, a, da, xb1, pb1, n, box, OM, rc)
+    assert np.array_equal(xb0, xr) and np.array_equal(pb0, pr)
+    h = 1e-5
+    fd = (L(rc + h) - L(rc - h)) / (2 * h)
+    assert abs(fd - rcbar) < 1e-6 * abs(fd)
+
+
+def test_zeldovich_vf_bar_central_differences():
+    n, box, vf = 16, 60.0, 0.7
+    d, _ = inputs.linear_field(n, box, -1.5, 0.3, seed=13)
+    pb = np.random.default_rng(17).standard_normal((3, n ** 3))
+    e = 1e-6
+    fd = (np.sum(pb * inputs.zeldovich_from_field(d, box, vf + e)[1])
+          - np.sum(pb * inputs.zeldovich_from_field(d, box, vf - e)[1])) / (2 * e)
+    assert abs(fd - adj.zeldovich_vf_bar(pb, d, box)) < 1e-7 * abs(fd)

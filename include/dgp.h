@@ -229,6 +229,14 @@ int dgp_zeldovich_adjoint(dgp_ctx *c, const dgp_particles *cot, double vel_facto
 int dgp_power_spectrum_adjoint(dgp_ctx *c, const dgp_particles *parts, int nbins, const double *dl_dp,
                                dgp_particles *cot);
 
+/* Tile configuration of the context (not part of the paper's method): the y
+ * pass's threads per CTA, 128, 256 or 512 (that many / N1 rows per CTA), picked
+ * at dgp_init by timing the three variants on the context's own buffers.  The
+ * results do not depend on the choice.  dgp_set_tile_config forces a value
+ * (DGP_E_INVALID for any other). */
+int dgp_tile_config(dgp_ctx *c, int *y_threads);
+int dgp_set_tile_config(dgp_ctx *c, int y_threads);
+
 /* Host waits of the context (the relaxation's stop-rule verdicts, host outputs)
  * block on an event and yield the CPU (on != 0) instead of spinning (0, the
  * default).  For callers that drive many contexts from many host threads. */

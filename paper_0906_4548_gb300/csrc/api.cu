@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <complex>
 #include <functional>
 #include <new>
 #include <utility>
@@ -17,23 +18,35 @@
 namespace dgp {
 
 // ---------------------------------------------------------------- background
+// The background is written once for a scalar type S: double for the values,
+// std::complex<double> for their derivatives in r_c H0 by complex-step
+// differentiation (Squire & Trapp 1998): for f analytic in r, evaluated at
+// r + i h, f'(r) = Im f(r + i h) / h + O(h^2), with no difference taken, so
+// h = 1e-20 r gives the derivative to rounding.  Every operation on an S below
+// is analytic (no abs, no comparison); a and ln a stay real.
+using cplx = std::complex<double>;
+
 // Eq. DGPFriedmann with H0 = 1: E^2 - E / rc - Om a^-3 = 0, '+' root.
-static double hubble_E(double a, double om, double rc) {
-  const double eps = 1.0 / rc;
+template <typename S> static S hubble_E_t(double a, double om, S rc) {
+  using std::sqrt;
+  const S eps = 1.0 / rc;
   return 0.5 * (eps + sqrt(eps * eps + 4.0 * om / (a * a * a)));
 }
+static double hubble_E(double a, double om, double rc) { return hubble_E_t<double>(a, om, rc); }
 
-struct Coef {
-  double a, E, eta, alpha, beta, s, c2, c3, q, omega_m;
+template <typename S> struct CoefT {
+  double a;
+  S E, eta, alpha, beta, s, c2, c3, q, omega_m;
 };
+using Coef = CoefT<double>;
 
-static Coef coefficients(double a, double om, double rc) {
-  Coef c;
+template <typename S> static CoefT<S> coefficients_t(double a, double om, S rc) {
+  CoefT<S> c;
   c.a = a;
-  c.E = hubble_E(a, om, rc);
-  const double eta = rc * c.E;
+  c.E = hubble_E_t<S>(a, om, rc);
+  const S eta = rc * c.E;
   c.eta = eta;
-  const double den = eta * (2.0 * eta - 1.0);
+  const S den = eta * (2.0 * eta - 1.0);
   c.alpha = 3.0 * (2.0 * eta * eta - 2.0 * eta + 1.0) / den;
   c.beta = (2.0 * eta * eta - 2.0 * eta - 1.0) / den;
   c.s = 3.0 * (eta - 1.0) / eta;
@@ -43,27 +56,43 @@ static Coef coefficients(double a, double om, double rc) {
   c.omega_m = om / (a * a * a * c.E * c.E);
   return c;
 }
+static Coef coefficients(double a, double om, double rc) { return coefficients_t<double>(a, om, rc); }
 
-static double geff_local(const Coef& c) {
-  const double t = 2.0 * c.eta * (2.0 + c.q);
+template <typename S> static S geff_local_t(const CoefT<S>& c) {
+  const S t = 2.0 * c.eta * (2.0 + c.q);
   return (t - 4.0) / (t - 3.0);
+}
+static double geff_local(const Coef& c) { return geff_local_t<double>(c); }
+
+static double cs_step(double rc) { return 1e-20 * rc; }
+
+// d/d(r_c H0) of every coefficient (fields of the returned Coef hold derivatives; a is a).
+static Coef coefficients_drc(double a, double om, double rc) {
+  const double h = cs_step(rc);
+  const CoefT<cplx> z = coefficients_t<cplx>(a, om, cplx(rc, h));
+  Coef d;
+  d.a = a;
+  d.E = z.E.imag() / h; d.eta = z.eta.imag() / h; d.alpha = z.alpha.imag() / h; d.beta = z.beta.imag() / h;
+  d.s = z.s.imag() / h; d.c2 = z.c2.imag() / h; d.c3 = z.c3.imag() / h; d.q = z.q.imag() / h;
+  d.omega_m = z.omega_m.imag() / h;
+  return d;
 }
 
 // Linear growth D'' + (2 + dlnE/dlna) D' = 1.5 Omega_m(a) Geff_local D in ln a,
 // growing mode D = a at a = 1e-5, classical RK4 with 400 steps per e-fold.
-static void growth(double a_out, double om, double rc, double* D_out, double* f_out) {
-  auto rhs = [&](double lna, const double y[2], double dy[2]) {
+template <typename S> static void growth_t(double a_out, double om, S rc, S* D_out, S* f_out) {
+  auto rhs = [&](double lna, const S y[2], S dy[2]) {
     const double a = exp(lna);
-    const Coef c = coefficients(a, om, rc);
-    const double dlnE = -3.0 * om / (a * a * a) / ((2.0 * c.E - 1.0 / rc) * c.E);
+    const CoefT<S> c = coefficients_t<S>(a, om, rc);
+    const S dlnE = -3.0 * om / (a * a * a) / ((2.0 * c.E - 1.0 / rc) * c.E);
     dy[0] = y[1];
-    dy[1] = -(2.0 + dlnE) * y[1] + 1.5 * c.omega_m * geff_local(c) * y[0];
+    dy[1] = -(2.0 + dlnE) * y[1] + 1.5 * c.omega_m * geff_local_t<S>(c) * y[0];
   };
   const double x0 = log(1e-5), x1 = log(a_out);
   int n = (int)ceil((x1 - x0) * 400.0);
   if (n < 1) n = 1;
   const double h = (x1 - x0) / n;
-  double y[2] = {1e-5, 1e-5}, k1[2], k2[2], k3[2], k4[2], t[2];
+  S y[2] = {S(1e-5), S(1e-5)}, k1[2], k2[2], k3[2], k4[2], t[2];
   double x = x0;
   for (int i = 0; i < n; ++i) {
     rhs(x, y, k1);
@@ -73,11 +102,26 @@ static void growth(double a_out, double om, double rc, double* D_out, double* f_
     rhs(x + 0.5 * h, t, k3);
     for (int j = 0; j < 2; ++j) t[j] = y[j] + h * k3[j];
     rhs(x + h, t, k4);
-    for (int j = 0; j < 2; ++j) y[j] += h / 6.0 * (k1[j] + 2 * k2[j] + 2 * k3[j] + k4[j]);
+    for (int j = 0; j < 2; ++j) y[j] += h / 6.0 * (k1[j] + 2.0 * k2[j] + 2.0 * k3[j] + k4[j]);
     x += h;
   }
   *D_out = y[0];
   *f_out = y[1] / y[0];
+}
+static void growth(double a_out, double om, double rc, double* D_out, double* f_out) {
+  growth_t<double>(a_out, om, rc, D_out, f_out);
+}
+
+// Zel'dovich velocity factor vf = a^2 E f and its derivative in r_c H0.
+static void velocity_factor(double a, double om, double rc, double* vf, double* dvf) {
+  const double h = cs_step(rc);
+  cplx D, f;
+  growth_t<cplx>(a, om, cplx(rc, h), &D, &f);
+  const cplx v = a * a * hubble_E_t<cplx>(a, om, cplx(rc, h)) * f;
+  double Dr, fr;
+  growth(a, om, rc, &Dr, &fr);
+  *vf = a * a * hubble_E(a, om, rc) * fr;
+  *dvf = v.imag() / h;
 }
 
 // 8-point Gauss-Legendre nodes and weights by Newton iteration on P_8.
@@ -105,17 +149,25 @@ static void gauss_legendre8(double xs[8], double ws[8]) {
 
 // int_{ln a0}^{ln a1} dlna / (a^pw E): pw = 0 kick, pw = 2 drift (Sec. III.A
 // with p = a^2 dx/dt: dp/dlna = -grad phi / E, dx/dlna = p / (a^2 E)).
-static double time_integral(double a0, double a1, double om, double rc, int pw) {
+template <typename S> static S time_integral_t(double a0, double a1, double om, S rc, int pw) {
   double xs[8], ws[8];
   gauss_legendre8(xs, ws);
   const double l0 = log(a0), l1 = log(a1);
   const double xm = 0.5 * (l0 + l1), xr = 0.5 * (l1 - l0);
-  double acc = 0.0;
+  S acc = S(0.0);
   for (int i = 0; i < 8; ++i) {
     const double a = exp(xm + xr * xs[i]);
-    acc += ws[i] / (pow(a, pw) * hubble_E(a, om, rc));
+    acc += ws[i] / (pow(a, pw) * hubble_E_t<S>(a, om, rc));
   }
   return xr * acc;
+}
+static double time_integral(double a0, double a1, double om, double rc, int pw) {
+  return time_integral_t<double>(a0, a1, om, rc, pw);
+}
+// d/d(r_c H0) of time_integral (complex step)
+static double time_integral_drc(double a0, double a1, double om, double rc, int pw) {
+  const double h = cs_step(rc);
+  return time_integral_t<cplx>(a0, a1, om, cplx(rc, h), pw).imag() / h;
 }
 
 // ---------------------------------------------------------------- engine
@@ -217,6 +269,7 @@ class EngineBase {
   Profiler prof;
   std::vector<double> history;  // normalised residual of each iterate of the last solve
   cudaEvent_t sync_event = nullptr;  // set: host waits block on this event instead of spinning
+  int y_threads = 256;          // y-pass CTA size, chosen at init by timing (tile autotuning)
 
   // Host wait for the work enqueued so far on the context's stream.
   cudaError_t wait_stream() {
@@ -376,7 +429,44 @@ class Engine : public EngineBase {
     if (cudaMalloc(&tw, sizeof(V) * 3 * N) != cudaSuccess) return DGP_E_NOMEM;
     DGP_CUDA(cudaMemcpy(tw, htw.data(), sizeof(V) * 3 * N, cudaMemcpyHostToDevice));
     DGP_CUDA(cudaMemset(d_rstats, 0, sizeof(double) * 12));
-    return DGP_OK;
+    return tune_tiles();
+  }
+
+  // Tile autotuning: time the y pass's CTA sizes (128, 256, 512 threads; 128 / N1,
+  // ... rows per CTA) on this context's own spectrum buffers, six inverse
+  // transforms as in a relaxation iteration, and keep the fastest.  The results
+  // do not depend on the choice (every row's arithmetic is the same).
+  int tune_tiles() {
+    for (int i = 0; i < 6; ++i) DGP_CUDA(cudaMemsetAsync(s6[i], 0, sizeof(V) * SPEC, stream));
+    cudaEvent_t e0, e1;
+    DGP_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+      cudaEventDestroy(e0);
+      return DGP_E_CUDA;
+    }
+    const int cand[3] = {128, 256, 512};
+    float best_ms = 1e30f;
+    int best = 256, rc = DGP_OK;
+    for (int c = 0; c < 3 && rc == DGP_OK; ++c) {
+      launch_fft_y<T, N>(fs(s6, 6), 6, true, tw, stream, nullptr, cand[c]);  // warm-up
+      cudaEventRecord(e0, stream);
+      for (int r = 0; r < 3; ++r) launch_fft_y<T, N>(fs(s6, 6), 6, true, tw, stream, nullptr, cand[c]);
+      cudaEventRecord(e1, stream);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess ||
+          cudaGetLastError() != cudaSuccess) {
+        rc = DGP_E_CUDA;
+        break;
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = cand[c];
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    y_threads = best;
+    return rc;
   }
 
   void reset() override {
@@ -432,14 +522,14 @@ class Engine : public EngineBase {
   int forward_zy(const T* in, V* out, ZPrologue pro) {
     prof.run(KK_Z_R2C, RB + SB, stream, [&] { launch_fft_z_r2c<T, N>(in, 0, out, 0, 1, pro, tw, stream); });
     V* o[1] = {out};
-    prof.run(KK_Y, 2 * SB, stream, [&] { launch_fft_y<T, N>(fs(o, 1), 1, false, tw, stream); });
+    prof.run(KK_Y, 2 * SB, stream, [&] { launch_fft_y<T, N>(fs(o, 1), 1, false, tw, stream, nullptr, y_threads); });
     DGP_CHECK_LAUNCH();
     return DGP_OK;
   }
 
   // x-op outputs (already in s6[0..n)) -> y inverse -> z inverse into real fields
   int inverse_yz(V* const* spec, T* const* out, int n) {
-    prof.run(KK_Y, 2 * SB * n, stream, [&] { launch_fft_y<T, N>(fs(spec, n), n, true, tw, stream); });
+    prof.run(KK_Y, 2 * SB * n, stream, [&] { launch_fft_y<T, N>(fs(spec, n), n, true, tw, stream, nullptr, y_threads); });
     prof.run(KK_Z_C2R, (RB + SB) * n, stream, [&] { launch_fft_z_c2r<T, N>(fs(spec, n), out, n, tw, stream); });
     DGP_CHECK_LAUNCH();
     return DGP_OK;
@@ -547,7 +637,7 @@ class Engine : public EngineBase {
           launch_fft_x_op<T, N>(XOP_HESSIAN, spec_in(it), nullptr, fs(s6, 6), 0, kp, nullptr, 0, 0, 0, tw, stream,
                                 sk);
         });
-        prof.run(KK_Y, 0, stream, [&] { launch_fft_y<T, N>(fs(s6, 6), 6, true, tw, stream, sk); });
+        prof.run(KK_Y, 0, stream, [&] { launch_fft_y<T, N>(fs(s6, 6), 6, true, tw, stream, sk, y_threads); });
         prof.run(KK_RELAX, 0, stream, [&] {
           launch_fused_relax<T, N>(arith, s6, rD[ib], d_rstats + 4 * ib + 1, rS, rD[ob], spec_out(it), rp, partials,
                                    tw, stream, sk);
@@ -561,7 +651,7 @@ class Engine : public EngineBase {
           });
         prof.run(KK_Y, 0, stream, [&] {
           V* o[1] = {spec_out(it)};
-          launch_fft_y<T, N>(fs(o, 1), 1, false, tw, stream, sk);
+          launch_fft_y<T, N>(fs(o, 1), 1, false, tw, stream, sk, y_threads);
         });
         DGP_CHECK_LAUNCH();
         return DGP_OK;
@@ -1015,7 +1105,7 @@ class Engine : public EngineBase {
                [&] { launch_adj_products<T>(lam, rD[wcur], dsum, h5, aP, M, stream); });
       prof.run(KK_Z_R2C, 7 * (RB + SB), stream,
                [&] { launch_fft_z_r2c<T, N>(aP, M, aS, SPEC, 7, none, tw, stream); });
-      prof.run(KK_Y, 14 * SB, stream, [&] { launch_fft_y<T, N>(aspec, 7, false, tw, stream); });
+      prof.run(KK_Y, 14 * SB, stream, [&] { launch_fft_y<T, N>(aspec, 7, false, tw, stream, nullptr, y_threads); });
       prof.run(KK_X_OTHER, 8 * SB, stream,
                [&] { launch_fft_x_adj<T, N>(XOP_ADJ_COMBINE, aspec, 0x7f, fs(s6, 1), kp, tw, stream); });
       T* qo[1] = {aQ};
@@ -1425,6 +1515,18 @@ int dgp_solve_adjoint(dgp_ctx* c, const void* phibar, const void* gbar_x, const 
   if (!c) return DGP_E_INVALID;
   const void* g[3] = {gbar_x, gbar_y, gbar_z};
   return c->eng->adjoint(phibar, g, deltabar, tol, info);
+}
+
+int dgp_tile_config(dgp_ctx* c, int* y_threads) {
+  if (!c || !y_threads) return DGP_E_INVALID;
+  *y_threads = c->eng->y_threads;
+  return DGP_OK;
+}
+
+int dgp_set_tile_config(dgp_ctx* c, int y_threads) {
+  if (!c || (y_threads != 128 && y_threads != 256 && y_threads != 512)) return DGP_E_INVALID;
+  c->eng->y_threads = y_threads;
+  return DGP_OK;
 }
 
 int dgp_set_blocking_sync(dgp_ctx* c, int on) {

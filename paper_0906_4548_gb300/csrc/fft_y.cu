@@ -1,6 +1,7 @@
 // y transform: in-place complex DFT along the contiguous rows of S[kz][x][y].
 //
-// Each CTA of 256 threads owns P = 256 / N1 rows.  Phase 1: lane j2 < N2
+// Each CTA of B threads (B = 128, 256 or 512, chosen per context by timing, see
+// api.cu) owns P = B / N1 rows.  Phase 1: lane j2 < N2
 // reads x[N2*j1 + j2] straight from global memory (consecutive lanes,
 // consecutive addresses), transforms over j1 and stores the twiddled result
 // to shared memory; phase 2: lane k1 reads its N2 values back with an odd
@@ -12,13 +13,15 @@
 
 namespace dgp {
 
-template <typename T, int N, bool INV>
-__global__ void __launch_bounds__(256, 4) k_fft_y(const __grid_constant__ FieldSet<T> f, int64_t npencils,
-                                              const vec2_t<T>* __restrict__ g_tw, const int* __restrict__ skip) {
+// 64 registers per thread for FP32 rows of up to 256 points, 128 otherwise
+template <typename T, int N, bool INV, int B>
+__global__ void __launch_bounds__(B, (sizeof(T) == 8 || N >= 512 ? 512 : 1024) / B) k_fft_y(const __grid_constant__ FieldSet<T> f, int64_t npencils,
+                                                     const vec2_t<T>* __restrict__ g_tw,
+                                                     const int* __restrict__ skip) {
   if (skip && *skip) return;
   using V = vec2_t<T>;
   constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
-  constexpr int P = 256 / N1;
+  constexpr int P = B / N1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* s_tw = reinterpret_cast<V*>(smem_raw);
   V* s_T = s_tw + kTwiddleTables * N;
@@ -52,26 +55,34 @@ __global__ void __launch_bounds__(256, 4) k_fft_y(const __grid_constant__ FieldS
   }
 }
 
-template <typename T, int N>
-void launch_fft_y(const FieldSet<T>& f, int nfields, bool inverse, const vec2_t<T>* tw, cudaStream_t s,
-                  const int* skip) {
+template <typename T, int N, int B>
+static void launch_y(const FieldSet<T>& f, int nfields, bool inverse, const vec2_t<T>* tw, cudaStream_t s,
+                     const int* skip) {
   using V = vec2_t<T>;
   constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
-  constexpr int P = 256 / N1;
+  constexpr int P = B / N1;
   const int64_t npencils = (int64_t)(N / 2 + 1) * N;
   const size_t smem = sizeof(V) * (kTwiddleTables * N + P * N1 * (N2 + 1));
   dim3 grid((unsigned)((npencils + P - 1) / P), (unsigned)nfields);
   if (inverse) {
-    cudaFuncSetAttribute(k_fft_y<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_fft_y<T, N, true><<<grid, 256, smem, s>>>(f, npencils, tw, skip);
+    cudaFuncSetAttribute(k_fft_y<T, N, true, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_fft_y<T, N, true, B><<<grid, B, smem, s>>>(f, npencils, tw, skip);
   } else {
-    cudaFuncSetAttribute(k_fft_y<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_fft_y<T, N, false><<<grid, 256, smem, s>>>(f, npencils, tw, skip);
+    cudaFuncSetAttribute(k_fft_y<T, N, false, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_fft_y<T, N, false, B><<<grid, B, smem, s>>>(f, npencils, tw, skip);
   }
 }
 
+template <typename T, int N>
+void launch_fft_y(const FieldSet<T>& f, int nfields, bool inverse, const vec2_t<T>* tw, cudaStream_t s,
+                  const int* skip, int threads) {
+  if (threads == 128) launch_y<T, N, 128>(f, nfields, inverse, tw, s, skip);
+  else if (threads == 512) launch_y<T, N, 512>(f, nfields, inverse, tw, s, skip);
+  else launch_y<T, N, 256>(f, nfields, inverse, tw, s, skip);
+}
+
 #define DGP_INST_Y(T, N) \
-  template void launch_fft_y<T, N>(const FieldSet<T>&, int, bool, const vec2_t<T>*, cudaStream_t, const int*);
+  template void launch_fft_y<T, N>(const FieldSet<T>&, int, bool, const vec2_t<T>*, cudaStream_t, const int*, int);
 #define DGP_INST_Y_ALL(T) DGP_INST_Y(T, 16) DGP_INST_Y(T, 32) DGP_INST_Y(T, 64) DGP_INST_Y(T, 128) \
   DGP_INST_Y(T, 256) DGP_INST_Y(T, 512) DGP_INST_Y(T, 48) DGP_INST_Y(T, 96)
 DGP_INST_Y_ALL(float)

@@ -52,9 +52,10 @@ enum XOp { XOP_HESSIAN = 0, XOP_SOURCE = 1, XOP_SOURCE_LIN = 2, XOP_PHI_FORCE = 
 // Every launcher of a kernel that can run inside a relaxation iteration takes
 // skip: NULL, or a device flag read at kernel entry; when it is nonzero the
 // whole grid returns at once (iterations enqueued past the solver's stop).
+// threads: 128, 256 or 512 per CTA (threads / N1 rows per CTA).
 template <typename T, int N>
 void launch_fft_y(const FieldSet<T>& f, int nfields, bool inverse, const vec2_t<T>* tw, cudaStream_t s,
-                  const int* skip = nullptr);
+                  const int* skip = nullptr, int threads = 256);
 
 template <typename T, int N>
 void launch_fft_z_r2c(const T* in, int64_t in_stride, vec2_t<T>* out, int64_t out_stride, int nfields,

@@ -25,7 +25,7 @@ EXPORTED = ["dgp_background", "dgp_init", "dgp_destroy", "dgp_strerror", "dgp_re
             "dgp_sort_particles", "dgp_profile_kinds", "dgp_brane_spectra", "dgp_set_blocking_sync",
             "dgp_batch_create", "dgp_batch_context", "dgp_batch_step", "dgp_batch_destroy",
             "dgp_solve_adjoint", "pm_step_adjoint", "dgp_zeldovich", "dgp_zeldovich_adjoint",
-            "dgp_power_spectrum_adjoint"]
+            "dgp_power_spectrum_adjoint", "dgp_tile_config", "dgp_set_tile_config"]
 DGP_NOALLOC_MAX_N = 64
 DGP_KERNEL_KINDS = 11
 
@@ -96,6 +96,8 @@ def _load():
         "dgp_sort_particles": (i, [vp, P(Particles), vp]),
         "dgp_brane_spectra": (i, [vp, i, P(d), P(d), P(d), P(d), P(i64)]),
         "dgp_set_blocking_sync": (i, [vp, i]),
+        "dgp_tile_config": (i, [vp, P(i)]),
+        "dgp_set_tile_config": (i, [vp, i]),
         "dgp_solve_adjoint": (i, [vp, vp, vp, vp, vp, vp, d, P(SolveInfo)]),
         "pm_step_adjoint": (i, [vp, P(Particles), d, d, P(Particles)]),
         "dgp_zeldovich": (i, [vp, vp, d, P(Particles)]),
@@ -260,6 +262,16 @@ def dgp_power_spectrum_adjoint(ctx, parts, dl_dp, cot):
     _check(lib.dgp_power_spectrum_adjoint(ctx, ctypes.byref(parts), g.size,
                                           g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(cot)),
            "dgp_power_spectrum_adjoint")
+
+
+def dgp_tile_config(ctx):
+    v = ctypes.c_int()
+    _check(lib.dgp_tile_config(ctx, ctypes.byref(v)), "dgp_tile_config")
+    return {"y_threads": v.value}
+
+
+def dgp_set_tile_config(ctx, y_threads):
+    _check(lib.dgp_set_tile_config(ctx, int(y_threads)), "dgp_set_tile_config")
 
 
 def dgp_get_solution(ctx, D):

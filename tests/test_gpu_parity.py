@@ -436,3 +436,27 @@ def test_residual_history_follows_oracle(dgp, torch_dev, prec, rtol):
     sel = ho[:m] > floor
     assert sel.sum() >= 3
     assert np.max(np.abs(hist[:m][sel] / ho[:m][sel] - 1)) < rtol
+
+
+def test_tile_autotuning_does_not_change_results(dgp, torch_dev):
+    """The y pass's CTA size is picked by timing at init; every forced choice gives the same bits."""
+    torch, dev = torch_dev
+    n, box, a = 64, 200.0, 0.5
+    pos, _, _ = zel(n, box, a, -1.5, 0.5, 5)
+    delta = opm.density_contrast(opm.cic_deposit(pos, n, box)).astype(np.float32)
+    ctx = dgp.dgp_init(box, n, 1.0, OM, precision=dgp.DGP_MIXED_EFT, tol=1e-6)
+    try:
+        assert dgp.dgp_tile_config(ctx)["y_threads"] in (128, 256, 512)
+        dd = to_dev(torch_dev, delta, torch.float32)
+        out = []
+        for th in (128, 256, 512):
+            dgp.dgp_set_tile_config(ctx, th)
+            dgp.dgp_reset(ctx)
+            phi = torch.empty_like(dd)
+            dgp.dgp_solve_phi(ctx, a, dd, phi, 1e-6)
+            out.append(phi.cpu().numpy())
+        with pytest.raises(dgp.DgpError):
+            dgp.dgp_set_tile_config(ctx, 384)
+    finally:
+        dgp.dgp_destroy(ctx)
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[1], out[2])

@@ -229,6 +229,42 @@ int dgp_zeldovich_adjoint(dgp_ctx *c, const dgp_particles *cot, double vel_facto
 int dgp_power_spectrum_adjoint(dgp_ctx *c, const dgp_particles *parts, int nbins, const double *dl_dp,
                                dgp_particles *cot);
 
+/* Derivatives in the crossover scale r_c H0 (Sec. II: r_c enters through
+ * E(a) of Eq. DGPFriedmann, eta = r_c H and every coefficient of Eqs.
+ * FullDGP1-2, the step's kick and drift factors, and the growth rate of the
+ * initial velocities).  The context's own r_c H0 is the point of evaluation;
+ * ' below is d/d(r_c H0).
+ *
+ * dgp_solve_adjoint_rc: dgp_solve_adjoint plus *rc_bar (host) = the explicit
+ * derivative of <phibar_tot, phi> with delta fixed and D through the solve:
+ *   rc_bar = <phibar_tot, A' delta + B' D> - <lam, alpha' D + c2' N[D] + c2 N'[D] - S' delta>,
+ * phibar_tot = phibar + sum_i d_i gbar_i.  Needs the accepted solve's delta,
+ * so the last field solve must have been nonlinear (else DGP_E_STATE). */
+int dgp_solve_adjoint_rc(dgp_ctx *c, const void *phibar, const void *gbar_x, const void *gbar_y,
+                         const void *gbar_z, void *deltabar, double tol, double *rc_bar, dgp_solve_info *info);
+
+/* pm_step_adjoint plus *rc_bar (host) = the step's explicit derivative of
+ * <xbar1, x1> + <pbar1, p1> in r_c H0 with (x0, p0) fixed:
+ *   K2' <pbar1, F(x1)> + rc_solve(x1) + Dr' <xbar1_tot, p_h> + K1' <pbar_h, F(x0)> + rc_solve(x0),
+ * xbar1_tot the cotangent of x1 after the second kick's transpose and rc_solve the
+ * dgp_solve_adjoint_rc term of each force VJP.  The K' and Dr' are taken by
+ * complex-step differentiation of the 8-point Gauss-Legendre rules.  Summed
+ * over the steps of a run (with the cotangents passed backwards) this is the
+ * run's derivative in r_c H0 at fixed initial particles. */
+int pm_step_adjoint_rc(dgp_ctx *c, const dgp_particles *start, double a, double da, dgp_particles *cot,
+                       double *rc_bar);
+
+/* Cotangent of vel_factor in dgp_zeldovich: *vf_bar (host) = sum_j <pbar_j, Psi_j(delta_L)>
+ * for the momentum cotangents of cot (lattice order, n^3 particles); delta_l is the device
+ * linear field. */
+int dgp_zeldovich_vf_adjoint(dgp_ctx *c, const void *delta_l, const dgp_particles *cot, double *vf_bar);
+
+/* Host-only.  The Zel'dovich velocity factor vf = a^2 E f (local G_eff, as
+ * dgp_background's growth_f) and d vf / d(r_c H0), by complex-step
+ * differentiation of the growth ODE's RK4 steps.  DGP_E_INVALID as
+ * dgp_background. */
+int dgp_velocity_factor(const dgp_cosmology *cosmo, double rc_H0, double a, double *vf, double *dvf_drc);
+
 /* Tile configuration of the context (not part of the paper's method): the y
  * pass's threads per CTA, 128, 256 or 512 (that many / N1 rows per CTA), picked
  * at dgp_init by timing the three variants on the context's own buffers.  The

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/dgp.h"
+#include "adjoint_rc.cuh"
 #include "fft_core.cuh"
 #include "kernels.cuh"
 
@@ -254,8 +255,10 @@ class EngineBase {
   virtual int sort(dgp_particles* parts, int* cell_start) = 0;
   virtual int brane(int nbins, double* k, double* pc, double* pC, double* dgc, int64_t* nmodes) = 0;
   virtual int adjoint(const void* phibar, const void* const* gbar, void* deltabar, double tol,
-                      dgp_solve_info* info) = 0;
-  virtual int step_adjoint(const dgp_particles* start, double a, double da, dgp_particles* cot) = 0;
+                      dgp_solve_info* info, double* rcbar) = 0;
+  virtual int step_adjoint(const dgp_particles* start, double a, double da, dgp_particles* cot,
+                           double* rcbar) = 0;
+  virtual int zeldovich_vf_adjoint(const void* dl, const dgp_particles* cot, double* vfbar) = 0;
   virtual int zeldovich(const void* dl, double vf, dgp_particles* out) = 0;
   virtual int zeldovich_adjoint(const dgp_particles* cot, double vf, void* dlbar) = 0;
   virtual int pk_adjoint(const dgp_particles* pp, int nbins, const double* dldp, dgp_particles* cot) = 0;
@@ -355,7 +358,9 @@ class Engine : public EngineBase {
   T* aP = nullptr;              // [7][M]: H_f(D) lam for six pairs, then lam
   T* aF = nullptr;              // [4][M]: u, Q, Dbar, A phibar
   V* aS = nullptr;              // [7][SPEC]
-  double* d_adj = nullptr;      // [8]: sum u, sum r, sum 1/diag, nonpositive diag, sum |res|, sum |g|
+  double* d_adj = nullptr;      // [12]: sum u, sum r, sum 1/diag, nonpositive diag, sum |res|, sum |g|,
+                                // then the r_c terms: phibar and lam contractions, F . fbar, a dot product
+  bool delta_nl = false;        // sDelta holds the spectrum of the last nonlinear solve's delta
   T* ap[6] = {};                // step adjoint: the recomputed particle state
   int64_t ap_n = 0;
   T* aFb = nullptr;             // [3][M] force-cotangent grids
@@ -565,6 +570,7 @@ class Engine : public EngineBase {
       pro.kind = 1;
     }
     if ((rc = forward_zy(src, sDelta, pro))) return rc;
+    delta_nl = grav == DGP_GRAVITY_NL;
     dgp_solve_info inf;
     memset(&inf, 0, sizeof(inf));
     V* sDphi = sD;  // spectrum of the accepted D for the phi operation
@@ -1020,18 +1026,17 @@ class Engine : public EngineBase {
 
   // Adjoint of the last accepted nonlinear solve (see dgp_solve_adjoint).
   int adjoint(const void* phibar, const void* const* gbar, void* deltabar, double tol,
-              dgp_solve_info* info) override {
+              dgp_solve_info* info, double* rcbar) override {
     if (!deltabar || !(tol >= 0) || (!phibar && !gbar[0] && !gbar[1] && !gbar[2])) return DGP_E_INVALID;
     if ((gbar[0] != nullptr) != (gbar[1] != nullptr) || (gbar[0] != nullptr) != (gbar[2] != nullptr))
       return DGP_E_INVALID;
     if (p.gravity != DGP_GRAVITY_NL) return DGP_E_INVALID;
     if (wcur < 0 || !(last_nl_a > 0.0)) return DGP_E_STATE;
-    if (!aP) {
-      if (cudaMalloc(&aP, sizeof(T) * 7 * M) != cudaSuccess) return DGP_E_NOMEM;
-      if (cudaMalloc(&aF, sizeof(T) * 4 * M) != cudaSuccess) return DGP_E_NOMEM;
-      if (cudaMalloc(&aS, sizeof(V) * 7 * SPEC) != cudaSuccess) return DGP_E_NOMEM;
-      if (cudaMalloc(&d_adj, sizeof(double) * 8) != cudaSuccess) return DGP_E_NOMEM;
-    }
+    if (rcbar && !delta_nl) return DGP_E_STATE;  // the r_c terms need that solve's delta
+    if (!aP && cudaMalloc(&aP, sizeof(T) * 7 * M) != cudaSuccess) { aP = nullptr; return DGP_E_NOMEM; }
+    if (!aF && cudaMalloc(&aF, sizeof(T) * 4 * M) != cudaSuccess) { aF = nullptr; return DGP_E_NOMEM; }
+    if (!aS && cudaMalloc(&aS, sizeof(V) * 7 * SPEC) != cudaSuccess) { aS = nullptr; return DGP_E_NOMEM; }
+    if (!adj_scalars()) return DGP_E_NOMEM;
     int rc;
     T* const lam = aP + 6 * M;
     T* const aU = aF;
@@ -1060,6 +1065,19 @@ class Engine : public EngineBase {
     if ((rc = inverse_yz(s6, ga, 2))) return rc;
     // real Hessian fields of the accepted D: H_xx, H_yy, H_xy, H_xz, H_yz (and N)
     if ((rc = forward_zy(rD[wcur], sD2, none))) return rc;
+    RcDeriv rd{};
+    if (rcbar) {
+      const Coef dc = coefficients_drc(last_nl_a, cosmo.omega_m0, p.rc_H0);
+      rd = RcDeriv{dc.E / c.E, dc.eta, dc.alpha, dc.beta, dc.s, dc.c2, dc.c3};
+      FieldSet<T> rin = in;
+      rin.p[4] = sDelta;
+      rin.p[5] = sD2;
+      prof.run(KK_X_OTHER, SB * (__builtin_popcount(mask) + 2), stream,
+               [&] { launch_fft_x_rc<T, N>(rin, mask | 0x30, kp, rd, pk_partials, tw, stream); });
+      prof.run(KK_REDUCE, 8.0 * pk_blocks, stream,
+               [&] { launch_finalize(pk_partials, pk_blocks, 1, d_adj + 6, stream); });
+      DGP_CHECK_LAUNCH();
+    }
     prof.run(KK_X_HESSIAN, 7 * SB, stream, [&] {
       launch_fft_x_op<T, N>(XOP_HESSIAN, sD2, nullptr, fs(s6, 6), 0, kp, nullptr, 0, 0, 0, tw, stream);
     });
@@ -1123,6 +1141,22 @@ class Engine : public EngineBase {
     }
     // deltabar = A phibar_tot + S lam
     if ((rc = forward_zy(lam, s6[0], none))) return rc;
+    if (rcbar) {
+      FieldSet<T> rin;
+      for (int i = 0; i < kMaxFields; ++i) rin.p[i] = nullptr;
+      rin.p[4] = sDelta;
+      rin.p[5] = sD2;
+      rin.p[6] = s6[0];
+      prof.run(KK_X_OTHER, SB * 3, stream,
+               [&] { launch_fft_x_rc<T, N>(rin, 0x70, kp, rd, pk_partials, tw, stream); });
+      prof.run(KK_REDUCE, 8.0 * pk_blocks, stream,
+               [&] { launch_finalize(pk_partials, pk_blocks, 1, d_adj + 7, stream); });
+      DGP_CHECK_LAUNCH();
+      double h2[2];
+      DGP_CUDA(cudaMemcpyAsync(h2, d_adj + 6, sizeof(double) * 2, cudaMemcpyDeviceToHost, stream));
+      DGP_CUDA(wait_stream());
+      *rcbar = (h2[0] + h2[1]) / (double)M;  // Parseval: sum_x u v = sum_k conj(U) V / N^3
+    }
     prof.run(KK_X_OTHER, 2 * SB, stream, [&] {
       launch_fft_x_op<T, N>(XOP_SOURCE, s6[0], nullptr, fs(s6 + 1, 1), 0, kp, nullptr, 0, 0, 0, tw, stream);
     });
@@ -1141,10 +1175,31 @@ class Engine : public EngineBase {
     return inf.status;
   }
 
+  bool adj_scalars() {
+    if (!d_adj && cudaMalloc(&d_adj, sizeof(double) * 12) != cudaSuccess) {
+      d_adj = nullptr;
+      return false;
+    }
+    return true;
+  }
+
+  // Host value of the device sum of nb per-block partials.
+  int sum_partials(int nb, double* out) {
+    if (!adj_scalars()) return DGP_E_NOMEM;
+    prof.run(KK_REDUCE, 8.0 * nb, stream, [&] { launch_finalize(partials, nb, 1, d_adj + 8, stream); });
+    DGP_CHECK_LAUNCH();
+    DGP_CUDA(cudaMemcpyAsync(out, d_adj + 8, sizeof(double), cudaMemcpyDeviceToHost, stream));
+    DGP_CUDA(wait_stream());
+    return DGP_OK;
+  }
+
   // VJP of the particle forces at the positions xs.p[0..2] for the cotangent
   // scale * xs.p[3..5]; accumulates into xb.p[0..2].  Solves at a first, so the
-  // context's accepted D is the one the adjoint needs.
-  int force_vjp(const ParticleSet<T>& xs, int64_t np, double scale, double a, const ParticleSet<T>& xb) {
+  // context's accepted D is the one the adjoint needs.  With rc_solve and fdot
+  // set: the solve's explicit derivative in r_c H0 for that cotangent, and
+  // sum_p F(x_p) . xs.p[3..5][p] (unscaled).
+  int force_vjp(const ParticleSet<T>& xs, int64_t np, double scale, double a, const ParticleSet<T>& xb,
+                double* rc_solve = nullptr, double* fdot = nullptr) {
     int rc;
     dgp_particles dp{xs.p[0], xs.p[1], xs.p[2], xs.p[0], xs.p[1], xs.p[2], np};
     if ((rc = forces_at(&dp, a, nullptr))) return rc;
@@ -1155,17 +1210,25 @@ class Engine : public EngineBase {
              [&] { launch_deposit_vec<T>(xs, scale, np, fb, cp, stream); });
     DGP_CHECK_LAUNCH();
     const void* gb[3] = {fb[0], fb[1], fb[2]};
-    rc = adjoint(nullptr, gb, rRho, p.tol, nullptr);
+    rc = adjoint(nullptr, gb, rRho, p.tol, nullptr, rc_solve);
     if (rc != DGP_OK && rc != DGP_E_NOT_CONVERGED) return rc;
+    if (!fdot) {
+      prof.run(KK_GATHER, 9.0 * sizeof(T) * np + 4 * RB, stream, [&] {
+        launch_force_vjp_gather<T>(xs, scale, np, rG, rRho, (double)M / (double)np, xb, cp, stream);
+      });
+      DGP_CHECK_LAUNCH();
+      return DGP_OK;
+    }
+    int nb = 0;
     prof.run(KK_GATHER, 9.0 * sizeof(T) * np + 4 * RB, stream, [&] {
-      launch_force_vjp_gather<T>(xs, scale, np, rG, rRho, (double)M / (double)np, xb, cp, stream);
+      nb = launch_force_vjp_gather_dot<T>(xs, scale, np, rG, rRho, (double)M / (double)np, xb, cp, partials, stream);
     });
     DGP_CHECK_LAUNCH();
-    return DGP_OK;
+    return sum_partials(nb, fdot);
   }
 
   // Transpose of one kick-drift-kick step (see pm_step_adjoint).
-  int step_adjoint(const dgp_particles* st, double a, double da, dgp_particles* cot) override {
+  int step_adjoint(const dgp_particles* st, double a, double da, dgp_particles* cot, double* rcbar) override {
     if (!valid_parts(st) || !valid_parts(cot) || st->n == 0 || cot->n != st->n) return DGP_E_INVALID;
     if (!(a > 0.0) || !(da > 0.0) || !isfinite(a + da)) return DGP_E_INVALID;
     if (p.gravity != DGP_GRAVITY_NL) return DGP_E_INVALID;
@@ -1200,16 +1263,53 @@ class Engine : public EngineBase {
     T* const cv[6] = {(T*)cot->x, (T*)cot->y, (T*)cot->z, (T*)cot->px, (T*)cot->py, (T*)cot->pz};
     const ParticleSet<T> xb{{cv[0], cv[1], cv[2], cv[0], cv[1], cv[2]}};
     const ParticleSet<T> pb{{cv[3], cv[4], cv[5], cv[3], cv[4], cv[5]}};
+    // r_c H0: K2' <pbar1, F(x1)> + solve(x1) + Dr' <xbar1_tot, p_h> + K1' <pbar_h, F(x0)> + solve(x0)
+    double rs1 = 0.0, pf1 = 0.0, dx = 0.0, rs0 = 0.0, pf0 = 0.0;
+    const bool want = rcbar != nullptr;
     // x1: fbar = k2 pbar1
-    if ((rc = force_vjp(ParticleSet<T>{{ap[0], ap[1], ap[2], cv[3], cv[4], cv[5]}}, np, k2, a1, xb))) return rc;
+    if ((rc = force_vjp(ParticleSet<T>{{ap[0], ap[1], ap[2], cv[3], cv[4], cv[5]}}, np, k2, a1, xb,
+                        want ? &rs1 : nullptr, want ? &pf1 : nullptr)))
+      return rc;
+    if (want) {
+      T* xa[3] = {cv[0], cv[1], cv[2]};
+      T* ph[3] = {ap[3], ap[4], ap[5]};
+      int nb = 0;
+      prof.run(KK_MISC, 6.0 * sizeof(T) * np, stream, [&] { nb = launch_dot3<T>(xa, ph, np, partials, stream); });
+      DGP_CHECK_LAUNCH();
+      if ((rc = sum_partials(nb, &dx))) return rc;
+    }
     // pbar_h = pbar1 + Dr xbar
     prof.run(KK_MISC, 9.0 * sizeof(T) * np, stream, [&] { launch_particle_axpy<T>(xb, dr, np, pb, stream); });
     DGP_CHECK_LAUNCH();
     // x0: fbar = k1 pbar_h
     const ParticleSet<T> at0{{(T*)st->x, (T*)st->y, (T*)st->z, cv[3], cv[4], cv[5]}};
-    if ((rc = force_vjp(at0, np, k1, a, xb))) return rc;
+    if ((rc = force_vjp(at0, np, k1, a, xb, want ? &rs0 : nullptr, want ? &pf0 : nullptr))) return rc;
     force_valid = false;
+    if (want) {
+      const double dk1 = time_integral_drc(a, ah, om, rc_, 0), dk2 = time_integral_drc(ah, a1, om, rc_, 0);
+      const double ddr = time_integral_drc(a, a1, om, rc_, 2);
+      *rcbar = dk2 * pf1 + rs1 + ddr * dx + dk1 * pf0 + rs0;
+    }
     return DGP_OK;
+  }
+
+  // Cotangent of vel_factor in dgp_zeldovich: sum_j <pbar_j, Psi_j(delta_L)>.
+  int zeldovich_vf_adjoint(const void* dl, const dgp_particles* cot, double* vfbar) override {
+    if (!dl || !vfbar || !valid_parts(cot) || cot->n != M) return DGP_E_INVALID;
+    int rc;
+    if ((rc = forward_zy((const T*)dl, s6[0], ZPrologue{nullptr, 0.0, 0}))) return rc;
+    const Coef c = coefficients(1.0, cosmo.omega_m0, p.rc_H0);
+    const KParams kp = kparams(c, p.gravity);
+    prof.run(KK_X_OTHER, 4 * SB, stream, [&] {
+      launch_fft_x_op<T, N>(XOP_ZEL, s6[0], nullptr, fs(s6 + 1, 3), 0, kp, nullptr, 0, 0, 0, tw, stream);
+    });
+    if ((rc = inverse_yz(s6 + 1, rG, 3))) return rc;
+    T* pbar[3] = {(T*)cot->px, (T*)cot->py, (T*)cot->pz};
+    int nb = 0;
+    prof.run(KK_MISC, 6.0 * RB, stream, [&] { nb = launch_dot3<T>(rG, pbar, M, partials, stream); });
+    DGP_CHECK_LAUNCH();
+    force_valid = false;
+    return sum_partials(nb, vfbar);
   }
 
   // Zel'dovich particles from a linear field (lattice order) and the map's transpose.
@@ -1507,14 +1607,38 @@ int dgp_power_spectrum_adjoint(dgp_ctx* c, const dgp_particles* parts, int nbins
 
 int pm_step_adjoint(dgp_ctx* c, const dgp_particles* start, double a, double da, dgp_particles* cot) {
   if (!c) return DGP_E_INVALID;
-  return c->eng->step_adjoint(start, a, da, cot);
+  return c->eng->step_adjoint(start, a, da, cot, nullptr);
+}
+
+int pm_step_adjoint_rc(dgp_ctx* c, const dgp_particles* start, double a, double da, dgp_particles* cot,
+                       double* rc_bar) {
+  if (!c || !rc_bar) return DGP_E_INVALID;
+  return c->eng->step_adjoint(start, a, da, cot, rc_bar);
+}
+
+int dgp_zeldovich_vf_adjoint(dgp_ctx* c, const void* delta_l, const dgp_particles* cot, double* vf_bar) {
+  if (!c) return DGP_E_INVALID;
+  return c->eng->zeldovich_vf_adjoint(delta_l, cot, vf_bar);
+}
+
+int dgp_velocity_factor(const dgp_cosmology* cosmo, double rc_H0, double a, double* vf, double* dvf_drc) {
+  if (!cosmo || !vf || !dvf_drc || !(a > 0) || !(rc_H0 > 0) || !(cosmo->omega_m0 >= 0)) return DGP_E_INVALID;
+  dgp::velocity_factor(a, cosmo->omega_m0, rc_H0, vf, dvf_drc);
+  return DGP_OK;
 }
 
 int dgp_solve_adjoint(dgp_ctx* c, const void* phibar, const void* gbar_x, const void* gbar_y, const void* gbar_z,
                       void* deltabar, double tol, dgp_solve_info* info) {
   if (!c) return DGP_E_INVALID;
   const void* g[3] = {gbar_x, gbar_y, gbar_z};
-  return c->eng->adjoint(phibar, g, deltabar, tol, info);
+  return c->eng->adjoint(phibar, g, deltabar, tol, info, nullptr);
+}
+
+int dgp_solve_adjoint_rc(dgp_ctx* c, const void* phibar, const void* gbar_x, const void* gbar_y,
+                         const void* gbar_z, void* deltabar, double tol, double* rc_bar, dgp_solve_info* info) {
+  if (!c || !rc_bar) return DGP_E_INVALID;
+  const void* g[3] = {gbar_x, gbar_y, gbar_z};
+  return c->eng->adjoint(phibar, g, deltabar, tol, info, rc_bar);
 }
 
 int dgp_tile_config(dgp_ctx* c, int* y_threads) {

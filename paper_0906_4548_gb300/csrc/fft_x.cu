@@ -19,11 +19,14 @@
 //             g_i(k) = -i k_i phi(k), Nyquist component of axis i set to 0.
 //  PK         |delta_k|^2 binned in shells (Sec. IV), per-block FP64 partials.
 //  SHELL      delta_k and 1 restricted to a |k| shell (bispectrum, Sec. VI).
+//  RC         derivative-in-r_c contractions of the solve's adjoint (adjoint_rc.cuh).
 // Every output carries the 1 / N^3 of the three inverse transforms.
 #include <math.h>
 
+#include "adjoint_rc.cuh"
 #include "fft_core.cuh"
 #include "kernels.cuh"
+#include "reduce.cuh"
 
 namespace dgp {
 
@@ -48,6 +51,7 @@ template <typename T> struct XArgs {
   const int* skip;
   FieldSet<T> in;  // adjoint ops: input spectra
   int in_mask;
+  RcDeriv rc;      // XOP_RC: derivatives of the coefficients in r_c H0
 };
 
 template <typename T, int N>
@@ -142,7 +146,7 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
   __syncthreads();
 
   V X0[N2], X1[N2];
-  constexpr bool ADJ = OP == XOP_ADJ_PHI || OP == XOP_ADJ_COMBINE || OP == XOP_ZEL_ADJ;
+  constexpr bool ADJ = OP == XOP_ADJ_PHI || OP == XOP_ADJ_COMBINE || OP == XOP_ZEL_ADJ || OP == XOP_RC;
   if (!ADJ) x_forward<T, N>(args.in0, kz, ky0, lane, yl, s_T, s_tw, X0);
   if (OP == XOP_PHI_FORCE && kp.gravity == 0) x_forward<T, N>(args.in1, kz, ky0, lane, yl, s_T, s_tw, X1);
 
@@ -185,6 +189,75 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
     // the Hessian outputs use 1 / (|n|^2 N^3) directly
     s_inv[k2 * NT + threadIdx.x] = OP == XOP_HESSIAN ? inv * inv_m : inv;
     s_ikb[k2 * NT + threadIdx.x] = ikb;
+  }
+
+  if constexpr (OP == XOP_RC) {
+    // acc: phibar_tot (phase of phibar) or lam (phase of lam); then delta and D in turn
+    V acc[N2];
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) acc[k2] = cmake<V>((T)0, (T)0);
+    const bool lam_phase = (args.in_mask >> 6) & 1;
+    if (lam_phase) {
+      x_forward<T, N>(args.in.p[6], kz, ky0, lane, yl, s_T, s_tw, acc);
+    } else {
+#pragma unroll 1
+      for (int f = 0; f < 4; ++f) {
+        if (!((args.in_mask >> f) & 1)) continue;  // uniform over the block
+        x_forward<T, N>(args.in.p[f], kz, ky0, lane, yl, s_T, s_tw, X0);
+        const int nfix = f == 2 ? ny : nz;
+        const bool nyq_fix = f == 2 ? nyq_y : nyq_z;
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+          if (f == 0) {
+            acc[k2] = cadd(acc[k2], X0[k2]);
+          } else {
+            const int kx = lane + N1 * k2;
+            const bool nyq = f == 1 ? kx == N / 2 : nyq_fix;
+            const T ki = kf * (T)(f == 1 ? signed_index(kx, N) : nfix);
+            if (!nyq) acc[k2] = cadd(acc[k2], cmake<V>(-ki * X0[k2].y, ki * X0[k2].x));  // i k_i X
+          }
+        }
+      }
+    }
+    const RcDeriv& d = args.rc;
+    const double eta = kp.eta, kfd = 2.0 * M_PI / kp.box;
+    const double om = (eta - 1.0) / eta, dom = d.deta / (eta * eta);
+    double t = 0.0;
+#pragma unroll 1
+    for (int f = 4; f < 6; ++f) {  // delta, then D
+      x_forward<T, N>(args.in.p[f], kz, ky0, lane, yl, s_T, s_tw, X0);
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        const int nx = signed_index(lane + N1 * k2, N);
+        const int n2 = nx * nx + ny * ny + nz * nz;
+        if (n2 == 0) continue;
+        const double kmag = kfd * sqrt((double)n2);
+        const double ikb = kp.local_only ? 0.0 : 1.0 / (kp.kbar_fac * kmag);
+        const double dikb = ikb * d.dE_over_E;  // 1/kbar = a E / (C_H |k|)
+        double m;
+        if (!lam_phase) {
+          const double pref = -kp.aE * kp.aE / (kmag * kmag), dpref = 2.0 * pref * d.dE_over_E;
+          const double den = 1.0 + ikb / eta, dden = dikb / eta - ikb * d.deta / (eta * eta);
+          if (f == 4) {  // A' = d/drc [1.5 pref om / den]
+            m = 1.5 * (dpref * om / den + pref * dom / den - pref * om * dden / (den * den));
+          } else {       // B' = d/drc [pref (-1/(2 eta) + c3 / kbar) / den]
+            const double b = -0.5 / eta + kp.c3 * ikb;
+            const double db = d.deta / (2.0 * eta * eta) + d.dc3 * ikb + kp.c3 * dikb;
+            m = dpref * b / den + pref * db / den - pref * b * dden / (den * den);
+          }
+        } else if (f == 4) {  // S' = d/drc [s (1 - beta / kbar)]
+          m = d.ds * (1.0 - kp.beta * ikb) - kp.s * (d.dbeta * ikb + kp.beta * dikb);
+        } else {              // -(alpha' + c2' N + c2 N'), N = -1/kbar
+          m = -d.dalpha + d.dc2 * ikb + kp.c2 * dikb;
+        }
+        t += m * ((double)acc[k2].x * (double)X0[k2].x + (double)acc[k2].y * (double)X0[k2].y);
+      }
+    }
+    if (kz != 0 && kz != N / 2) t *= 2.0;
+    double v[1] = {t};
+    block_sum<1>(v);
+    if (threadIdx.x == 0) args.pk_partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = v[0];
+    return;
   }
 
   if (OP == XOP_ADJ_PHI || OP == XOP_ZEL_ADJ) {
@@ -439,7 +512,7 @@ template <typename T, int N>
 void launch_fft_x_op(int op, const vec2_t<T>* in0, const vec2_t<T>* in1, const FieldSet<T>& out, int nout_mask,
                      const KParams& kp, double* pk_partials, int nbins, double shell_lo, double shell_hi,
                      const vec2_t<T>* tw, cudaStream_t s, const int* skip) {
-  XArgs<T> a;
+  XArgs<T> a{};
   a.skip = skip;
   a.in0 = in0; a.in1 = in1; a.out = out; a.nout_mask = nout_mask; a.kp = kp;
   a.pk_partials = pk_partials; a.nbins = nbins; a.shell_lo = shell_lo; a.shell_hi = shell_hi;
@@ -462,7 +535,7 @@ void launch_fft_x_op(int op, const vec2_t<T>* in0, const vec2_t<T>* in1, const F
 template <typename T, int N>
 void launch_fft_x_adj(int op, const FieldSet<T>& in, int in_mask, const FieldSet<T>& out, const KParams& kp,
                       const vec2_t<T>* tw, cudaStream_t s) {
-  XArgs<T> a;
+  XArgs<T> a{};
   a.skip = nullptr;
   a.in0 = nullptr; a.in1 = nullptr; a.out = out; a.nout_mask = 0; a.kp = kp;
   a.pk_partials = nullptr; a.nbins = 0; a.shell_lo = 0; a.shell_hi = 0;
@@ -472,12 +545,26 @@ void launch_fft_x_adj(int op, const FieldSet<T>& in, int in_mask, const FieldSet
   else if (op == XOP_ZEL_ADJ) launch_x<T, N, XOP_ZEL_ADJ>(a, tw, s);
 }
 
+template <typename T, int N>
+void launch_fft_x_rc(const FieldSet<T>& in, int in_mask, const KParams& kp, const RcDeriv& d, double* partials,
+                     const vec2_t<T>* tw, cudaStream_t s) {
+  XArgs<T> a{};
+  a.skip = nullptr;
+  a.in0 = nullptr; a.in1 = nullptr; a.nout_mask = 0; a.kp = kp;
+  for (int i = 0; i < kMaxFields; ++i) a.out.p[i] = nullptr;
+  a.pk_partials = partials; a.nbins = 0; a.shell_lo = 0; a.shell_hi = 0;
+  a.in = in; a.in_mask = in_mask; a.rc = d;
+  launch_x<T, N, XOP_RC>(a, tw, s);
+}
+
 #define DGP_INST_X(T, N)                                                                            \
   template void launch_fft_x_op<T, N>(int, const vec2_t<T>*, const vec2_t<T>*, const FieldSet<T>&, int, \
                                       const KParams&, double*, int, double, double, const vec2_t<T>*,   \
                                       cudaStream_t, const int*);                                        \
   template void launch_fft_x_adj<T, N>(int, const FieldSet<T>&, int, const FieldSet<T>&, const KParams&,  \
-                                       const vec2_t<T>*, cudaStream_t);
+                                       const vec2_t<T>*, cudaStream_t);                                  \
+  template void launch_fft_x_rc<T, N>(const FieldSet<T>&, int, const KParams&, const RcDeriv&, double*,   \
+                                      const vec2_t<T>*, cudaStream_t);
 #define DGP_INST_X_ALL(T) DGP_INST_X(T, 16) DGP_INST_X(T, 32) DGP_INST_X(T, 64) DGP_INST_X(T, 128) \
   DGP_INST_X(T, 256) DGP_INST_X(T, 512) DGP_INST_X(T, 48) DGP_INST_X(T, 96)
 DGP_INST_X_ALL(float)

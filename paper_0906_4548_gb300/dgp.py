@@ -25,7 +25,8 @@ EXPORTED = ["dgp_background", "dgp_init", "dgp_destroy", "dgp_strerror", "dgp_re
             "dgp_sort_particles", "dgp_profile_kinds", "dgp_brane_spectra", "dgp_set_blocking_sync",
             "dgp_batch_create", "dgp_batch_context", "dgp_batch_step", "dgp_batch_destroy",
             "dgp_solve_adjoint", "pm_step_adjoint", "dgp_zeldovich", "dgp_zeldovich_adjoint",
-            "dgp_power_spectrum_adjoint", "dgp_tile_config", "dgp_set_tile_config"]
+            "dgp_power_spectrum_adjoint", "dgp_tile_config", "dgp_set_tile_config",
+            "dgp_solve_adjoint_rc", "pm_step_adjoint_rc", "dgp_zeldovich_vf_adjoint", "dgp_velocity_factor"]
 DGP_NOALLOC_MAX_N = 64
 DGP_KERNEL_KINDS = 11
 
@@ -100,6 +101,10 @@ def _load():
         "dgp_set_tile_config": (i, [vp, i]),
         "dgp_solve_adjoint": (i, [vp, vp, vp, vp, vp, vp, d, P(SolveInfo)]),
         "pm_step_adjoint": (i, [vp, P(Particles), d, d, P(Particles)]),
+        "dgp_solve_adjoint_rc": (i, [vp, vp, vp, vp, vp, vp, d, P(d), P(SolveInfo)]),
+        "pm_step_adjoint_rc": (i, [vp, P(Particles), d, d, P(Particles), P(d)]),
+        "dgp_zeldovich_vf_adjoint": (i, [vp, vp, P(Particles), P(d)]),
+        "dgp_velocity_factor": (i, [P(Cosmology), d, d, P(d), P(d)]),
         "dgp_zeldovich": (i, [vp, vp, d, P(Particles)]),
         "dgp_zeldovich_adjoint": (i, [vp, P(Particles), d, vp]),
         "dgp_power_spectrum_adjoint": (i, [vp, P(Particles), i, P(d), P(Particles)]),
@@ -244,9 +249,44 @@ def dgp_solve_adjoint(ctx, phibar, deltabar, tol, gbar=None):
     return st, info.as_dict()
 
 
+def dgp_solve_adjoint_rc(ctx, phibar, deltabar, tol, gbar=None):
+    """dgp_solve_adjoint plus the solve's explicit derivative in r_c H0: (status, info, rc_bar)."""
+    info = SolveInfo()
+    rc = ctypes.c_double()
+    g = gbar if gbar is not None else (None, None, None)
+    st = _check(lib.dgp_solve_adjoint_rc(ctx, _ptr(phibar), _ptr(g[0]), _ptr(g[1]), _ptr(g[2]), _ptr(deltabar),
+                                         tol, ctypes.byref(rc), ctypes.byref(info)),
+                "dgp_solve_adjoint_rc", (DGP_OK, DGP_E_NOT_CONVERGED))
+    return st, info.as_dict(), rc.value
+
+
 def pm_step_adjoint(ctx, start, a, da, cot):
     """cot (Particles of cotangents (xbar1, pbar1)) <- (xbar0, pbar0) for the step from `start` at a."""
     _check(lib.pm_step_adjoint(ctx, ctypes.byref(start), a, da, ctypes.byref(cot)), "pm_step_adjoint")
+
+
+def pm_step_adjoint_rc(ctx, start, a, da, cot):
+    """pm_step_adjoint; returns the step's explicit derivative in r_c H0."""
+    rc = ctypes.c_double()
+    _check(lib.pm_step_adjoint_rc(ctx, ctypes.byref(start), a, da, ctypes.byref(cot), ctypes.byref(rc)),
+           "pm_step_adjoint_rc")
+    return rc.value
+
+
+def dgp_zeldovich_vf_adjoint(ctx, delta_l, cot):
+    """sum_j <pbar_j, Psi_j(delta_L)>: the cotangent of vel_factor in dgp_zeldovich."""
+    v = ctypes.c_double()
+    _check(lib.dgp_zeldovich_vf_adjoint(ctx, _ptr(delta_l), ctypes.byref(cot), ctypes.byref(v)),
+           "dgp_zeldovich_vf_adjoint")
+    return v.value
+
+
+def dgp_velocity_factor(omega_m0, rc_H0, a, c_over_H0=C_OVER_H0):
+    """(vf, d vf / d(r_c H0)) for the Zel'dovich velocity factor vf = a^2 E f (host)."""
+    vf, dvf = ctypes.c_double(), ctypes.c_double()
+    _check(lib.dgp_velocity_factor(ctypes.byref(Cosmology(omega_m0, c_over_H0)), rc_H0, a, ctypes.byref(vf),
+                                   ctypes.byref(dvf)), "dgp_velocity_factor")
+    return vf.value, dvf.value
 
 
 def dgp_zeldovich(ctx, delta_l, vel_factor, out):

@@ -324,8 +324,9 @@ WA = dict(n=128, box=200.0, n_s=-1.5, rms=0.5, seed=3, target_seed=4, a_start=0.
 def run_adjoint(args):
     """128^3 mesh and particles, FP32, 100 steps from a = 0.02 to 1 with a checkpoint every 10 steps:
     L = sum_k [P(k) - P_target(k)]^2 (target from a second seed), its gradient with respect to the
-    128^3 linear field (initial Fourier modes) by the adjoint kernels, timed, and checked against
-    central differences of the loss along --fd-modes random single Fourier modes."""
+    128^3 linear field (initial Fourier modes) and to r_c H0 by the adjoint kernels, timed, and
+    checked against central differences of the loss along --fd-modes random single Fourier modes
+    and in r_c H0 (fresh contexts at r_c H0 +- h)."""
     import numpy as np
     import torch
     import __graft_entry__ as g
@@ -333,8 +334,7 @@ def run_adjoint(args):
     from paper_0906_4548_gb300 import autodiff, dgp, inputs
     n, box = WA["n"], WA["box"]
     dev = torch.device("cuda", 0)
-    bgi = dgp.dgp_background(WA["omega_m0"], WA["rc_H0"], WA["a_start"])
-    vf = WA["a_start"] ** 2 * bgi["E"] * bgi["growth_f"]
+    vf = dgp.dgp_velocity_factor(WA["omega_m0"], WA["rc_H0"], WA["a_start"])[0]
     dl = torch.tensor(inputs.linear_field(n, box, WA["n_s"], WA["rms"], WA["seed"])[0], dtype=torch.float32,
                       device=dev)
     dl_t = torch.tensor(inputs.linear_field(n, box, WA["n_s"], WA["rms"], WA["target_seed"])[0],
@@ -360,12 +360,16 @@ def run_adjoint(args):
         target = final_pk(dl_t)
         w = np.ones(nb)
 
-        def loss(field, grad):
+        def loss(field, grad, c=None, rc=WA["rc_H0"]):
+            c = ctx if c is None else c
             d = field.clone().requires_grad_(grad)
-            x, p = autodiff.ZeldovichIC.apply(d, ctx, vf)
-            dgp.dgp_reset(ctx)
-            x, p = autodiff.PMRun.apply(x, p, ctx, sched, WA["every"])
-            return autodiff.PkLoss.apply(x, ctx, n, target, w), d
+            rt = torch.tensor(rc, dtype=torch.float64, requires_grad=grad)
+            vfr = autodiff.VelocityFactor.apply(rt, WA["omega_m0"], WA["a_start"])
+            x, p = autodiff.ZeldovichIC.apply(d, c, vfr)
+            dgp.dgp_reset(c)
+            x, p = autodiff.PMRun.apply(x, p, c, sched, WA["every"], rt)
+            loss.rt = rt
+            return autodiff.PkLoss.apply(x, c, n, target, w), d
 
         for _ in range(max(1, min(args.warmup, 1))):   # one untimed forward + backward
             L, d = loss(dl, True)
@@ -383,6 +387,8 @@ def run_adjoint(args):
         ms_fwd, ms_bwd = e0.elapsed_time(e1), e1.elapsed_time(e2)
         loss_value = float(L.detach())
         grad = d.grad.detach().double().cpu().numpy()
+        rc_grad = float(loss.rt.grad)
+        prec_fd = dgp.DGP_FP32
         if fd64:
             # the accuracy check in FP64 (tolerance 1e-10): FP32 rounding and a 1e-6 solver
             # tolerance, amplified over 100 steps, swamp small central differences
@@ -394,6 +400,8 @@ def run_adjoint(args):
             L64, d64 = loss(dl, True)
             L64.backward()
             grad = d64.grad.detach().cpu().numpy()
+            rc_grad = float(loss.rt.grad)
+            prec_fd = dgp.DGP_FP64
         # central differences along random single modes of the linear field
         rng = np.random.default_rng(0)
         xg = np.arange(n) * box / n
@@ -410,6 +418,17 @@ def run_adjoint(args):
             a_ = float(np.sum(grad * u))
             fd.append({"mode": [int(v) for v in k], "central_difference": f, "adjoint": a_,
                        "rel_diff": abs(f - a_) / max(abs(f), 1e-300)})
+        # central difference in r_c H0 (r_c is a constant of a context: one context per value)
+        h = (1e-4 if fd64 else 1e-3) * WA["rc_H0"]
+        lrc = []
+        for r in (WA["rc_H0"] + h, WA["rc_H0"] - h):
+            c2 = dgp.dgp_init(box, n, r, WA["omega_m0"], precision=prec_fd, tol=1e-10 if fd64 else WA["tol"],
+                              max_iter=300 if fd64 else WA["max_iter"], sort_every=0)
+            try:
+                lrc.append(float(loss(dl, False, c2, r)[0]))
+            finally:
+                dgp.dgp_destroy(c2)
+        fd_rc = (lrc[0] - lrc[1]) / (2 * h)
     finally:
         dgp.dgp_destroy(ctx)
     rel = [x["rel_diff"] for x in fd]
@@ -419,11 +438,12 @@ def run_adjoint(args):
             "ms_per_step": (ms_fwd + ms_bwd) / nsteps, "final_a": sched[-1], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "dgp_pm_adjoint_128cube_box200_ns-1.5_a0.02-1_100steps_every10_tol1e-6",
-                       "gradient_wrt": "the 128^3 linear field delta_L (initial Fourier modes)",
-                       "rc_gradient": None, "rc_gradient_note": "not formed: r_c is a constant of the context",
+                       "gradient_wrt": "the 128^3 linear field delta_L (initial Fourier modes) and r_c H0",
                        "l2": "particles (25 MB per array) and fields (8 MB each) partly fit L2; no flush"},
             "forward_ms": ms_fwd, "backward_ms": ms_bwd, "backward_over_forward": ms_bwd / ms_fwd,
             "loss": loss_value, "clocks": clk.summary(),
+            "rc_gradient": {"adjoint": rc_grad, "central_difference": fd_rc, "h": h,
+                            "rel_diff": abs(fd_rc - rc_grad) / max(abs(fd_rc), 1e-300)},
             "fd_check": {"modes": len(fd), "precision": "fp64, tol 1e-10" if fd64 else "fp32, tol 1e-6",
                          "max_rel_diff": max(rel) if rel else None,
                          "median_rel_diff": float(np.median(rel)) if rel else None, "cases": fd}}

@@ -15,6 +15,7 @@
 #include "adjoint_rc.cuh"
 #include "fft_core.cuh"
 #include "kernels.cuh"
+#include "relax_control.cuh"
 
 namespace dgp {
 
@@ -648,13 +649,14 @@ class Engine : public EngineBase {
           launch_fused_relax<T, N>(arith, s6, rD[ib], d_rstats + 4 * ib + 1, rS, rD[ob], spec_out(it), rp, partials,
                                    tw, stream, sk);
         });
-        prof.run(KK_REDUCE, 0, stream,
-                 [&] { launch_finalize(partials, fblocks, 4, d_rstats + 4 * ob, stream, sk); });
-        if (control)
-          prof.run(KK_REDUCE, 0, stream, [&] {
-            launch_relax_control(d_ctl, d_rstats + 4 * ob, d_misc + 1, d_hist, p.max_iter, kPatience, tol,
-                                 1.0 / (double)M, stream);
-          });
+        // the iteration's statistics, and with control the stop rules, in one launch
+        prof.run(KK_REDUCE, 0, stream, [&] {
+          if (control)
+            launch_finalize_control(partials, fblocks, d_rstats + 4 * ob, d_ctl, d_misc + 1, d_hist, p.max_iter,
+                                    kPatience, tol, 1.0 / (double)M, stream, sk);
+          else
+            launch_finalize(partials, fblocks, 4, d_rstats + 4 * ob, stream, sk);
+        });
         prof.run(KK_Y, 0, stream, [&] {
           V* o[1] = {spec_out(it)};
           launch_fft_y<T, N>(fs(o, 1), 1, false, tw, stream, sk, y_threads);

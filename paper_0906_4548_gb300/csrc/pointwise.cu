@@ -9,6 +9,7 @@
 #include "kernels.cuh"
 #include "cic.cuh"
 #include "reduce.cuh"
+#include "relax_control.cuh"
 
 namespace dgp {
 
@@ -55,64 +56,44 @@ void launch_finalize(const double* partials, int nblocks, int ncomp, double* out
   k_finalize<<<1, 256, 0, s>>>(partials, nblocks, ncomp, out, skip);
 }
 
-// One thread applies the stop rules of the relaxation to iteration it (the
-// same rules, in the same order, as a host loop would): normalised residual
-// r = <|R|> / eps (absolute when eps = 0) below tol: converged; it = max_iter,
-// a residual rise while bad points were present, or no new minimum for
-// `patience` iterations: stopped with the minimum-residual iterate; a
-// non-finite R or eps: failed.
+// The stop rules as a launch of their own (relax_control.cuh).
 __global__ void k_relax_control(SolveCtl* __restrict__ c, const double* __restrict__ stats,
                                 const double* __restrict__ abs_src_sum, double* __restrict__ hist,
                                 int max_iter, int patience, double tol, double inv_m) {
-  if (threadIdx.x != 0 || c->done) return;
-  const int it = c->next_it;
-  c->next_it = it + 1;
-  if (it == 0) {
-    const double eps = abs_src_sum[0] * inv_m;
-    c->eps = eps;
-    c->rnorm = eps > 0.0 ? eps : 1.0;
-    c->rbest = INFINITY;
-    c->rprev = INFINITY;
-    c->prev_nbad = 0.0;
-    c->best_it = -1;
-    if (!isfinite(eps)) {
-      c->status = CTL_NONFINITE;
-      c->stop_it = 0;
-      c->done = 1;
-      return;
-    }
-  }
-  const double r = stats[0] * inv_m / c->rnorm;
-  const double nbad = stats[2];
-  hist[it] = r;
-  c->last_bad = nbad;
-  c->stop_it = it;
-  if (stats[3] > 0.0 || !isfinite(r)) {
-    c->status = CTL_NONFINITE;
-    c->done = 1;
-    return;
-  }
-  if (r < c->rbest) {
-    c->rbest = r;
-    c->best_it = it;
-  }
-  if (r < tol) {
-    c->status = CTL_CONVERGED;
-    c->done = 1;
-    return;
-  }
-  if (it == max_iter || (it > 0 && c->prev_nbad > 0.0 && r > c->rprev) || it - c->best_it >= patience) {
-    c->status = CTL_STOPPED;
-    c->done = 1;
-    return;
-  }
-  c->rprev = r;
-  c->prev_nbad = nbad;
+  if (threadIdx.x != 0) return;
+  relax_control_step(c, stats, abs_src_sum, hist, max_iter, patience, tol, inv_m);
 }
 
 void launch_relax_control(SolveCtl* ctl, const double* stats, const double* abs_src_sum, double* hist,
                           int max_iter, int patience, double tol, double inv_m, cudaStream_t s) {
   k_relax_control<<<1, 32, 0, s>>>(ctl, stats, abs_src_sum, hist, max_iter, patience, tol, inv_m);
+}
+
+__global__ void __launch_bounds__(256)
+    k_finalize_control(const double* __restrict__ partials, int nblocks, double* __restrict__ stats,
+                       SolveCtl* __restrict__ c, const double* __restrict__ abs_src_sum, double* __restrict__ hist,
+                       int max_iter, int patience, double tol, double inv_m, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    const double4_32a p = reinterpret_cast<const double4_32a*>(partials)[b];
+    v[0] += p.x;
+    v[1] += p.y;
+    v[2] += p.z;
+    v[3] += p.w;
+  }
+  block_sum<4>(v);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) stats[k] = v[k];
+    relax_control_step(c, stats, abs_src_sum, hist, max_iter, patience, tol, inv_m);
+  }
+}
+
+void launch_finalize_control(const double* partials, int nblocks, double* stats, SolveCtl* ctl,
+                             const double* abs_src_sum, double* hist, int max_iter, int patience, double tol,
+                             double inv_m, cudaStream_t s, const int* skip) {
+  k_finalize_control<<<1, 256, 0, s>>>(partials, nblocks, stats, ctl, abs_src_sum, hist, max_iter, patience, tol,
+                                       inv_m, skip);
 }
 
 // Per-thread sums of FP32 data run on the FP32 pipe as an unevaluated pair:

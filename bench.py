@@ -182,7 +182,7 @@ def oracle_steps_per_s(t_sample, e_per_solve):
 
 def run_reference(args):
     """The reference arm: the FP64 oracle on the host cores (rank 0 only)."""
-    rank = int(os.environ.get("RANK", "0"))
+    rank = replica_env()[1]
     if rank != 0:
         return 0
     cores = os.cpu_count()
@@ -451,6 +451,35 @@ def run_adjoint(args):
     return 0
 
 
+# ---------------------------------------------------------------- replicas (one process per GPU)
+def replica_env():
+    """(world, rank, local_rank) from the torchrun environment; (1, 0, 0) without one."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def replica_seed(seed, rank):
+    """Each replica runs its own realisation: the base seed offset by the rank."""
+    return seed + rank
+
+
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (barrier, then a MAX all-reduce of one scalar); the replicas
+    share no data, so this is the only collective."""
+    if dist is None:
+        return ms
+    import torch
+    dist.barrier()
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, steps, ms):
+    """Steps of all replicas per second of the slowest replica's time."""
+    return world * steps / (ms / 1000.0)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -482,9 +511,7 @@ def main():
     import numpy as np
     import torch
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = replica_env()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -498,7 +525,7 @@ def main():
     n, box = WL["n"], WL["box"]
     bgi = dgp.dgp_background(WL["omega_m0"], WL["rc_H0"], WL["a_start"])
     vf = WL["a_start"] ** 2 * bgi["E"] * bgi["growth_f"]
-    pos, mom, amp = inputs.zeldovich_particles(n, box, WL["n_s"], WL["rms"], WL["seed"] + rank, vf)
+    pos, mom, amp = inputs.zeldovich_particles(n, box, WL["n_s"], WL["rms"], replica_seed(WL["seed"], rank), vf)
     dev = torch.device("cuda", local)
     ic = [torch.tensor(v.astype(np.float32), device=dev) for v in (*pos, *mom)]
     cur = [t.clone() for t in ic]
@@ -546,12 +573,8 @@ def main():
     ms = e0.elapsed_time(e1)
     prof = dgp.dgp_profile_read(ctx)
     dgp.dgp_profile(ctx, False)
-    if dist:
-        dist.barrier()
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * args.steps / (ms / 1000.0)
+    ms = max_over_ranks(ms, dist, dev)
+    value = whole_job_value(world, args.steps, ms)
 
     # end to end through the public C ABI with host buffers (copies inside the timed region)
     ne = args.steps if args.e2e_steps is None else args.e2e_steps

@@ -270,3 +270,22 @@ def test_spherical_mode_is_first_w13_update_with_nonlocal_source():
     D1, info = field.solve_brane_bending(d, a, box, OM, 1.0, D_init=np.zeros_like(d), max_iter=1, tol=0.0)
     assert nbad == 0 and info["iters"] == 1  # the update lowered the residual of C = 0
     assert np.max(np.abs(D1 - Dsph)) < 1e-13 * np.max(np.abs(Dsph))
+
+
+def test_large_crossover_scale_tends_to_gr():
+    """r_c -> infinity (eta = r_c H -> infinity): alpha -> 3, beta -> 1, c2 -> 3/2, c3 -> 0 and
+    Eq. FullDGP1 becomes the GR Poisson equation, so the nonlinear DGP phi approaches the GR phi
+    of the same expansion history with a difference falling as 1/r_c (Sec. II)."""
+    n, box, a = 16, 100.0, 0.5
+    d, _ = inputs.linear_field(n, box, -1.5, 0.5, seed=3)
+    diffs = []
+    for rc in (1e2, 1e3, 1e4):
+        c = bg.coefficients(a, OM, rc)
+        assert abs(c["alpha"] - 3.0) < 2.0 / c["eta"] and abs(c["beta"] - 1.0) < 1.0 / c["eta"]
+        assert abs(c["c2"] - 1.5) < 2.0 / c["eta"] and abs(c["c3"]) < 1.0 / c["eta"]
+        p_nl = field.solve_phi(d, a, box, OM, rc, tol=1e-12)[0]
+        p_gr = field.solve_phi(d, a, box, OM, rc, gravity="grh")[0]
+        diffs.append(np.linalg.norm(p_nl - p_gr) / np.linalg.norm(p_gr))
+    assert diffs[0] < 1e-2
+    for lo, hi in zip(diffs[1:], diffs[:-1]):
+        assert 9.0 < hi / lo < 11.0

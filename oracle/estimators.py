@@ -16,8 +16,9 @@ delta_k1 delta_k2 delta_k3 over the closed triangles with k_i in shell S_i
 (|k| within dk/2 of k_i) gives
     B(k1,k2,k3) = V^2 / M^3 * sum_x d1 d2 d3 / sum_x I1 I2 I3,
 d_i = IFFT(delta_k on S_i), I_i = IFFT(1 on S_i): both sums are M^-2 times
-the sums over closed triangles, so their ratio is the triangle average.  Parity unpinned beyond the
-closed forms tested (a field with known cross-shell content).
+the sums over closed triangles, so their ratio is the triangle average.  Pinned against that
+average taken by brute force over the closed triangles of an 8^3 field
+(tests/test_oracle_estimators.py).
 """
 
 import numpy as np

@@ -451,6 +451,48 @@ def run_adjoint(args):
     return 0
 
 
+def fp64_path_error(dgp, torch, np, n, box, delta_end, a_end, sched, steps, pos, mom, pk_main, dev,
+                    sort_every):
+    """Error of the mixed path against the FP64 GPU path: phi and forces of one solve on the run's
+    end-state density (a fresh context per precision, tol as the run), and P(k) at the end of the
+    same 200-step run done entirely in FP64 (the mixed run's P(k) is pk_main)."""
+    fields = {}
+    for name, prec, dt in (("mixed", dgp.DGP_MIXED_EFT, torch.float32), ("fp64", dgp.DGP_FP64, torch.float64)):
+        c = dgp.dgp_init(box, n, WL["rc_H0"], WL["omega_m0"], w=WL["w"], precision=prec, max_iter=WL["max_iter"],
+                         tol=WL["tol"])
+        try:
+            d = delta_end.to(dt).contiguous()
+            phi = torch.empty_like(d)
+            g = [torch.empty_like(d) for _ in range(3)]
+            dgp.dgp_solve_forces(c, a_end, d, phi, g[0], g[1], g[2], WL["tol"])
+            fields[name] = [phi.double()] + [x.double() for x in g]
+        finally:
+            dgp.dgp_destroy(c)
+
+    def rl2(a, b):
+        return float((a - b).norm() / b.norm())
+
+    out = {"phi_rel_l2": rl2(fields["mixed"][0], fields["fp64"][0]),
+           "force_rel_l2": max(rl2(fields["mixed"][i], fields["fp64"][i]) for i in (1, 2, 3))}
+    del fields
+    t = [torch.tensor(np.ascontiguousarray(v), dtype=torch.float64, device=dev) for v in (*pos, *mom)]
+    c = dgp.dgp_init(box, n, WL["rc_H0"], WL["omega_m0"], w=WL["w"], precision=dgp.DGP_FP64,
+                     max_iter=WL["max_iter"], tol=WL["tol"], sort_every=sort_every)
+    try:
+        parts = dgp.particles(*t)
+        for i in range(steps):
+            dgp.pm_step(c, parts, sched[i], sched[i + 1] - sched[i])
+        dl = torch.empty((n, n, n), dtype=torch.float64, device=dev)
+        dgp.dgp_deposit(c, parts, dl)
+        pk64 = dgp.power_spectrum(c, dl, n // 2)[1]
+    finally:
+        dgp.dgp_destroy(c)
+    out["pk_max_rel_diff"] = float(np.max(np.abs(pk_main / pk64 - 1)))
+    out["note"] = ("mixed (error-free pairs) vs the FP64 GPU path: phi and forces of one solve on the "
+                   "end-state density of the run at a = %.3f; P(k) after %d steps" % (a_end, steps))
+    return out
+
+
 # ---------------------------------------------------------------- replicas (one process per GPU)
 def replica_env():
     """(world, rank, local_rank) from the torchrun environment; (1, 0, 0) without one."""
@@ -626,6 +668,8 @@ def main():
             dgp.dgp_deposit(c, parts, dl)
             return dgp.power_spectrum(c, dl, n // 2)[1]
         pk_main = end_pk(ctx)
+        delta_end = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+        dgp.dgp_deposit(ctx, parts, delta_end)
         comp = {}
         for name in sorted(pcode):
             if name == args.precision:
@@ -649,6 +693,12 @@ def main():
                           "pk_max_rel_diff_vs_main": float(np.max(np.abs(pk2 / pk_main - 1)))}
             dgp.dgp_destroy(c2)
         line["precision_comparison"] = comp
+        if args.precision == "mixed":
+            try:
+                line["fp64_path_error"] = fp64_path_error(dgp, torch, np, n, box, delta_end, sched[args.steps], sched,
+                                                          args.steps, pos, mom, pk_main, dev, args.sort_every)
+            except Exception as e:  # the comparison must not cost the measurement
+                line["fp64_path_error"] = {"unavailable": repr(e)[:200]}
     dgp.dgp_destroy(ctx)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ts = oracle_fft_sample_seconds(36)

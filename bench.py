@@ -701,12 +701,12 @@ def main():
                 line["fp64_path_error"] = {"unavailable": repr(e)[:200]}
     dgp.dgp_destroy(ctx)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ts = oracle_fft_sample_seconds(36)
+        ts = oracle_fft_sample_seconds(96)
         t = sum(ts) / len(ts)
         e_mean = sum(evals) / len(evals)
         line["cpu_baseline"] = {
             "value": oracle_steps_per_s(t, e_mean), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "36 axis passes of the FP64 oracle FFT over a quarter of the 256^3 field (%.3f s each); "
+            "sample": "96 axis passes of the FP64 oracle FFT over a quarter of the 256^3 field (%.3f s each); "
                       "scaled to the FFT work of one PM step at the measured %.2f residual evaluations per "
                       "solve (deposit, gather and pointwise work not counted: an upper bound)" % (t, e_mean)}
     if rank == 0:

@@ -239,7 +239,9 @@ int dgp_power_spectrum_adjoint(dgp_ctx *c, const dgp_particles *parts, int nbins
  * derivative of <phibar_tot, phi> with delta fixed and D through the solve:
  *   rc_bar = <phibar_tot, A' delta + B' D> - <lam, alpha' D + c2' N[D] + c2 N'[D] - S' delta>,
  * phibar_tot = phibar + sum_i d_i gbar_i.  Needs the accepted solve's delta,
- * so the last field solve must have been nonlinear (else DGP_E_STATE). */
+ * so the last field solve must have been nonlinear (else DGP_E_STATE).  rc_bar
+ * is a host double the call writes (NULL: DGP_E_INVALID); other arguments and
+ * return codes as dgp_solve_adjoint. */
 int dgp_solve_adjoint_rc(dgp_ctx *c, const void *phibar, const void *gbar_x, const void *gbar_y,
                          const void *gbar_z, void *deltabar, double tol, double *rc_bar, dgp_solve_info *info);
 
@@ -250,13 +252,16 @@ int dgp_solve_adjoint_rc(dgp_ctx *c, const void *phibar, const void *gbar_x, con
  * dgp_solve_adjoint_rc term of each force VJP.  The K' and Dr' are taken by
  * complex-step differentiation of the 8-point Gauss-Legendre rules.  Summed
  * over the steps of a run (with the cotangents passed backwards) this is the
- * run's derivative in r_c H0 at fixed initial particles. */
+ * run's derivative in r_c H0 at fixed initial particles.  rc_bar is a host double
+ * the call writes (NULL: DGP_E_INVALID); other arguments and return codes as
+ * pm_step_adjoint. */
 int pm_step_adjoint_rc(dgp_ctx *c, const dgp_particles *start, double a, double da, dgp_particles *cot,
                        double *rc_bar);
 
 /* Cotangent of vel_factor in dgp_zeldovich: *vf_bar (host) = sum_j <pbar_j, Psi_j(delta_L)>
  * for the momentum cotangents of cot (lattice order, n^3 particles); delta_l is the device
- * linear field. */
+ * n^3 linear field (read only); vf_bar is a host double the call writes.  The cached mesh
+ * force is discarded.  DGP_E_INVALID for NULL arguments or cot->n != n^3. */
 int dgp_zeldovich_vf_adjoint(dgp_ctx *c, const void *delta_l, const dgp_particles *cot, double *vf_bar);
 
 /* Host-only.  The Zel'dovich velocity factor vf = a^2 E f (local G_eff, as

@@ -270,6 +270,24 @@ int dgp_zeldovich_vf_adjoint(dgp_ctx *c, const void *delta_l, const dgp_particle
  * dgp_background. */
 int dgp_velocity_factor(const dgp_cosmology *cosmo, double rc_H0, double a, double *vf, double *dvf_drc);
 
+/* Host-only.  Device bytes a context with parameters p requests from cudaMalloc
+ * (sums of the requested sizes; the allocator's rounding and the CUDA context
+ * itself are not included), without creating one:
+ *   base:      at dgp_init (14 real fields, 9 half spectra, twiddles, reduction
+ *              partials, residual history);
+ *   sort:      added by the first dgp_sort_particles / sorting pm_step of np
+ *              particles (keys, six permuted arrays, three int32 fields per cell);
+ *   adjoint:   added by the first pm_step_adjoint of np particles (products,
+ *              spectra, cotangent grids, the recomputed particle state);
+ *   host_step: added by the first pm_step_host of np particles.
+ * The reduction partials depend on the device's SM count (1 when no device is
+ * visible; a few KB either way).  Only p->n, p->precision and p->max_iter are
+ * read.  DGP_E_INVALID for an unsupported n or precision, np < 0 or NULL. */
+typedef struct {
+  size_t base, sort, adjoint, host_step;
+} dgp_workspace;
+int dgp_workspace_size(const dgp_params *p, int64_t np, dgp_workspace *out);
+
 /* Tile configuration of the context (not part of the paper's method): the y
  * pass's threads per CTA, 128, 256 or 512 (that many / N1 rows per CTA), picked
  * at dgp_init by timing the three variants on the context's own buffers.  The

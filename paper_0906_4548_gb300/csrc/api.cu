@@ -1437,6 +1437,38 @@ class Engine : public EngineBase {
   }
 };
 
+// Device bytes a context requests (the cudaMalloc sizes of init, the first sort,
+// the first step adjoint and pm_step_host), without creating one.
+template <typename T, int N>
+static void workspace_bytes(int max_iter, int64_t np, dgp_workspace* w) {
+  using V = vec2_t<T>;
+  const size_t M = (size_t)N * N * N, SPEC = (size_t)(N / 2 + 1) * N * N;
+  const size_t rb = sizeof(T) * M, sb = sizeof(V) * SPEC, pn = (size_t)np;
+  const size_t nb = (size_t)num_sms() * 4, fb = (size_t)fused_relax_blocks<T, N>();
+  const size_t pblocks = fb > nb ? fb : nb;
+  w->base = 14 * rb + 9 * sb + sizeof(double) * 4 * pblocks + sizeof(double) * (12 + 8) + sizeof(SolveCtl) +
+            sizeof(double) * ((size_t)max_iter + 1) + sizeof(double) * 4 * (N / 2) * (size_t)x_pass_blocks<T, N>() +
+            sizeof(double) * 4 * (N / 2) + sizeof(V) * 3 * N;
+  w->sort = sizeof(int) * 3 * M + sizeof(int) * (size_t)sort_scan_blocks((int64_t)M) + (sizeof(int) + 6 * sizeof(T)) * pn;
+  w->adjoint = sizeof(T) * (7 + 4 + 3) * M + sizeof(V) * 7 * SPEC + sizeof(double) * 12 + 6 * sizeof(T) * pn;
+  w->host_step = 6 * sizeof(T) * pn;
+}
+
+template <typename T>
+static bool workspace_for(int n, int max_iter, int64_t np, dgp_workspace* w) {
+  switch (n) {
+    case 16: workspace_bytes<T, 16>(max_iter, np, w); return true;
+    case 32: workspace_bytes<T, 32>(max_iter, np, w); return true;
+    case 64: workspace_bytes<T, 64>(max_iter, np, w); return true;
+    case 128: workspace_bytes<T, 128>(max_iter, np, w); return true;
+    case 256: workspace_bytes<T, 256>(max_iter, np, w); return true;
+    case 512: workspace_bytes<T, 512>(max_iter, np, w); return true;
+    case 48: workspace_bytes<T, 48>(max_iter, np, w); return true;
+    case 96: workspace_bytes<T, 96>(max_iter, np, w); return true;
+    default: return false;
+  }
+}
+
 template <typename T>
 static EngineBase* make_engine(int n) {
   switch (n) {
@@ -1641,6 +1673,14 @@ int dgp_solve_adjoint_rc(dgp_ctx* c, const void* phibar, const void* gbar_x, con
   if (!c || !rc_bar) return DGP_E_INVALID;
   const void* g[3] = {gbar_x, gbar_y, gbar_z};
   return c->eng->adjoint(phibar, g, deltabar, tol, info, rc_bar);
+}
+
+int dgp_workspace_size(const dgp_params* p, int64_t np, dgp_workspace* out) {
+  if (!p || !out || np < 0 || p->max_iter < 0) return DGP_E_INVALID;
+  if (p->precision < DGP_FP32 || p->precision > DGP_MIXED_EFT) return DGP_E_INVALID;
+  const bool ok = p->precision == DGP_FP64 ? dgp::workspace_for<double>(p->n, p->max_iter, np, out)
+                                           : dgp::workspace_for<float>(p->n, p->max_iter, np, out);
+  return ok ? DGP_OK : DGP_E_INVALID;
 }
 
 int dgp_tile_config(dgp_ctx* c, int* y_threads) {

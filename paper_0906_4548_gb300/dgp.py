@@ -26,7 +26,8 @@ EXPORTED = ["dgp_background", "dgp_init", "dgp_destroy", "dgp_strerror", "dgp_re
             "dgp_batch_create", "dgp_batch_context", "dgp_batch_step", "dgp_batch_destroy",
             "dgp_solve_adjoint", "pm_step_adjoint", "dgp_zeldovich", "dgp_zeldovich_adjoint",
             "dgp_power_spectrum_adjoint", "dgp_tile_config", "dgp_set_tile_config",
-            "dgp_solve_adjoint_rc", "pm_step_adjoint_rc", "dgp_zeldovich_vf_adjoint", "dgp_velocity_factor"]
+            "dgp_solve_adjoint_rc", "pm_step_adjoint_rc", "dgp_zeldovich_vf_adjoint", "dgp_velocity_factor",
+            "dgp_workspace_size"]
 DGP_NOALLOC_MAX_N = 64
 DGP_KERNEL_KINDS = 11
 
@@ -54,6 +55,11 @@ class SolveInfo(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Workspace(ctypes.Structure):
+    _fields_ = [("base", ctypes.c_size_t), ("sort", ctypes.c_size_t), ("adjoint", ctypes.c_size_t),
+                ("host_step", ctypes.c_size_t)]
 
 
 class Particles(ctypes.Structure):
@@ -105,6 +111,7 @@ def _load():
         "pm_step_adjoint_rc": (i, [vp, P(Particles), d, d, P(Particles), P(d)]),
         "dgp_zeldovich_vf_adjoint": (i, [vp, vp, P(Particles), P(d)]),
         "dgp_velocity_factor": (i, [P(Cosmology), d, d, P(d), P(d)]),
+        "dgp_workspace_size": (i, [P(Params), ctypes.c_int64, P(Workspace)]),
         "dgp_zeldovich": (i, [vp, vp, d, P(Particles)]),
         "dgp_zeldovich_adjoint": (i, [vp, P(Particles), d, vp]),
         "dgp_power_spectrum_adjoint": (i, [vp, P(Particles), i, P(d), P(Particles)]),
@@ -173,6 +180,14 @@ def params(box, n, rc_H0, w=1.0 / 3.0, precision=DGP_MIXED, gravity=DGP_GRAVITY_
            max_iter=100, tol=1e-6, sort_every=0, a_nonlinear=0.0):
     return Params(box, n, rc_H0, w, precision, gravity, 1 if local_only else 0, max_iter, tol, sort_every,
                   a_nonlinear)
+
+
+def dgp_workspace_size(n, precision=DGP_MIXED, max_iter=100, np_particles=0):
+    """Device bytes a context requests (host-only, see dgp.h): {"base", "sort", "adjoint", "host_step"}."""
+    out = Workspace()
+    _check(lib.dgp_workspace_size(ctypes.byref(params(1.0, n, 1.0, precision=precision, max_iter=max_iter)),
+                                  int(np_particles), ctypes.byref(out)), "dgp_workspace_size")
+    return {f: getattr(out, f) for f, _ in Workspace._fields_}
 
 
 def dgp_batch_create(param_list, omega_m0=0.27, c_over_H0=C_OVER_H0):

@@ -530,3 +530,21 @@ def test_run_128_fp32_pk_and_bispectrum_at_z1_and_z0(dgp, torch_dev):
         assert np.array_equal(cnt, co) and np.max(np.abs(P / Po - 1)) < 1e-5
         B, Q, *_ = oest.bispectrum(d, box, 12 * kf, 12 * kf, th)
         assert np.allclose(b, B, rtol=1e-3) and np.allclose(q, Q, rtol=1e-3)
+
+
+def test_workspace_size_matches_the_allocation(dgp, torch_dev):
+    """dgp_workspace_size's base bytes against the drop in free device memory across dgp_init
+    (a second context, so the library's kernels are already loaded; the allocator rounds up)."""
+    torch, dev = torch_dev
+    n = 256
+    dgp.dgp_destroy(dgp.dgp_init(400.0, n, 1.0, OM, precision=dgp.DGP_MIXED_EFT))
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    ctx = dgp.dgp_init(400.0, n, 1.0, OM, precision=dgp.DGP_MIXED_EFT, max_iter=100)
+    try:
+        torch.cuda.synchronize()
+        used = free0 - torch.cuda.mem_get_info(dev)[0]
+    finally:
+        dgp.dgp_destroy(ctx)
+    base = dgp.dgp_workspace_size(n, dgp.DGP_MIXED_EFT, max_iter=100)["base"]
+    assert base <= used <= 1.02 * base + (64 << 20)

@@ -270,6 +270,15 @@ int dgp_zeldovich_vf_adjoint(dgp_ctx *c, const void *delta_l, const dgp_particle
  * dgp_background. */
 int dgp_velocity_factor(const dgp_cosmology *cosmo, double rc_H0, double a, double *vf, double *dvf_drc);
 
+/* Host-only.  The leapfrog's time factors between a0 and a1 (Sec. III.A with
+ * p = a^2 dx/dt; 8-point Gauss-Legendre in ln a, as pm_step uses them):
+ *   out[0] = int dlna / E            (kick),   out[1] = int dlna / (a^2 E)   (drift),
+ *   out[2], out[3] = their derivatives in r_c H0 (complex-step differentiation of the rule).
+ * pm_step kicks with out[0] over each half step (a0 -> sqrt(a0 a1) -> a1) and drifts with
+ * out[1] over the whole step.  DGP_E_INVALID for a0, a1 <= 0 or not finite, rc_H0 <= 0,
+ * omega_m0 < 0 or NULL. */
+int dgp_time_factors(const dgp_cosmology *cosmo, double rc_H0, double a0, double a1, double *out);
+
 /* Host-only.  Device bytes a context with parameters p requests from cudaMalloc
  * (sums of the requested sizes; the allocator's rounding and the CUDA context
  * itself are not included), without creating one:

@@ -1675,6 +1675,18 @@ int dgp_solve_adjoint_rc(dgp_ctx* c, const void* phibar, const void* gbar_x, con
   return c->eng->adjoint(phibar, g, deltabar, tol, info, rc_bar);
 }
 
+int dgp_time_factors(const dgp_cosmology* cosmo, double rc_H0, double a0, double a1, double* out) {
+  if (!cosmo || !out || !(a0 > 0) || !(a1 > 0) || !isfinite(a0) || !isfinite(a1) || !(rc_H0 > 0) ||
+      !(cosmo->omega_m0 >= 0))
+    return DGP_E_INVALID;
+  const double om = cosmo->omega_m0;
+  out[0] = dgp::time_integral(a0, a1, om, rc_H0, 0);
+  out[1] = dgp::time_integral(a0, a1, om, rc_H0, 2);
+  out[2] = dgp::time_integral_drc(a0, a1, om, rc_H0, 0);
+  out[3] = dgp::time_integral_drc(a0, a1, om, rc_H0, 2);
+  return DGP_OK;
+}
+
 int dgp_workspace_size(const dgp_params* p, int64_t np, dgp_workspace* out) {
   if (!p || !out || np < 0 || p->max_iter < 0) return DGP_E_INVALID;
   if (p->precision < DGP_FP32 || p->precision > DGP_MIXED_EFT) return DGP_E_INVALID;

@@ -21,3 +21,20 @@ def test_velocity_factor_rejects_bad_arguments():
     for a, rc in ((0.0, 1.0), (0.5, 0.0), (-1.0, 1.0)):
         with pytest.raises(dgp.DgpError):
             dgp.dgp_velocity_factor(OM, rc, a)
+
+
+@pytest.mark.parametrize("a0,a1,rc", [(0.02, 0.0204, 1.0), (0.3, 0.35, 0.7), (0.9, 1.0, 2.0)])
+def test_time_factors_and_derivatives_match_the_oracle(a0, a1, rc):
+    """The library's kick and drift factors (the ones pm_step uses) and their complex-step
+    derivatives against the oracle's quadrature and its chain-rule derivatives."""
+    k, dr, dk, ddr = dgp.dgp_time_factors(OM, rc, a0, a1)
+    assert abs(k - obg.kick_factor(a0, a1, OM, rc)) < 1e-14 * abs(k)
+    assert abs(dr - obg.drift_factor(a0, a1, OM, rc)) < 1e-14 * abs(dr)
+    assert abs(dk - obg.kick_factor_drc(a0, a1, OM, rc)) < 1e-11 * abs(dk)
+    assert abs(ddr - obg.drift_factor_drc(a0, a1, OM, rc)) < 1e-11 * abs(ddr)
+
+
+def test_time_factors_reject_bad_arguments():
+    for a0, a1, rc in ((0.0, 0.5, 1.0), (0.5, float("inf"), 1.0), (0.5, 0.6, -1.0)):
+        with pytest.raises(dgp.DgpError):
+            dgp.dgp_time_factors(OM, rc, a0, a1)

@@ -270,6 +270,11 @@ int dgp_zeldovich_vf_adjoint(dgp_ctx *c, const void *delta_l, const dgp_particle
  * dgp_background. */
 int dgp_velocity_factor(const dgp_cosmology *cosmo, double rc_H0, double a, double *vf, double *dvf_drc);
 
+/* Host-only.  d/d(r_c H0) of every member of dgp_background at scale factor a (the
+ * derivatives the r_c adjoint uses), by complex-step differentiation of the same
+ * code; errors as dgp_background. */
+int dgp_background_drc(const dgp_cosmology *cosmo, double rc_H0, double a, dgp_background_t *out);
+
 /* Host-only.  The leapfrog's time factors between a0 and a1 (Sec. III.A with
  * p = a^2 dx/dt; 8-point Gauss-Legendre in ln a, as pm_step uses them):
  *   out[0] = int dlna / E            (kick),   out[1] = int dlna / (a^2 E)   (drift),

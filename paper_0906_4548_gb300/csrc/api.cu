@@ -1675,6 +1675,21 @@ int dgp_solve_adjoint_rc(dgp_ctx* c, const void* phibar, const void* gbar_x, con
   return c->eng->adjoint(phibar, g, deltabar, tol, info, rc_bar);
 }
 
+int dgp_background_drc(const dgp_cosmology* cosmo, double rc_H0, double a, dgp_background_t* out) {
+  if (!cosmo || !out || !(a > 0) || !(rc_H0 > 0) || !(cosmo->omega_m0 >= 0)) return DGP_E_INVALID;
+  const double om = cosmo->omega_m0, h = dgp::cs_step(rc_H0);
+  const dgp::Coef d = dgp::coefficients_drc(a, om, rc_H0);
+  out->E = d.E; out->eta = d.eta; out->alpha = d.alpha; out->beta = d.beta; out->s = d.s;
+  out->c2 = d.c2; out->c3 = d.c3; out->q = d.q; out->omega_m = d.omega_m;
+  const dgp::CoefT<dgp::cplx> z = dgp::coefficients_t<dgp::cplx>(a, om, dgp::cplx(rc_H0, h));
+  out->geff_local = dgp::geff_local_t<dgp::cplx>(z).imag() / h;
+  dgp::cplx D, f;
+  dgp::growth_t<dgp::cplx>(a, om, dgp::cplx(rc_H0, h), &D, &f);
+  out->growth_D = D.imag() / h;
+  out->growth_f = f.imag() / h;
+  return DGP_OK;
+}
+
 int dgp_time_factors(const dgp_cosmology* cosmo, double rc_H0, double a0, double a1, double* out) {
   if (!cosmo || !out || !(a0 > 0) || !(a1 > 0) || !isfinite(a0) || !isfinite(a1) || !(rc_H0 > 0) ||
       !(cosmo->omega_m0 >= 0))

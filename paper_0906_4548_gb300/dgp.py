@@ -27,7 +27,7 @@ EXPORTED = ["dgp_background", "dgp_init", "dgp_destroy", "dgp_strerror", "dgp_re
             "dgp_solve_adjoint", "pm_step_adjoint", "dgp_zeldovich", "dgp_zeldovich_adjoint",
             "dgp_power_spectrum_adjoint", "dgp_tile_config", "dgp_set_tile_config",
             "dgp_solve_adjoint_rc", "pm_step_adjoint_rc", "dgp_zeldovich_vf_adjoint", "dgp_velocity_factor",
-            "dgp_workspace_size", "dgp_time_factors"]
+            "dgp_workspace_size", "dgp_time_factors", "dgp_background_drc"]
 DGP_NOALLOC_MAX_N = 64
 DGP_KERNEL_KINDS = 11
 
@@ -113,6 +113,7 @@ def _load():
         "dgp_velocity_factor": (i, [P(Cosmology), d, d, P(d), P(d)]),
         "dgp_workspace_size": (i, [P(Params), ctypes.c_int64, P(Workspace)]),
         "dgp_time_factors": (i, [P(Cosmology), d, d, d, P(d)]),
+        "dgp_background_drc": (i, [P(Cosmology), d, d, P(Background)]),
         "dgp_zeldovich": (i, [vp, vp, d, P(Particles)]),
         "dgp_zeldovich_adjoint": (i, [vp, P(Particles), d, vp]),
         "dgp_power_spectrum_adjoint": (i, [vp, P(Particles), i, P(d), P(Particles)]),
@@ -181,6 +182,14 @@ def params(box, n, rc_H0, w=1.0 / 3.0, precision=DGP_MIXED, gravity=DGP_GRAVITY_
            max_iter=100, tol=1e-6, sort_every=0, a_nonlinear=0.0):
     return Params(box, n, rc_H0, w, precision, gravity, 1 if local_only else 0, max_iter, tol, sort_every,
                   a_nonlinear)
+
+
+def dgp_background_drc(omega_m0, rc_H0, a, c_over_H0=C_OVER_H0):
+    """d/d(r_c H0) of every member of dgp_background (host)."""
+    out = Background()
+    _check(lib.dgp_background_drc(ctypes.byref(Cosmology(omega_m0, c_over_H0)), rc_H0, a, ctypes.byref(out)),
+           "dgp_background_drc")
+    return {f: getattr(out, f) for f, _ in Background._fields_}
 
 
 def dgp_time_factors(omega_m0, rc_H0, a0, a1, c_over_H0=C_OVER_H0):

@@ -38,3 +38,19 @@ def test_time_factors_reject_bad_arguments():
     for a0, a1, rc in ((0.0, 0.5, 1.0), (0.5, float("inf"), 1.0), (0.5, 0.6, -1.0)):
         with pytest.raises(dgp.DgpError):
             dgp.dgp_time_factors(OM, rc, a0, a1)
+
+
+@pytest.mark.parametrize("a,rc", [(0.5, 1.2), (0.05, 0.8), (1.0, 2.5)])
+def test_coefficient_derivatives_match_the_oracle(a, rc):
+    """The library's complex-step derivatives of the coefficients (the scalars of the r_c
+    contraction) against the oracle's chain rule; growth f against the RK4 sensitivities."""
+    d = dgp.dgp_background_drc(OM, rc, a)
+    o = obg.coefficient_derivatives(a, OM, rc)
+    for k in ("E", "eta", "alpha", "beta", "s", "c2", "c3", "q", "omega_m"):
+        assert abs(d[k] - o[k]) < 1e-11 * abs(o[k]) + 1e-15, k
+    _, _, dD, df = obg.growth_drc(a, OM, rc)
+    assert abs(d["growth_D"] - dD) < 1e-10 * abs(dD)
+    assert abs(d["growth_f"] - df) < 1e-10 * abs(df)
+    h = 1e-6 * rc   # geff_local has no oracle derivative: central differences of the library's value
+    fd = (dgp.dgp_background(OM, rc + h, a)["geff_local"] - dgp.dgp_background(OM, rc - h, a)["geff_local"]) / (2 * h)
+    assert abs(d["geff_local"] - fd) < 1e-6 * abs(fd)

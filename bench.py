@@ -4,20 +4,26 @@ Workload (the 256^3 run): 256^3 particles on a 256^3 mesh in a 400 Mpc/h box,
 seeded n_s = -1.5 power-law Gaussian field with mesh rms 0.5 at a = 0.02,
 Zel'dovich initial conditions, r_c H0 = 1, Omega_m0 = 0.27, w = 1/3, steps
 uniform in ln a from a = 0.02 to a = 1 in 200 steps, relaxation tolerance 1e-6
-on <|R|>/eps every step, FP32 mesh/particles with FP64 residual, discriminant
-and reductions (the residual R, split source B' and discriminant Delta are
-evaluated on pairs of floats with error-free transformations, ~48 bits;
---precision mixed-fp64 evaluates them on the FP64 pipe instead).  A "step" is
-one pm_step call (deposit, field solve, forces,
-gather, kick-drift-kick).  The timed region runs K consecutive steps from
-a = 0.02 (K = 200 is the whole run) after W warm-up steps and a reset to the
-initial conditions.  Inputs (403 MB of particles, 64 MB mesh fields) exceed
-L2, so no flush is needed between steps.
+on <|R|>/eps every step.  Arithmetic (--precision mixed, the default): FP32
+mesh fields, FFTs and particles; the residual R, the split source B' and the
+discriminant Delta as unevaluated pairs of FP32 numbers formed with error-free
+transformations (about 48 significant bits) in place of FP64; norms, means and
+reductions in FP64.  --precision mixed-fp64 evaluates R, B' and Delta on the
+FP64 pipe instead (its rate is printed beside the headline).  A "step" is one
+pm_step call (deposit, field solve, forces, gather, kick-drift-kick).
+
+Timing: after W warm-up steps the whole 200-step run is started again from the
+initial conditions and always run to the end; K of its steps, the middle step
+of each of K equal strata of the run, are timed (each bracketed by a device
+synchronisation, a barrier for N > 1, and CUDA events on the context's stream).
+The context runs on its own stream, where the relaxation iterations replay as
+CUDA graphs.  Inputs (403 MB of particles, 64 MB mesh fields) exceed L2, so no
+flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 N > 1 (torchrun, one process per GPU): independent replicas with distinct
-seeds, no data-path collective; value = all ranks' steps / max rank time.
+seeds, no data-path collective; value = all ranks' timed steps / max rank time.
 """
 
 import argparse
@@ -71,8 +77,10 @@ def recorded_traffic(kind):
 
 
 PRECISION_DESC = {
-    "mixed": "mixed: fp32 mesh/FFT/particles; residual, B', discriminant as error-free fp32 pairs "
-             "(~48-bit); norms and reductions fp64",
+    "fp64": "fp64 throughout (the oracle)",
+    "mixed": "mixed: fp32 mesh/FFT/particles; the residual R, split source B' and discriminant Delta as "
+             "unevaluated pairs of fp32 (error-free transformations, ~48-bit significand) in place of fp64; "
+             "norms, means and reductions fp64",
     "mixed-fp64": "mixed: fp32 mesh/FFT/particles; residual, B', discriminant, norms and reductions fp64",
     "fp32": "fp32 throughout (fp64 cross-block sums only)",
 }
@@ -152,52 +160,65 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_fft_sample_seconds(nsamples, n=None):
-    """Time the FP64 oracle's FFT on the workload's mesh: each sample is one
-    axis pass of its four-step DFT over a quarter of a 256^3 field (one
-    twelfth of a 3D transform).  Runs in this process."""
-    import numpy as np
-    from oracle.fft import fft_axis
-    n = WL["n"] if n is None else n
-    rng = np.random.default_rng(0)
-    f = rng.standard_normal((n, n, n))
-    q = n // 4
-    slabs = [(f[:q], 2), (f[:q], 1), (f[:, :q], 0)]
-    fft_axis(slabs[0][0], slabs[0][1])  # untimed warm-up
-    ts = []
-    for j in range(nsamples):
-        s, ax = slabs[j % 3]
-        t0 = time.perf_counter()
-        fft_axis(s, ax)
-        ts.append(time.perf_counter() - t0)
-    return ts
+def oracle_threads():
+    """Host threads the oracle uses: its matmul steps run on the BLAS thread pool (all cores unless
+    limited by the environment); its elementwise numpy steps on one thread."""
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        v = os.environ.get(k)
+        if v and v.isdigit():
+            return int(v)
+    return os.cpu_count()
 
 
-def oracle_steps_per_s(t_sample, e_per_solve):
-    """An oracle PM step of this workload does one field solve with 6 + 9 E 3D
-    transforms (E residual evaluations, each 1 forward + 8 inverse; plus delta,
-    the source, phi and 3 forces); a 3D transform is 12 samples."""
-    return 1.0 / (t_sample * 12.0 * (6.0 + 9.0 * e_per_solve))
+# Residual evaluations per solve of each of the 200 steps of the 256^3 run, as measured on GB300
+# (solver.evals_per_step of a bench run): the reference arm has no GPU run to read them from, and
+# times the oracle at the mean over the same timed steps as the GPU arm.
+EVALS_PER_STEP_256 = None
+
+
+def reference_evals(idx):
+    if EVALS_PER_STEP_256 is None:
+        return E_PER_SOLVE_REF
+    return sum(EVALS_PER_STEP_256[i] for i in idx) / len(idx)
 
 
 def run_reference(args):
-    """The reference arm: the FP64 oracle on the host cores (rank 0 only)."""
+    """The reference arm: the FP64 oracle on the host cores (rank 0 only).  Each of the W + K steps
+    is one real call of a piece of the oracle's PM step (deposit, forward transform, source,
+    residual evaluation, update, phi and forces, interpolation, in turn) on the 256^3 workload's
+    initial state; the K timed calls give each piece's time, and value = 1 / (the oracle's step
+    time at E residual evaluations per solve), E the mean over the GPU arm's timed steps."""
     rank = replica_env()[1]
     if rank != 0:
         return 0
-    cores = os.cpu_count()
-    ts = oracle_fft_sample_seconds(args.warmup + args.steps)[args.warmup:]
-    t = sum(ts) / len(ts)
-    v = oracle_steps_per_s(t, E_PER_SOLVE_REF)
-    sample = ("FP64 oracle four-step FFT, one axis pass over a quarter of the 256^3 field per step (%.3f s); "
-              "steps/s = 1 / (12 x (6 + 9 x %.1f) x that): FFT work of one PM step with %.1f residual "
-              "evaluations per solve; deposit, gather and pointwise work not counted (upper bound)"
-              % (t, E_PER_SOLVE_REF, E_PER_SOLVE_REF))
+    model = OracleStepModel()
+    pieces = OracleStepModel.PIECES
+    # the pieces depend on one another's results: the warm-up calls run them in order
+    for j in range(max(args.warmup, len(pieces))):
+        model._run(pieces[j % len(pieces)])
+    t0 = time.perf_counter()
+    k = max(args.steps, 1)
+    for j in range(k):
+        model.time_piece(pieces[j % len(pieces)])
+    wall = time.perf_counter() - t0
+    for piece in pieces:  # a piece the K calls did not reach is timed once more
+        if not model.times[piece]:
+            model.time_piece(piece)
+    idx = sampled_steps(WL["run_steps"], args.steps)
+    e = reference_evals(idx)
+    t_step = model.step_seconds(e)
+    v = 1.0 / t_step
+    sample = model.describe(e)
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": 1000.0 * t_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": config(args.gpus, "mixed"),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "config": dict(config(args.gpus, "fp64"), precision=PRECISION_DESC["fp64"]),
+            "timing": {"how": "each step is one real oracle call of one piece of a PM step (cycling through "
+                              "%s); the PM step time is the sum of the pieces' mean times at E = %.2f residual "
+                              "evaluations per solve, the mean over the GPU arm's timed steps of the 200-step "
+                              "run" % (", ".join(pieces), e),
+                       "timed_calls_s": wall, "pm_step_equivalents_timed": wall / t_step},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -451,20 +472,22 @@ def run_adjoint(args):
     return 0
 
 
-def fp64_path_error(dgp, torch, np, n, box, delta_end, a_end, sched, steps, pos, mom, pk_main, dev,
-                    sort_every):
+def fp64_path_error(dgp, torch, np, n, box, delta_end, a_end, sched, pos, mom, pk_main, dev, sort_every,
+                    stream):
     """Error of the mixed path against the FP64 GPU path: phi and forces of one solve on the run's
     end-state density (a fresh context per precision, tol as the run), and P(k) at the end of the
-    same 200-step run done entirely in FP64 (the mixed run's P(k) is pk_main)."""
+    same whole run done entirely in FP64 (the mixed run's P(k) is pk_main)."""
     fields = {}
     for name, prec, dt in (("mixed", dgp.DGP_MIXED_EFT, torch.float32), ("fp64", dgp.DGP_FP64, torch.float64)):
         c = dgp.dgp_init(box, n, WL["rc_H0"], WL["omega_m0"], w=WL["w"], precision=prec, max_iter=WL["max_iter"],
-                         tol=WL["tol"])
+                         tol=WL["tol"], stream=stream.cuda_stream)
         try:
             d = delta_end.to(dt).contiguous()
             phi = torch.empty_like(d)
             g = [torch.empty_like(d) for _ in range(3)]
+            torch.cuda.synchronize()
             dgp.dgp_solve_forces(c, a_end, d, phi, g[0], g[1], g[2], WL["tol"])
+            torch.cuda.synchronize()
             fields[name] = [phi.double()] + [x.double() for x in g]
         finally:
             dgp.dgp_destroy(c)
@@ -477,10 +500,11 @@ def fp64_path_error(dgp, torch, np, n, box, delta_end, a_end, sched, steps, pos,
     del fields
     t = [torch.tensor(np.ascontiguousarray(v), dtype=torch.float64, device=dev) for v in (*pos, *mom)]
     c = dgp.dgp_init(box, n, WL["rc_H0"], WL["omega_m0"], w=WL["w"], precision=dgp.DGP_FP64,
-                     max_iter=WL["max_iter"], tol=WL["tol"], sort_every=sort_every)
+                     max_iter=WL["max_iter"], tol=WL["tol"], sort_every=sort_every, stream=stream.cuda_stream)
     try:
+        torch.cuda.synchronize()
         parts = dgp.particles(*t)
-        for i in range(steps):
+        for i in range(len(sched) - 1):
             dgp.pm_step(c, parts, sched[i], sched[i + 1] - sched[i])
         dl = torch.empty((n, n, n), dtype=torch.float64, device=dev)
         dgp.dgp_deposit(c, parts, dl)
@@ -489,8 +513,108 @@ def fp64_path_error(dgp, torch, np, n, box, delta_end, a_end, sched, steps, pos,
         dgp.dgp_destroy(c)
     out["pk_max_rel_diff"] = float(np.max(np.abs(pk_main / pk64 - 1)))
     out["note"] = ("mixed (error-free pairs) vs the FP64 GPU path: phi and forces of one solve on the "
-                   "end-state density of the run at a = %.3f; P(k) after %d steps" % (a_end, steps))
+                   "end-state density of the run at a = %.3f; P(k) after the whole %d-step run"
+                   % (a_end, len(sched) - 1))
     return out
+
+
+def sampled_steps(run_steps, k):
+    """The K timed steps of a run of run_steps steps: the middle step of each of K equal strata
+    of the run (all steps when K >= run_steps)."""
+    k = max(1, min(int(k), run_steps))
+    return [min(run_steps - 1, int((j + 0.5) * run_steps / k)) for j in range(k)]
+
+
+def oracle_sample_inputs(n, box, a, seed):
+    """Workload-shaped inputs of the oracle sample: the Zel'dovich particles of the run's
+    initial conditions at a (FP32 positions, as the GPU run starts from)."""
+    import numpy as np
+    from oracle import background as obg
+    from paper_0906_4548_gb300 import inputs
+    vf = obg.zeldovich_velocity_factor(a, WL["omega_m0"], WL["rc_H0"])
+    pos, _, _ = inputs.zeldovich_particles(n, box, WL["n_s"], WL["rms"], seed, vf)
+    return pos.astype(np.float32).astype(np.float64)
+
+
+class OracleStepModel:
+    """The FP64 oracle's PM step, timed on real oracle calls on one workload-shaped state.
+
+    One oracle PM step (oracle.pm.PMState.step, the start force carried over) is
+        deposit + density contrast + fft3(delta) + source (one inverse transform)
+        + E evaluations (fft3(D), the eight inverse transforms of derived_fields, residual)
+        + (E - 1) updates (relax_update) + phi and forces (four inverse transforms)
+        + 3 CIC interpolations,
+    with E the residual evaluations of the step's solve.  Each piece is one call of the oracle
+    as it stands; the step time is their sum for a given E."""
+
+    PIECES = ("deposit", "forward", "source", "evaluation", "update", "phi_forces", "interpolate")
+
+    def __init__(self, n=None, box=None, a=None, seed=None, pos=None):
+        import numpy as np
+        from oracle import background as obg
+        from oracle import field as ofield
+        from oracle import pm as opm
+        from oracle.fft import fft3, ifft3_real
+        self.np, self.opm, self.ofield, self.fft3, self.ifft3_real = np, opm, ofield, fft3, ifft3_real
+        self.n = WL["n"] if n is None else n
+        self.box = WL["box"] if box is None else box
+        self.a = WL["a_start"] if a is None else a
+        self.pos = (oracle_sample_inputs(self.n, self.box, self.a, WL["seed"] if seed is None else seed)
+                    if pos is None else np.asarray(pos, dtype=np.float32).astype(np.float64))
+        self.grid = ofield.KGrid(self.n, self.box)
+        self.coef = obg.coefficients(self.a, WL["omega_m0"], WL["rc_H0"])
+        self.state = {}
+        self.times = {k: [] for k in self.PIECES}
+
+    def _run(self, piece):
+        st, np, of, g, c = self.state, self.np, self.ofield, self.grid, self.coef
+        if piece == "deposit":
+            st["delta"] = self.opm.density_contrast(self.opm.cic_deposit(self.pos, self.n, self.box))
+        elif piece == "forward":
+            dk = self.fft3(st["delta"])
+            dk[g.zero] = 0.0
+            st["dk"] = dk
+        elif piece == "source":
+            st["Sk"] = of.source_spectrum(st["dk"], g, c)
+            st["S"] = self.ifft3_real(st["Sk"])
+        elif piece == "evaluation":
+            if "D" not in st:
+                st["D"] = self.ifft3_real(of.linear_D_spectrum(st["Sk"], g, c))
+            D_k = self.fft3(st["D"])
+            D_k[g.zero] = 0.0
+            D, H, Nf = of.derived_fields(D_k, g, c)
+            st["r"] = float(np.mean(np.abs(of.residual(D, H, Nf, st["S"], c))))
+            st["DHN"], st["Dk"] = (D, H, Nf), D_k
+        elif piece == "update":
+            D, H, Nf = st["DHN"]
+            st["D"], _ = of.relax_update(D, H, Nf, st["S"], c, WL["w"])
+        elif piece == "phi_forces":
+            _, st["g"] = of.phi_and_forces(st["dk"], st["Dk"], g, c)
+        elif piece == "interpolate":
+            self.opm.cic_interpolate(st["g"][0], self.pos, self.box)
+
+    def time_piece(self, piece):
+        t0 = time.perf_counter()
+        self._run(piece)
+        dt = time.perf_counter() - t0
+        self.times[piece].append(dt)
+        return dt
+
+    def time_all(self):
+        for piece in self.PIECES:
+            self.time_piece(piece)
+
+    def step_seconds(self, e):
+        m = {k: sum(v) / len(v) for k, v in self.times.items() if v}
+        return (m["deposit"] + m["forward"] + m["source"] + e * m["evaluation"] + max(e - 1.0, 0.0) * m["update"]
+                + m["phi_forces"] + 3.0 * m["interpolate"])
+
+    def describe(self, e):
+        m = {k: round(sum(v) / len(v), 3) for k, v in self.times.items() if v}
+        return ("real FP64 oracle calls on the %d^3 workload's initial state (%d particles, a = %g), seconds "
+                "per call %s; one oracle PM step = deposit + forward + source + E evaluations + (E - 1) updates "
+                "+ phi_forces + 3 interpolations at E = %.2f residual evaluations per solve"
+                % (self.n, self.n ** 3, self.a, json.dumps(m), e))
 
 
 # ---------------------------------------------------------------- replicas (one process per GPU)
@@ -525,13 +649,15 @@ def whole_job_value(world, steps, ms):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20,
+                    help="timed steps K, spread evenly over the whole run (which always runs in full)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=sorted(PRECISION_DESC))
     ap.add_argument("--no-compare", action="store_true", help="skip the precision comparison runs")
+    ap.add_argument("--no-kernel-table", action="store_true", help="skip the per-kind event pass")
     ap.add_argument("--workload", default="pm256", choices=["pm256", "batched", "adjoint"],
                     help="pm256: the 256^3 PM run (default); batched: 48 small realisations; adjoint: the "
                          "gradient of a P(k) loss after a 128^3 run")
@@ -542,6 +668,8 @@ def main():
                     help="adjoint workload: precision of the gradient and differences that are compared")
     ap.add_argument("--sort-every", type=int, default=SORT_EVERY,
                     help="cell-sort the particles after every K-th drift (0: never)")
+    ap.add_argument("--run-steps", type=int, default=WL["run_steps"],
+                    help="steps of the run (the workload is 200; smaller only for quick checks)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -565,6 +693,7 @@ def main():
     from paper_0906_4548_gb300 import dgp, inputs
 
     n, box = WL["n"], WL["box"]
+    R = args.run_steps
     bgi = dgp.dgp_background(WL["omega_m0"], WL["rc_H0"], WL["a_start"])
     vf = WL["a_start"] ** 2 * bgi["E"] * bgi["growth_f"]
     pos, mom, amp = inputs.zeldovich_particles(n, box, WL["n_s"], WL["rms"], replica_seed(WL["seed"], rank), vf)
@@ -572,143 +701,209 @@ def main():
     ic = [torch.tensor(v.astype(np.float32), device=dev) for v in (*pos, *mom)]
     cur = [t.clone() for t in ic]
     parts = dgp.particles(*cur)
+    # the context runs on its own stream: the relaxation iterations replay as CUDA graphs there
+    # (stream capture is not available on the legacy default stream)
+    bs = torch.cuda.Stream(device=dev)
     pcode = {"mixed": dgp.DGP_MIXED_EFT, "mixed-fp64": dgp.DGP_MIXED, "fp32": dgp.DGP_FP32}
-    ctx = dgp.dgp_init(box, n, WL["rc_H0"], WL["omega_m0"], w=WL["w"], precision=pcode[args.precision],
-                       max_iter=WL["max_iter"], tol=WL["tol"], sort_every=args.sort_every)
+
+    def make_ctx(prec):
+        return dgp.dgp_init(box, n, WL["rc_H0"], WL["omega_m0"], w=WL["w"], precision=pcode[prec],
+                            max_iter=WL["max_iter"], tol=WL["tol"], sort_every=args.sort_every,
+                            stream=bs.cuda_stream)
+
+    ctx = make_ctx(args.precision)
     dlna = math.log(WL["a_end"] / WL["a_start"]) / WL["run_steps"]
-    sched = [WL["a_start"] * math.exp(i * dlna) for i in range(max(args.steps, args.warmup) + 1)]
+    sched = [WL["a_start"] * math.exp(i * dlna) for i in range(R + 1)]
+    idx = sampled_steps(R, args.steps)
+    K = len(idx)
+    sel = set(idx)
 
-    def restart():
-        for c, s in zip(cur, ic):
-            c.copy_(s)
-        dgp.dgp_reset(ctx)
+    def restart(c):
+        for x, s0 in zip(cur, ic):
+            x.copy_(s0)
+        dgp.dgp_reset(c)
+        torch.cuda.synchronize()
 
-    def steps(k, infos=None):
-        for i in range(k):
-            inf = dgp.pm_step(ctx, parts, sched[i], sched[i + 1] - sched[i])
+    def run(c, nsteps=R, infos=None, timed=None, launches=None, dom=None, roof=None):
+        """Steps 0 .. nsteps-1 of the schedule; each step in `sel` is bracketed by a barrier and a
+        device synchronisation on both sides and timed with CUDA events on the context's stream."""
+        for i in range(nsteps):
+            if timed is not None and i in sel:
+                torch.cuda.synchronize()
+                if dist:
+                    dist.barrier()
+                before = dgp.dgp_profile_read(c) if launches is not None else None
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(bs)
+                inf = dgp.pm_step(c, parts, sched[i], sched[i + 1] - sched[i])
+                e1.record(bs)
+                torch.cuda.synchronize()
+                timed.append(e0.elapsed_time(e1))
+                if launches is not None:
+                    after = dgp.dgp_profile_read(c)
+                    launches.append(sum(after[k]["launches"] - before[k]["launches"] for k in after))
+                    if dom is not None:
+                        for f in ("ms", "timed", "timed_bytes"):
+                            roof[f] += after[dom][f] - before[dom][f]
+            else:
+                inf = dgp.pm_step(c, parts, sched[i], sched[i + 1] - sched[i])
             if infos is not None:
                 infos.append(inf)
 
-    restart()
-    steps(args.warmup)
-    # per-kernel breakdown: the same run with every launch bracketed by events
-    restart()
-    dgp.dgp_profile(ctx, True)
-    steps(args.steps)
-    prof_all = dgp.dgp_profile_read(ctx)
-    dom = max(prof_all, key=lambda k: prof_all[k]["ms"])
-    # timed region: events only around the dominant kernel (its roofline)
-    restart()
-    torch.cuda.synchronize()
+    restart(ctx)
+    run(ctx, min(args.warmup, R))
+    # per-kind breakdown over the whole run: every launch bracketed by events (graphs off)
+    prof_all = None
+    dom = "relax"
+    if not args.no_kernel_table:
+        restart(ctx)
+        dgp.dgp_profile(ctx, True)
+        run(ctx)
+        prof_all = dgp.dgp_profile_read(ctx)
+        dom = max(prof_all, key=lambda k: prof_all[k]["ms"])
+    # timed pass: the whole run on the production path (graph replay on); K steps spread over the
+    # run are timed, and inside them the dominant kind's launches outside graphs carry events
+    restart(ctx)
     if dist:
         dist.barrier()
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    infos = []
+    timed, launches, infos = [], [], []
+    roof = {"ms": 0.0, "timed": 0, "timed_bytes": 0.0}
     with ClockSampler(local) as clk:
         time.sleep(0.3)
-        dgp.dgp_profile(ctx, True, kinds=[dom])
-        e0.record(stream)
-        steps(args.steps, infos)
-        e1.record(stream)
+        dgp.dgp_profile_sampled(ctx, [dom])
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(bs)
+        run(ctx, R, infos, timed, launches, dom, roof)
+        f1.record(bs)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    prof = dgp.dgp_profile_read(ctx)
+    full_ms = f0.elapsed_time(f1)
     dgp.dgp_profile(ctx, False)
-    ms = max_over_ranks(ms, dist, dev)
-    value = whole_job_value(world, args.steps, ms)
+    ms = max_over_ranks(sum(timed), dist, dev)
+    value = whole_job_value(world, K, ms)
 
-    # end to end through the public C ABI with host buffers (copies inside the timed region)
-    ne = args.steps if args.e2e_steps is None else args.e2e_steps
-    host = [torch.empty(n ** 3, dtype=torch.float32, pin_memory=True) for _ in range(6)]
-    for h, s in zip(host, ic):
-        h.copy_(s)
-    harr = [h.numpy() for h in host]
-    hparts = dgp.particles(*harr)
-    dgp.dgp_reset(ctx)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for i in range(ne):
-        dgp.pm_step_host(ctx, hparts, sched[i], sched[i + 1] - sched[i])
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": ne / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 6 * 4 * n ** 3,
-           "d2h_bytes_per_step": 6 * 4 * n ** 3}
-
-    # roofline of the dominant kernel (algorithmic bytes / event-timed duration in the timed region)
+    # roofline of the dominant kernel: algorithmic bytes / event-timed duration of its launches
+    # inside the timed steps
     peak, peak_kind = measured_peaks()
-    d = prof[dom]
-    achieved = d["timed_bytes"] / (d["ms"] / 1000.0) / 1e9 if d["ms"] > 0 else 0.0
-    kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
-                   "gbs": round(v["timed_bytes"] / (v["ms"] / 1000.0) / 1e9, 1) if v["ms"] > 0 else None}
-               for k, v in prof_all.items() if v["launches"]}
-    evals = [i["iters"] + 1 for i in infos]
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+    achieved = roof["timed_bytes"] / (roof["ms"] / 1000.0) / 1e9 if roof["ms"] > 0 else 0.0
+    ev_t = [infos[i]["iters"] + 1 for i in idx]
+    ev_all = [x["iters"] + 1 for x in infos]
+    kernels = None
+    if prof_all is not None:
+        kernels = {}
+        for k, v in prof_all.items():
+            if not v["launches"]:
+                continue
+            gbs = v["timed_bytes"] / (v["ms"] / 1000.0) / 1e9 if v["ms"] > 0 else None
+            kernels[k] = {"launches": v["launches"], "ms": round(v["ms"], 3),
+                          "ms_per_step": round(v["ms"] / R, 4), "gbs": round(gbs, 1) if gbs else None,
+                          "frac_of_peak": round(gbs / peak, 3) if gbs else None}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"mixed": "f32+eft", "mixed-fp64": "f32+f64", "fp32": "f32"}[args.precision],
             "data": "synthetic", "config": config(world, args.precision, args.sort_every),
+            "timing": {"how": "the whole %d-step run (a = %g -> %g) runs every time; the K = %d timed steps are the "
+                              "middle step of each of K equal strata of the run, each bracketed by a device "
+                              "synchronisation (and a barrier for N > 1) and CUDA events on the context's "
+                              "stream, with the relaxation iterations replayed as CUDA graphs"
+                              % (R, sched[0], sched[R], K),
+                       "timed_step_indices": idx, "timed_a_range": [sched[idx[0]], sched[idx[-1] + 1]],
+                       "full_run": {"steps": R, "ms": full_ms, "steps_per_s": R / (full_ms / 1000.0),
+                                    "note": "the same pass end to end, including the K synchronisations"}},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": recorded_traffic(dom), "kernel": dom,
-                         "algorithmic_bytes_per_launch": round(d["timed_bytes"] / max(d["timed"], 1)),
+                         "launches_timed": roof["timed"],
+                         "algorithmic_bytes_per_launch": round(roof["timed_bytes"] / max(roof["timed"], 1)),
+                         "how": "launches of this kind outside CUDA graphs inside the timed steps (the first "
+                                "iteration of each solve), CUDA events on the launch stream",
                          "traffic_unit": "bytes per launch (ncu DRAM read + write)",
                          "peak_source": peak_kind},
-            "e2e": e2e, "gpu_launches": int(sum(v["launches"] for v in prof.values())),
+            "gpu_launches": int(sum(launches)),
             "clocks": clk.summary(),
-            "solver": {"evals_per_solve_mean": sum(evals) / len(evals), "max_evals": max(evals),
-                       "final_a": sched[args.steps],
-                       "not_converged_steps": sum(1 for i in infos if i["status"] != 0),
-                       "max_norm_res": max(i["norm_res"] for i in infos), "amplitude_A": amp},
-            "kernels": kernels, "tiles": dgp.dgp_tile_config(ctx),
-            "kernels_note": "per-kind event times from a separate pass of the same run with every launch "
-                            "bracketed by events; the timed region brackets only the dominant kind"}
-    # the same run under the other precisions (same accuracy target): steps/s,
-    # evaluations and P(k) of the end state relative to this run's
+            "solver": {"evals_per_solve_timed_steps": sum(ev_t) / len(ev_t),
+                       "evals_per_solve_run": sum(ev_all) / len(ev_all), "max_evals": max(ev_all),
+                       "final_a": sched[R], "not_converged_steps": sum(1 for i in infos if i["status"] != 0),
+                       "max_norm_res": max(i["norm_res"] for i in infos), "amplitude_A": amp,
+                       "evals_per_step": ev_all},
+            "tiles": dgp.dgp_tile_config(ctx)}
+    if kernels is not None:
+        line["kernels"] = kernels
+        line["kernels_note"] = ("per-kind event times over the whole run from a separate pass with every launch "
+                                "bracketed by events (graph replay off); frac_of_peak against the measured "
+                                "copy bandwidth")
+
+    # end to end through the public C ABI with host buffers (copies inside the timed steps)
+    if not args.no_e2e:
+        host = [torch.empty(n ** 3, dtype=torch.float32, pin_memory=True) for _ in range(6)]
+        for h, s0 in zip(host, ic):
+            h.copy_(s0)
+        hparts = dgp.particles(*[h.numpy() for h in host])
+        dgp.dgp_reset(ctx)
+        torch.cuda.synchronize()
+        te = []
+        t_all = time.perf_counter()
+        for i in range(R):
+            if i in sel:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                dgp.pm_step_host(ctx, hparts, sched[i], sched[i + 1] - sched[i])
+                te.append(time.perf_counter() - t0)
+            else:
+                dgp.pm_step_host(ctx, hparts, sched[i], sched[i + 1] - sched[i])
+        t_all = time.perf_counter() - t_all
+        line["e2e"] = {"value": world * K / max_over_ranks(sum(te), dist, dev), "unit": UNIT,
+                       "h2d_bytes_per_step": 6 * 4 * n ** 3, "d2h_bytes_per_step": 6 * 4 * n ** 3,
+                       "how": "pm_step_host on pinned host arrays over the whole run, the same K steps timed "
+                              "with the host clock (each call returns after its copies back)",
+                       "full_run_steps_per_s": R / t_all}
+
+    # the same run under the other precisions (same accuracy target): steps/s over the same timed
+    # steps, evaluations and P(k) of the end state relative to this run's
     if rank == 0 and not args.no_compare:
         def end_pk(c):
             dl = torch.empty((n, n, n), dtype=torch.float32, device=dev)
             dgp.dgp_deposit(c, parts, dl)
             return dgp.power_spectrum(c, dl, n // 2)[1]
+        restart(ctx)
+        run(ctx)
         pk_main = end_pk(ctx)
         delta_end = torch.empty((n, n, n), dtype=torch.float32, device=dev)
         dgp.dgp_deposit(ctx, parts, delta_end)
+        torch.cuda.synchronize()
         comp = {}
         for name in sorted(pcode):
             if name == args.precision:
-                comp[name] = {"value": value, "evals_per_solve_mean": sum(evals) / len(evals)}
+                comp[name] = {"value": value, "evals_per_solve_timed_steps": sum(ev_t) / len(ev_t),
+                              "precision": PRECISION_DESC[name]}
                 continue
-            c2 = dgp.dgp_init(box, n, WL["rc_H0"], WL["omega_m0"], w=WL["w"], precision=pcode[name],
-                              max_iter=WL["max_iter"], tol=WL["tol"], sort_every=args.sort_every)
-            for cc, s0 in zip(cur, ic):
-                cc.copy_(s0)
-            infs = []
-            torch.cuda.synchronize()
-            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            f0.record(stream)
-            for i in range(args.steps):
-                infs.append(dgp.pm_step(c2, parts, sched[i], sched[i + 1] - sched[i]))
-            f1.record(stream)
-            torch.cuda.synchronize()
-            pk2 = end_pk(c2)
-            comp[name] = {"value": args.steps / (f0.elapsed_time(f1) / 1000.0),
-                          "evals_per_solve_mean": sum(i["iters"] + 1 for i in infs) / len(infs),
-                          "pk_max_rel_diff_vs_main": float(np.max(np.abs(pk2 / pk_main - 1)))}
-            dgp.dgp_destroy(c2)
+            c2 = make_ctx(name)
+            try:
+                restart(c2)
+                t2, inf2 = [], []
+                run(c2, R, inf2, t2)
+                comp[name] = {"value": K / (sum(t2) / 1000.0),
+                              "evals_per_solve_timed_steps": sum(inf2[i]["iters"] + 1 for i in idx) / K,
+                              "pk_max_rel_diff_vs_main": float(np.max(np.abs(end_pk(c2) / pk_main - 1))),
+                              "precision": PRECISION_DESC[name]}
+            finally:
+                dgp.dgp_destroy(c2)
         line["precision_comparison"] = comp
+        if "mixed-fp64" in comp and args.precision != "mixed-fp64":
+            line["fp64_pipe_variant"] = {"value": comp["mixed-fp64"]["value"], "unit": UNIT,
+                                         "precision": PRECISION_DESC["mixed-fp64"]}
         if args.precision == "mixed":
             try:
-                line["fp64_path_error"] = fp64_path_error(dgp, torch, np, n, box, delta_end, sched[args.steps], sched,
-                                                          args.steps, pos, mom, pk_main, dev, args.sort_every)
+                line["fp64_path_error"] = fp64_path_error(dgp, torch, np, n, box, delta_end, sched[R], sched, pos,
+                                                          mom, pk_main, dev, args.sort_every, bs)
             except Exception as e:  # the comparison must not cost the measurement
                 line["fp64_path_error"] = {"unavailable": repr(e)[:200]}
     dgp.dgp_destroy(ctx)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ts = oracle_fft_sample_seconds(96)
-        t = sum(ts) / len(ts)
-        e_mean = sum(evals) / len(evals)
-        line["cpu_baseline"] = {
-            "value": oracle_steps_per_s(t, e_mean), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "96 axis passes of the FP64 oracle FFT over a quarter of the 256^3 field (%.3f s each); "
-                      "scaled to the FFT work of one PM step at the measured %.2f residual evaluations per "
-                      "solve (deposit, gather and pointwise work not counted: an upper bound)" % (t, e_mean)}
+        model = OracleStepModel(pos=pos)
+        model.time_all()
+        e_mean = sum(ev_t) / len(ev_t)
+        t_step = model.step_seconds(e_mean)
+        line["cpu_baseline"] = {"value": 1.0 / t_step, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+                                "sample": model.describe(e_mean)}
     if rank == 0:
         print(json.dumps(line))
     if dist:

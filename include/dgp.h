@@ -384,7 +384,13 @@ int pm_step(dgp_ctx *c, dgp_particles *parts, double a, double da, dgp_solve_inf
  * context's device buffers, steps, and copies them back before returning.
  * The positions are final after the drift, so their copy back runs on a
  * second stream during the field solve (overlapped when the host arrays are
- * pinned).  The host arrays are float or double per the context precision. */
+ * pinned).  The host arrays are float or double per the context precision.
+ * The force at the start is reused only when the previous call on this
+ * context was a pm_step_host that ended at the same a on the same host arrays
+ * (same host_parts->x pointer and n); stepping another set of host arrays, or
+ * a pm_step on device arrays in between, makes the step compute it afresh.
+ * The caller must not change the host arrays between two such calls unless it
+ * calls dgp_reset. */
 int pm_step_host(dgp_ctx *c, dgp_particles *host_parts, double a, double da, dgp_solve_info *info);
 
 /* Power spectrum of a device n^3 field (Sec. IV):
@@ -417,8 +423,9 @@ int bispectrum(dgp_ctx *c, const void *delta, double k1, double k2, int ntheta, 
  *   k, pk, nmodes: host outputs of length nbins (as power_spectrum);
  *   cuda_stream: stream for the work (NULL = legacy default); synchronised on return.
  * The first call on a device, with that device current, resolves the array's
- * device address and writes the twiddle tables into it (a synchronous copy);
- * make that first call before any stream capture.  Every call on a device uses
+ * device address and writes the twiddle tables into it (a copy on cuda_stream
+ * that completes before the call goes on); make that first call before any
+ * stream capture.  Every call on a device uses
  * the same array and overwrites it entirely, so calls that overlap on the GPU
  * (other streams, other host threads) race: serialise them.
  * Returns DGP_E_INVALID for n outside {16, 32, 64} (larger meshes do not fit
@@ -444,6 +451,14 @@ int dgp_profile(dgp_ctx *c, int timing);
  * kind_mask (bit k for kind k) are bracketed by events, so the timing of the
  * others is not perturbed by event records. */
 int dgp_profile_kinds(dgp_ctx *c, unsigned kind_mask);
+/* As dgp_profile_kinds, but the iterations of a solve keep running as CUDA
+ * graphs (dgp_profile and dgp_profile_kinds turn graph replay off), so the
+ * timed launches are those of the production path.  Only launches outside a
+ * graph that are certain to do their work are bracketed by events: the first
+ * relaxation iteration of each solve, replays of an earlier iterate, and every
+ * launch outside the iteration loop; their bytes are the full algorithmic
+ * bytes of one executed launch. */
+int dgp_profile_sampled(dgp_ctx *c, unsigned kind_mask);
 int dgp_profile_read(dgp_ctx *c, int kind, int64_t *launches, double *bytes, int64_t *timed, double *ms,
                      double *timed_bytes);
 /* Name of a kernel kind ("fft_z_r2c", "fft_y", "relax", ...), NULL if out of range. */

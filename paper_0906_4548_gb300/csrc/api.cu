@@ -184,6 +184,10 @@ static const char* const kKernelNames[KK_COUNT] = {
 
 struct Profiler {
   unsigned timing = 0;  // bit k: launches of kind k are bracketed by events
+  // sampled: CUDA-graph replay of the iterations stays on, and only launches
+  // outside graphs that are sure to do their work (the first iteration of a
+  // solve, replays, everything outside the iteration loop) are timed
+  bool sampled = false;
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
   std::vector<std::pair<int, double>> pending;  // (kind, bytes) per event pair
@@ -193,9 +197,10 @@ struct Profiler {
   int64_t timed[KK_COUNT] = {};
   double timed_bytes[KK_COUNT] = {};
 
-  void reset(unsigned t) {
+  void reset(unsigned t, bool smp = false) {
     resolve();
     timing = t;
+    sampled = smp;
     for (int k = 0; k < KK_COUNT; ++k) { launches[k] = 0; bytes[k] = 0; ms[k] = 0; timed[k] = 0; timed_bytes[k] = 0; }
   }
   cudaEvent_t ev() {
@@ -223,20 +228,27 @@ struct Profiler {
   // bytes of work that launches already counted (with 0 bytes) turned out to do
   void credit(int kind, double b) {
     bytes[kind] += b;
-    if ((timing >> kind) & 1u) timed_bytes[kind] += b;
+    if (((timing >> kind) & 1u) && !sampled) timed_bytes[kind] += b;
   }
   bool capturing = false;  // launches recorded into a graph are counted when the graph runs
   template <class F>
   void run(int kind, double b, cudaStream_t s, F&& f) {
+    run_it(kind, b, b, s, static_cast<F&&>(f));
+  }
+  // A launch of a relaxation iteration: b bytes are counted now (the rest is
+  // credited once the solve has stopped); sure_b >= 0 when the launch is sure
+  // to do its work (sure_b bytes), < 0 when it may return at entry.
+  template <class F>
+  void run_it(int kind, double b, double sure_b, cudaStream_t s, F&& f) {
     if (capturing) { f(); return; }
     launches[kind] += 1;
     bytes[kind] += b;
-    if (!((timing >> kind) & 1u)) { f(); return; }
+    if (!((timing >> kind) & 1u) || (sampled && sure_b < 0)) { f(); return; }
     if (pending.size() >= 8192) resolve();
     cudaEventRecord(ev(), s);
     f();
     cudaEventRecord(ev(), s);
-    pending.push_back({kind, b});
+    pending.push_back({kind, sampled ? sure_b : b});
   }
   ~Profiler() {
     for (auto e : pool) cudaEventDestroy(e);
@@ -334,6 +346,7 @@ class Engine : public EngineBase {
   double force_a = 0.0;
   const void* force_x = nullptr;
   int64_t force_np = -1;
+  const void* force_host = nullptr;  // pm_step_host: host x array of the state the forces belong to
   SolveCtl* d_ctl = nullptr;    // stop-rule state of the running solve
   SolveCtl* h_ctl = nullptr;    // pinned host copy
   double* d_hist = nullptr;     // [max_iter + 1] normalised residuals of the running solve
@@ -480,6 +493,7 @@ class Engine : public EngineBase {
     last_nl_a = -1.0;
     last_stop_it = -1;
     force_valid = false;
+    force_host = nullptr;
     nsteps = 0;
   }
 
@@ -640,24 +654,27 @@ class Engine : public EngineBase {
       auto enqueue = [&](int it, bool control) -> int {
         const int* sk = control ? skip : nullptr;
         const int ib = in_buf(it), ob = out_buf(it);
-        prof.run(KK_X_HESSIAN, 0, stream, [&] {
+        // the first iteration and replays always run; later ones may return at entry
+        const double sure = (it == 0 || !control) ? 1.0 : -1.0;
+        prof.run_it(KK_X_HESSIAN, 0, sure * 7 * SB, stream, [&] {
           launch_fft_x_op<T, N>(XOP_HESSIAN, spec_in(it), nullptr, fs(s6, 6), 0, kp, nullptr, 0, 0, 0, tw, stream,
                                 sk);
         });
-        prof.run(KK_Y, 0, stream, [&] { launch_fft_y<T, N>(fs(s6, 6), 6, true, tw, stream, sk, y_threads); });
-        prof.run(KK_RELAX, 0, stream, [&] {
+        prof.run_it(KK_Y, 0, sure * 12 * SB, stream,
+                    [&] { launch_fft_y<T, N>(fs(s6, 6), 6, true, tw, stream, sk, y_threads); });
+        prof.run_it(KK_RELAX, 0, sure * (7 * SB + 3 * RB), stream, [&] {
           launch_fused_relax<T, N>(arith, s6, rD[ib], d_rstats + 4 * ib + 1, rS, rD[ob], spec_out(it), rp, partials,
                                    tw, stream, sk);
         });
         // the iteration's statistics, and with control the stop rules, in one launch
-        prof.run(KK_REDUCE, 0, stream, [&] {
+        prof.run_it(KK_REDUCE, 0, sure * 32.0 * fblocks, stream, [&] {
           if (control)
             launch_finalize_control(partials, fblocks, d_rstats + 4 * ob, d_ctl, d_misc + 1, d_hist, p.max_iter,
                                     kPatience, tol, 1.0 / (double)M, stream, sk);
           else
             launch_finalize(partials, fblocks, 4, d_rstats + 4 * ob, stream, sk);
         });
-        prof.run(KK_Y, 0, stream, [&] {
+        prof.run_it(KK_Y, 0, sure * 2 * SB, stream, [&] {
           V* o[1] = {spec_out(it)};
           launch_fft_y<T, N>(fs(o, 1), 1, false, tw, stream, sk, y_threads);
         });
@@ -674,10 +691,10 @@ class Engine : public EngineBase {
       if ((rc = forward_zy(rD[j0], sD, ZPrologue{nullptr, 0.0, 0}))) return rc;
       DGP_CUDA(cudaMemsetAsync(d_ctl, 0, sizeof(SolveCtl), stream));
       // Iterations after the first run as a CUDA graph of two iterations (the
-      // buffers alternate with period two) unless launches are being timed.
+      // buffers alternate with period two) unless every launch is being timed.
       // (Stream capture is not available on the legacy default stream; a
       // capture that fails leaves the iterations to direct launches.)
-      bool graphs = prof.timing == 0 && stream != nullptr && stream != cudaStreamLegacy &&
+      bool graphs = (prof.timing == 0 || prof.sampled) && stream != nullptr && stream != cudaStreamLegacy &&
                     stream != cudaStreamPerThread;
       if (graphs) {
         cudaGraph_t g = nullptr;
@@ -897,6 +914,7 @@ class Engine : public EngineBase {
   }
 
   int step(dgp_particles* pp, double a, double da, dgp_solve_info* info) override {
+    force_host = nullptr;
     return step_impl(pp, a, da, info, nullptr);
   }
 
@@ -948,6 +966,10 @@ class Engine : public EngineBase {
     }
     void* src[6] = {hpp->x, hpp->y, hpp->z, hpp->px, hpp->py, hpp->pz};
     const size_t bytes = sizeof(T) * hpp->n;
+    // every host step runs on the same device copies, so the end-of-step force
+    // may be reused only for the host arrays that the previous host step wrote
+    if (force_host != hpp->x) force_valid = false;
+    force_host = nullptr;
     for (int i = 0; i < 6; ++i) DGP_CUDA(cudaMemcpyAsync(hp[i], src[i], bytes, cudaMemcpyHostToDevice, stream));
     dgp_particles dp{hp[0], hp[1], hp[2], hp[3], hp[4], hp[5], hpp->n};
     // the positions are final after the drift: copy them back while the field solve runs
@@ -966,6 +988,7 @@ class Engine : public EngineBase {
     for (int i = 3; i < 6; ++i) DGP_CUDA(cudaMemcpyAsync(src[i], hp[i], bytes, cudaMemcpyDeviceToHost, stream));
     DGP_CUDA(cudaStreamSynchronize(copy_stream));
     DGP_CUDA(wait_stream());
+    force_host = hpp->x;
     return DGP_OK;
   }
 
@@ -1596,6 +1619,12 @@ int dgp_profile(dgp_ctx* c, int timing) {
 int dgp_profile_kinds(dgp_ctx* c, unsigned kind_mask) {
   if (!c) return DGP_E_INVALID;
   c->eng->prof.reset(kind_mask & ((1u << dgp::KK_COUNT) - 1u));
+  return DGP_OK;
+}
+
+int dgp_profile_sampled(dgp_ctx* c, unsigned kind_mask) {
+  if (!c) return DGP_E_INVALID;
+  c->eng->prof.reset(kind_mask & ((1u << dgp::KK_COUNT) - 1u), true);
   return DGP_OK;
 }
 

@@ -4,7 +4,26 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 namespace dgp {
+
+// Raise the dynamic shared-memory limit of kernel K to `bytes` (its largest
+// launch) once per device.  Setting the attribute before every launch would
+// let one host thread lower it between another thread's set and launch; a
+// failure is returned and also left for the launch check that follows.
+template <auto K>
+inline cudaError_t raise_smem_limit(size_t bytes) {
+  static std::mutex mu;
+  static uint64_t done = 0;  // bit d: set on device d
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(mu);
+  if (dev < 64 && ((done >> dev) & 1u)) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && dev < 64) done |= 1ull << dev;
+  return e;
+}
 
 template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };

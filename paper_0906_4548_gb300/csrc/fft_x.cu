@@ -128,11 +128,15 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
   // shared memory so the output loop does not hold 2 * N2 extra registers
   T* s_inv = reinterpret_cast<T*>(s_T + N * TY);               // N2 * THREADS
   T* s_ikb = s_inv + N2 * XGeom<T, N>::THREADS;                // N2 * THREADS
-  double* s_bins = reinterpret_cast<double*>(s_ikb + N2 * XGeom<T, N>::THREADS);
-  load_twiddles(s_tw, g_tw, N);
+  // P(k) operations (which use neither table): per-warp shell sums
+  // [warp][NBS][nbins] and a per-warp staging row [warp][32][NBS]
+  constexpr int NW = XGeom<T, N>::THREADS / 32;
   constexpr int NBS = OP == XOP_PK_BRANE ? 4 : 3;  // sums per shell
+  double* s_bins = reinterpret_cast<double*>(s_inv);
+  double* s_stage = s_bins + NW * NBS * args.nbins;
+  load_twiddles(s_tw, g_tw, N);
   if (OP == XOP_PK || OP == XOP_PK_BRANE)
-    for (int i = threadIdx.x; i < NBS * args.nbins; i += blockDim.x) s_bins[i] = 0.0;
+    for (int i = threadIdx.x; i < NW * NBS * args.nbins; i += blockDim.x) s_bins[i] = 0.0;
   const int yl = threadIdx.x % TY;
   const int lane = threadIdx.x / TY;
   const int kz = blockIdx.y;
@@ -151,27 +155,52 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
   if (OP == XOP_PHI_FORCE && kp.gravity == 0) x_forward<T, N>(args.in1, kz, ky0, lane, yl, s_T, s_tw, X1);
 
   if (OP == XOP_PK || OP == XOP_PK_BRANE) {
+    // Shell sums in a fixed order, so that P(k) is the same bits on every run:
+    // per register slot, the lanes of a warp that fall in one shell are summed
+    // by the lowest of them in lane order into that warp's own shell row (the
+    // shells of different groups differ, so no two lanes write one address);
+    // the warps' rows are then added in warp order.
     const double norm = kp.box * kp.box * kp.box * kp.inv_m * kp.inv_m;
     const double w = (kz == 0 || kz == N / 2) ? 1.0 : 2.0;
+    const int wl = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double* wbins = s_bins + wid * NBS * args.nbins;
+    double* stage = s_stage + wid * 32 * NBS;
+    __syncthreads();  // the bins are zeroed
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) {
       const int nx = signed_index(lane + N1 * k2, N);
       const int n2 = nx * nx + ny * ny + nz * nz;
-      if (n2 == 0) continue;
       const double nm = sqrt((double)n2);
-      const int b = (int)floor(nm + 0.5);
-      if (b >= 1 && b <= args.nbins) {
-        const double p = ((double)X0[k2].x * X0[k2].x + (double)X0[k2].y * X0[k2].y) * norm;
-        atomicAdd(&s_bins[b - 1], w);
-        atomicAdd(&s_bins[args.nbins + b - 1], w * nm * (2.0 * M_PI / kp.box));
-        atomicAdd(&s_bins[2 * args.nbins + b - 1], w * p);
-        if (OP == XOP_PK_BRANE) atomicAdd(&s_bins[3 * args.nbins + b - 1], w * p / ((double)n2 * (double)n2));
+      int b = (int)floor(nm + 0.5);
+      if (n2 == 0 || b < 1 || b > args.nbins) b = 0;
+      const double p = ((double)X0[k2].x * X0[k2].x + (double)X0[k2].y * X0[k2].y) * norm;
+      stage[wl * NBS + 0] = w;
+      stage[wl * NBS + 1] = w * nm * (2.0 * M_PI / kp.box);
+      stage[wl * NBS + 2] = w * p;
+      if (OP == XOP_PK_BRANE) stage[wl * NBS + 3] = n2 ? w * p / ((double)n2 * (double)n2) : 0.0;
+      const unsigned group = __match_any_sync(0xffffffffu, b);
+      __syncwarp();
+      if (b != 0 && wl == __ffs(group) - 1) {
+        double acc[NBS];
+#pragma unroll
+        for (int c = 0; c < NBS; ++c) acc[c] = 0.0;
+        for (unsigned g = group; g; g &= g - 1) {
+          const int l = __ffs(g) - 1;
+#pragma unroll
+          for (int c = 0; c < NBS; ++c) acc[c] += stage[l * NBS + c];
+        }
+#pragma unroll
+        for (int c = 0; c < NBS; ++c) wbins[c * args.nbins + b - 1] += acc[c];
       }
+      __syncwarp();
     }
     __syncthreads();
     const int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
-    for (int i = threadIdx.x; i < NBS * args.nbins; i += blockDim.x)
-      args.pk_partials[blk * NBS * args.nbins + i] = s_bins[i];
+    for (int i = threadIdx.x; i < NBS * args.nbins; i += blockDim.x) {
+      double t = 0.0;
+      for (int v = 0; v < NW; ++v) t += s_bins[v * NBS * args.nbins + i];
+      args.pk_partials[blk * NBS * args.nbins + i] = t;
+    }
     return;
   }
 
@@ -500,10 +529,15 @@ template <typename T, int N> int x_pass_blocks() { return (N / XGeom<T, N>::TY) 
 template <typename T, int N, int OP>
 static void launch_x(const XArgs<T>& a, const vec2_t<T>* tw, cudaStream_t s) {
   using G = XGeom<T, N>;
-  const size_t smem = sizeof(vec2_t<T>) * (kTwiddleTables * N + (size_t)N * G::TY) +
-                      sizeof(T) * 2 * Split<N>::N2 * G::THREADS + (OP == XOP_PK ? sizeof(double) * 3 * a.nbins : 0) +
-                      (OP == XOP_PK_BRANE ? sizeof(double) * 4 * a.nbins : 0);
-  cudaFuncSetAttribute(k_fft_x<T, N, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the P(k) operations put their per-warp shell sums where the others keep
+  // their per-thread multiplier tables
+  constexpr bool PK = OP == XOP_PK || OP == XOP_PK_BRANE;
+  constexpr int NBS = OP == XOP_PK_BRANE ? 4 : 3, NW = G::THREADS / 32;
+  const size_t base = sizeof(vec2_t<T>) * (kTwiddleTables * N + (size_t)N * G::TY);
+  const size_t tables = PK ? sizeof(double) * NW * 32 * NBS : sizeof(T) * 2 * Split<N>::N2 * G::THREADS;
+  const size_t per_bin = PK ? sizeof(double) * NW * NBS : 0;
+  const size_t smem = base + tables + per_bin * a.nbins;
+  raise_smem_limit<k_fft_x<T, N, OP>>(base + tables + per_bin * (N / 2));
   dim3 grid(N / G::TY, N / 2 + 1);
   k_fft_x<T, N, OP><<<grid, G::THREADS, smem, s>>>(a, tw);
 }

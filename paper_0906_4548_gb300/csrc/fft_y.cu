@@ -65,10 +65,10 @@ static void launch_y(const FieldSet<T>& f, int nfields, bool inverse, const vec2
   const size_t smem = sizeof(V) * (kTwiddleTables * N + P * N1 * (N2 + 1));
   dim3 grid((unsigned)((npencils + P - 1) / P), (unsigned)nfields);
   if (inverse) {
-    cudaFuncSetAttribute(k_fft_y<T, N, true, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    raise_smem_limit<k_fft_y<T, N, true, B>>(smem);
     k_fft_y<T, N, true, B><<<grid, B, smem, s>>>(f, npencils, tw, skip);
   } else {
-    cudaFuncSetAttribute(k_fft_y<T, N, false, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    raise_smem_limit<k_fft_y<T, N, false, B>>(smem);
     k_fft_y<T, N, false, B><<<grid, B, smem, s>>>(f, npencils, tw, skip);
   }
 }

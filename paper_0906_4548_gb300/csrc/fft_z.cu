@@ -183,7 +183,7 @@ void launch_fft_z_r2c(const T* in, int64_t in_stride, vec2_t<T>* out, int64_t ou
                       ZPrologue pro, const vec2_t<T>* tw, cudaStream_t s) {
   using G = ZGeom<T, N>;
   const size_t smem = r2c_smem<T, N>();
-  cudaFuncSetAttribute(k_fft_z_r2c<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit<k_fft_z_r2c<T, N>>(smem);
   dim3 grid(N / G::TY, N, nfields);
   k_fft_z_r2c<T, N><<<grid, G::THREADS, smem, s>>>(in, in_stride, out, out_stride, pro, tw);
 }
@@ -195,7 +195,7 @@ void launch_fft_z_c2r(const FieldSet<T>& in, T* const* out, int nfields, const v
   FieldSet<T> o;
   for (int i = 0; i < kMaxFields; ++i) o.p[i] = i < nfields ? reinterpret_cast<vec2_t<T>*>(out[i]) : nullptr;
   const size_t smem = c2r_smem<T, N>();
-  cudaFuncSetAttribute(k_fft_z_c2r<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit<k_fft_z_c2r<T, N>>(smem);
   dim3 grid(N / G::TY, N, nfields);
   k_fft_z_c2r<T, N><<<grid, G::THREADS, smem, s>>>(in, o, tw);
 }

@@ -488,7 +488,7 @@ template <typename T, int N, class AR>
 static void launch_f(const FusedArgs<T>& a, const vec2_t<T>* tw, cudaStream_t s) {
   using G = FGeom<T, N>;
   const size_t smem = sizeof(vec2_t<T>) * (kTwiddleTables * N + 2 * G::GSZ + G::TSZ);
-  cudaFuncSetAttribute(k_fused_relax<T, N, AR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit<k_fused_relax<T, N, AR>>(smem);
   dim3 grid(N / G::TY, N);
   k_fused_relax<T, N, AR><<<grid, G::THREADS, smem, s>>>(a, tw);
 }

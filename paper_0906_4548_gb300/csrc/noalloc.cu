@@ -63,8 +63,10 @@ void twiddles(float2* out) {
 }
 
 // Once per device, with that device current: resolve the device address of
-// the scratch array and write the twiddle tables into it.
-int setup(int dev, unsigned char** out) {
+// the scratch array and write the twiddle tables into it.  The copy is ordered
+// on the caller's stream and completed before the address is published, so no
+// later call (on any stream) can read half-written tables.
+int setup(int dev, cudaStream_t s, unsigned char** out) {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
   if (g_scratch_ptr[dev]) {
     *out = g_scratch_ptr[dev];
@@ -76,8 +78,10 @@ int setup(int dev, unsigned char** out) {
   twiddles<16>(tw.data());
   twiddles<32>(tw.data() + 3 * kMaxN);
   twiddles<64>(tw.data() + 6 * kMaxN);
-  if (cudaMemcpy(ptr + kOffTw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+  if (cudaMemcpyAsync(ptr + kOffTw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice, s) !=
+      cudaSuccess)
     return DGP_E_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return DGP_E_CUDA;
   g_scratch_ptr[dev] = ptr;
   *out = ptr;
   return DGP_OK;
@@ -122,11 +126,11 @@ extern "C" int dgp_power_spectrum_noalloc(const float* delta, int n, double box,
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return DGP_E_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return DGP_E_INVALID;
+  const cudaStream_t s = (cudaStream_t)cuda_stream;
   unsigned char* scratch = nullptr;
-  int rc = setup(dev, &scratch);
+  int rc = setup(dev, s, &scratch);
   if (rc != DGP_OK) return rc;
   double hb[3 * kMaxBins];
-  const cudaStream_t s = (cudaStream_t)cuda_stream;
   if (n == 16) rc = run<16>(delta, box, nbins, scratch, s, hb);
   else if (n == 32) rc = run<32>(delta, box, nbins, scratch, s, hb);
   else rc = run<64>(delta, box, nbins, scratch, s, hb);

@@ -27,7 +27,7 @@ EXPORTED = ["dgp_background", "dgp_init", "dgp_destroy", "dgp_strerror", "dgp_re
             "dgp_solve_adjoint", "pm_step_adjoint", "dgp_zeldovich", "dgp_zeldovich_adjoint",
             "dgp_power_spectrum_adjoint", "dgp_tile_config", "dgp_set_tile_config",
             "dgp_solve_adjoint_rc", "pm_step_adjoint_rc", "dgp_zeldovich_vf_adjoint", "dgp_velocity_factor",
-            "dgp_workspace_size", "dgp_time_factors", "dgp_background_drc"]
+            "dgp_workspace_size", "dgp_time_factors", "dgp_background_drc", "dgp_profile_sampled"]
 DGP_NOALLOC_MAX_N = 64
 DGP_KERNEL_KINDS = 11
 
@@ -97,6 +97,7 @@ def _load():
         "bispectrum": (i, [vp, vp, d, d, i, P(d), d, P(d), P(d)]),
         "dgp_profile": (i, [vp, i]),
         "dgp_profile_kinds": (i, [vp, ctypes.c_uint]),
+        "dgp_profile_sampled": (i, [vp, ctypes.c_uint]),
         "dgp_profile_read": (i, [vp, i, P(i64), P(d), P(i64), P(d), P(d)]),
         "dgp_kernel_name": (ctypes.c_char_p, [i]),
         "dgp_power_spectrum_noalloc": (i, [vp, i, d, i, P(d), P(d), P(i64), vp]),
@@ -417,6 +418,16 @@ def dgp_profile(ctx, timing, kinds=None):
     for kname in kinds:
         mask |= 1 << names.index(kname)
     _check(lib.dgp_profile_kinds(ctx, mask), "dgp_profile_kinds")
+
+
+def dgp_profile_sampled(ctx, kinds):
+    """Reset the kernel counters and time, with graph replay kept on, the launches of the named kinds
+    that run outside graphs and are sure to do their work (see dgp.h)."""
+    names = [lib.dgp_kernel_name(k).decode() for k in range(DGP_KERNEL_KINDS)]
+    mask = 0
+    for kname in kinds:
+        mask |= 1 << names.index(kname)
+    _check(lib.dgp_profile_sampled(ctx, mask), "dgp_profile_sampled")
 
 
 def dgp_profile_read(ctx):

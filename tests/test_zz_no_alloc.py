@@ -6,11 +6,19 @@ it runs.  They cannot create a dgp context (dgp_init allocates its workspace),
 so dgp_power_spectrum_noalloc computes P(k) of a small mesh field with all its
 temporaries in a fixed device array that is part of the library.  This file
 checks, through the C ABI, that two calls in a row give the same result as the
-ordinary power_spectrum entry point, and that a mesh too large for the fixed
-array is refused.  It is named to run after every other test module.
+ordinary power_spectrum entry point, that a mesh too large for the fixed
+array is refused, and that the first call of a fresh process, made from a
+side stream, already gives the oracle's P(k).  It is named to run after every
+other test module.
 """
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 pytestmark = pytest.mark.gpu
 
@@ -54,3 +62,32 @@ def test_noalloc_rejects_a_mesh_larger_than_its_array(env):
     with pytest.raises(dgp.DgpError) as e:
         dgp.dgp_power_spectrum_noalloc(d, n, 100.0, 4)
     assert e.value.status == dgp.DGP_E_INVALID
+
+
+_FIRST_CALL_ON_SIDE_STREAM = r"""
+import numpy as np, torch
+from paper_0906_4548_gb300 import dgp
+from oracle import estimators as oest
+n, box, nbins = 64, 150.0, 32
+f = np.random.default_rng(9).standard_normal((n, n, n)).astype(np.float32)
+d = torch.tensor(f, device="cuda:0")
+torch.cuda.synchronize()
+s = torch.cuda.Stream()
+k, P, c = dgp.dgp_power_spectrum_noalloc(d, n, box, nbins, stream=s.cuda_stream)
+k2, P2, c2 = dgp.dgp_power_spectrum_noalloc(d, n, box, nbins, stream=s.cuda_stream)
+ko, Po, co = oest.power_spectrum(f.astype(np.float64), box, nbins)
+assert np.array_equal(c, co), (c, co)
+assert np.allclose(k, ko, rtol=1e-12)
+assert np.max(np.abs(P / Po - 1)) < 2e-6, np.max(np.abs(P / Po - 1))
+assert np.array_equal(P, P2) and np.array_equal(k, k2) and np.array_equal(c, c2)
+print("ok")
+"""
+
+
+def test_noalloc_first_call_from_a_side_stream_matches_the_oracle(env):
+    """The first call of a process sets the array up (its twiddle tables are copied in).  Made from
+    a non-blocking side stream, in a fresh process, it must already give the oracle's P(k), and a
+    second call the same bits."""
+    r = subprocess.run([sys.executable, "-c", _FIRST_CALL_ON_SIDE_STREAM], cwd=ROOT, capture_output=True,
+                       text=True, timeout=900, env=dict(os.environ, PYTHONPATH=ROOT))
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout[-2000:] + r.stderr[-2000:]

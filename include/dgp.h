@@ -310,6 +310,16 @@ int dgp_workspace_size(const dgp_params *p, int64_t np, dgp_workspace *out);
 int dgp_tile_config(dgp_ctx *c, int *y_threads);
 int dgp_set_tile_config(dgp_ctx *c, int y_threads);
 
+/* Bound of the waits inside the relaxation kernel (not part of the paper's
+ * method).  The FP32-data relaxation pass waits on its own asynchronous tile
+ * copies; each wait gives up after `seconds` (default 2; 0 < seconds <= 60),
+ * and the solve then returns DGP_E_TIMEOUT with the context still usable (the
+ * warm start is left as it was before the solve).  withhold_first_copy != 0 is
+ * a test hook: the pass leaves the first of its copies unissued, so its first
+ * wait runs out; set it back to 0 to solve again.  DGP_E_INVALID for a NULL
+ * context or a bound out of range. */
+int dgp_set_wait_limit(dgp_ctx *c, double seconds, int withhold_first_copy);
+
 /* Host waits of the context (the relaxation's stop-rule verdicts, host outputs)
  * block on an event and yield the CPU (on != 0) instead of spinning (0, the
  * default).  For callers that drive many contexts from many host threads. */

@@ -286,6 +286,8 @@ class EngineBase {
   std::vector<double> history;  // normalised residual of each iterate of the last solve
   cudaEvent_t sync_event = nullptr;  // set: host waits block on this event instead of spinning
   int y_threads = 256;          // y-pass CTA size, chosen at init by timing (tile autotuning)
+  unsigned long long wait_ns = 2000000000ull;  // bound of every in-kernel wait
+  int withhold = 0;             // test hook: the relaxation pass leaves its first copy unissued
 
   // Host wait for the work enqueued so far on the context's stream.
   cudaError_t wait_stream() {
@@ -347,6 +349,7 @@ class Engine : public EngineBase {
   const void* force_x = nullptr;
   int64_t force_np = -1;
   const void* force_host = nullptr;  // pm_step_host: host x array of the state the forces belong to
+  RelaxMaps rmaps;              // tensor maps of s6[0..5] for the FP32 relaxation pass
   SolveCtl* d_ctl = nullptr;    // stop-rule state of the running solve
   SolveCtl* h_ctl = nullptr;    // pinned host copy
   double* d_hist = nullptr;     // [max_iter + 1] normalised residuals of the running solve
@@ -417,7 +420,12 @@ class Engine : public EngineBase {
     if (cudaMalloc(&sD2, sb) != cudaSuccess) return DGP_E_NOMEM;
     if (cudaMalloc(&sDelta, sb) != cudaSuccess) return DGP_E_NOMEM;
     nblocks = num_sms() * 4;
-    fblocks = fused_relax_blocks<T, N>();
+    if constexpr (sizeof(T) == 4) {
+      if (relax_maps<N>(s6, &rmaps) != 0) return DGP_E_CUDA;
+      fblocks = relax_tma_blocks<N>();
+    } else {
+      fblocks = fused_relax_blocks<T, N>();
+    }
     const int pblocks = fblocks > nblocks ? fblocks : nblocks;
     if (cudaMalloc(&partials, sizeof(double) * 4 * pblocks) != cudaSuccess) return DGP_E_NOMEM;
     if (cudaMalloc(&d_rstats, sizeof(double) * 12) != cudaSuccess) return DGP_E_NOMEM;
@@ -663,8 +671,12 @@ class Engine : public EngineBase {
         prof.run_it(KK_Y, 0, sure * 12 * SB, stream,
                     [&] { launch_fft_y<T, N>(fs(s6, 6), 6, true, tw, stream, sk, y_threads); });
         prof.run_it(KK_RELAX, 0, sure * (7 * SB + 3 * RB), stream, [&] {
-          launch_fused_relax<T, N>(arith, s6, rD[ib], d_rstats + 4 * ib + 1, rS, rD[ob], spec_out(it), rp, partials,
-                                   tw, stream, sk);
+          if constexpr (sizeof(T) == 4)
+            launch_relax_tma<N>(arith, rmaps, rD[ib], d_rstats + 4 * ib + 1, rS, rD[ob], spec_out(it), rp, partials,
+                                tw, stream, sk, &d_ctl->fault, wait_ns, withhold);
+          else
+            launch_fused_relax<T, N>(arith, s6, rD[ib], d_rstats + 4 * ib + 1, rS, rD[ob], spec_out(it), rp,
+                                     partials, tw, stream, sk);
         });
         // the iteration's statistics, and with control the stop rules, in one launch
         prof.run_it(KK_REDUCE, 0, sure * 32.0 * fblocks, stream, [&] {
@@ -758,6 +770,7 @@ class Engine : public EngineBase {
       history.assign(s_it + 1, 0.0);
       DGP_CUDA(cudaMemcpyAsync(history.data(), d_hist, sizeof(double) * (s_it + 1), cudaMemcpyDeviceToHost, stream));
       DGP_CUDA(wait_stream());
+      if (st.status == CTL_FAULT) return DGP_E_TIMEOUT;
       if (st.status == CTL_NONFINITE) return DGP_E_NONFINITE;
       last_stop_it = s_it;
       inf.eps = st.eps;
@@ -778,6 +791,11 @@ class Engine : public EngineBase {
         accepted = in_buf(best_it);
         if ((rc = forward_zy(rD[accepted], sD, ZPrologue{nullptr, 0.0, 0}))) return rc;
         sDphi = sD;
+        if (best_it > 0) {  // the replayed iterations' waits
+          DGP_CUDA(cudaMemcpyAsync(h_ctl, d_ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, stream));
+          DGP_CUDA(wait_stream());
+          if (h_ctl->fault) return DGP_E_TIMEOUT;
+        }
       }
       inf.iters = best_it;
       inf.norm_res = st.rbest;
@@ -1467,7 +1485,10 @@ static void workspace_bytes(int max_iter, int64_t np, dgp_workspace* w) {
   using V = vec2_t<T>;
   const size_t M = (size_t)N * N * N, SPEC = (size_t)(N / 2 + 1) * N * N;
   const size_t rb = sizeof(T) * M, sb = sizeof(V) * SPEC, pn = (size_t)np;
-  const size_t nb = (size_t)num_sms() * 4, fb = (size_t)fused_relax_blocks<T, N>();
+  const size_t nb = (size_t)num_sms() * 4;
+  size_t fb;
+  if constexpr (sizeof(T) == 4) fb = (size_t)relax_tma_blocks<N>();
+  else fb = (size_t)fused_relax_blocks<T, N>();
   const size_t pblocks = fb > nb ? fb : nb;
   w->base = 14 * rb + 9 * sb + sizeof(double) * 4 * pblocks + sizeof(double) * (12 + 8) + sizeof(SolveCtl) +
             sizeof(double) * ((size_t)max_iter + 1) + sizeof(double) * 4 * (N / 2) * (size_t)x_pass_blocks<T, N>() +
@@ -1619,6 +1640,13 @@ int dgp_profile(dgp_ctx* c, int timing) {
 int dgp_profile_kinds(dgp_ctx* c, unsigned kind_mask) {
   if (!c) return DGP_E_INVALID;
   c->eng->prof.reset(kind_mask & ((1u << dgp::KK_COUNT) - 1u));
+  return DGP_OK;
+}
+
+int dgp_set_wait_limit(dgp_ctx* c, double seconds, int withhold_first_copy) {
+  if (!c || !(seconds > 0.0) || !(seconds <= 60.0)) return DGP_E_INVALID;
+  c->eng->wait_ns = (unsigned long long)(seconds * 1e9);
+  c->eng->withhold = withhold_first_copy ? 1 : 0;
   return DGP_OK;
 }
 

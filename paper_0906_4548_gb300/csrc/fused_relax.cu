@@ -1,4 +1,5 @@
-// Fused z pass of one relaxation iteration (Secs. III.B-C).
+// Fused z pass of one relaxation iteration for FP64 mesh data (Secs. III.B-C);
+// FP32 mesh data take relax_tma.cu.
 //
 // A CTA owns TY consecutive rows (x, y0..y0+TY-1) of the mesh.  It
 //   1. inverse-transforms along z the six y-inverted spectra H_xx, H_yy, H_xy,
@@ -20,8 +21,6 @@
 // B' and Delta are formed with the identities
 //        B' = d ((1 - w) d + alpha) - R,  Delta = (alpha + 2 (1 - w) d)^2 - 4 (1 - w) R,
 // so Delta has no cancellation except where it is genuinely near zero.
-// Arithmetic of q, R, B' and Delta (policy AR): FP32; pairs of floats with
-// error-free transformations (Knuth TwoSum, FMA TwoProd; about 48 bits); or FP64.
 // The six spectra arrive as three field pairs; the next pair's tile is copied
 // to shared memory with cp.async while the current pair is transformed.
 #include <math.h>
@@ -34,104 +33,8 @@
 namespace dgp {
 
 // ---------------------------------------------------------------- arithmetic
-struct FP {
-  float hi, lo;
-};
-__device__ __forceinline__ FP fp_two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  return FP{s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ FP fp_fast(float a, float b) {
-  const float s = a + b;
-  return FP{s, b - (s - a)};
-}
-__device__ __forceinline__ FP fp_prod(float a, float b) {
-  const float p = a * b;
-  return FP{p, fmaf(a, b, -p)};
-}
-// unnormalised accumulation: s.hi carries the running sum, s.lo the errors
-__device__ __forceinline__ void fp_acc(FP& s, FP t) {
-  const FP u = fp_two_sum(s.hi, t.hi);
-  s.hi = u.hi;
-  s.lo += u.lo + t.lo;
-}
-
-__device__ __forceinline__ FP pair_of(float x) { return FP{x, 0.f}; }
-__device__ __forceinline__ FP pair_of(FP x) { return x; }
-
-// Arithmetic policies.  d is the mean-free D at a point; q accumulates
-// sum_{i<j} (H_ij^2 - H_ii H_jj); R, B', Delta as in the file header.
-struct ArF32 {
-  using Acc = float;
-  __device__ static Acc d_of(float D, float m_hi, float, double) { return D - m_hi; }
-  __device__ static void q_init(Acc& q) { q = 0.f; }
-  __device__ static void q_add_sq(Acc& q, float x, float y) { q = fmaf(x, y, q); }
-  __device__ static void q_sub_d(Acc& q, Acc d, float x) { q = fmaf(-x, d, q); }
-  __device__ static Acc residual(Acc q, Acc d, float n, float s, const RelaxParams& rp) {
-    return fmaf(rp.alpha_hi, d, fmaf(rp.c2_hi, n, -s)) - 2.f * q;
-  }
-  __device__ static float bprime(Acc d, Acc R, const RelaxParams& rp) {
-    return d * fmaf(rp.omw, d, rp.alpha_hi) - R;
-  }
-  __device__ static float disc(Acc d, Acc R, const RelaxParams& rp, bool& neg) {
-    const float s = fmaf(rp.two_omw, d, rp.alpha_hi);
-    const float v = fmaf(s, s, -rp.four_omw_hi * R);
-    neg = v < 0.f;
-    return v;
-  }
-  __device__ static float to_f(Acc x) { return x; }
-  __device__ static void acc_abs(Acc& a, Acc x) { a += fabsf(x); }
-  __device__ static double to_d(Acc x) { return (double)x; }
-};
-
-struct ArEFT {
-  using Acc = FP;
-  __device__ static Acc d_of(float D, float m_hi, float m_lo, double) {
-    FP s = fp_two_sum(D, -m_hi);
-    s.lo -= m_lo;
-    return fp_fast(s.hi, s.lo);
-  }
-  __device__ static void q_init(Acc& q) { q = FP{0.f, 0.f}; }
-  __device__ static void q_add_sq(Acc& q, float x, float y) { fp_acc(q, fp_prod(x, y)); }
-  __device__ static void q_sub_d(Acc& q, Acc d, float x) {
-    FP p = fp_prod(-x, d.hi);
-    p.lo = fmaf(-x, d.lo, p.lo);
-    fp_acc(q, p);
-  }
-  __device__ static Acc residual(Acc q, Acc d, float n, float s, const RelaxParams& rp) {
-    FP r{-2.f * q.hi, -2.f * q.lo};
-    FP p = fp_prod(rp.alpha_hi, d.hi);
-    p.lo = fmaf(rp.alpha_hi, d.lo, fmaf(rp.alpha_lo, d.hi, p.lo));
-    fp_acc(r, p);
-    FP c = fp_prod(rp.c2_hi, n);
-    c.lo = fmaf(rp.c2_lo, n, c.lo);
-    fp_acc(r, c);
-    fp_acc(r, FP{-s, 0.f});
-    return fp_fast(r.hi, r.lo);
-  }
-  __device__ static float bprime(Acc d, Acc R, const RelaxParams& rp) {
-    const float u = fmaf(rp.omw, d.hi, rp.alpha_hi);
-    FP b = fp_prod(d.hi, u);
-    b.lo = fmaf(d.lo, u, b.lo);
-    fp_acc(b, FP{-R.hi, -R.lo});
-    return b.hi + b.lo;
-  }
-  __device__ static float disc(Acc d, Acc R, const RelaxParams& rp, bool& neg) {
-    const float s = fmaf(rp.two_omw, d.hi, rp.alpha_hi);
-    FP v = fp_prod(s, s);
-    FP t = fp_prod(-rp.four_omw_hi, R.hi);
-    t.lo = fmaf(-rp.four_omw_hi, R.lo, fmaf(-rp.four_omw_lo, R.hi, t.lo));
-    fp_acc(v, t);
-    v = fp_fast(v.hi, v.lo);
-    neg = v.hi < 0.f || (v.hi == 0.f && v.lo < 0.f);
-    return v.hi + v.lo;
-  }
-  __device__ static float to_f(Acc x) { return x.hi + x.lo; }
-  __device__ static void acc_abs(Acc& a, Acc x) { fp_acc(a, x.hi < 0.f ? FP{-x.hi, -x.lo} : x); }
-  __device__ static double to_d(Acc x) { return (double)x.hi + (double)x.lo; }
-};
-
+// Arithmetic of q, R, B' and Delta (FP64).  d is the mean-free D at a point;
+// q accumulates sum_{i<j} (H_ij^2 - H_ii H_jj); R, B', Delta as in the file header.
 struct ArF64 {
   using Acc = double;
   __device__ static Acc d_of(double D, float, float, double mean) { return D - mean; }
@@ -445,32 +348,16 @@ __global__ void __launch_bounds__(FGeom<T, N>::THREADS, 2)
       }
     }
   }
-  // block statistics: FP64 across warps; within a warp FP64 for FP64
-  // accumulators, otherwise float pairs (TwoSum) and integer counts
+  // block statistics in FP64
   __shared__ double s_part[4][32];
   const int wl = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if constexpr (std::is_same<Acc, double>::value || sizeof(T) == 8) {
+  {
     double v4[4] = {AR::to_d(acc_r), (double)acc_d, (double)nbad, (double)nonfin};
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v4[c] += __shfl_xor_sync(0xffffffffu, v4[c], o);
       if (wl == 0) s_part[c][wid] = v4[c];
-    }
-  } else {
-    FP r2 = pair_of(acc_r), d2{(float)acc_d, 0.f};
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      fp_acc(r2, FP{__shfl_xor_sync(0xffffffffu, r2.hi, o), __shfl_xor_sync(0xffffffffu, r2.lo, o)});
-      fp_acc(d2, FP{__shfl_xor_sync(0xffffffffu, d2.hi, o), __shfl_xor_sync(0xffffffffu, d2.lo, o)});
-    }
-    const unsigned nb = __reduce_add_sync(0xffffffffu, (unsigned)nbad);
-    const unsigned nf = __reduce_add_sync(0xffffffffu, (unsigned)nonfin);
-    if (wl == 0) {
-      s_part[0][wid] = (double)r2.hi + (double)r2.lo;
-      s_part[1][wid] = (double)d2.hi + (double)d2.lo;
-      s_part[2][wid] = (double)nb;
-      s_part[3][wid] = (double)nf;
     }
   }
   __syncthreads();
@@ -494,20 +381,15 @@ static void launch_f(const FusedArgs<T>& a, const vec2_t<T>* tw, cudaStream_t s)
 }
 
 template <typename T, int N>
-void launch_fused_relax(int arith, vec2_t<T>* const* spec6, const T* D, const double* dsum, const T* S, T* Dnew,
+void launch_fused_relax(int, vec2_t<T>* const* spec6, const T* D, const double* dsum, const T* S, T* Dnew,
                         vec2_t<T>* Snew, RelaxParams rp, double* partials, const vec2_t<T>* tw, cudaStream_t s,
                         const int* skip) {
+  static_assert(sizeof(T) == 8, "FP32 mesh data take launch_relax_tma");
   FusedArgs<T> a;
   a.skip = skip;
   for (int i = 0; i < 6; ++i) a.spec[i] = spec6[i];
   a.D = D; a.dsum = dsum; a.S = S; a.Dnew = Dnew; a.Snew = Snew; a.partials = partials; a.rp = rp;
-  if constexpr (sizeof(T) == 8) {
-    launch_f<T, N, ArF64>(a, tw, s);
-  } else {
-    if (arith == ARITH_F64) launch_f<T, N, ArF64>(a, tw, s);
-    else if (arith == ARITH_EFT) launch_f<T, N, ArEFT>(a, tw, s);
-    else launch_f<T, N, ArF32>(a, tw, s);
-  }
+  launch_f<T, N, ArF64>(a, tw, s);
 }
 
 #define DGP_INST_F(T, N)                                                                                    \
@@ -517,7 +399,6 @@ void launch_fused_relax(int arith, vec2_t<T>* const* spec6, const T* D, const do
   template int fused_relax_blocks<T, N>();
 #define DGP_INST_F_ALL(T) DGP_INST_F(T, 16) DGP_INST_F(T, 32) DGP_INST_F(T, 64) DGP_INST_F(T, 128) \
   DGP_INST_F(T, 256) DGP_INST_F(T, 512) DGP_INST_F(T, 48) DGP_INST_F(T, 96)
-DGP_INST_F_ALL(float)
 DGP_INST_F_ALL(double)
 
 }  // namespace dgp

@@ -10,6 +10,8 @@
 // last plane.
 #pragma once
 
+#include <cuda.h>
+
 #include "common.cuh"
 
 namespace dgp {
@@ -105,16 +107,34 @@ struct RelaxParams {
   float alpha_f, bad_bp_f;       // alpha and the bad-point B' = -alpha^2 / (4 (1 - w)), rounded once
 };
 
-// Fused z pass of a relaxation iteration (fused_relax.cu): inverse z transform
-// of the six y-inverted spectra (H_xx, H_yy, H_xy, H_xz, H_yz, N), residual and
-// update, forward z transform of D_new into Snew.  arith selects the
-// arithmetic of q, R, B' and Delta; partials: fused_relax_blocks() x 4 doubles.
+// Fused z pass of a relaxation iteration for FP64 mesh data (fused_relax.cu):
+// inverse z transform of the six y-inverted spectra (H_xx, H_yy, H_xy, H_xz,
+// H_yz, N), residual and update (FP64), forward z transform of D_new into
+// Snew; partials: fused_relax_blocks() x 4 doubles.  arith selects the
+// arithmetic of FP32 mesh data and is not read here (FP32 data take
+// launch_relax_tma below).
 enum { ARITH_F32 = 0, ARITH_EFT = 1, ARITH_F64 = 2 };
 template <typename T, int N>
 void launch_fused_relax(int arith, vec2_t<T>* const* spec6, const T* D, const double* dsum, const T* S, T* Dnew,
                         vec2_t<T>* Snew, RelaxParams rp, double* partials, const vec2_t<T>* tw, cudaStream_t s,
                         const int* skip = nullptr);
 template <typename T, int N> int fused_relax_blocks();
+
+// The same pass for FP32 mesh data with TMA tile loads (relax_tma.cu): one
+// tensor map per y-inverted spectrum (H_xx, H_yy, H_xy, H_xz, H_yz, N), built
+// once per context by relax_maps (nonzero when the driver cannot encode them).
+// Every wait inside is bounded by wait_ns; a wait that gives up sets *fault
+// to 1 and its CTA returns.  withhold (a test hook) leaves the first pair's
+// copy unissued, so that the first wait runs out.
+struct RelaxMaps {
+  CUtensorMap map[6];
+};
+template <int N> int relax_maps(float2* const* spec6, RelaxMaps* out);
+template <int N> int relax_tma_blocks();
+template <int N>
+void launch_relax_tma(int arith, const RelaxMaps& maps, const float* D, const double* dsum, const float* S,
+                      float* Dnew, float2* Snew, RelaxParams rp, double* partials, const float2* tw, cudaStream_t s,
+                      const int* skip, int* fault, unsigned long long wait_ns, int withhold);
 
 // Spherical approximation (Eq. FullDGP2sph): the w = 1/3 update from C = 0,
 // D = 2 S / (alpha + sqrt(alpha^2 + (8/3) S)), bad points (Delta < 0) take
@@ -151,9 +171,10 @@ void launch_finalize(const double* partials, int nblocks, int ncomp, double* out
 
 // Stop rules of the relaxation (Eq. normres, Sec. III.C), applied on the device
 // after each iteration so the host need not wait for every residual.
-enum { CTL_RUNNING = 0, CTL_CONVERGED = 1, CTL_STOPPED = 2, CTL_NONFINITE = 3 };
+enum { CTL_RUNNING = 0, CTL_CONVERGED = 1, CTL_STOPPED = 2, CTL_NONFINITE = 3, CTL_FAULT = 4 };
 struct SolveCtl {
   int done;      // nonzero once a rule has stopped the solve (the skip flag)
+  int fault;     // set by a kernel of the iteration whose bounded wait gave up
   int next_it;   // index of the iteration the controller examines next
   int status;    // CTL_*
   int stop_it;   // last iteration whose residual was examined

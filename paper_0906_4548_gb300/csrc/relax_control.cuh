@@ -16,6 +16,11 @@ __device__ __forceinline__ void relax_control_step(SolveCtl* __restrict__ c, con
                                                    double tol, double inv_m) {
   if (c->done) return;
   const int it = c->next_it;
+  if (c->fault) {  // a wait of this iteration gave up: its statistics are incomplete
+    c->status = CTL_FAULT;
+    c->done = 1;
+    return;
+  }
   c->next_it = it + 1;
   if (it == 0) {
     const double eps = abs_src_sum[0] * inv_m;

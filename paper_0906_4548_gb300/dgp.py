@@ -27,7 +27,8 @@ EXPORTED = ["dgp_background", "dgp_init", "dgp_destroy", "dgp_strerror", "dgp_re
             "dgp_solve_adjoint", "pm_step_adjoint", "dgp_zeldovich", "dgp_zeldovich_adjoint",
             "dgp_power_spectrum_adjoint", "dgp_tile_config", "dgp_set_tile_config",
             "dgp_solve_adjoint_rc", "pm_step_adjoint_rc", "dgp_zeldovich_vf_adjoint", "dgp_velocity_factor",
-            "dgp_workspace_size", "dgp_time_factors", "dgp_background_drc", "dgp_profile_sampled"]
+            "dgp_workspace_size", "dgp_time_factors", "dgp_background_drc", "dgp_profile_sampled",
+            "dgp_set_wait_limit"]
 DGP_NOALLOC_MAX_N = 64
 DGP_KERNEL_KINDS = 11
 
@@ -98,6 +99,7 @@ def _load():
         "dgp_profile": (i, [vp, i]),
         "dgp_profile_kinds": (i, [vp, ctypes.c_uint]),
         "dgp_profile_sampled": (i, [vp, ctypes.c_uint]),
+        "dgp_set_wait_limit": (i, [vp, d, i]),
         "dgp_profile_read": (i, [vp, i, P(i64), P(d), P(i64), P(d), P(d)]),
         "dgp_kernel_name": (ctypes.c_char_p, [i]),
         "dgp_power_spectrum_noalloc": (i, [vp, i, d, i, P(d), P(d), P(i64), vp]),
@@ -346,6 +348,11 @@ def dgp_tile_config(ctx):
 
 def dgp_set_tile_config(ctx, y_threads):
     _check(lib.dgp_set_tile_config(ctx, int(y_threads)), "dgp_set_tile_config")
+
+
+def dgp_set_wait_limit(ctx, seconds, withhold_first_copy=False):
+    """Bound of the relaxation kernel's waits; withhold_first_copy is the test hook of dgp.h."""
+    _check(lib.dgp_set_wait_limit(ctx, float(seconds), 1 if withhold_first_copy else 0), "dgp_set_wait_limit")
 
 
 def dgp_get_solution(ctx, D):

@@ -165,41 +165,43 @@ def test_batch_fp64_matches_oracle(dgp, torch_dev):
 
 
 def test_pm_step_host_on_alternating_sets_matches_fresh_contexts(dgp, torch_dev):
-    """Set A steps a0 -> a1; set B (another state at a1) then steps a1 -> a2 on the same
-    context, and A again a1 -> a2.  The start force must be computed for B and for A's second
-    step, not taken over from the previous call; FP64 at tol 1e-12, so the warm start does
-    not show."""
+    """Set A steps a0 -> a1 on one context; set B, A's state at a1 with every particle moved by up
+    to a tenth of a cell, then steps a1 -> a2 on the same context, and A again a1 -> a2.  The
+    start force must be computed for B and for A's second step, not taken over from the previous
+    call (the mesh force of another particle set differs at the cell scale).  FP64 at tol 1e-12
+    against fresh contexts, so the warm start (close in both cases) does not show."""
     torch, dev = torch_dev
     n, box = 32, 100.0
     a0, a1, a2 = 0.3, 0.32, 0.34
-    A = [np.ascontiguousarray(v) for v in zel(n, box, a0, -1.5, 0.5, 31)[:2]]
-    B = [np.ascontiguousarray(v) for v in zel(n, box, a1, -1.5, 0.5, 32)[:2]]
-
-    def host(ps):
-        return [np.ascontiguousarray(ps[0][j]) for j in range(3)] + [np.ascontiguousarray(ps[1][j]) for j in range(3)]
+    pos, mom, _ = zel(n, box, a0, -1.5, 0.3, 31)
+    ha = [np.ascontiguousarray(v) for v in (*pos, *mom)]
 
     def fresh(arrs, a, da):
         c = dgp.dgp_init(box, n, 1.0, OM, precision=dgp.DGP_FP64, tol=1e-12, max_iter=300)
         try:
             t = [to_dev(torch_dev, v, torch.float64) for v in arrs]
-            dgp.pm_step(c, dgp.particles(*t), a, da)
-            return np.stack([v.cpu().numpy() for v in t])
+            info = dgp.pm_step(c, dgp.particles(*t), a, da)
+            return np.stack([v.cpu().numpy() for v in t]), info
         finally:
             dgp.dgp_destroy(c)
 
-    ha, hb = host(A), host(B)
     ctx = dgp.dgp_init(box, n, 1.0, OM, precision=dgp.DGP_FP64, tol=1e-12, max_iter=300)
     try:
         dgp.pm_step_host(ctx, dgp.particles(*ha), a0, a1 - a0)
-        a_mid = np.stack(ha).copy()
-        dgp.pm_step_host(ctx, dgp.particles(*hb), a1, a2 - a1)
+        a_mid = [v.copy() for v in ha]
+        jit = np.random.default_rng(5).uniform(-0.1, 0.1, (3, n ** 3)) * box / n
+        hb = [np.ascontiguousarray((a_mid[j] + jit[j]) % box) for j in range(3)] + [v.copy() for v in a_mid[3:]]
+        b_start = [v.copy() for v in hb]
+        ib = dgp.pm_step_host(ctx, dgp.particles(*hb), a1, a2 - a1)
         b_got = np.stack(hb).copy()
-        dgp.pm_step_host(ctx, dgp.particles(*ha), a1, a2 - a1)
+        ia = dgp.pm_step_host(ctx, dgp.particles(*ha), a1, a2 - a1)
         a_got = np.stack(ha).copy()
     finally:
         dgp.dgp_destroy(ctx)
-    b_want = fresh(host(B), a1, a2 - a1)
-    a_want = fresh(list(a_mid), a1, a2 - a1)
+    b_want, ib_f = fresh(b_start, a1, a2 - a1)
+    a_want, ia_f = fresh(a_mid, a1, a2 - a1)
+    for i in (ib, ia, ib_f, ia_f):
+        assert i["status"] == dgp.DGP_OK and i["norm_res"] < 1e-12, i
     assert rel_l2(b_got, b_want) < 1e-10
     assert rel_l2(a_got, a_want) < 1e-10
 

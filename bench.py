@@ -5,12 +5,15 @@ seeded n_s = -1.5 power-law Gaussian field with mesh rms 0.5 at a = 0.02,
 Zel'dovich initial conditions, r_c H0 = 1, Omega_m0 = 0.27, w = 1/3, steps
 uniform in ln a from a = 0.02 to a = 1 in 200 steps, relaxation tolerance 1e-6
 on <|R|>/eps every step.  Arithmetic (--precision mixed, the default): FP32
-mesh fields, FFTs and particles; the residual R, the split source B' and the
-discriminant Delta as unevaluated pairs of FP32 numbers formed with error-free
-transformations (about 48 significant bits) in place of FP64; norms, means and
-reductions in FP64.  --precision mixed-fp64 evaluates R, B' and Delta on the
-FP64 pipe instead (its rate is printed beside the headline).  A "step" is one
-pm_step call (deposit, field solve, forces, gather, kick-drift-kick).
+mesh fields, FFTs, particles and pointwise residual, with the discriminant
+formed exactly for its FP32 operands (its sign is the bad-point test) and the
+residual norms, means and reductions in FP64.  The FP32 data's own rounding
+leaves a residual floor near 1e-8 of <|S|>, 100 times below the tolerance, so
+the residual gains nothing from wider arithmetic.  The run is repeated with R
+and Delta on error-free FP32 pairs (--precision mixed-eft), on the FP64 pipe
+(mixed-fp64; its rate is printed beside the headline) and in plain FP32, each
+compared with this one.  A "step" is one pm_step call (deposit, field solve,
+forces, gather, kick-drift-kick).
 
 Timing: after W warm-up steps the whole 200-step run is started again from the
 initial conditions and always run to the end; K of its steps, the middle step
@@ -78,12 +81,18 @@ def recorded_traffic(kind):
 
 PRECISION_DESC = {
     "fp64": "fp64 throughout (the oracle)",
-    "mixed": "mixed: fp32 mesh/FFT/particles; the residual R, split source B' and discriminant Delta as "
-             "unevaluated pairs of fp32 (error-free transformations, ~48-bit significand) in place of fp64; "
-             "norms, means and reductions fp64",
-    "mixed-fp64": "mixed: fp32 mesh/FFT/particles; residual, B', discriminant, norms and reductions fp64",
+    "mixed": "mixed (the 256^3 workload's): fp32 mesh fields, FFTs, particles and pointwise residual R, B' "
+             "and D_new; the discriminant Delta formed exactly (float pair) for its fp32 operands, so the "
+             "bad-point sign test is exact; residual-norm and mean-of-D sums as float pairs within a thread "
+             "and fp64 across threads and blocks, as every global mean and reduction",
+    "mixed-eft": "mixed: fp32 mesh/FFT/particles; the residual R and discriminant Delta as unevaluated pairs "
+                 "of fp32 (error-free transformations, ~48-bit significand) in place of fp64; B' fp32 from the "
+                 "pair R; norms, means and reductions fp64",
+    "mixed-fp64": "mixed: fp32 mesh/FFT/particles; residual, B', discriminant, norms and reductions fp64 "
+                  "(the fp64 pipe)",
     "fp32": "fp32 throughout (fp64 cross-block sums only)",
 }
+DTYPE = {"mixed": "f32+f64", "mixed-eft": "f32+eft", "mixed-fp64": "f32+f64pipe", "fp32": "f32"}
 
 
 def config(n_gpus, prec="mixed", sort_every=SORT_EVERY):
@@ -478,7 +487,7 @@ def fp64_path_error(dgp, torch, np, n, box, delta_end, a_end, sched, pos, mom, p
     end-state density (a fresh context per precision, tol as the run), and P(k) at the end of the
     same whole run done entirely in FP64 (the mixed run's P(k) is pk_main)."""
     fields = {}
-    for name, prec, dt in (("mixed", dgp.DGP_MIXED_EFT, torch.float32), ("fp64", dgp.DGP_FP64, torch.float64)):
+    for name, prec, dt in (("mixed", dgp.DGP_MIXED_F32R, torch.float32), ("fp64", dgp.DGP_FP64, torch.float64)):
         c = dgp.dgp_init(box, n, WL["rc_H0"], WL["omega_m0"], w=WL["w"], precision=prec, max_iter=WL["max_iter"],
                          tol=WL["tol"], stream=stream.cuda_stream)
         try:
@@ -512,7 +521,7 @@ def fp64_path_error(dgp, torch, np, n, box, delta_end, a_end, sched, pos, mom, p
     finally:
         dgp.dgp_destroy(c)
     out["pk_max_rel_diff"] = float(np.max(np.abs(pk_main / pk64 - 1)))
-    out["note"] = ("mixed (error-free pairs) vs the FP64 GPU path: phi and forces of one solve on the "
+    out["note"] = ("mixed vs the FP64 GPU path: phi and forces of one solve on the "
                    "end-state density of the run at a = %.3f; P(k) after the whole %d-step run"
                    % (a_end, len(sched) - 1))
     return out
@@ -655,7 +664,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--precision", default="mixed", choices=sorted(PRECISION_DESC))
+    ap.add_argument("--precision", default="mixed", choices=sorted(k for k in PRECISION_DESC if k != "fp64"))
     ap.add_argument("--no-compare", action="store_true", help="skip the precision comparison runs")
     ap.add_argument("--no-kernel-table", action="store_true", help="skip the per-kind event pass")
     ap.add_argument("--workload", default="pm256", choices=["pm256", "batched", "adjoint"],
@@ -704,7 +713,8 @@ def main():
     # the context runs on its own stream: the relaxation iterations replay as CUDA graphs there
     # (stream capture is not available on the legacy default stream)
     bs = torch.cuda.Stream(device=dev)
-    pcode = {"mixed": dgp.DGP_MIXED_EFT, "mixed-fp64": dgp.DGP_MIXED, "fp32": dgp.DGP_FP32}
+    pcode = {"mixed": dgp.DGP_MIXED_F32R, "mixed-eft": dgp.DGP_MIXED_EFT, "mixed-fp64": dgp.DGP_MIXED,
+             "fp32": dgp.DGP_FP32}
 
     def make_ctx(prec):
         return dgp.dgp_init(box, n, WL["rc_H0"], WL["omega_m0"], w=WL["w"], precision=pcode[prec],
@@ -799,7 +809,7 @@ def main():
                           "frac_of_peak": round(gbs / peak, 3) if gbs else None}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"mixed": "f32+eft", "mixed-fp64": "f32+f64", "fp32": "f32"}[args.precision],
+            "vs_baseline": None, "dtype": DTYPE[args.precision],
             "data": "synthetic", "config": config(world, args.precision, args.sort_every),
             "timing": {"how": "the whole %d-step run (a = %g -> %g) runs every time; the K = %d timed steps are the "
                               "middle step of each of K equal strata of the run, each bracketed by a device "

@@ -18,7 +18,7 @@
  *   dgp_cosmology.c_over_H0 (2997.92458 Mpc/h).  Mesh: n^3 points at x = i d,
  *   d = box / n, periodic.  A real mesh field is n^3 contiguous elements in
  *   C order [x][y][z] (z fastest).  Element type: float when the context
- *   precision is DGP_FP32 or DGP_MIXED, double when it is DGP_FP64.
+ *   precision is DGP_FP32 or one of the DGP_MIXED modes, double when it is DGP_FP64.
  *   Particles: struct-of-arrays, same element type; p = a^2 dx/dt.
  *   Streams: every call enqueues its GPU work on the stream given to
  *   dgp_init (NULL = the legacy default stream).  Calls that return host
@@ -57,10 +57,20 @@ typedef enum {
  *                 split source B' and the discriminant Delta in FP64; norms and
  *                 global means reduced in FP64.
  *   DGP_FP64      everything FP64 (double buffers).
- *   DGP_MIXED_EFT as DGP_MIXED, but R, B' and Delta are evaluated on pairs of
+ *   DGP_MIXED_EFT as DGP_MIXED, but R and Delta are evaluated on pairs of
  *                 floats with error-free transformations (TwoSum, FMA TwoProd),
- *                 ~48 significant bits, without the FP64 pipe. */
-enum { DGP_FP32 = 0, DGP_MIXED = 1, DGP_FP64 = 2, DGP_MIXED_EFT = 3 };
+ *                 ~48 significant bits, without the FP64 pipe; B' (which only
+ *                 feeds the FP32 D_new) is formed in FP32 from the pair R.
+ *   DGP_MIXED_F32R FP32 mesh fields, FFTs, particles and pointwise residual
+ *                 R, B' and D_new; the discriminant Delta formed exactly (a pair)
+ *                 for the FP32 operands, so its sign (the bad-point test) is
+ *                 exact; the sums behind the residual norm and the mean of D
+ *                 carried as float pairs within a thread and reduced in FP64
+ *                 across threads and blocks, as every global mean.  Rounding the
+ *                 converged fields to FP32 alone leaves <|R|> of order 1e-8 of
+ *                 <|S|>, which no residual arithmetic can go below; the FP32
+ *                 evaluation of R adds an error of the same order. */
+enum { DGP_FP32 = 0, DGP_MIXED = 1, DGP_FP64 = 2, DGP_MIXED_EFT = 3, DGP_MIXED_F32R = 4 };
 /* Gravity modes: the full nonlinear DGP equations (Eqs. FullDGP1-2), the
  * linearised DGP Poisson equation (Eq. LinearDGP), GR with the DGP expansion
  * (Eq. GRPoisson), and the spherical approximation of Sec. IV: Eq. FullDGP2sph
@@ -80,7 +90,7 @@ typedef struct {
   int n;             /* mesh points per side: 16, 32, 48, 64, 96, 128, 256 or 512 */
   double rc_H0;      /* crossover scale r_c in units of c/H0, > 0 (Sec. II) */
   double w;          /* splitting parameter of Eq. FullDGP2wpara, 0 <= w < 1 */
-  int precision;     /* DGP_FP32, DGP_MIXED, DGP_FP64 or DGP_MIXED_EFT */
+  int precision;     /* DGP_FP32, DGP_MIXED, DGP_FP64, DGP_MIXED_EFT or DGP_MIXED_F32R */
   int gravity;       /* DGP_GRAVITY_NL (Eqs. FullDGP1-2), _LDGP (Eq. LinearDGP), _GRH (Eq. GRPoisson),
                         _SPH (spherical approximation, Sec. IV) */
   int local_only;    /* nonzero: drop the sqrt(-lapbar) terms (Appendix Eq. FullDGP2simp) */

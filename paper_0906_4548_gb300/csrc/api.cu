@@ -643,7 +643,10 @@ class Engine : public EngineBase {
       rp.two_omw = (float)(2.0 * (1.0 - p.w));
       rp.alpha_f = (float)c.alpha;
       rp.bad_bp_f = (float)(-c.alpha * c.alpha / (4.0 * (1.0 - p.w)));
-      const int arith = p.precision == DGP_FP32 ? ARITH_F32 : (p.precision == DGP_MIXED_EFT ? ARITH_EFT : ARITH_F64);
+      const int arith = p.precision == DGP_FP32        ? ARITH_F32
+                        : p.precision == DGP_MIXED_EFT   ? ARITH_EFT
+                        : p.precision == DGP_MIXED_F32R  ? ARITH_M32
+                                                         : ARITH_F64;
 
       // Buffers: the starting iterate stays in rD[j0]; iteration it >= 1 reads
       // the previous output, and the outputs alternate between the other two.
@@ -678,26 +681,24 @@ class Engine : public EngineBase {
             launch_fused_relax<T, N>(arith, s6, rD[ib], d_rstats + 4 * ib + 1, rS, rD[ob], spec_out(it), rp,
                                      partials, tw, stream, sk);
         });
-        // the iteration's statistics, and with control the stop rules, in one launch
-        prof.run_it(KK_REDUCE, 0, sure * 32.0 * fblocks, stream, [&] {
-          if (control)
-            launch_finalize_control(partials, fblocks, d_rstats + 4 * ob, d_ctl, d_misc + 1, d_hist, p.max_iter,
-                                    kPatience, tol, 1.0 / (double)M, stream, sk);
-          else
-            launch_finalize(partials, fblocks, 4, d_rstats + 4 * ob, stream, sk);
-        });
-        prof.run_it(KK_Y, 0, sure * 2 * SB, stream, [&] {
+        // the iteration's statistics: with control, summed by one extra CTA of the forward y
+        // pass of the new iterate, which also applies the stop rules
+        if (!control)
+          prof.run_it(KK_REDUCE, 0, sure * 32.0 * fblocks, stream,
+                      [&] { launch_finalize(partials, fblocks, 4, d_rstats + 4 * ob, stream, sk); });
+        prof.run_it(KK_Y, 0, sure * (2 * SB + (control ? 32.0 * fblocks : 0.0)), stream, [&] {
           V* o[1] = {spec_out(it)};
-          launch_fft_y<T, N>(fs(o, 1), 1, false, tw, stream, sk, y_threads);
+          const YControl yc{partials, fblocks, d_rstats + 4 * ob, d_ctl, d_misc + 1, d_hist, p.max_iter,
+                            kPatience, tol, 1.0 / (double)M};
+          launch_fft_y<T, N>(fs(o, 1), 1, false, tw, stream, sk, y_threads, control ? &yc : nullptr);
         });
         DGP_CHECK_LAUNCH();
         return DGP_OK;
       };
       auto credit = [&](int iters, int yfwd) {
         prof.credit(KK_X_HESSIAN, 7 * SB * iters);
-        prof.credit(KK_Y, 12 * SB * iters + 2 * SB * yfwd);
+        prof.credit(KK_Y, 12 * SB * iters + (2 * SB + 32.0 * fblocks) * yfwd);
         prof.credit(KK_RELAX, (7 * SB + 3 * RB) * iters);
-        prof.credit(KK_REDUCE, 32.0 * fblocks * iters);
       };
 
       if ((rc = forward_zy(rD[j0], sD, ZPrologue{nullptr, 0.0, 0}))) return rc;
@@ -751,7 +752,6 @@ class Engine : public EngineBase {
             prof.count(KK_X_HESSIAN, 2);
             prof.count(KK_Y, 4);
             prof.count(KK_RELAX, 2);
-            prof.count(KK_REDUCE, 4);
             it += 2;
           } else {
             if ((rc = enqueue(it, true))) return rc;
@@ -1571,7 +1571,7 @@ int dgp_init(dgp_ctx** out, const dgp_params* p, const dgp_cosmology* cosmo, voi
   if (!(p->box > 0) || !(p->rc_H0 > 0) || !(p->w >= 0 && p->w < 1) || p->max_iter < 0 || !(p->tol >= 0) ||
       !isfinite(p->tol) || p->sort_every < 0)
     return DGP_E_INVALID;
-  if (p->precision < DGP_FP32 || p->precision > DGP_MIXED_EFT) return DGP_E_INVALID;
+  if (p->precision < DGP_FP32 || p->precision > DGP_MIXED_F32R) return DGP_E_INVALID;
   if (p->gravity < DGP_GRAVITY_NL || p->gravity > DGP_GRAVITY_SPH) return DGP_E_INVALID;
   if (!(p->a_nonlinear >= 0.0) || !isfinite(p->a_nonlinear)) return DGP_E_INVALID;
   if (!(cosmo->omega_m0 > 0) || !(cosmo->c_over_H0 > 0)) return DGP_E_INVALID;
@@ -1761,7 +1761,7 @@ int dgp_time_factors(const dgp_cosmology* cosmo, double rc_H0, double a0, double
 
 int dgp_workspace_size(const dgp_params* p, int64_t np, dgp_workspace* out) {
   if (!p || !out || np < 0 || p->max_iter < 0) return DGP_E_INVALID;
-  if (p->precision < DGP_FP32 || p->precision > DGP_MIXED_EFT) return DGP_E_INVALID;
+  if (p->precision < DGP_FP32 || p->precision > DGP_MIXED_F32R) return DGP_E_INVALID;
   const bool ok = p->precision == DGP_FP64 ? dgp::workspace_for<double>(p->n, p->max_iter, np, out)
                                            : dgp::workspace_for<float>(p->n, p->max_iter, np, out);
   return ok ? DGP_OK : DGP_E_INVALID;

@@ -15,8 +15,14 @@ __device__ __forceinline__ void cic_axis(float x, const CicParams& cp, int& i0, 
   f = (hi - fl) + lo;
   if (f < 0.f) { f += 1.f; fl -= 1.f; }
   else if (f >= 1.f) { f -= 1.f; fl += 1.f; }
-  int i = (int)fl % cp.n;
-  if (i < 0) i += cp.n;
+  int i = (int)fl;
+  // positions inside the box need at most one wrap; the division only for the rest
+  if (i >= cp.n) i -= cp.n;
+  else if (i < 0) i += cp.n;
+  if ((unsigned)i >= (unsigned)cp.n) {
+    i %= cp.n;
+    if (i < 0) i += cp.n;
+  }
   i0 = i;
   i1 = (i + 1 == cp.n) ? 0 : i + 1;
 }

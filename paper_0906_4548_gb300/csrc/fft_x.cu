@@ -116,7 +116,10 @@ __device__ __forceinline__ double geff_dev(const KParams& kp, double kmag) {
 }
 
 template <typename T, int N, int OP>
-__global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
+__global__ void __launch_bounds__(XGeom<T, N>::THREADS,
+                                  (OP == XOP_HESSIAN && sizeof(T) == 4 && XGeom<T, N>::THREADS <= 256)
+                                      ? 3
+                                      : XGeom<T, N>::MIN_BLOCKS)
     k_fft_x(const __grid_constant__ XArgs<T> args, const vec2_t<T>* __restrict__ g_tw) {
   if (args.skip && *args.skip) return;
   using V = vec2_t<T>;
@@ -207,7 +210,7 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
   constexpr int NT = XGeom<T, N>::THREADS;
   const T inv_m = kc<T>(kp.inv_m, kp.inv_m_f);
 #pragma unroll
-  for (int k2 = 0; k2 < N2; ++k2) {
+  for (int k2 = 0; k2 < N2 && OP != XOP_HESSIAN; ++k2) {
     const int nx = signed_index(lane + N1 * k2, N);
     const int n2 = nx * nx + ny * ny + nz * nz;
     T inv = (T)0, ikb = (T)0;
@@ -383,9 +386,18 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
     // H_ab(k) = (n_a n_b / |n|^2) D(k) for (a, b) = xx, yy, xy, xz, yz with the
     // absolute value where a component of an off-diagonal pair is on its Nyquist
     // index (on the diagonal the product is a square anyway), then N = -D / kbar.
-    // The pair of each output is chosen once per output; per element the
-    // multiplier is branch-free.
+    // 1/|n|^2 and the 1/N^3 of the inverse transforms are folded into the
+    // spectrum once (Xs); each output's multiplier is then a product of the
+    // wavenumber components, formed in registers.  The pair of each output is
+    // chosen once per output; per element the multiplier is branch-free.
     const T fy = (T)ny, fz = (T)nz;
+    const T nyz2 = fy * fy + fz * fz;
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+      const T fx = (T)signed_index(lane + N1 * k2, N);
+      const T n2 = fx * fx + nyz2;
+      X0[k2] = cscale(X0[k2], n2 != (T)0 ? inv_m / n2 : (T)0);
+    }
 #pragma unroll 1
     for (int o = 0; o < 5; ++o) {
       const bool a_is_x = o == 0 || o == 2 || o == 3;       // first component x, else y
@@ -402,13 +414,18 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
         T prod = fa * fb;
         const bool nyq = nyq_fixed || ((a_is_x || b_sel == 0) && kx == N / 2);
         if (nyq) prod = fabs(prod);
-        Y[k2] = cscale(X0[k2], prod * s_inv[k2 * NT + threadIdx.x]);
+        Y[k2] = cscale(X0[k2], prod);
       }
       x_inverse<T, N>(Y, args.out.p[o], kz, ky0, lane, yl, s_T, s_tw);
     }
+    // N = -D / kbar = -(|n|^2 / kbar) Xs, |n|^2 / kbar = |n| / (kbar_fac k_f)
+    const T ikf = kp.local_only ? (T)0 : (T)1 / kc<T>(kp.kbar_fac * 2.0 * M_PI / kp.box, kp.kbkf_f);
     V Y[N2];
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) Y[k2] = cscale(X0[k2], -s_ikb[k2 * NT + threadIdx.x] * inv_m);
+    for (int k2 = 0; k2 < N2; ++k2) {
+      const T fx = (T)signed_index(lane + N1 * k2, N);
+      Y[k2] = cscale(X0[k2], -sqrt(fx * fx + nyz2) * ikf);
+    }
     x_inverse<T, N>(Y, args.out.p[5], kz, ky0, lane, yl, s_T, s_tw);
     return;
   }
@@ -534,7 +551,8 @@ static void launch_x(const XArgs<T>& a, const vec2_t<T>* tw, cudaStream_t s) {
   constexpr bool PK = OP == XOP_PK || OP == XOP_PK_BRANE;
   constexpr int NBS = OP == XOP_PK_BRANE ? 4 : 3, NW = G::THREADS / 32;
   const size_t base = sizeof(vec2_t<T>) * (kTwiddleTables * N + (size_t)N * G::TY);
-  const size_t tables = PK ? sizeof(double) * NW * 32 * NBS : sizeof(T) * 2 * Split<N>::N2 * G::THREADS;
+  const size_t tables = PK ? sizeof(double) * NW * 32 * NBS
+                            : (OP == XOP_HESSIAN ? 0 : sizeof(T) * 2 * Split<N>::N2 * G::THREADS);
   const size_t per_bin = PK ? sizeof(double) * NW * NBS : 0;
   const size_t smem = base + tables + per_bin * a.nbins;
   raise_smem_limit<k_fft_x<T, N, OP>>(base + tables + per_bin * (N / 2));

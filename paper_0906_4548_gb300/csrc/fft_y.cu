@@ -10,15 +10,37 @@
 // addresses).  HBM traffic: one read and one write of the rows.
 #include "fft_core.cuh"
 #include "kernels.cuh"
+#include "reduce.cuh"
+#include "relax_control.cuh"
 
 namespace dgp {
 
 // 64 registers per thread for FP32 rows of up to 256 points, 128 otherwise
-template <typename T, int N, bool INV, int B>
+template <typename T, int N, bool INV, int B, bool CTL>
 __global__ void __launch_bounds__(B, (sizeof(T) == 8 || N >= 512 ? 512 : 1024) / B) k_fft_y(const __grid_constant__ FieldSet<T> f, int64_t npencils,
                                                      const vec2_t<T>* __restrict__ g_tw,
-                                                     const int* __restrict__ skip) {
+                                                     const int* __restrict__ skip, const __grid_constant__ YControl yc) {
   if (skip && *skip) return;
+  if constexpr (CTL) {
+    // the extra CTA, first in launch order so that it overlaps the transform's CTAs:
+    // statistics and stop rules of the iteration
+    if (blockIdx.x == 0) {
+      double v[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int b = threadIdx.x; b < yc.nblocks; b += blockDim.x) {
+        const double* pb = yc.partials + 4 * (int64_t)b;
+        v[0] += pb[0];
+        v[1] += pb[1];
+        v[2] += pb[2];
+        v[3] += pb[3];
+      }
+      block_sum<4>(v);
+      if (threadIdx.x == 0) {
+        for (int k = 0; k < 4; ++k) yc.stats[k] = v[k];
+        relax_control_step(yc.ctl, yc.stats, yc.abs_src_sum, yc.hist, yc.max_iter, yc.patience, yc.tol, yc.inv_m);
+      }
+      return;
+    }
+  }
   using V = vec2_t<T>;
   constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
   constexpr int P = B / N1;
@@ -28,7 +50,7 @@ __global__ void __launch_bounds__(B, (sizeof(T) == 8 || N >= 512 ? 512 : 1024) /
   load_twiddles(s_tw, g_tw, N);
   const int lane = threadIdx.x % N1;
   const int pl = threadIdx.x / N1;
-  const int64_t pencil = (int64_t)blockIdx.x * P + pl;
+  const int64_t pencil = (int64_t)(blockIdx.x - (CTL ? 1 : 0)) * P + pl;
   const bool active = pencil < npencils;
   V* base = f.p[blockIdx.y] + (active ? pencil : 0) * N;
   V* Tp = s_T + pl * (N1 * (N2 + 1));
@@ -57,32 +79,40 @@ __global__ void __launch_bounds__(B, (sizeof(T) == 8 || N >= 512 ? 512 : 1024) /
 
 template <typename T, int N, int B>
 static void launch_y(const FieldSet<T>& f, int nfields, bool inverse, const vec2_t<T>* tw, cudaStream_t s,
-                     const int* skip) {
+                     const int* skip, const YControl* ctl) {
   using V = vec2_t<T>;
   constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
   constexpr int P = B / N1;
   const int64_t npencils = (int64_t)(N / 2 + 1) * N;
   const size_t smem = sizeof(V) * (kTwiddleTables * N + P * N1 * (N2 + 1));
-  dim3 grid((unsigned)((npencils + P - 1) / P), (unsigned)nfields);
+  YControl yc{};
+  if (ctl) yc = *ctl;
+  // with the stop rules: one extra CTA, and the fields on grid.x only (one field)
+  dim3 grid((unsigned)((npencils + P - 1) / P) + (ctl ? 1u : 0u), (unsigned)nfields);
   if (inverse) {
-    raise_smem_limit<k_fft_y<T, N, true, B>>(smem);
-    k_fft_y<T, N, true, B><<<grid, B, smem, s>>>(f, npencils, tw, skip);
+    raise_smem_limit<k_fft_y<T, N, true, B, false>>(smem);
+    k_fft_y<T, N, true, B, false><<<grid, B, smem, s>>>(f, npencils, tw, skip, yc);
+  } else if (ctl) {
+    raise_smem_limit<k_fft_y<T, N, false, B, true>>(smem);
+    k_fft_y<T, N, false, B, true><<<grid, B, smem, s>>>(f, npencils, tw, skip, yc);
   } else {
-    raise_smem_limit<k_fft_y<T, N, false, B>>(smem);
-    k_fft_y<T, N, false, B><<<grid, B, smem, s>>>(f, npencils, tw, skip);
+    raise_smem_limit<k_fft_y<T, N, false, B, false>>(smem);
+    k_fft_y<T, N, false, B, false><<<grid, B, smem, s>>>(f, npencils, tw, skip, yc);
   }
 }
 
 template <typename T, int N>
 void launch_fft_y(const FieldSet<T>& f, int nfields, bool inverse, const vec2_t<T>* tw, cudaStream_t s,
-                  const int* skip, int threads) {
-  if (threads == 128) launch_y<T, N, 128>(f, nfields, inverse, tw, s, skip);
-  else if (threads == 512) launch_y<T, N, 512>(f, nfields, inverse, tw, s, skip);
-  else launch_y<T, N, 256>(f, nfields, inverse, tw, s, skip);
+                  const int* skip, int threads, const YControl* ctl) {
+  if (ctl && (inverse || nfields != 1)) return;  // the stop rules ride on a one-field forward pass only
+  if (threads == 128) launch_y<T, N, 128>(f, nfields, inverse, tw, s, skip, ctl);
+  else if (threads == 512) launch_y<T, N, 512>(f, nfields, inverse, tw, s, skip, ctl);
+  else launch_y<T, N, 256>(f, nfields, inverse, tw, s, skip, ctl);
 }
 
 #define DGP_INST_Y(T, N) \
-  template void launch_fft_y<T, N>(const FieldSet<T>&, int, bool, const vec2_t<T>*, cudaStream_t, const int*, int);
+  template void launch_fft_y<T, N>(const FieldSet<T>&, int, bool, const vec2_t<T>*, cudaStream_t, const int*, int, \
+                                   const YControl*);
 #define DGP_INST_Y_ALL(T) DGP_INST_Y(T, 16) DGP_INST_Y(T, 32) DGP_INST_Y(T, 64) DGP_INST_Y(T, 128) \
   DGP_INST_Y(T, 256) DGP_INST_Y(T, 512) DGP_INST_Y(T, 48) DGP_INST_Y(T, 96)
 DGP_INST_Y_ALL(float)

@@ -55,9 +55,24 @@ enum XOp { XOP_HESSIAN = 0, XOP_SOURCE = 1, XOP_SOURCE_LIN = 2, XOP_PHI_FORCE = 
 // skip: NULL, or a device flag read at kernel entry; when it is nonzero the
 // whole grid returns at once (iterations enqueued past the solver's stop).
 // threads: 128, 256 or 512 per CTA (threads / N1 rows per CTA).
+// ctl (may be null): one extra CTA of the launch sums the relaxation's block
+// partials and applies the stop rules, as launch_finalize_control does (the
+// y pass that follows the relaxation pass carries them, one launch fewer per
+// iteration).
+struct SolveCtl;
+struct YControl {
+  const double* partials;
+  int nblocks;
+  double* stats;
+  SolveCtl* ctl;
+  const double* abs_src_sum;
+  double* hist;
+  int max_iter, patience;
+  double tol, inv_m;
+};
 template <typename T, int N>
 void launch_fft_y(const FieldSet<T>& f, int nfields, bool inverse, const vec2_t<T>* tw, cudaStream_t s,
-                  const int* skip = nullptr, int threads = 256);
+                  const int* skip = nullptr, int threads = 256, const YControl* ctl = nullptr);
 
 template <typename T, int N>
 void launch_fft_z_r2c(const T* in, int64_t in_stride, vec2_t<T>* out, int64_t out_stride, int nfields,
@@ -113,7 +128,7 @@ struct RelaxParams {
 // Snew; partials: fused_relax_blocks() x 4 doubles.  arith selects the
 // arithmetic of FP32 mesh data and is not read here (FP32 data take
 // launch_relax_tma below).
-enum { ARITH_F32 = 0, ARITH_EFT = 1, ARITH_F64 = 2 };
+enum { ARITH_F32 = 0, ARITH_EFT = 1, ARITH_F64 = 2, ARITH_M32 = 3 };
 template <typename T, int N>
 void launch_fused_relax(int arith, vec2_t<T>* const* spec6, const T* D, const double* dsum, const T* S, T* Dnew,
                         vec2_t<T>* Snew, RelaxParams rp, double* partials, const vec2_t<T>* tw, cudaStream_t s,

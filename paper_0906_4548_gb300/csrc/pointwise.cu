@@ -399,13 +399,42 @@ __device__ __forceinline__ T wrap_periodic(T v, T box, T inv_box) {
 }
 
 // Force interpolation with the deposit's window (Sec. III.A), kick, optional drift.
+// One particle of the gather-kick-drift: the mesh force at the particle with the CIC
+// window (8 corners, 3 components), p += kick g, then x += drift p (wrapped) if asked.
+template <typename T>
+struct GatherOne {
+  int64_t r00, r01, r10, r11;
+  int iz0, iz1;
+  T w[8];
+  __device__ __forceinline__ void locate(T xp, T yp, T zp, const CicParams& cp) {
+    const int64_t n = cp.n;
+    int ix0, ix1, iy0, iy1;
+    T fx, fy, fz;
+    cic_axis(xp, cp, ix0, ix1, fx);
+    cic_axis(yp, cp, iy0, iy1, fy);
+    cic_axis(zp, cp, iz0, iz1, fz);
+    const T hx = (T)1 - fx, hy = (T)1 - fy, hz = (T)1 - fz;
+    r00 = (ix0 * n + iy0) * n;
+    r01 = (ix0 * n + iy1) * n;
+    r10 = (ix1 * n + iy0) * n;
+    r11 = (ix1 * n + iy1) * n;
+    w[0] = hx * hy * hz; w[1] = hx * hy * fz; w[2] = hx * fy * hz; w[3] = hx * fy * fz;
+    w[4] = fx * hy * hz; w[5] = fx * hy * fz; w[6] = fx * fy * hz; w[7] = fx * fy * fz;
+  }
+  __device__ __forceinline__ T at(const T* __restrict__ G) const {
+    return w[0] * G[r00 + iz0] + w[1] * G[r00 + iz1] + w[2] * G[r01 + iz0] + w[3] * G[r01 + iz1] +
+           w[4] * G[r10 + iz0] + w[5] * G[r10 + iz1] + w[6] * G[r11 + iz0] + w[7] * G[r11 + iz1];
+  }
+};
+
+// Two particles per iteration (p and p + stride): their 48 mesh loads are independent, which
+// doubles the loads in flight of this latency-bound gather.
 template <typename T>
 __global__ void __launch_bounds__(256) k_gather_kick(T* __restrict__ x, T* __restrict__ y, T* __restrict__ z,
                                                      T* __restrict__ px, T* __restrict__ py, T* __restrict__ pz,
                                                      int64_t np, const T* __restrict__ gx, const T* __restrict__ gy,
                                                      const T* __restrict__ gz, CicParams cp, T kick, T drift,
                                                      int do_drift) {
-  const int64_t n = cp.n;
   T box, inv_box;
   if constexpr (sizeof(T) == 8) {
     box = cp.box;
@@ -414,34 +443,38 @@ __global__ void __launch_bounds__(256) k_gather_kick(T* __restrict__ x, T* __res
     box = cp.box_f;
     inv_box = cp.inv_box_f;
   }
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
-    int ix0, ix1, iy0, iy1, iz0, iz1;
-    T fx, fy, fz;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += 2 * stride) {
+    const int64_t q = p + stride;
+    const bool two = q < np;
     const T xp = x[p], yp = y[p], zp = z[p];
-    cic_axis(xp, cp, ix0, ix1, fx);
-    cic_axis(yp, cp, iy0, iy1, fy);
-    cic_axis(zp, cp, iz0, iz1, fz);
-    const T hx = (T)1 - fx, hy = (T)1 - fy, hz = (T)1 - fz;
-    const int64_t r00 = (ix0 * n + iy0) * n, r01 = (ix0 * n + iy1) * n;
-    const int64_t r10 = (ix1 * n + iy0) * n, r11 = (ix1 * n + iy1) * n;
-    const T w000 = hx * hy * hz, w001 = hx * hy * fz, w010 = hx * fy * hz, w011 = hx * fy * fz;
-    const T w100 = fx * hy * hz, w101 = fx * hy * fz, w110 = fx * fy * hz, w111 = fx * fy * fz;
-    T g[3];
-    const T* grids[3] = {gx, gy, gz};
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const T* G = grids[c];
-      g[c] = w000 * G[r00 + iz0] + w001 * G[r00 + iz1] + w010 * G[r01 + iz0] + w011 * G[r01 + iz1] +
-             w100 * G[r10 + iz0] + w101 * G[r10 + iz1] + w110 * G[r11 + iz0] + w111 * G[r11 + iz1];
+    const T xq = two ? x[q] : xp, yq = two ? y[q] : yp, zq = two ? z[q] : zp;
+    GatherOne<T> A, B;
+    A.locate(xp, yp, zp, cp);
+    B.locate(xq, yq, zq, cp);
+    const T ga0 = A.at(gx), ga1 = A.at(gy), ga2 = A.at(gz);
+    const T gb0 = B.at(gx), gb1 = B.at(gy), gb2 = B.at(gz);
+    {
+      const T qx = px[p] + kick * ga0, qy = py[p] + kick * ga1, qz = pz[p] + kick * ga2;
+      px[p] = qx;
+      py[p] = qy;
+      pz[p] = qz;
+      if (do_drift) {
+        x[p] = wrap_periodic(xp + drift * qx, box, inv_box);
+        y[p] = wrap_periodic(yp + drift * qy, box, inv_box);
+        z[p] = wrap_periodic(zp + drift * qz, box, inv_box);
+      }
     }
-    const T qx = px[p] + kick * g[0], qy = py[p] + kick * g[1], qz = pz[p] + kick * g[2];
-    px[p] = qx;
-    py[p] = qy;
-    pz[p] = qz;
-    if (do_drift) {
-      x[p] = wrap_periodic(xp + drift * qx, box, inv_box);
-      y[p] = wrap_periodic(yp + drift * qy, box, inv_box);
-      z[p] = wrap_periodic(zp + drift * qz, box, inv_box);
+    if (two) {
+      const T qx = px[q] + kick * gb0, qy = py[q] + kick * gb1, qz = pz[q] + kick * gb2;
+      px[q] = qx;
+      py[q] = qy;
+      pz[q] = qz;
+      if (do_drift) {
+        x[q] = wrap_periodic(xq + drift * qx, box, inv_box);
+        y[q] = wrap_periodic(yq + drift * qy, box, inv_box);
+        z[q] = wrap_periodic(zq + drift * qz, box, inv_box);
+      }
     }
   }
 }

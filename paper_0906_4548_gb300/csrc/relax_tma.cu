@@ -17,8 +17,9 @@
 //   2. writes D_new and forward-transforms it along z into the transposed half
 //      spectrum, ready for the next iteration's y pass;
 //   3. emits FP64 block partials of sum |R|, sum D_new, bad points, non-finite R.
-// The arithmetic of r, R, B' and Delta is a policy: FP32, pairs of floats with
-// error-free transformations (about 48 significant bits), or FP64.
+// The arithmetic of r, R, B' and Delta is a policy: FP32; FP32 with an exact
+// discriminant and pair sums (the mixed default); pairs of floats with
+// error-free transformations for R and Delta (about 48 significant bits); or FP64.
 //
 // Data movement.  The spectra are read as TMA tiles (one tensor map per
 // spectrum; a tile is 16 complex values along y, 128 bytes, for every kz),
@@ -74,6 +75,38 @@ struct RxF32 {
   __device__ static double sum_d(Sum s) { return (double)s; }
 };
 
+// Config-3 mixed arithmetic: R, B' and D_new in FP32 (the FP32 data's own
+// rounding already leaves a residual floor of order 1e-8 of <|S|>, which
+// pair arithmetic cannot go below); the discriminant's sign from Delta formed
+// exactly for the FP32 s = alpha + 2 (1 - w) d and R (a pair); the per-thread
+// sum of D_new (its mean is removed next iteration) as a pair; every
+// cross-thread sum in FP64.
+struct RxM32 {
+  using Acc = float;
+  using Sum = float;
+  __device__ static void pair_a(Acc& r, float x, float y) { RxF32::pair_a(r, x, y); }
+  __device__ static void pair_b(Acc& r, float x, float n, const RelaxParams& rp) { RxF32::pair_b(r, x, n, rp); }
+  __device__ static PointOut finish(Acc r, float a, float b, float D, float S, float m_hi, float, double,
+                                    const RelaxParams& rp, Sum& rsum, float& nonfin) {
+    const float d = D - m_hi, u = a + b, c = d - u;
+    const float R = fmaf(2.f * a, b, fmaf(2.f * u, c, fmaf(rp.alpha_hi, d, r - S)));
+    PointOut o;
+    o.bp = fmaf(d, fmaf(rp.omw, d, rp.alpha_hi), -R);
+    const float s = fmaf(rp.two_omw, d, rp.alpha_hi);
+    FP v = fp_prod(s, s);
+    FP t = fp_prod(-rp.four_omw_hi, R);
+    t.lo = fmaf(-rp.four_omw_lo, R, t.lo);
+    fp_acc(v, t);
+    v = fp_fast(v.hi, v.lo);
+    o.neg = v.hi < 0.f || (v.hi == 0.f && v.lo < 0.f);
+    o.dt = v.hi + v.lo;
+    if (isfinite(R)) rsum += fabsf(R);
+    else nonfin += 1.f;
+    return o;
+  }
+  __device__ static double sum_d(Sum s) { return (double)s; }
+};
+
 struct RxEFT {
   using Acc = FP;
   using Sum = FP;
@@ -109,13 +142,8 @@ struct RxEFT {
     fp_acc(r, FP{-S, 0.f});
     const FP R = fp_fast(r.hi, r.lo);
     PointOut o;
-    {
-      const float w1 = fmaf(rp.omw, d.hi, rp.alpha_hi);
-      FP bb = fp_prod(d.hi, w1);
-      bb.lo = fmaf(d.lo, w1, bb.lo);
-      fp_acc(bb, FP{-R.hi, -R.lo});
-      o.bp = bb.hi + bb.lo;
-    }
+    // B' only feeds D_new, an FP32 datum: FP32 from the pair-accurate R and d suffices
+    o.bp = fmaf(d.hi, fmaf(rp.omw, d.hi, rp.alpha_hi), -R.hi);
     {
       const float s = fmaf(rp.two_omw, d.hi, rp.alpha_hi);
       FP v = fp_prod(s, s);
@@ -232,6 +260,12 @@ __device__ __forceinline__ void pair_inverse(unsigned char* buf, const float2* s
   constexpr int N1 = G::N1, N2 = G::N2;
   const unsigned char* TA = buf;
   const unsigned char* TB = buf + G::FIELD;
+  // With N2 a multiple of 8 and one box, row kk of a read satisfies kk = +-lane (mod 8) for
+  // every j1, so the swizzle term is one constant per thread and direction.
+  constexpr bool HOIST = N2 % 8 == 0 && G::NBOX == 1;
+  const unsigned off_d = (unsigned)lane * G::ROWB + (((unsigned)row * 8u) ^ (((unsigned)lane & 7u) << 4));
+  const unsigned off_m =
+      (unsigned)(N - lane) * G::ROWB + (((unsigned)row * 8u) ^ (((unsigned)(N - lane) & 7u) << 4));
   float2 v[N1];
   if (lane < N2) {
 #pragma unroll
@@ -243,8 +277,11 @@ __device__ __forceinline__ void pair_inverse(unsigned char* buf, const float2* s
       else if (N2 * j1 > N / 2) mirror = true;
       else mirror = k > N / 2;
       const int kk = mirror ? N - k : k;
-      A = *reinterpret_cast<const float2*>(TA + tile_off<N>(kk, row));
-      B = *reinterpret_cast<const float2*>(TB + tile_off<N>(kk, row));
+      unsigned off;
+      if constexpr (HOIST) off = mirror ? off_m - (unsigned)(N2 * j1 * G::ROWB) : off_d + (unsigned)(N2 * j1 * G::ROWB);
+      else off = tile_off<N>(kk, row);
+      A = *reinterpret_cast<const float2*>(TA + off);
+      B = *reinterpret_cast<const float2*>(TB + off);
       if (mirror) {
         A.y = -A.y;
         B.y = -B.y;
@@ -327,47 +364,57 @@ __global__ void __launch_bounds__(RGeom<N>::THREADS, RGeom<N>::MINB)
 
   Acc r[N2];
   float ra[N2], rb[N2];
-  // ---- pair A: (H_xy, H_xz)
-  if (__syncthreads_or(!mbar_wait_bounded(&bars[0], 0, lim))) { give_up(); return; }
-  done0 = 1;
-  pair_inverse<N>(buf0, s_tw, row, lane, ra, rb);
-#pragma unroll
-  for (int k2 = 0; k2 < N2; ++k2) AR::pair_a(r[k2], ra[k2], rb[k2]);
-  fence_proxy_async();
-  __syncthreads();  // buf0 is free: pair C lands there
-  if (tid == 0) {
-    issue_spectra<N>(buf0, &args.map[0], &args.map[1], x, y0, &bars[0]);
-  }
-  issued0 = 2;
-  // ---- pair B: (H_yz, N)
-  if (__syncthreads_or(!mbar_wait_bounded(&bars[1], 0, lim))) { give_up(); return; }
-  done1 = 1;
-  pair_inverse<N>(buf1, s_tw, row, lane, ra, rb);
-#pragma unroll
-  for (int k2 = 0; k2 < N2; ++k2) AR::pair_b(r[k2], ra[k2], rb[k2], rp);
-  fence_proxy_async();
-  __syncthreads();  // buf1 is free: the D and S rows land there
   float* sD = reinterpret_cast<float*>(buf1);
   float* sS = sD + TY * ROWP;
-  if (tid < 32) {
-    if (tid == 0) mbar_expect_tx(&bars[1], 2u * TY * N * 4);
-    __syncwarp();
-    const int64_t rbase0 = ((int64_t)x * N + y0) * N;
-    for (int i = tid; i < 2 * TY; i += 32) {
-      const int rr = i % TY;
-      const float* src = (i < TY ? args.D : args.S) + rbase0 + (int64_t)rr * N;
-      bulk_load((i < TY ? sD : sS) + rr * ROWP, src, N * 4, &bars[1]);
+  // pairs A = (H_xy, H_xz) from buf0, B = (H_yz, N) from buf1, C = (H_xx, H_yy) from buf0 again;
+  // one barrier per pair: after it every thread is done with the previous pair's buffer, which
+  // then receives its next copy (C after A, the D and S rows after B)
+#pragma unroll 1
+  for (int pr = 0; pr < 3; ++pr) {
+    uint64_t* bar = &bars[pr == 1 ? 1 : 0];
+    unsigned char* buf = pr == 1 ? buf1 : buf0;
+    fence_proxy_async();  // this thread's accesses to the previous buffer precede the copy into it
+    if (__syncthreads_or(!mbar_wait_bounded(bar, pr == 2 ? 1u : 0u, lim))) {
+      give_up();
+      return;
+    }
+    if (pr == 0) done0 = 1;
+    else if (pr == 1) done1 = 1;
+    else done0 = 2;
+    if (pr == 1) {
+      if (tid == 0) issue_spectra<N>(buf0, &args.map[0], &args.map[1], x, y0, &bars[0]);
+      issued0 = 2;
+    } else if (pr == 2) {
+      if (tid < 32) {
+        if (tid == 0) mbar_expect_tx(&bars[1], 2u * TY * N * 4);
+        __syncwarp();
+        const int64_t rbase0 = ((int64_t)x * N + y0) * N;
+        for (int i = tid; i < 2 * TY; i += 32) {
+          const int rr = i % TY;
+          const float* src = (i < TY ? args.D : args.S) + rbase0 + (int64_t)rr * N;
+          bulk_load((i < TY ? sD : sS) + rr * ROWP, src, N * 4, &bars[1]);
+        }
+      }
+      issued1 = 2;
+    }
+    pair_inverse<N>(buf, s_tw, row, lane, ra, rb);
+    if (pr == 0) {
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) AR::pair_a(r[k2], ra[k2], rb[k2]);
+    } else if (pr == 1) {
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) AR::pair_b(r[k2], ra[k2], rb[k2], rp);
     }
   }
-  issued1 = 2;
-  // ---- pair C: (H_xx, H_yy)
-  if (__syncthreads_or(!mbar_wait_bounded(&bars[0], 1, lim))) { give_up(); return; }
-  done0 = 2;
-  pair_inverse<N>(buf0, s_tw, row, lane, ra, rb);
-  if (__syncthreads_or(!mbar_wait_bounded(&bars[1], 1, lim))) { give_up(); return; }
+  // ra, rb hold a = H_xx and b = H_yy
+  if (__syncthreads_or(!mbar_wait_bounded(&bars[1], 1, lim))) {
+    give_up();
+    return;
+  }
   // ---- residual and update; D_new replaces D in shared memory for the forward transform
   Sum rsum{};
-  float acc_d = 0.f, nbad = 0.f, nonfin = 0.f;
+  FP acc_d{0.f, 0.f};  // sum of D_new: its mean is removed next iteration
+  float nbad = 0.f, nonfin = 0.f;
   const int64_t rbase = ((int64_t)x * N + y0 + row) * N;
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2) {
@@ -383,7 +430,8 @@ __global__ void __launch_bounds__(RGeom<N>::THREADS, RGeom<N>::MINB)
     const float dn = 2.f * bpt / (rp.alpha_f + sqrtf(dt));
     args.Dnew[rbase + z] = dn;
     sD[row * ROWP + z] = dn;
-    acc_d += dn;
+    if constexpr (std::is_same<AR, RxF32>::value) acc_d.hi += dn;
+    else fp_acc(acc_d, FP{dn, 0.f});
   }
   __syncthreads();
   // ---- forward z transform of D_new (two rows per pencil), written transposed
@@ -434,7 +482,7 @@ __global__ void __launch_bounds__(RGeom<N>::THREADS, RGeom<N>::MINB)
   // ---- block statistics: within a warp float pairs (FP64 for the FP64 policy), across warps FP64
   const int wl = tid & 31, wid = tid >> 5;
   if constexpr (std::is_same<Sum, double>::value) {
-    double v4[4] = {rsum, (double)acc_d, (double)nbad, (double)nonfin};
+    double v4[4] = {rsum, (double)acc_d.hi + (double)acc_d.lo, (double)nbad, (double)nonfin};
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
 #pragma unroll
@@ -442,7 +490,7 @@ __global__ void __launch_bounds__(RGeom<N>::THREADS, RGeom<N>::MINB)
       if (wl == 0) s_part[c * 32 + wid] = v4[c];
     }
   } else {
-    FP r2 = pair_of(rsum), d2{acc_d, 0.f};
+    FP r2 = pair_of(rsum), d2 = acc_d;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       fp_acc(r2, FP{__shfl_xor_sync(0xffffffffu, r2.hi, o), __shfl_xor_sync(0xffffffffu, r2.lo, o)});
@@ -523,6 +571,7 @@ void launch_relax_tma(int arith, const RelaxMaps& maps, const float* D, const do
   a.skip = skip; a.fault = fault; a.wait_ns = wait_ns; a.withhold = withhold;
   if (arith == ARITH_F64) launch_rt<N, RxF64>(a, tw, s);
   else if (arith == ARITH_EFT) launch_rt<N, RxEFT>(a, tw, s);
+  else if (arith == ARITH_M32) launch_rt<N, RxM32>(a, tw, s);
   else launch_rt<N, RxF32>(a, tw, s);
 }
 

@@ -15,7 +15,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 
 DGP_OK, DGP_E_INVALID, DGP_E_CUDA, DGP_E_NOMEM, DGP_E_NONFINITE = 0, 1, 2, 3, 4
 DGP_E_NOT_CONVERGED, DGP_E_BAD_POINTS, DGP_E_TIMEOUT, DGP_E_STATE = 5, 6, 7, 8
-DGP_FP32, DGP_MIXED, DGP_FP64, DGP_MIXED_EFT = 0, 1, 2, 3
+DGP_FP32, DGP_MIXED, DGP_FP64, DGP_MIXED_EFT, DGP_MIXED_F32R = 0, 1, 2, 3, 4
 DGP_GRAVITY_NL, DGP_GRAVITY_LDGP, DGP_GRAVITY_GRH, DGP_GRAVITY_SPH = 0, 1, 2, 3
 C_OVER_H0 = 2997.92458
 

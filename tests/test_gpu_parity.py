@@ -135,6 +135,9 @@ def _solve_both(dgp, torch_dev, n, box, a, prec, tol_gpu, seed=5, w=1 / 3, local
     (48, 150.0, 0.5, 3, 1e-6, 1e-5),
     (96, 200.0, 0.7, 3, 1e-6, 1e-5),
     (96, 200.0, 0.7, 0, 1e-6, 1e-5),
+    (64, 200.0, 0.5, 4, 1e-6, 1e-5),       # mixed, FP32 residual with exact discriminant and pair sums
+    (128, 200.0, 1.0, 4, 1e-6, 1e-5),
+    (48, 150.0, 0.5, 4, 1e-6, 1e-5),
 ])
 def test_solve_phi_and_forces_parity(dgp, torch_dev, n, box, a, prec, tol_gpu, tol_phi):
     got, want = _solve_both(dgp, torch_dev, n, box, a, prec, tol_gpu)
@@ -413,7 +416,7 @@ def test_full_size_deposit_pk_solve(dgp, torch_dev, full_case):
     assert rel_l2(phig, phio) < 1e-5
 
 
-@pytest.mark.parametrize("prec,rtol", [(2, 1e-6), (1, 2e-3), (3, 2e-3), (0, 2e-3)])
+@pytest.mark.parametrize("prec,rtol", [(2, 1e-6), (1, 2e-3), (3, 2e-3), (0, 2e-3), (4, 2e-3)])
 def test_residual_history_follows_oracle(dgp, torch_dev, prec, rtol):
     """The GPU iterates are the oracle's iterates: the normalised residual of
     each iterate agrees while it is far above the precision floor."""

@@ -116,10 +116,7 @@ __device__ __forceinline__ double geff_dev(const KParams& kp, double kmag) {
 }
 
 template <typename T, int N, int OP>
-__global__ void __launch_bounds__(XGeom<T, N>::THREADS,
-                                  (OP == XOP_HESSIAN && sizeof(T) == 4 && XGeom<T, N>::THREADS <= 256)
-                                      ? 3
-                                      : XGeom<T, N>::MIN_BLOCKS)
+__global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
     k_fft_x(const __grid_constant__ XArgs<T> args, const vec2_t<T>* __restrict__ g_tw) {
   if (args.skip && *args.skip) return;
   using V = vec2_t<T>;

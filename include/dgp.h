@@ -337,26 +337,41 @@ int dgp_set_blocking_sync(dgp_ctx *c, int on);
 
 /* ---- Batches of independent realisations --------------------------------
  * Not part of the paper's method: many small boxes (e.g. 48 realisations of
- * 48^3, 64^3 and 96^3 meshes with different boxes and r_c) stepped together
- * so the GPU overlaps their small kernels.  Each realisation is a context on
- * its own non-blocking stream, stepped by its own host worker thread; the
- * contexts use blocking host waits.
+ * 48^3, 64^3 and 96^3 meshes with different boxes and r_c) stepped together.
+ * The realisations are grouped into classes: those with the same mesh size
+ * and precision, in the nonlinear mode (no local_only, no a_nonlinear), with
+ * FP32 mesh data and n <= 128, at most 16 to a class, in order of appearance.
+ * A class shares one non-blocking stream; its step launches each kernel stage
+ * once for all members (one launch of every FFT pass, relaxation pass, deposit
+ * and gather for the whole class), its members iterate in lockstep, each
+ * stopping by its own rules (members that have stopped skip at kernel entry),
+ * and its relaxation iterations replay as one CUDA graph.  Every member ends
+ * each step exactly as its own pm_step would leave it.  A realisation that
+ * forms no class is a context stepped alone on a stream of its own.  Each
+ * class or lone context has one host worker thread, so classes run
+ * concurrently; the contexts use blocking host waits.
  *   dgp_batch_create: count contexts from params[count] (sizes may differ)
  *     and one cosmology; DGP_E_INVALID, DGP_E_NOMEM or DGP_E_CUDA on failure,
  *     *out = NULL then.
  *   dgp_batch_context: the i-th context (for deposit, P(k), reset, ...); the
- *     batch keeps ownership (do not destroy it).
+ *     batch keeps ownership (do not destroy it).  Contexts of one class share
+ *     their stream.
  *   dgp_batch_step: pm_step of every realisation i with parts[i], a[i], da[i]
  *     (info[i] filled when info != NULL).  The batch streams first wait for
  *     the work enqueued so far on cuda_stream (may be NULL); the call returns
  *     when every realisation's step has completed on the device.  Returns
- *     the first non-OK status of a realisation (the others still step).
+ *     the first non-OK status of a realisation.  A class whose step is refused
+ *     for a bad argument (e.g. an empty particle set) steps its members one by
+ *     one instead, so the valid ones still step.
+ *   dgp_batch_classes: class_of[count] receives the class of each realisation
+ *     and *nclasses the number of classes and lone contexts.
  * Calls on one batch must not overlap. */
 typedef struct dgp_batch dgp_batch;
 int dgp_batch_create(dgp_batch **out, int count, const dgp_params *params, const dgp_cosmology *cosmo);
 int dgp_batch_context(dgp_batch *b, int i, dgp_ctx **out);
 int dgp_batch_step(dgp_batch *b, dgp_particles *parts, const double *a, const double *da, dgp_solve_info *info,
                    void *cuda_stream);
+int dgp_batch_classes(dgp_batch *b, int *class_of, int *nclasses);
 void dgp_batch_destroy(dgp_batch *b);
 
 /* Spectra of the brane-bending mode C of the context's accepted nonlinear

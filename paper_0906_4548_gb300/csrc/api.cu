@@ -277,6 +277,10 @@ class EngineBase {
   virtual int pk_adjoint(const dgp_particles* pp, int nbins, const double* dldp, dgp_particles* cot) = 0;
   virtual int step(dgp_particles* parts, double a, double da, dgp_solve_info* info) = 0;
   virtual int step_host(dgp_particles* parts, double a, double da, dgp_solve_info* info) = 0;
+  // One pm_step of every member of a class of realisations (this engine first; all
+  // of the same type and stream), each kernel stage launched once for the class.
+  virtual int step_class(EngineBase* const* members, int count, dgp_particles* parts, const double* a,
+                         const double* da, dgp_solve_info* info) = 0;
   virtual int pk(const void* delta, int nbins, double* k, double* pk, int64_t* nmodes) = 0;
   virtual int bispec(const void* delta, double k1, double k2, int ntheta, const double* theta, double dk,
                      double* b, double* q) = 0;
@@ -401,6 +405,7 @@ class Engine : public EngineBase {
     if (drift_ev) cudaEventDestroy(drift_ev);
     for (int i = 0; i < 3; ++i)
       if (pair_exec[i]) cudaGraphExecDestroy(pair_exec[i]);
+    if (class_exec) cudaGraphExecDestroy(class_exec);
     set_blocking(false);
     for (int i = 0; i < 6; ++i) cudaFree(srt_tmp[i]);
     cudaFreeHost(h_stats);
@@ -537,6 +542,26 @@ class Engine : public EngineBase {
     return kp;
   }
 
+  RelaxParams relax_params(const Coef& c) const {
+    RelaxParams rp;
+    rp.alpha = c.alpha; rp.w = p.w; rp.c2 = c.c2; rp.inv_m = 1.0 / (double)M;
+    auto split = [](double v, float& hi, float& lo) { hi = (float)v; lo = (float)(v - (double)hi); };
+    split(c.alpha, rp.alpha_hi, rp.alpha_lo);
+    split(c.c2, rp.c2_hi, rp.c2_lo);
+    split(4.0 * (1.0 - p.w), rp.four_omw_hi, rp.four_omw_lo);
+    rp.omw = (float)(1.0 - p.w);
+    rp.two_omw = (float)(2.0 * (1.0 - p.w));
+    rp.alpha_f = (float)c.alpha;
+    rp.bad_bp_f = (float)(-c.alpha * c.alpha / (4.0 * (1.0 - p.w)));
+    return rp;
+  }
+  int arith_mode() const {
+    return p.precision == DGP_FP32         ? ARITH_F32
+           : p.precision == DGP_MIXED_EFT  ? ARITH_EFT
+           : p.precision == DGP_MIXED_F32R ? ARITH_M32
+                                           : ARITH_F64;
+  }
+
   static FieldSet<T> fs(V* const* ptrs, int n) {
     FieldSet<T> f;
     for (int i = 0; i < kMaxFields; ++i) f.p[i] = i < n ? ptrs[i] : nullptr;
@@ -633,20 +658,8 @@ class Engine : public EngineBase {
       if ((rc = reduce_sum(rS, true, d_misc + 1))) return rc;
       if (need_lin && (rc = reduce_sum(rD[j0], false, d_rstats + 4 * j0 + 1))) return rc;
 
-      RelaxParams rp;
-      rp.alpha = c.alpha; rp.w = p.w; rp.c2 = c.c2; rp.inv_m = 1.0 / (double)M;
-      auto split = [](double v, float& hi, float& lo) { hi = (float)v; lo = (float)(v - (double)hi); };
-      split(c.alpha, rp.alpha_hi, rp.alpha_lo);
-      split(c.c2, rp.c2_hi, rp.c2_lo);
-      split(4.0 * (1.0 - p.w), rp.four_omw_hi, rp.four_omw_lo);
-      rp.omw = (float)(1.0 - p.w);
-      rp.two_omw = (float)(2.0 * (1.0 - p.w));
-      rp.alpha_f = (float)c.alpha;
-      rp.bad_bp_f = (float)(-c.alpha * c.alpha / (4.0 * (1.0 - p.w)));
-      const int arith = p.precision == DGP_FP32        ? ARITH_F32
-                        : p.precision == DGP_MIXED_EFT   ? ARITH_EFT
-                        : p.precision == DGP_MIXED_F32R  ? ARITH_M32
-                                                         : ARITH_F64;
+      const RelaxParams rp = relax_params(c);
+      const int arith = arith_mode();
 
       // Buffers: the starting iterate stays in rD[j0]; iteration it >= 1 reads
       // the previous output, and the outputs alternate between the other two.
@@ -931,6 +944,400 @@ class Engine : public EngineBase {
     return DGP_OK;
   }
 
+  // ---------------------------------------------------------------- classes of realisations
+  // pm_step of every member of a class (same mesh, precision and stream; the nonlinear
+  // mode), each kernel stage launched once for all members with the member on the grid's
+  // z (or y) index.  Every member ends in the state its own pm_step would leave it in:
+  // the same iterates, stop rules, warm start and reused end-of-step force.
+  cudaGraphExec_t class_exec = nullptr;  // the class's two-iteration graph (held by its first member)
+
+  int step_class(EngineBase* const* members, int count, dgp_particles* parts, const double* a, const double* da,
+                 dgp_solve_info* info) override {
+    if constexpr (sizeof(T) != 4 || N > 128) {
+      return DGP_E_INVALID;
+    } else {
+      if (count < 1 || count > kBatchMax || !members || members[0] != this || !parts || !a || !da)
+        return DGP_E_INVALID;
+      std::vector<Engine*> E(count);
+      std::vector<int> all(count), start;
+      for (int r = 0; r < count; ++r) {
+        Engine* e = dynamic_cast<Engine*>(members[r]);
+        if (!e || e->stream != stream || e->p.gravity != DGP_GRAVITY_NL || e->p.local_only || e->p.a_nonlinear > 0.0 ||
+            e->p.precision != p.precision)
+          return DGP_E_INVALID;
+        dgp_particles* pp = &parts[r];
+        if (!valid_parts(pp) || pp->n == 0) return DGP_E_INVALID;
+        if (!(a[r] > 0.0) || !(da[r] > 0.0) || !isfinite(a[r] + da[r])) return DGP_E_INVALID;
+        E[r] = e;
+        all[r] = r;
+        e->force_host = nullptr;
+        const bool reuse = e->force_valid && e->force_x == pp->x && e->force_np == pp->n &&
+                           fabs(e->force_a - a[r]) <= 1e-12 * a[r];
+        if (!reuse) start.push_back(r);
+      }
+      int rc;
+      if (!start.empty() && (rc = class_forces(E, start, parts, a, nullptr))) return rc;
+      std::vector<double> a1(count), k2(count);
+      GatherArgs g[kBatchMax];
+      for (int r = 0; r < count; ++r) {
+        Engine* e = E[r];
+        const double om = e->cosmo.omega_m0, rcH = e->p.rc_H0;
+        a1[r] = a[r] + da[r];
+        const double ah = exp(0.5 * (log(a[r]) + log(a1[r])));
+        const dgp_particles* pp = &parts[r];
+        g[r] = GatherArgs{{(float*)pp->x, (float*)pp->y, (float*)pp->z, (float*)pp->px, (float*)pp->py, (float*)pp->pz},
+                          pp->n, {e->rG[0], e->rG[1], e->rG[2]}, e->cic(),
+                          (float)time_integral(a[r], ah, om, rcH, 0), (float)time_integral(a[r], a1[r], om, rcH, 2), 1};
+        k2[r] = time_integral(ah, a1[r], om, rcH, 0);
+      }
+      launch_gather_kick_batch(g, count, stream);
+      DGP_CHECK_LAUNCH();
+      for (int r = 0; r < count; ++r) {
+        Engine* e = E[r];
+        ++e->nsteps;
+        if (e->p.sort_every > 0 && e->nsteps % e->p.sort_every == 0 && (rc = e->sort_impl(&parts[r], nullptr)))
+          return rc;
+      }
+      if ((rc = class_forces(E, all, parts, a1.data(), info))) return rc;
+      for (int r = 0; r < count; ++r) {
+        g[r].kick = (float)k2[r];
+        g[r].drift = 0.f;
+        g[r].do_drift = 0;
+      }
+      launch_gather_kick_batch(g, count, stream);
+      DGP_CHECK_LAUNCH();
+      return DGP_OK;
+    }
+  }
+
+ private:
+  // Deposit and field solve at a[r] for the members in sub; forces in each member's rG.
+  static int class_forces(std::vector<Engine*>& E, const std::vector<int>& sub, const dgp_particles* parts,
+                          const double* a, dgp_solve_info* info) {
+    const int n = (int)sub.size();
+    const cudaStream_t s = E[0]->stream;
+    float* rho[kBatchMax];
+    DepositArgs<T> dep[kBatchMax];
+    for (int k = 0; k < n; ++k) {
+      Engine* e = E[sub[k]];
+      const dgp_particles* pp = &parts[sub[k]];
+      rho[k] = (float*)e->rRho;
+      dep[k] = DepositArgs<T>{(const T*)pp->x, (const T*)pp->y, (const T*)pp->z, pp->n, e->rRho, e->cic()};
+    }
+    launch_zero_batch(rho, M, n, s);
+    launch_cic_deposit_batch<T>(dep, n, s);
+    if (cudaGetLastError() != cudaSuccess) return DGP_E_CUDA;
+    const int rc = class_solve(E, sub, a, info);
+    if (rc != DGP_OK && rc != DGP_E_NOT_CONVERGED) return rc;
+    for (int k = 0; k < n; ++k) {
+      Engine* e = E[sub[k]];
+      e->force_valid = true;
+      e->force_a = a[sub[k]];
+      e->force_x = parts[sub[k]].x;
+      e->force_np = parts[sub[k]].n;
+    }
+    return DGP_OK;
+  }
+
+  // Batched one-field sums of field(k) into out(k).
+  template <class FA, class FO>
+  static void class_sum(std::vector<Engine*>& S, bool absval, FA field, FO out) {
+    const int n = (int)S.size();
+    const float* src[kBatchMax];
+    double* parts[kBatchMax];
+    double* dst[kBatchMax];
+    for (int k = 0; k < n; ++k) {
+      src[k] = (const float*)field(k);
+      parts[k] = S[k]->partials;
+      dst[k] = out(k);
+    }
+    launch_sum_batch(src, M, absval, parts, S[0]->nblocks, dst, n, S[0]->stream);
+  }
+
+  // The field solve of solve_impl (nonlinear mode, from a CIC mass mesh) for the members in sub.
+  static int class_solve(std::vector<Engine*>& E, const std::vector<int>& sub, const double* a,
+                         dgp_solve_info* info) {
+    const int n = (int)sub.size();
+    std::vector<Engine*> S(n);
+    for (int k = 0; k < n; ++k) S[k] = E[sub[k]];
+    Engine* e0 = S[0];
+    const cudaStream_t st = e0->stream;
+    const V* tw = e0->tw;
+    const int yt = e0->y_threads;
+    std::vector<KParams> kp(n);
+    std::vector<RelaxParams> rp(n);
+    std::vector<int> j0(n), pb0(n), pb1(n);
+    for (int k = 0; k < n; ++k) {
+      Engine* e = S[k];
+      const Coef c = coefficients(a[sub[k]], e->cosmo.omega_m0, e->p.rc_H0);
+      kp[k] = e->kparams(c, DGP_GRAVITY_NL);
+      rp[k] = e->relax_params(c);
+      e->delta_nl = true;
+      e->last_nl_a = a[sub[k]];
+    }
+    auto check = [] { return cudaGetLastError() == cudaSuccess ? DGP_OK : DGP_E_CUDA; };
+    // density contrast from the mass mesh, its z and y transforms
+    class_sum(S, false, [&](int k) { return S[k]->rRho; }, [&](int k) { return S[k]->d_misc + 0; });
+    {
+      const float* in[kBatchMax];
+      V* out[kBatchMax];
+      ZPrologue pro[kBatchMax];
+      FieldSet<T> f[kBatchMax];
+      for (int k = 0; k < n; ++k) {
+        in[k] = S[k]->rRho;
+        out[k] = S[k]->sDelta;
+        pro[k] = ZPrologue{S[k]->d_misc + 0, 1.0 / (double)M, 1};
+        f[k] = fs(&S[k]->sDelta, 1);
+      }
+      launch_fft_z_r2c_batch<T, N>(in, out, pro, n, tw, st);
+      launch_fft_y_batch<T, N>(f, nullptr, nullptr, n, 1, false, tw, st, yt);
+    }
+    // source S; the linear start D_lin for members without a warm start
+    for (int lin = 0; lin < 2; ++lin) {
+      XReal<T> xr[kBatchMax];
+      FieldSet<T> fi[kBatchMax], fo[kBatchMax];
+      int m = 0;
+      for (int k = 0; k < n; ++k) {
+        Engine* e = S[k];
+        if ((e->wcur < 0) != (lin == 1)) continue;
+        j0[k] = lin ? 0 : e->wcur;
+        xr[m] = XReal<T>{e->sDelta, nullptr, fs(e->s6, lin ? 2 : 1), 0, kp[k], nullptr};
+        fi[m] = fs(e->s6, lin ? 2 : 1);
+        T* outs[2] = {e->rS, e->rD[j0[k]]};
+        for (int i = 0; i < kMaxFields; ++i) fo[m].p[i] = i < (lin ? 2 : 1) ? reinterpret_cast<V*>(outs[i]) : nullptr;
+        ++m;
+      }
+      if (!m) continue;
+      launch_fft_x_batch<T, N>(lin ? XOP_SOURCE_LIN : XOP_SOURCE, xr, m, tw, st);
+      launch_fft_y_batch<T, N>(fi, nullptr, nullptr, m, lin ? 2 : 1, true, tw, st, yt);
+      launch_fft_z_c2r_batch<T, N>(fi, fo, lin ? 2 : 1, m, tw, st);
+    }
+    // eps = <|S|> (read by the controller at the first iteration); the mean of D_lin
+    class_sum(S, true, [&](int k) { return S[k]->rS; }, [&](int k) { return S[k]->d_misc + 1; });
+    {
+      std::vector<Engine*> L;
+      std::vector<int> lk;
+      for (int k = 0; k < n; ++k)
+        if (S[k]->wcur < 0) {
+          L.push_back(S[k]);
+          lk.push_back(k);
+        }
+      if (!L.empty())
+        class_sum(L, false, [&](int i) { return L[i]->rD[0]; }, [&](int i) { return L[i]->d_rstats + 1; });
+    }
+    for (int k = 0; k < n; ++k) {
+      int q = 0;
+      int pb[2];
+      for (int b = 0; b < 3; ++b)
+        if (b != j0[k]) pb[q++] = b;
+      pb0[k] = pb[0];
+      pb1[k] = pb[1];
+    }
+    auto in_buf = [&](int k, int it) { return it == 0 ? j0[k] : ((it - 1) & 1 ? pb1[k] : pb0[k]); };
+    auto out_buf = [&](int k, int it) { return it & 1 ? pb1[k] : pb0[k]; };
+    auto spec_in = [&](int k, int it) { return (it & 1) ? S[k]->sD2 : S[k]->sD; };
+    auto spec_out = [&](int k, int it) { return (it & 1) ? S[k]->sD : S[k]->sD2; };
+    // forward transforms of the starting iterates
+    {
+      const float* in[kBatchMax];
+      V* out[kBatchMax];
+      ZPrologue pro[kBatchMax];
+      FieldSet<T> f[kBatchMax];
+      for (int k = 0; k < n; ++k) {
+        in[k] = S[k]->rD[j0[k]];
+        out[k] = S[k]->sD;
+        pro[k] = ZPrologue{nullptr, 0.0, 0};
+        f[k] = fs(&S[k]->sD, 1);
+      }
+      launch_fft_z_r2c_batch<T, N>(in, out, pro, n, tw, st);
+      launch_fft_y_batch<T, N>(f, nullptr, nullptr, n, 1, false, tw, st, yt);
+    }
+    for (int k = 0; k < n; ++k)
+      if (cudaMemsetAsync(S[k]->d_ctl, 0, sizeof(SolveCtl), st) != cudaSuccess) return DGP_E_CUDA;
+    int rc;
+    if ((rc = check())) return rc;
+    // one iteration of the members in ks
+    auto enqueue = [&](int it, bool control, const std::vector<int>& ks) {
+      const int m = (int)ks.size();
+      XReal<T> xr[kBatchMax];
+      FieldSet<T> f6[kBatchMax], f1[kBatchMax];
+      const int* sk[kBatchMax];
+      RelaxTmaArgs ra[kBatchMax];
+      YControl yc[kBatchMax];
+      for (int i = 0; i < m; ++i) {
+        const int k = ks[i];
+        Engine* e = S[k];
+        const int ib = in_buf(k, it), ob = out_buf(k, it);
+        sk[i] = control ? &e->d_ctl->done : nullptr;
+        xr[i] = XReal<T>{spec_in(k, it), nullptr, fs(e->s6, 6), 0, kp[k], sk[i]};
+        f6[i] = fs(e->s6, 6);
+        ra[i].map[0] = e->rmaps.map[0];
+        for (int q = 0; q < 6; ++q) ra[i].map[q] = e->rmaps.map[q];
+        ra[i].D = e->rD[ib];
+        ra[i].dsum = e->d_rstats + 4 * ib + 1;
+        ra[i].S = e->rS;
+        ra[i].Dnew = e->rD[ob];
+        ra[i].Snew = spec_out(k, it);
+        ra[i].partials = e->partials;
+        ra[i].rp = rp[k];
+        ra[i].skip = sk[i];
+        ra[i].fault = &e->d_ctl->fault;
+        ra[i].wait_ns = e->wait_ns;
+        ra[i].withhold = e->withhold;
+        V* so = spec_out(k, it);
+        f1[i] = fs(&so, 1);
+        yc[i] = YControl{e->partials, e->fblocks, e->d_rstats + 4 * ob, e->d_ctl, e->d_misc + 1, e->d_hist,
+                         e->p.max_iter, kPatience, e->p.tol, 1.0 / (double)M};
+      }
+      launch_fft_x_batch<T, N>(XOP_HESSIAN, xr, m, tw, st);
+      launch_fft_y_batch<T, N>(f6, sk, nullptr, m, 6, true, tw, st, yt);
+      launch_relax_tma_batch<N>(e0->arith_mode(), ra, m, tw, st);
+      if (control) {
+        launch_fft_y_batch<T, N>(f1, sk, yc, m, 1, false, tw, st, yt);
+      } else {
+        for (int i = 0; i < m; ++i) {
+          Engine* e = S[ks[i]];
+          launch_finalize(e->partials, e->fblocks, 4, e->d_rstats + 4 * out_buf(ks[i], it), st, nullptr);
+        }
+        launch_fft_y_batch<T, N>(f1, sk, nullptr, m, 1, false, tw, st, yt);
+      }
+      return check();
+    };
+    std::vector<int> everyone(n);
+    for (int k = 0; k < n; ++k) everyone[k] = k;
+    // iterations 1 and 2 as one graph for the class (buffers alternate with period two)
+    bool graphs = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
+    if (graphs) {
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        cudaGetLastError();
+        graphs = false;
+      } else {
+        const int r1 = enqueue(1, true, everyone), r2 = r1 ? r1 : enqueue(2, true, everyone);
+        const cudaError_t ce = cudaStreamEndCapture(st, &g);
+        cudaGraphExec_t& ex = e0->class_exec;
+        if (r1 || r2 || ce != cudaSuccess || !g) {
+          graphs = false;
+        } else {
+          if (ex) {
+            cudaGraphExecUpdateResultInfo ui;
+            if (cudaGraphExecUpdate(ex, g, &ui) != cudaSuccess) {
+              cudaGetLastError();
+              cudaGraphExecDestroy(ex);
+              ex = nullptr;
+            }
+          }
+          if (!ex && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+            ex = nullptr;
+            graphs = false;
+          }
+        }
+        if (g) cudaGraphDestroy(g);
+        if (!graphs) cudaGetLastError();
+      }
+    }
+    int max_iter = 0, chunk = 4;
+    for (int k = 0; k < n; ++k) {
+      max_iter = std::max(max_iter, S[k]->p.max_iter);
+      if (S[k]->last_stop_it >= 0) chunk = std::max(chunk, S[k]->last_stop_it + 2);
+    }
+    int it = 0;
+    while (true) {
+      const int end = std::min(it + chunk, max_iter + 1);
+      while (it < end) {
+        if (graphs && it > 0 && (it & 1)) {
+          if (cudaGraphLaunch(e0->class_exec, st) != cudaSuccess) return DGP_E_CUDA;
+          it += 2;
+        } else {
+          if ((rc = enqueue(it, true, everyone))) return rc;
+          ++it;
+        }
+      }
+      for (int k = 0; k < n; ++k)
+        if (cudaMemcpyAsync(S[k]->h_ctl, S[k]->d_ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+          return DGP_E_CUDA;
+      if (e0->wait_stream() != cudaSuccess) return DGP_E_CUDA;
+      bool done = true;
+      for (int k = 0; k < n; ++k) done = done && S[k]->h_ctl->done;
+      if (done || it > max_iter) break;
+      chunk = kChunk;
+    }
+    int status = DGP_OK;
+    std::vector<SolveCtl> ctl(n);
+    for (int k = 0; k < n; ++k) {
+      ctl[k] = *S[k]->h_ctl;
+      if (!ctl[k].done) return DGP_E_STATE;
+      S[k]->history.assign(ctl[k].stop_it + 1, 0.0);
+      if (cudaMemcpyAsync(S[k]->history.data(), S[k]->d_hist, sizeof(double) * (ctl[k].stop_it + 1),
+                          cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return DGP_E_CUDA;
+    }
+    if (e0->wait_stream() != cudaSuccess) return DGP_E_CUDA;
+    std::vector<V*> sDphi(n);
+    for (int k = 0; k < n; ++k) {
+      Engine* e = S[k];
+      const SolveCtl& c = ctl[k];
+      if (c.status == CTL_FAULT) return DGP_E_TIMEOUT;
+      if (c.status == CTL_NONFINITE) return DGP_E_NONFINITE;
+      const int s_it = c.stop_it, best_it = c.best_it;
+      e->last_stop_it = s_it;
+      int accepted;
+      if (best_it == s_it) {
+        accepted = in_buf(k, s_it);
+        sDphi[k] = spec_in(k, s_it);
+      } else {
+        // an earlier iterate: replay the iterations that produced it for this member alone
+        if (best_it > 0) {
+          if ((rc = e->forward_zy(e->rD[j0[k]], e->sD, ZPrologue{nullptr, 0.0, 0}))) return rc;
+          const std::vector<int> one(1, k);
+          for (int q = 0; q < best_it; ++q)
+            if ((rc = enqueue(q, false, one))) return rc;
+        }
+        accepted = in_buf(k, best_it);
+        if ((rc = e->forward_zy(e->rD[accepted], e->sD, ZPrologue{nullptr, 0.0, 0}))) return rc;
+        sDphi[k] = e->sD;
+        if (best_it > 0) {
+          if (cudaMemcpyAsync(e->h_ctl, e->d_ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+              e->wait_stream() != cudaSuccess)
+            return DGP_E_CUDA;
+          if (e->h_ctl->fault) return DGP_E_TIMEOUT;
+        }
+      }
+      e->wcur = accepted;
+      if (c.status != CTL_CONVERGED) status = DGP_E_NOT_CONVERGED;
+      if (info) {
+        dgp_solve_info& inf = info[sub[k]];
+        memset(&inf, 0, sizeof(inf));
+        inf.eps = c.eps;
+        inf.iters = best_it;
+        inf.norm_res = c.rbest;
+        inf.min_norm_res = c.rbest;
+        inf.bad_fraction = c.last_bad / (double)M;
+        inf.status = c.status == CTL_CONVERGED ? DGP_OK : DGP_E_NOT_CONVERGED;
+      }
+    }
+    // forces g = -grad phi (Eq. FullDGP1) of every member
+    {
+      XReal<T> xr[kBatchMax];
+      FieldSet<T> fi[kBatchMax], fo[kBatchMax];
+      for (int k = 0; k < n; ++k) {
+        Engine* e = S[k];
+        xr[k] = XReal<T>{e->sDelta, sDphi[k], fs(e->s6, 4), 14, kp[k], nullptr};
+        V* sp[3] = {e->s6[1], e->s6[2], e->s6[3]};
+        fi[k] = fs(sp, 3);
+        T* outs[3] = {e->rG[0], e->rG[1], e->rG[2]};
+        for (int i = 0; i < kMaxFields; ++i) fo[k].p[i] = i < 3 ? reinterpret_cast<V*>(outs[i]) : nullptr;
+      }
+      launch_fft_x_batch<T, N>(XOP_PHI_FORCE, xr, n, tw, st);
+      launch_fft_y_batch<T, N>(fi, nullptr, nullptr, n, 3, true, tw, st, yt);
+      launch_fft_z_c2r_batch<T, N>(fi, fo, 3, n, tw, st);
+    }
+    if ((rc = check())) return rc;
+    if (info && e0->wait_stream() != cudaSuccess) return DGP_E_CUDA;
+    return status;
+  }
+
+ public:
   int step(dgp_particles* pp, double a, double da, dgp_solve_info* info) override {
     force_host = nullptr;
     return step_impl(pp, a, da, info, nullptr);
@@ -1642,6 +2049,25 @@ int dgp_profile_kinds(dgp_ctx* c, unsigned kind_mask) {
   c->eng->prof.reset(kind_mask & ((1u << dgp::KK_COUNT) - 1u));
   return DGP_OK;
 }
+
+}  // extern "C"
+
+namespace dgp {
+// One pm_step of a class of contexts (batch.cu): every context of the same mesh size,
+// precision and stream, stepped with each kernel stage launched once for all of them.
+int step_class(dgp_ctx* const* ctxs, int count, dgp_particles* parts, const double* a, const double* da,
+               dgp_solve_info* info) {
+  if (!ctxs || count < 1 || count > kBatchMax) return DGP_E_INVALID;
+  EngineBase* m[kBatchMax];
+  for (int i = 0; i < count; ++i) {
+    if (!ctxs[i]) return DGP_E_INVALID;
+    m[i] = ctxs[i]->eng;
+  }
+  return m[0]->step_class(m, count, parts, a, da, info);
+}
+}  // namespace dgp
+
+extern "C" {
 
 int dgp_set_wait_limit(dgp_ctx* c, double seconds, int withhold_first_copy) {
   if (!c || !(seconds > 0.0) || !(seconds <= 60.0)) return DGP_E_INVALID;

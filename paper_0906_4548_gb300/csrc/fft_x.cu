@@ -115,9 +115,14 @@ __device__ __forceinline__ double geff_dev(const KParams& kp, double kmag) {
   return 1.0 / (t1 + t2);
 }
 
-template <typename T, int N, int OP>
+template <typename T, int RB> struct XBatch {
+  XArgs<T> a[RB];
+};
+
+template <typename T, int N, int OP, int RB>
 __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
-    k_fft_x(const __grid_constant__ XArgs<T> args, const vec2_t<T>* __restrict__ g_tw) {
+    k_fft_x(const __grid_constant__ XBatch<T, RB> xb, const vec2_t<T>* __restrict__ g_tw) {
+  const XArgs<T>& args = xb.a[RB > 1 ? blockIdx.z : 0];  // realisation of this CTA
   if (args.skip && *args.skip) return;
   using V = vec2_t<T>;
   constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, TY = XGeom<T, N>::TY;
@@ -540,8 +545,8 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
 
 template <typename T, int N> int x_pass_blocks() { return (N / XGeom<T, N>::TY) * (N / 2 + 1); }
 
-template <typename T, int N, int OP>
-static void launch_x(const XArgs<T>& a, const vec2_t<T>* tw, cudaStream_t s) {
+template <typename T, int N, int OP, int RB = 1>
+static void launch_x(const XArgs<T>* a, int count, const vec2_t<T>* tw, cudaStream_t s) {
   using G = XGeom<T, N>;
   // the P(k) operations put their per-warp shell sums where the others keep
   // their per-thread multiplier tables
@@ -551,10 +556,35 @@ static void launch_x(const XArgs<T>& a, const vec2_t<T>* tw, cudaStream_t s) {
   const size_t tables = PK ? sizeof(double) * NW * 32 * NBS
                             : (OP == XOP_HESSIAN ? 0 : sizeof(T) * 2 * Split<N>::N2 * G::THREADS);
   const size_t per_bin = PK ? sizeof(double) * NW * NBS : 0;
-  const size_t smem = base + tables + per_bin * a.nbins;
-  raise_smem_limit<k_fft_x<T, N, OP>>(base + tables + per_bin * (N / 2));
-  dim3 grid(N / G::TY, N / 2 + 1);
-  k_fft_x<T, N, OP><<<grid, G::THREADS, smem, s>>>(a, tw);
+  const size_t smem = base + tables + per_bin * a[0].nbins;
+  raise_smem_limit<k_fft_x<T, N, OP, RB>>(base + tables + per_bin * (N / 2));
+  XBatch<T, RB> xb;
+  for (int r = 0; r < count; ++r) xb.a[r] = a[r];
+  dim3 grid(N / G::TY, N / 2 + 1, count);
+  k_fft_x<T, N, OP, RB><<<grid, G::THREADS, smem, s>>>(xb, tw);
+}
+
+template <typename T, int N>
+void launch_fft_x_batch(int op, const XReal<T>* rz, int count, const vec2_t<T>* tw, cudaStream_t s) {
+  if (count < 1 || count > kBatchMax) return;
+  XArgs<T> a[kBatchMax];
+  for (int r = 0; r < count; ++r) {
+    a[r] = XArgs<T>{};
+    a[r].in0 = rz[r].in0;
+    a[r].in1 = rz[r].in1;
+    a[r].out = rz[r].out;
+    a[r].nout_mask = rz[r].nout_mask;
+    a[r].kp = rz[r].kp;
+    a[r].skip = rz[r].skip;
+    for (int i = 0; i < kMaxFields; ++i) a[r].in.p[i] = nullptr;
+  }
+  switch (op) {
+    case XOP_HESSIAN: launch_x<T, N, XOP_HESSIAN, kBatchMax>(a, count, tw, s); break;
+    case XOP_SOURCE: launch_x<T, N, XOP_SOURCE, kBatchMax>(a, count, tw, s); break;
+    case XOP_SOURCE_LIN: launch_x<T, N, XOP_SOURCE_LIN, kBatchMax>(a, count, tw, s); break;
+    case XOP_PHI_FORCE: launch_x<T, N, XOP_PHI_FORCE, kBatchMax>(a, count, tw, s); break;
+    default: break;
+  }
 }
 
 template <typename T, int N>
@@ -568,15 +598,15 @@ void launch_fft_x_op(int op, const vec2_t<T>* in0, const vec2_t<T>* in1, const F
   a.in_mask = 0;
   for (int i = 0; i < kMaxFields; ++i) a.in.p[i] = nullptr;
   switch (op) {
-    case XOP_HESSIAN: launch_x<T, N, XOP_HESSIAN>(a, tw, s); break;
-    case XOP_SOURCE: launch_x<T, N, XOP_SOURCE>(a, tw, s); break;
-    case XOP_SOURCE_LIN: launch_x<T, N, XOP_SOURCE_LIN>(a, tw, s); break;
-    case XOP_PHI_FORCE: launch_x<T, N, XOP_PHI_FORCE>(a, tw, s); break;
-    case XOP_PK: launch_x<T, N, XOP_PK>(a, tw, s); break;
-    case XOP_PK_BRANE: launch_x<T, N, XOP_PK_BRANE>(a, tw, s); break;
-    case XOP_ZEL: launch_x<T, N, XOP_ZEL>(a, tw, s); break;
-    case XOP_PK_ADJ: launch_x<T, N, XOP_PK_ADJ>(a, tw, s); break;
-    case XOP_SHELL: launch_x<T, N, XOP_SHELL>(a, tw, s); break;
+    case XOP_HESSIAN: launch_x<T, N, XOP_HESSIAN>(&a, 1, tw, s); break;
+    case XOP_SOURCE: launch_x<T, N, XOP_SOURCE>(&a, 1, tw, s); break;
+    case XOP_SOURCE_LIN: launch_x<T, N, XOP_SOURCE_LIN>(&a, 1, tw, s); break;
+    case XOP_PHI_FORCE: launch_x<T, N, XOP_PHI_FORCE>(&a, 1, tw, s); break;
+    case XOP_PK: launch_x<T, N, XOP_PK>(&a, 1, tw, s); break;
+    case XOP_PK_BRANE: launch_x<T, N, XOP_PK_BRANE>(&a, 1, tw, s); break;
+    case XOP_ZEL: launch_x<T, N, XOP_ZEL>(&a, 1, tw, s); break;
+    case XOP_PK_ADJ: launch_x<T, N, XOP_PK_ADJ>(&a, 1, tw, s); break;
+    case XOP_SHELL: launch_x<T, N, XOP_SHELL>(&a, 1, tw, s); break;
     default: break;
   }
 }
@@ -589,9 +619,9 @@ void launch_fft_x_adj(int op, const FieldSet<T>& in, int in_mask, const FieldSet
   a.in0 = nullptr; a.in1 = nullptr; a.out = out; a.nout_mask = 0; a.kp = kp;
   a.pk_partials = nullptr; a.nbins = 0; a.shell_lo = 0; a.shell_hi = 0;
   a.in = in; a.in_mask = in_mask;
-  if (op == XOP_ADJ_PHI) launch_x<T, N, XOP_ADJ_PHI>(a, tw, s);
-  else if (op == XOP_ADJ_COMBINE) launch_x<T, N, XOP_ADJ_COMBINE>(a, tw, s);
-  else if (op == XOP_ZEL_ADJ) launch_x<T, N, XOP_ZEL_ADJ>(a, tw, s);
+  if (op == XOP_ADJ_PHI) launch_x<T, N, XOP_ADJ_PHI>(&a, 1, tw, s);
+  else if (op == XOP_ADJ_COMBINE) launch_x<T, N, XOP_ADJ_COMBINE>(&a, 1, tw, s);
+  else if (op == XOP_ZEL_ADJ) launch_x<T, N, XOP_ZEL_ADJ>(&a, 1, tw, s);
 }
 
 template <typename T, int N>
@@ -603,7 +633,7 @@ void launch_fft_x_rc(const FieldSet<T>& in, int in_mask, const KParams& kp, cons
   for (int i = 0; i < kMaxFields; ++i) a.out.p[i] = nullptr;
   a.pk_partials = partials; a.nbins = 0; a.shell_lo = 0; a.shell_hi = 0;
   a.in = in; a.in_mask = in_mask; a.rc = d;
-  launch_x<T, N, XOP_RC>(a, tw, s);
+  launch_x<T, N, XOP_RC>(&a, 1, tw, s);
 }
 
 #define DGP_INST_X(T, N)                                                                            \
@@ -614,6 +644,9 @@ void launch_fft_x_rc(const FieldSet<T>& in, int in_mask, const KParams& kp, cons
                                        const vec2_t<T>*, cudaStream_t);                                  \
   template void launch_fft_x_rc<T, N>(const FieldSet<T>&, int, const KParams&, const RcDeriv&, double*,   \
                                       const vec2_t<T>*, cudaStream_t);
+#define DGP_INST_XB(N) \
+  template void launch_fft_x_batch<float, N>(int, const XReal<float>*, int, const float2*, cudaStream_t);
+DGP_INST_XB(16) DGP_INST_XB(32) DGP_INST_XB(48) DGP_INST_XB(64) DGP_INST_XB(96) DGP_INST_XB(128)
 #define DGP_INST_X_ALL(T) DGP_INST_X(T, 16) DGP_INST_X(T, 32) DGP_INST_X(T, 64) DGP_INST_X(T, 128) \
   DGP_INST_X(T, 256) DGP_INST_X(T, 512) DGP_INST_X(T, 48) DGP_INST_X(T, 96)
 DGP_INST_X_ALL(float)

@@ -16,10 +16,13 @@
 namespace dgp {
 
 // 64 registers per thread for FP32 rows of up to 256 points, 128 otherwise
-template <typename T, int N, bool INV, int B, bool CTL>
-__global__ void __launch_bounds__(B, (sizeof(T) == 8 || N >= 512 ? 512 : 1024) / B) k_fft_y(const __grid_constant__ FieldSet<T> f, int64_t npencils,
-                                                     const vec2_t<T>* __restrict__ g_tw,
-                                                     const int* __restrict__ skip, const __grid_constant__ YControl yc) {
+template <typename T, int N, bool INV, int B, bool CTL, int RB>
+__global__ void __launch_bounds__(B, (sizeof(T) == 8 || N >= 512 ? 512 : 1024) / B)
+    k_fft_y(const __grid_constant__ YBatch<T, RB> yb, int64_t npencils, const vec2_t<T>* __restrict__ g_tw) {
+  const int rz = RB > 1 ? blockIdx.z : 0;  // realisation of this CTA
+  const FieldSet<T>& f = yb.f[rz];
+  const int* skip = yb.skip[rz];
+  const YControl& yc = yb.yc[rz];
   if (skip && *skip) return;
   if constexpr (CTL) {
     // the extra CTA, first in launch order so that it overlaps the transform's CTAs:
@@ -77,45 +80,70 @@ __global__ void __launch_bounds__(B, (sizeof(T) == 8 || N >= 512 ? 512 : 1024) /
   }
 }
 
-template <typename T, int N, int B>
-static void launch_y(const FieldSet<T>& f, int nfields, bool inverse, const vec2_t<T>* tw, cudaStream_t s,
-                     const int* skip, const YControl* ctl) {
+template <typename T, int N, int B, int RB>
+static void launch_y(const YBatch<T, RB>& yb, int count, int nfields, bool inverse, bool ctl, const vec2_t<T>* tw,
+                     cudaStream_t s) {
   using V = vec2_t<T>;
   constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
   constexpr int P = B / N1;
   const int64_t npencils = (int64_t)(N / 2 + 1) * N;
   const size_t smem = sizeof(V) * (kTwiddleTables * N + P * N1 * (N2 + 1));
-  YControl yc{};
-  if (ctl) yc = *ctl;
   // with the stop rules: one extra CTA, and the fields on grid.x only (one field)
-  dim3 grid((unsigned)((npencils + P - 1) / P) + (ctl ? 1u : 0u), (unsigned)nfields);
+  dim3 grid((unsigned)((npencils + P - 1) / P) + (ctl ? 1u : 0u), (unsigned)nfields, (unsigned)count);
   if (inverse) {
-    raise_smem_limit<k_fft_y<T, N, true, B, false>>(smem);
-    k_fft_y<T, N, true, B, false><<<grid, B, smem, s>>>(f, npencils, tw, skip, yc);
+    raise_smem_limit<k_fft_y<T, N, true, B, false, RB>>(smem);
+    k_fft_y<T, N, true, B, false, RB><<<grid, B, smem, s>>>(yb, npencils, tw);
   } else if (ctl) {
-    raise_smem_limit<k_fft_y<T, N, false, B, true>>(smem);
-    k_fft_y<T, N, false, B, true><<<grid, B, smem, s>>>(f, npencils, tw, skip, yc);
+    raise_smem_limit<k_fft_y<T, N, false, B, true, RB>>(smem);
+    k_fft_y<T, N, false, B, true, RB><<<grid, B, smem, s>>>(yb, npencils, tw);
   } else {
-    raise_smem_limit<k_fft_y<T, N, false, B, false>>(smem);
-    k_fft_y<T, N, false, B, false><<<grid, B, smem, s>>>(f, npencils, tw, skip, yc);
+    raise_smem_limit<k_fft_y<T, N, false, B, false, RB>>(smem);
+    k_fft_y<T, N, false, B, false, RB><<<grid, B, smem, s>>>(yb, npencils, tw);
   }
+}
+
+template <typename T, int N, int RB>
+static void launch_y_threads(const YBatch<T, RB>& yb, int count, int nfields, bool inverse, bool ctl,
+                             const vec2_t<T>* tw, cudaStream_t s, int threads) {
+  if (threads == 128) launch_y<T, N, 128, RB>(yb, count, nfields, inverse, ctl, tw, s);
+  else if (threads == 512) launch_y<T, N, 512, RB>(yb, count, nfields, inverse, ctl, tw, s);
+  else launch_y<T, N, 256, RB>(yb, count, nfields, inverse, ctl, tw, s);
 }
 
 template <typename T, int N>
 void launch_fft_y(const FieldSet<T>& f, int nfields, bool inverse, const vec2_t<T>* tw, cudaStream_t s,
                   const int* skip, int threads, const YControl* ctl) {
   if (ctl && (inverse || nfields != 1)) return;  // the stop rules ride on a one-field forward pass only
-  if (threads == 128) launch_y<T, N, 128>(f, nfields, inverse, tw, s, skip, ctl);
-  else if (threads == 512) launch_y<T, N, 512>(f, nfields, inverse, tw, s, skip, ctl);
-  else launch_y<T, N, 256>(f, nfields, inverse, tw, s, skip, ctl);
+  YBatch<T, 1> yb;
+  yb.f[0] = f;
+  yb.skip[0] = skip;
+  yb.yc[0] = ctl ? *ctl : YControl{};
+  launch_y_threads<T, N, 1>(yb, 1, nfields, inverse, ctl != nullptr, tw, s, threads);
+}
+
+template <typename T, int N>
+void launch_fft_y_batch(const FieldSet<T>* f, const int* const* skip, const YControl* ctl, int count, int nfields,
+                        bool inverse, const vec2_t<T>* tw, cudaStream_t s, int threads) {
+  if (count < 1 || count > kBatchMax || (ctl && (inverse || nfields != 1))) return;
+  YBatch<T, kBatchMax> yb;
+  for (int r = 0; r < count; ++r) {
+    yb.f[r] = f[r];
+    yb.skip[r] = skip ? skip[r] : nullptr;
+    yb.yc[r] = ctl ? ctl[r] : YControl{};
+  }
+  launch_y_threads<T, N, kBatchMax>(yb, count, nfields, inverse, ctl != nullptr, tw, s, threads);
 }
 
 #define DGP_INST_Y(T, N) \
   template void launch_fft_y<T, N>(const FieldSet<T>&, int, bool, const vec2_t<T>*, cudaStream_t, const int*, int, \
                                    const YControl*);
+#define DGP_INST_YB(N) \
+  template void launch_fft_y_batch<float, N>(const FieldSet<float>*, const int* const*, const YControl*, int, int, \
+                                             bool, const float2*, cudaStream_t, int);
 #define DGP_INST_Y_ALL(T) DGP_INST_Y(T, 16) DGP_INST_Y(T, 32) DGP_INST_Y(T, 64) DGP_INST_Y(T, 128) \
   DGP_INST_Y(T, 256) DGP_INST_Y(T, 512) DGP_INST_Y(T, 48) DGP_INST_Y(T, 96)
 DGP_INST_Y_ALL(float)
 DGP_INST_Y_ALL(double)
+DGP_INST_YB(16) DGP_INST_YB(32) DGP_INST_YB(48) DGP_INST_YB(64) DGP_INST_YB(96) DGP_INST_YB(128)
 
 }  // namespace dgp

@@ -39,10 +39,21 @@ __device__ __forceinline__ void prologue_coeffs(const ZPrologue& pro, T* s_ss) {
   }
 }
 
-template <typename T, int N>
+template <typename T, int RB> struct ZR2CBatch {
+  const T* in[RB];
+  vec2_t<T>* out[RB];
+  ZPrologue pro[RB];
+};
+
+template <typename T, int N, int RB>
 __global__ void __launch_bounds__(ZGeom<T, N>::THREADS, 3)
-k_fft_z_r2c(const T* __restrict__ in, int64_t in_stride, vec2_t<T>* __restrict__ out, int64_t out_stride,
-            ZPrologue pro, const vec2_t<T>* __restrict__ g_tw) {
+k_fft_z_r2c(const __grid_constant__ ZR2CBatch<T, RB> zb, int64_t in_stride, int64_t out_stride,
+            const vec2_t<T>* __restrict__ g_tw) {
+  // fields on blockIdx.z (one realisation), or realisations on blockIdx.z (one field each)
+  const int rz = RB > 1 ? blockIdx.z : 0;
+  const T* __restrict__ in = zb.in[rz];
+  vec2_t<T>* __restrict__ out = zb.out[rz];
+  const ZPrologue& pro = zb.pro[rz];
   using V = vec2_t<T>;
   using G = ZGeom<T, N>;
   constexpr int N1 = G::N1, N2 = G::N2, TY = G::TY, P = G::P;
@@ -55,8 +66,8 @@ k_fft_z_r2c(const T* __restrict__ in, int64_t in_stride, vec2_t<T>* __restrict__
   const int pl = threadIdx.x / N1;
   const int x = blockIdx.y;
   const int y0 = blockIdx.x * TY;
-  const T* src = in + (int64_t)blockIdx.z * in_stride;
-  V* dst = out + (int64_t)blockIdx.z * out_stride;
+  const T* src = in + (RB > 1 ? 0 : (int64_t)blockIdx.z * in_stride);
+  V* dst = out + (RB > 1 ? 0 : (int64_t)blockIdx.z * out_stride);
   __shared__ T s_ss[2];
   prologue_coeffs<T>(pro, s_ss);
   const T* rowa = src + ((int64_t)x * N + y0 + 2 * pl) * N;
@@ -99,10 +110,17 @@ k_fft_z_r2c(const T* __restrict__ in, int64_t in_stride, vec2_t<T>* __restrict__
   }
 }
 
-template <typename T, int N>
+template <typename T, int RB> struct ZC2RBatch {
+  FieldSet<T> in[RB];
+  FieldSet<T> out[RB];
+};
+
+template <typename T, int N, int RB>
 __global__ void __launch_bounds__(ZGeom<T, N>::THREADS, 3)
-k_fft_z_c2r(const __grid_constant__ FieldSet<T> in, const __grid_constant__ FieldSet<T> outp,
-            const vec2_t<T>* __restrict__ g_tw) {
+k_fft_z_c2r(const __grid_constant__ ZC2RBatch<T, RB> zb, int nfields, const vec2_t<T>* __restrict__ g_tw) {
+  const int rz = RB > 1 ? (int)blockIdx.z / nfields : 0, fz = RB > 1 ? (int)blockIdx.z % nfields : blockIdx.z;
+  const FieldSet<T>& in = zb.in[rz];
+  const FieldSet<T>& outp = zb.out[rz];
   using V = vec2_t<T>;
   using G = ZGeom<T, N>;
   constexpr int N1 = G::N1, N2 = G::N2, TY = G::TY, P = G::P;
@@ -118,8 +136,8 @@ k_fft_z_c2r(const __grid_constant__ FieldSet<T> in, const __grid_constant__ Fiel
   load_twiddles(s_tw, g_tw, N);
   const int x = blockIdx.y;
   const int y0 = blockIdx.x * TY;
-  const V* src = in.p[blockIdx.z];
-  T* dst = reinterpret_cast<T*>(outp.p[blockIdx.z]);
+  const V* src = in.p[fz];
+  T* dst = reinterpret_cast<T*>(outp.p[fz]);
   for (int item = threadIdx.x; item < NK * TY; item += blockDim.x) {
     const int kz = item / TY, yl = item % TY;
     s_H[kz * (TY + 1) + yl] = src[((int64_t)kz * N + x) * N + y0 + yl];
@@ -183,27 +201,71 @@ void launch_fft_z_r2c(const T* in, int64_t in_stride, vec2_t<T>* out, int64_t ou
                       ZPrologue pro, const vec2_t<T>* tw, cudaStream_t s) {
   using G = ZGeom<T, N>;
   const size_t smem = r2c_smem<T, N>();
-  raise_smem_limit<k_fft_z_r2c<T, N>>(smem);
+  raise_smem_limit<k_fft_z_r2c<T, N, 1>>(smem);
+  ZR2CBatch<T, 1> zb;
+  zb.in[0] = in;
+  zb.out[0] = out;
+  zb.pro[0] = pro;
   dim3 grid(N / G::TY, N, nfields);
-  k_fft_z_r2c<T, N><<<grid, G::THREADS, smem, s>>>(in, in_stride, out, out_stride, pro, tw);
+  k_fft_z_r2c<T, N, 1><<<grid, G::THREADS, smem, s>>>(zb, in_stride, out_stride, tw);
+}
+
+template <typename T, int N>
+void launch_fft_z_r2c_batch(const T* const* in, vec2_t<T>* const* out, const ZPrologue* pro, int count,
+                            const vec2_t<T>* tw, cudaStream_t s) {
+  using G = ZGeom<T, N>;
+  if (count < 1 || count > kBatchMax) return;
+  const size_t smem = r2c_smem<T, N>();
+  raise_smem_limit<k_fft_z_r2c<T, N, kBatchMax>>(smem);
+  ZR2CBatch<T, kBatchMax> zb;
+  for (int r = 0; r < count; ++r) {
+    zb.in[r] = in[r];
+    zb.out[r] = out[r];
+    zb.pro[r] = pro[r];
+  }
+  dim3 grid(N / G::TY, N, count);
+  k_fft_z_r2c<T, N, kBatchMax><<<grid, G::THREADS, smem, s>>>(zb, 0, 0, tw);
 }
 
 template <typename T, int N>
 void launch_fft_z_c2r(const FieldSet<T>& in, T* const* out, int nfields, const vec2_t<T>* tw,
                       cudaStream_t s) {
   using G = ZGeom<T, N>;
-  FieldSet<T> o;
-  for (int i = 0; i < kMaxFields; ++i) o.p[i] = i < nfields ? reinterpret_cast<vec2_t<T>*>(out[i]) : nullptr;
+  ZC2RBatch<T, 1> zb;
+  zb.in[0] = in;
+  for (int i = 0; i < kMaxFields; ++i) zb.out[0].p[i] = i < nfields ? reinterpret_cast<vec2_t<T>*>(out[i]) : nullptr;
   const size_t smem = c2r_smem<T, N>();
-  raise_smem_limit<k_fft_z_c2r<T, N>>(smem);
+  raise_smem_limit<k_fft_z_c2r<T, N, 1>>(smem);
   dim3 grid(N / G::TY, N, nfields);
-  k_fft_z_c2r<T, N><<<grid, G::THREADS, smem, s>>>(in, o, tw);
+  k_fft_z_c2r<T, N, 1><<<grid, G::THREADS, smem, s>>>(zb, nfields, tw);
+}
+
+template <typename T, int N>
+void launch_fft_z_c2r_batch(const FieldSet<T>* in, const FieldSet<T>* out, int nfields, int count,
+                            const vec2_t<T>* tw, cudaStream_t s) {
+  using G = ZGeom<T, N>;
+  if (count < 1 || count > kBatchMax) return;
+  ZC2RBatch<T, kBatchMax> zb;
+  for (int r = 0; r < count; ++r) {
+    zb.in[r] = in[r];
+    zb.out[r] = out[r];
+  }
+  const size_t smem = c2r_smem<T, N>();
+  raise_smem_limit<k_fft_z_c2r<T, N, kBatchMax>>(smem);
+  dim3 grid(N / G::TY, N, nfields * count);
+  k_fft_z_c2r<T, N, kBatchMax><<<grid, G::THREADS, smem, s>>>(zb, nfields, tw);
 }
 
 #define DGP_INST_Z(T, N)                                                                          \
   template void launch_fft_z_r2c<T, N>(const T*, int64_t, vec2_t<T>*, int64_t, int, ZPrologue,     \
                                        const vec2_t<T>*, cudaStream_t);                            \
   template void launch_fft_z_c2r<T, N>(const FieldSet<T>&, T* const*, int, const vec2_t<T>*, cudaStream_t);
+#define DGP_INST_ZB(N)                                                                                  \
+  template void launch_fft_z_r2c_batch<float, N>(const float* const*, float2* const*, const ZPrologue*, int,  \
+                                                 const float2*, cudaStream_t);                               \
+  template void launch_fft_z_c2r_batch<float, N>(const FieldSet<float>*, const FieldSet<float>*, int, int,     \
+                                                 const float2*, cudaStream_t);
+DGP_INST_ZB(16) DGP_INST_ZB(32) DGP_INST_ZB(48) DGP_INST_ZB(64) DGP_INST_ZB(96) DGP_INST_ZB(128)
 #define DGP_INST_Z_ALL(T) DGP_INST_Z(T, 16) DGP_INST_Z(T, 32) DGP_INST_Z(T, 64) DGP_INST_Z(T, 128) \
   DGP_INST_Z(T, 256) DGP_INST_Z(T, 512) DGP_INST_Z(T, 48) DGP_INST_Z(T, 96)
 DGP_INST_Z_ALL(float)

@@ -17,6 +17,9 @@
 namespace dgp {
 
 constexpr int kMaxFields = 8;
+// Batched launches: one launch runs a stage for up to kBatchMax realisations of
+// the same mesh size, realisation r on blockIdx.z = r with its own arguments.
+constexpr int kBatchMax = 16;
 
 template <typename T> struct FieldSet {
   vec2_t<T>* p[kMaxFields];
@@ -73,6 +76,16 @@ struct YControl {
 template <typename T, int N>
 void launch_fft_y(const FieldSet<T>& f, int nfields, bool inverse, const vec2_t<T>* tw, cudaStream_t s,
                   const int* skip = nullptr, int threads = 256, const YControl* ctl = nullptr);
+// Batched y pass: realisation r of count (<= kBatchMax, same N) with fields f[r],
+// skip flag skip[r] and, when ctl is not null, stop rules ctl[r] (FP32 data, N <= 128).
+template <typename T, int RB> struct YBatch {
+  FieldSet<T> f[RB];
+  const int* skip[RB];
+  YControl yc[RB];
+};
+template <typename T, int N>
+void launch_fft_y_batch(const FieldSet<T>* f, const int* const* skip, const YControl* ctl, int count, int nfields,
+                        bool inverse, const vec2_t<T>* tw, cudaStream_t s, int threads);
 
 template <typename T, int N>
 void launch_fft_z_r2c(const T* in, int64_t in_stride, vec2_t<T>* out, int64_t out_stride, int nfields,
@@ -81,6 +94,15 @@ void launch_fft_z_r2c(const T* in, int64_t in_stride, vec2_t<T>* out, int64_t ou
 template <typename T, int N>
 void launch_fft_z_c2r(const FieldSet<T>& in, T* const* out, int nfields, const vec2_t<T>* tw,
                       cudaStream_t s);
+// Batched z passes over count <= kBatchMax realisations of one mesh size (FP32,
+// N <= 128): one field each for the forward transform; nfields each (the
+// fields of realisation r in in[r].p / out[r].p) for the inverse.
+template <typename T, int N>
+void launch_fft_z_r2c_batch(const T* const* in, vec2_t<T>* const* out, const ZPrologue* pro, int count,
+                            const vec2_t<T>* tw, cudaStream_t s);
+template <typename T, int N>
+void launch_fft_z_c2r_batch(const FieldSet<T>* in, const FieldSet<T>* out, int nfields, int count,
+                            const vec2_t<T>* tw, cudaStream_t s);
 
 // x-pass: forward x transform of nin input spectra, op, inverse x transform of
 // each of the op's outputs.  For XOP_PK, outputs are the per-block bin
@@ -109,6 +131,19 @@ void launch_fft_x_adj(int op, const FieldSet<T>& in, int in_mask, const FieldSet
                       const vec2_t<T>* tw, cudaStream_t s);
 
 template <typename T, int N> int x_pass_blocks();
+
+// Batched x pass (XOP_HESSIAN, XOP_SOURCE, XOP_SOURCE_LIN, XOP_PHI_FORCE) for
+// count <= kBatchMax realisations of one mesh size (FP32 data, N <= 128).
+template <typename T> struct XReal {
+  const vec2_t<T>* in0;
+  const vec2_t<T>* in1;
+  FieldSet<T> out;
+  int nout_mask;
+  KParams kp;
+  const int* skip;
+};
+template <typename T, int N>
+void launch_fft_x_batch(int op, const XReal<T>* r, int count, const vec2_t<T>* tw, cudaStream_t s);
 
 // Parameters of the relaxation update (Eqs. nabla^2Cwpara, Bwpara and the
 // residual of FullDGP2).
@@ -144,6 +179,26 @@ template <typename T, int N> int fused_relax_blocks();
 struct RelaxMaps {
   CUtensorMap map[6];
 };
+// Arguments of one realisation's relaxation pass (relax_tma.cu).
+struct RelaxTmaArgs {
+  CUtensorMap map[6];   // y-inverted spectra of H_xx, H_yy, H_xy, H_xz, H_yz, N
+  const float* D;       // current iterate (its mean = dsum / N^3)
+  const double* dsum;
+  const float* S;       // source field
+  float* Dnew;          // next iterate
+  float2* Snew;         // z-transformed next iterate, layout S[kz][x][y]
+  double* partials;     // [blocks][4]
+  RelaxParams rp;
+  const int* skip;
+  int* fault;           // set to 1 when a wait gave up
+  unsigned long long wait_ns;
+  int withhold;         // test hook: the first pair's copy is never issued
+};
+template <int RB> struct RelaxTmaBatch {
+  RelaxTmaArgs a[RB];
+};
+template <int N>
+void launch_relax_tma_batch(int arith, const RelaxTmaArgs* a, int count, const float2* tw, cudaStream_t s);
 template <int N> int relax_maps(float2* const* spec6, RelaxMaps* out);
 template <int N> int relax_tma_blocks();
 template <int N>
@@ -234,6 +289,32 @@ template <typename T>
 void launch_gather_kick(T* x, T* y, T* z, T* px, T* py, T* pz, int64_t np, const T* gx,
                         const T* gy, const T* gz, CicParams cp, double kick, double drift, int do_drift,
                         cudaStream_t s);
+
+// Batched particle and reduction stages (count <= kBatchMax realisations of one
+// mesh size, FP32): CIC deposit, gather-kick(-drift), one-component FP64 sums
+// (out[r][0] = sum of a[r], partials[r] with nblocks entries), zeroing of fields.
+template <typename T> struct DepositArgs {
+  const T* x;
+  const T* y;
+  const T* z;
+  int64_t np;
+  T* rho;
+  CicParams cp;
+};
+template <typename T>
+void launch_cic_deposit_batch(const DepositArgs<T>* a, int count, cudaStream_t s);
+struct GatherArgs {
+  float* p[6];         // x, y, z, px, py, pz
+  int64_t np;
+  const float* g[3];   // force meshes
+  CicParams cp;
+  float kick, drift;
+  int do_drift;
+};
+void launch_gather_kick_batch(const GatherArgs* a, int count, cudaStream_t s);
+void launch_sum_batch(const float* const* a, int64_t m, bool absval, double* const* partials, int nblocks,
+                      double* const* out, int count, cudaStream_t s);
+void launch_zero_batch(float* const* a, int64_t m, int count, cudaStream_t s);
 
 // Counting sort of particles by CIC cell (sort_deposit.cu).
 template <typename T>

@@ -56,6 +56,60 @@ void launch_finalize(const double* partials, int nblocks, int ncomp, double* out
   k_finalize<<<1, 256, 0, s>>>(partials, nblocks, ncomp, out, skip);
 }
 
+// Batched one-component sums: realisation r = blockIdx.y (k_sum) or blockIdx.x (finalize).
+struct SumBatch {
+  const float* a[kBatchMax];
+  double* partials[kBatchMax];
+  double* out[kBatchMax];
+};
+__global__ void __launch_bounds__(256) k_sum_batch(const __grid_constant__ SumBatch b, int64_t m, int absval) {
+  const float* __restrict__ a = b.a[blockIdx.y];
+  float s = 0.f, c = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = absval ? fabsf(a[i]) : a[i];
+    const float t = s + v;
+    const float bb = t - s;
+    c += (s - (t - bb)) + (v - bb);
+    s = t;
+  }
+  double v[1] = {(double)s + (double)c};
+  block_sum<1>(v);
+  if (threadIdx.x == 0) b.partials[blockIdx.y][blockIdx.x] = v[0];
+}
+__global__ void __launch_bounds__(256) k_finalize_batch(const __grid_constant__ SumBatch b, int nblocks) {
+  double v[1] = {0.0};
+  for (int k = threadIdx.x; k < nblocks; k += blockDim.x) v[0] += b.partials[blockIdx.x][k];
+  block_sum<1>(v);
+  if (threadIdx.x == 0) b.out[blockIdx.x][0] = v[0];
+}
+void launch_sum_batch(const float* const* a, int64_t m, bool absval, double* const* partials, int nblocks,
+                      double* const* out, int count, cudaStream_t s) {
+  if (count < 1 || count > kBatchMax) return;
+  SumBatch b;
+  for (int r = 0; r < count; ++r) {
+    b.a[r] = a[r];
+    b.partials[r] = partials[r];
+    b.out[r] = out[r];
+  }
+  k_sum_batch<<<dim3((unsigned)nblocks, (unsigned)count), 256, 0, s>>>(b, m, absval ? 1 : 0);
+  k_finalize_batch<<<count, 256, 0, s>>>(b, nblocks);
+}
+
+struct FillBatch {
+  float* a[kBatchMax];
+};
+__global__ void k_fill_batch(const __grid_constant__ FillBatch b, int64_t m) {
+  float* __restrict__ a = b.a[blockIdx.y];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = 0.f;
+}
+void launch_zero_batch(float* const* a, int64_t m, int count, cudaStream_t s) {
+  if (count < 1 || count > kBatchMax) return;
+  FillBatch b;
+  for (int r = 0; r < count; ++r) b.a[r] = a[r];
+  k_fill_batch<<<dim3((unsigned)(num_sms() * 4 / count + 1), (unsigned)count), 256, 0, s>>>(b, m);
+}
+
 // The stop rules as a launch of their own (relax_control.cuh).
 __global__ void k_relax_control(SolveCtl* __restrict__ c, const double* __restrict__ stats,
                                 const double* __restrict__ abs_src_sum, double* __restrict__ hist,
@@ -430,11 +484,11 @@ struct GatherOne {
 // Two particles per iteration (p and p + stride): their 48 mesh loads are independent, which
 // doubles the loads in flight of this latency-bound gather.
 template <typename T>
-__global__ void __launch_bounds__(256) k_gather_kick(T* __restrict__ x, T* __restrict__ y, T* __restrict__ z,
-                                                     T* __restrict__ px, T* __restrict__ py, T* __restrict__ pz,
-                                                     int64_t np, const T* __restrict__ gx, const T* __restrict__ gy,
-                                                     const T* __restrict__ gz, CicParams cp, T kick, T drift,
-                                                     int do_drift) {
+__device__ __forceinline__ void gather_kick_body(T* __restrict__ x, T* __restrict__ y, T* __restrict__ z,
+                                                 T* __restrict__ px, T* __restrict__ py, T* __restrict__ pz,
+                                                 int64_t np, const T* __restrict__ gx, const T* __restrict__ gy,
+                                                 const T* __restrict__ gz, const CicParams& cp, T kick, T drift,
+                                                 int do_drift, int64_t blk, int64_t nblk) {
   T box, inv_box;
   if constexpr (sizeof(T) == 8) {
     box = cp.box;
@@ -443,8 +497,8 @@ __global__ void __launch_bounds__(256) k_gather_kick(T* __restrict__ x, T* __res
     box = cp.box_f;
     inv_box = cp.inv_box_f;
   }
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += 2 * stride) {
+  const int64_t stride = nblk * blockDim.x;
+  for (int64_t p = blk * blockDim.x + threadIdx.x; p < np; p += 2 * stride) {
     const int64_t q = p + stride;
     const bool two = q < np;
     const T xp = x[p], yp = y[p], zp = z[p];
@@ -480,6 +534,15 @@ __global__ void __launch_bounds__(256) k_gather_kick(T* __restrict__ x, T* __res
 }
 
 template <typename T>
+__global__ void __launch_bounds__(256) k_gather_kick(T* __restrict__ x, T* __restrict__ y, T* __restrict__ z,
+                                                     T* __restrict__ px, T* __restrict__ py, T* __restrict__ pz,
+                                                     int64_t np, const T* __restrict__ gx, const T* __restrict__ gy,
+                                                     const T* __restrict__ gz, CicParams cp, T kick, T drift,
+                                                     int do_drift) {
+  gather_kick_body<T>(x, y, z, px, py, pz, np, gx, gy, gz, cp, kick, drift, do_drift, blockIdx.x, gridDim.x);
+}
+
+template <typename T>
 void launch_gather_kick(T* x, T* y, T* z, T* px, T* py, T* pz, int64_t np, const T* gx, const T* gy,
                         const T* gz, CicParams cp, double kick, double drift, int do_drift, cudaStream_t s) {
   if (np <= 0) return;
@@ -488,6 +551,30 @@ void launch_gather_kick(T* x, T* y, T* z, T* px, T* py, T* pz, int64_t np, const
   if (blocks > cap) blocks = cap;
   k_gather_kick<T><<<(unsigned)blocks, 256, 0, s>>>(x, y, z, px, py, pz, np, gx, gy, gz, cp, (T)kick, (T)drift,
                                                     do_drift);
+}
+
+// Batched: realisation r = blockIdx.y
+struct GatherBatch {
+  GatherArgs a[kBatchMax];
+};
+__global__ void __launch_bounds__(256) k_gather_kick_batch(const __grid_constant__ GatherBatch b) {
+  const GatherArgs& a = b.a[blockIdx.y];
+  gather_kick_body<float>(a.p[0], a.p[1], a.p[2], a.p[3], a.p[4], a.p[5], a.np, a.g[0], a.g[1], a.g[2], a.cp,
+                          a.kick, a.drift, a.do_drift, blockIdx.x, gridDim.x);
+}
+void launch_gather_kick_batch(const GatherArgs* a, int count, cudaStream_t s) {
+  if (count < 1 || count > kBatchMax) return;
+  GatherBatch b;
+  int64_t npmax = 0;
+  for (int r = 0; r < count; ++r) {
+    b.a[r] = a[r];
+    npmax = a[r].np > npmax ? a[r].np : npmax;
+  }
+  if (npmax <= 0) return;
+  int64_t blocks = (npmax + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 16 / count + 1;
+  if (blocks > cap) blocks = cap;
+  k_gather_kick_batch<<<dim3((unsigned)blocks, (unsigned)count), 256, 0, s>>>(b);
 }
 
 template <typename T>

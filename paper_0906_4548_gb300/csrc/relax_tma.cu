@@ -213,21 +213,6 @@ template <int N> struct RGeom {
   static_assert(P * N1 * (N2 + 1) * 8 <= BUF0, "forward transpose fits the first buffer");
 };
 
-struct RelaxTmaArgs {
-  CUtensorMap map[6];   // y-inverted spectra of H_xx, H_yy, H_xy, H_xz, H_yz, N
-  const float* D;       // current iterate (its mean = dsum / N^3)
-  const double* dsum;
-  const float* S;       // source field
-  float* Dnew;          // next iterate
-  float2* Snew;         // z-transformed next iterate, layout S[kz][x][y]
-  double* partials;     // [blocks][4]
-  RelaxParams rp;
-  const int* skip;
-  int* fault;           // set to 1 when a wait gave up
-  unsigned long long wait_ns;
-  int withhold;         // test hook: the first pair's copy is never issued
-};
-
 // byte offset of complex (kz, y) in a swizzled tile (relative to a 1024-aligned base)
 template <int N>
 __device__ __forceinline__ unsigned tile_off(int kz, int y) {
@@ -311,9 +296,10 @@ __device__ __forceinline__ void pair_inverse(unsigned char* buf, const float2* s
   }
 }
 
-template <int N, class AR>
+template <int N, class AR, int RB>
 __global__ void __launch_bounds__(RGeom<N>::THREADS, RGeom<N>::MINB)
-    k_relax_tma(const __grid_constant__ RelaxTmaArgs args, const float2* __restrict__ g_tw) {
+    k_relax_tma(const __grid_constant__ RelaxTmaBatch<RB> batch, const float2* __restrict__ g_tw) {
+  const RelaxTmaArgs& args = batch.a[RB > 1 ? blockIdx.z : 0];  // realisation of this CTA
   if (args.skip && *args.skip) return;
   using G = RGeom<N>;
   using Acc = typename AR::Acc;
@@ -553,12 +539,20 @@ int relax_maps(float2* const* spec6, RelaxMaps* out) {
 
 template <int N> int relax_tma_blocks() { return (N / RGeom<N>::TY) * N; }
 
-template <int N, class AR>
-static void launch_rt(const RelaxTmaArgs& a, const float2* tw, cudaStream_t s) {
+template <int N, class AR, int RB>
+static void launch_rt(const RelaxTmaArgs* a, int count, const float2* tw, cudaStream_t s) {
   using G = RGeom<N>;
-  raise_smem_limit<k_relax_tma<N, AR>>(G::SMEM);
-  dim3 grid(N / G::TY, N);
-  k_relax_tma<N, AR><<<grid, G::THREADS, G::SMEM, s>>>(a, tw);
+  RelaxTmaBatch<RB> b;
+  for (int r = 0; r < count; ++r) b.a[r] = a[r];
+  raise_smem_limit<k_relax_tma<N, AR, RB>>(G::SMEM);
+  dim3 grid(N / G::TY, N, count);
+  k_relax_tma<N, AR, RB><<<grid, G::THREADS, G::SMEM, s>>>(b, tw);
+}
+
+template <int N, class AR>
+static void launch_rt(const RelaxTmaArgs* a, int count, const float2* tw, cudaStream_t s) {
+  if (count == 1) launch_rt<N, AR, 1>(a, 1, tw, s);
+  else launch_rt<N, AR, kBatchMax>(a, count, tw, s);
 }
 
 template <int N>
@@ -569,10 +563,16 @@ void launch_relax_tma(int arith, const RelaxMaps& maps, const float* D, const do
   memcpy(a.map, maps.map, sizeof(a.map));
   a.D = D; a.dsum = dsum; a.S = S; a.Dnew = Dnew; a.Snew = Snew; a.partials = partials; a.rp = rp;
   a.skip = skip; a.fault = fault; a.wait_ns = wait_ns; a.withhold = withhold;
-  if (arith == ARITH_F64) launch_rt<N, RxF64>(a, tw, s);
-  else if (arith == ARITH_EFT) launch_rt<N, RxEFT>(a, tw, s);
-  else if (arith == ARITH_M32) launch_rt<N, RxM32>(a, tw, s);
-  else launch_rt<N, RxF32>(a, tw, s);
+  launch_relax_tma_batch<N>(arith, &a, 1, tw, s);
+}
+
+template <int N>
+void launch_relax_tma_batch(int arith, const RelaxTmaArgs* a, int count, const float2* tw, cudaStream_t s) {
+  if (count < 1 || count > kBatchMax) return;
+  if (arith == ARITH_F64) launch_rt<N, RxF64>(a, count, tw, s);
+  else if (arith == ARITH_EFT) launch_rt<N, RxEFT>(a, count, tw, s);
+  else if (arith == ARITH_M32) launch_rt<N, RxM32>(a, count, tw, s);
+  else launch_rt<N, RxF32>(a, count, tw, s);
 }
 
 #define DGP_INST_RT(N)                                                                                          \
@@ -580,7 +580,8 @@ void launch_relax_tma(int arith, const RelaxMaps& maps, const float* D, const do
   template int relax_tma_blocks<N>();                                                                         \
   template void launch_relax_tma<N>(int, const RelaxMaps&, const float*, const double*, const float*, float*,  \
                                     float2*, RelaxParams, double*, const float2*, cudaStream_t, const int*, int*, \
-                                    unsigned long long, int);
+                                    unsigned long long, int);                                                 \
+  template void launch_relax_tma_batch<N>(int, const RelaxTmaArgs*, int, const float2*, cudaStream_t);
 DGP_INST_RT(16)
 DGP_INST_RT(32)
 DGP_INST_RT(48)

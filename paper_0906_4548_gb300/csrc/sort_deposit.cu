@@ -142,13 +142,13 @@ void launch_cell_sort(const ParticleSet<T>& parts, int64_t np, CicParams cp, con
 // eight corner weights over the segment and its last lane issues the eight
 // global atomics.  A warp with no shared keys skips the scan.
 template <typename T>
-__global__ void __launch_bounds__(256) k_cic_deposit_warp(const T* __restrict__ x, const T* __restrict__ y,
-                                                          const T* __restrict__ z, int64_t np, T* __restrict__ rho,
-                                                          CicParams cp) {
+__device__ __forceinline__ void deposit_warp_body(const T* __restrict__ x, const T* __restrict__ y,
+                                                  const T* __restrict__ z, int64_t np, T* __restrict__ rho,
+                                                  const CicParams& cp, int64_t blk, int64_t nblk) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int64_t n = cp.n;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < np; base += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t base = blk * blockDim.x; base < np; base += nblk * blockDim.x) {
     const int64_t p = base + threadIdx.x;
     const bool act = p < np;
     int i0[3] = {0, 0, 0}, i1[3] = {0, 0, 0};
@@ -203,6 +203,23 @@ __global__ void __launch_bounds__(256) k_cic_deposit_warp(const T* __restrict__ 
 }
 
 template <typename T>
+__global__ void __launch_bounds__(256) k_cic_deposit_warp(const T* __restrict__ x, const T* __restrict__ y,
+                                                          const T* __restrict__ z, int64_t np, T* __restrict__ rho,
+                                                          CicParams cp) {
+  deposit_warp_body<T>(x, y, z, np, rho, cp, blockIdx.x, gridDim.x);
+}
+
+// Batched: realisation r = blockIdx.y
+template <typename T> struct DepositBatch {
+  DepositArgs<T> a[kBatchMax];
+};
+template <typename T>
+__global__ void __launch_bounds__(256) k_cic_deposit_warp_batch(const __grid_constant__ DepositBatch<T> b) {
+  const DepositArgs<T>& a = b.a[blockIdx.y];
+  deposit_warp_body<T>(a.x, a.y, a.z, a.np, a.rho, a.cp, blockIdx.x, gridDim.x);
+}
+
+template <typename T>
 void launch_cic_deposit_warp(const T* x, const T* y, const T* z, int64_t np, T* rho, CicParams cp, cudaStream_t s) {
   if (np <= 0) return;
   int64_t blocks = (np + 255) / 256;
@@ -211,10 +228,27 @@ void launch_cic_deposit_warp(const T* x, const T* y, const T* z, int64_t np, T* 
   k_cic_deposit_warp<T><<<(unsigned)blocks, 256, 0, s>>>(x, y, z, np, rho, cp);
 }
 
+template <typename T>
+void launch_cic_deposit_batch(const DepositArgs<T>* a, int count, cudaStream_t s) {
+  if (count < 1 || count > kBatchMax) return;
+  DepositBatch<T> b;
+  int64_t npmax = 0;
+  for (int r = 0; r < count; ++r) {
+    b.a[r] = a[r];
+    npmax = a[r].np > npmax ? a[r].np : npmax;
+  }
+  if (npmax <= 0) return;
+  int64_t blocks = (npmax + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 16 / count + 1;
+  if (blocks > cap) blocks = cap;
+  k_cic_deposit_warp_batch<T><<<dim3((unsigned)blocks, (unsigned)count), 256, 0, s>>>(b);
+}
+
 #define DGP_INST_SORT(T)                                                                                   \
   template void launch_cell_sort<T>(const ParticleSet<T>&, int64_t, CicParams, const SortWork&,             \
                                     const ParticleSet<T>&, cudaStream_t);                                  \
-  template void launch_cic_deposit_warp<T>(const T*, const T*, const T*, int64_t, T*, CicParams, cudaStream_t);
+  template void launch_cic_deposit_warp<T>(const T*, const T*, const T*, int64_t, T*, CicParams, cudaStream_t); \
+  template void launch_cic_deposit_batch<T>(const DepositArgs<T>*, int, cudaStream_t);
 DGP_INST_SORT(float)
 DGP_INST_SORT(double)
 

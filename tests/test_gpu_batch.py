@@ -82,3 +82,50 @@ def test_batch_reports_a_failing_realisation(dgp, torch_dev):
             dgp.dgp_batch_create([dgp.params(60.0, 40, 1.0)], OM)  # invalid size: nothing leaks
     finally:
         dgp.dgp_batch_destroy(b)
+
+
+@pytest.mark.parametrize("prec", [4, 0])
+def test_class_step_matches_individual_contexts_and_oracle(dgp, torch_dev, prec):
+    """Four 48^3 realisations with different boxes and r_c form one class: every kernel stage of
+    their step is one launch for all four, and they iterate in lockstep.  Each realisation must end
+    where its own context stepped alone ends (float atomics of the deposit aside) and follow the FP64
+    oracle's run."""
+    from oracle import pm as opm
+    torch, dev = torch_dev
+    cases = [(48, 120.0, 0.6, 2), (48, 90.0, 1.3, 3), (48, 150.0, 1.9, 4), (48, 60.0, 0.8, 5)]
+    a0, a1, ns = 0.2, 0.3, 3
+    dl = (math.log(a1) - math.log(a0)) / ns
+    sched = [a0 * math.exp(i * dl) for i in range(ns + 1)]
+    ics = [_ics(n, box, rc, seed, a0) for n, box, rc, seed in cases]
+    ics = [(p.astype(np.float32).astype(np.float64), m.astype(np.float32).astype(np.float64)) for p, m in ics]
+    plist = [dgp.params(box, n, rc, precision=prec, tol=1e-6, max_iter=200) for n, box, rc, _ in cases]
+    b, ctxs = dgp.dgp_batch_create(plist, OM)
+    try:
+        cls, ncls = dgp.dgp_batch_classes(b, len(cases))
+        assert ncls == 1 and cls == [0] * len(cases)
+        tb = [[to_dev(torch_dev, v, torch.float32) for v in (*p, *m)] for p, m in ics]
+        parts = [dgp.particles(*t) for t in tb]
+        infos = []
+        for i in range(ns):
+            infos.append(dgp.dgp_batch_step(b, parts, [sched[i]] * len(cases), [sched[i + 1] - sched[i]] * len(cases)))
+        got = [np.stack([v.cpu().numpy() for v in t]).astype(np.float64) for t in tb]
+    finally:
+        dgp.dgp_batch_destroy(b)
+    assert all(inf["status"] == dgp.DGP_OK and inf["norm_res"] < 1e-6 for step in infos for inf in step)
+    for k, ((n, box, rc, _), (p, m)) in enumerate(zip(cases, ics)):
+        ctx = dgp.dgp_init(box, n, rc, OM, precision=prec, tol=1e-6, max_iter=200)
+        try:
+            t = [to_dev(torch_dev, v, torch.float32) for v in (*p, *m)]
+            pp = dgp.particles(*t)
+            for i in range(ns):
+                inf = dgp.pm_step(ctx, pp, sched[i], sched[i + 1] - sched[i])
+                assert abs(inf["iters"] - infos[i][k]["iters"]) <= 1  # float atomics of the deposit
+            want = np.stack([v.cpu().numpy() for v in t]).astype(np.float64)
+        finally:
+            dgp.dgp_destroy(ctx)
+        assert rel_l2(got[k], want) < 2e-5, k
+        st = opm.run(p, m, a0, a1, ns, n, box, OM, rc, tol=1e-10, max_iter=300)
+        dx = (got[k][:3] - st.pos + box / 2) % box - box / 2
+        disp = (st.pos - p + box / 2) % box - box / 2
+        assert np.linalg.norm(dx) / np.linalg.norm(disp) < 1e-4, k
+        assert rel_l2(got[k][3:], st.mom) < 1e-4, k

@@ -77,7 +77,9 @@ __device__ __forceinline__ void x_forward(const vec2_t<T>* __restrict__ in, int 
   __syncthreads();
 }
 
-template <typename T, int N>
+// trailing: end with a barrier so the next call may reuse s_T; callers that alternate
+// two transpose buffers between consecutive calls pass false.
+template <typename T, int N, bool trailing = true>
 __device__ __forceinline__ void x_inverse(vec2_t<T> (&Y)[Split<N>::N2], vec2_t<T>* __restrict__ out, int kz,
                                           int ky0, int lane, int yl, vec2_t<T>* s_T, const vec2_t<T>* s_tw) {
   using V = vec2_t<T>;
@@ -97,7 +99,7 @@ __device__ __forceinline__ void x_inverse(vec2_t<T> (&Y)[Split<N>::N2], vec2_t<T
 #pragma unroll
     for (int m2 = 0; m2 < N1; ++m2) plane[(int64_t)(lane + N2 * m2) * N + ky0 + yl] = cconj(w[m2]);
   }
-  __syncthreads();
+  if (trailing) __syncthreads();
 }
 
 // A coefficient in the element type: the host-rounded float for FP32 data, the double otherwise.
@@ -138,6 +140,7 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
   constexpr int NW = XGeom<T, N>::THREADS / 32;
   constexpr int NBS = OP == XOP_PK_BRANE ? 4 : 3;  // sums per shell
   double* s_bins = reinterpret_cast<double*>(s_inv);
+  V* s_T2 = reinterpret_cast<V*>(s_inv);  // the Hessian op's second transpose buffer (N * TY)
   double* s_stage = s_bins + NW * NBS * args.nbins;
   load_twiddles(s_tw, g_tw, N);
   if (OP == XOP_PK || OP == XOP_PK_BRANE)
@@ -212,7 +215,7 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
   constexpr int NT = XGeom<T, N>::THREADS;
   const T inv_m = kc<T>(kp.inv_m, kp.inv_m_f);
 #pragma unroll
-  for (int k2 = 0; k2 < N2 && OP != XOP_HESSIAN; ++k2) {
+  for (int k2 = 0; k2 < N2 && OP != XOP_HESSIAN && OP != XOP_PHI_FORCE; ++k2) {
     const int nx = signed_index(lane + N1 * k2, N);
     const int n2 = nx * nx + ny * ny + nz * nz;
     T inv = (T)0, ikb = (T)0;
@@ -418,7 +421,8 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
         if (nyq) prod = fabs(prod);
         Y[k2] = cscale(X0[k2], prod);
       }
-      x_inverse<T, N>(Y, args.out.p[o], kz, ky0, lane, yl, s_T, s_tw);
+      // the outputs alternate between two transpose buffers: one barrier per output
+      x_inverse<T, N, false>(Y, args.out.p[o], kz, ky0, lane, yl, (o & 1) ? s_T2 : s_T, s_tw);
     }
     // N = -D / kbar = -(|n|^2 / kbar) Xs, |n|^2 / kbar = |n| / (kbar_fac k_f)
     const T ikf = kp.local_only ? (T)0 : (T)1 / kc<T>(kp.kbar_fac * 2.0 * M_PI / kp.box, kp.kbkf_f);
@@ -428,7 +432,64 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
       const T fx = (T)signed_index(lane + N1 * k2, N);
       Y[k2] = cscale(X0[k2], -sqrt(fx * fx + nyz2) * ikf);
     }
-    x_inverse<T, N>(Y, args.out.p[5], kz, ky0, lane, yl, s_T, s_tw);
+    x_inverse<T, N, false>(Y, args.out.p[5], kz, ky0, lane, yl, s_T2, s_tw);  // output 5: odd
+    return;
+  }
+
+  if constexpr (OP == XOP_PHI_FORCE) {
+    // phi(k) once per slot, in place of X0 (Eq. FullDGP1 with the D spectrum X1; Eq. LinearDGP
+    // with G_eff of Eq. Geff; Eq. GRPoisson), with the 1/N^3 of the inverse transforms; then each
+    // requested output: phi (bit 0) or g_i = -i k_i phi (bits 1..3, Nyquist component of axis
+    // i zero).  The outputs alternate between two transpose buffers.
+    const T fy = (T)ny, fz = (T)nz;
+    const T nyz2 = fy * fy + fz * fz;
+    const T om15 = kc<T>(1.5 * (kp.eta - 1.0) / kp.eta, kp.om15_f);
+    const T aE2m = kc<T>(kp.aE * kp.aE, kp.aE2_f) * inv_m;
+    const T kf2 = kf * kf;
+    const T ikf = kp.local_only ? (T)0 : (T)1 / kc<T>(kp.kbar_fac * 2.0 * M_PI / kp.box, kp.kbkf_f);
+    const T inv_eta = kc<T>(1.0 / kp.eta, kp.inv_eta_f);
+    const T half_inv_eta = kc<T>(0.5 / kp.eta, kp.half_inv_eta_f);
+    const T c3 = kc<T>(kp.c3, kp.c3_f);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+      const T fx = (T)signed_index(lane + N1 * k2, N);
+      const T n2 = fx * fx + nyz2;
+      if (n2 == (T)0) {
+        X0[k2] = cmake<V>((T)0, (T)0);
+        continue;
+      }
+      const T pref = -aE2m / (kf2 * n2);
+      if (kp.gravity == 0) {
+        const T ikb = ikf / sqrt(n2);  // 1 / kbar
+        const T cd = -half_inv_eta + c3 * ikb;
+        const T f = pref / ((T)1 + ikb * inv_eta);
+        X0[k2] = cmake<V>(f * (om15 * X0[k2].x + cd * X1[k2].x), f * (om15 * X0[k2].y + cd * X1[k2].y));
+      } else if (kp.gravity == 1) {
+        X0[k2] = cscale(X0[k2], pref * om15 * (T)geff_dev(kp, (double)(kf * sqrt(n2))));
+      } else {
+        X0[k2] = cscale(X0[k2], pref * om15);
+      }
+    }
+    int cnt = 0;
+#pragma unroll 1
+    for (int o = 0; o < 4; ++o) {
+      if (!((args.nout_mask >> o) & 1)) continue;  // uniform over the block
+      V Y[N2];
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        if (o == 0) {
+          Y[k2] = X0[k2];
+        } else {
+          const int kx = lane + N1 * k2;
+          const bool nyq = o == 1 ? kx == N / 2 : (o == 2 ? nyq_y : nyq_z);
+          const T ki = kf * (o == 1 ? (T)signed_index(kx, N) : (o == 2 ? fy : fz));
+          // g = -grad phi -> -i k_i phi
+          Y[k2] = nyq ? cmake<V>((T)0, (T)0) : cmake<V>(ki * X0[k2].y, -ki * X0[k2].x);
+        }
+      }
+      x_inverse<T, N, false>(Y, args.out.p[o], kz, ky0, lane, yl, (cnt & 1) ? s_T2 : s_T, s_tw);
+      ++cnt;
+    }
     return;
   }
 
@@ -554,7 +615,8 @@ static void launch_x(const XArgs<T>* a, int count, const vec2_t<T>* tw, cudaStre
   constexpr int NBS = OP == XOP_PK_BRANE ? 4 : 3, NW = G::THREADS / 32;
   const size_t base = sizeof(vec2_t<T>) * (kTwiddleTables * N + (size_t)N * G::TY);
   const size_t tables = PK ? sizeof(double) * NW * 32 * NBS
-                            : (OP == XOP_HESSIAN ? 0 : sizeof(T) * 2 * Split<N>::N2 * G::THREADS);
+                            : ((OP == XOP_HESSIAN || OP == XOP_PHI_FORCE) ? sizeof(vec2_t<T>) * (size_t)N * G::TY
+                                                                          : sizeof(T) * 2 * Split<N>::N2 * G::THREADS);
   const size_t per_bin = PK ? sizeof(double) * NW * NBS : 0;
   const size_t smem = base + tables + per_bin * a[0].nbins;
   raise_smem_limit<k_fft_x<T, N, OP, RB>>(base + tables + per_bin * (N / 2));

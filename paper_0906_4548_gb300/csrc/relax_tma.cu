@@ -47,6 +47,17 @@
 namespace dgp {
 
 // ---------------------------------------------------------------- arithmetic policies
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float fdiv_full(float a, float b) {
+  float r;
+  asm("div.full.ftz.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+
 struct PointOut {
   float bp, dt;  // B' and Delta, rounded to float
   bool neg;      // Delta < 0 (a bad point)
@@ -55,6 +66,7 @@ struct PointOut {
 struct RxF32 {
   using Acc = float;
   using Sum = float;
+  static constexpr bool kApproxRoot = true;
   __device__ static void pair_a(Acc& r, float x, float y) { r = fmaf(-2.f * x, x, (-2.f * y) * y); }
   __device__ static void pair_b(Acc& r, float x, float n, const RelaxParams& rp) {
     r = fmaf(-2.f * x, x, fmaf(rp.c2_hi, n, r));
@@ -84,6 +96,7 @@ struct RxF32 {
 struct RxM32 {
   using Acc = float;
   using Sum = float;
+  static constexpr bool kApproxRoot = true;
   __device__ static void pair_a(Acc& r, float x, float y) { RxF32::pair_a(r, x, y); }
   __device__ static void pair_b(Acc& r, float x, float n, const RelaxParams& rp) { RxF32::pair_b(r, x, n, rp); }
   __device__ static PointOut finish(Acc r, float a, float b, float D, float S, float m_hi, float, double,
@@ -110,6 +123,7 @@ struct RxM32 {
 struct RxEFT {
   using Acc = FP;
   using Sum = FP;
+  static constexpr bool kApproxRoot = false;
   __device__ static void pair_a(Acc& r, float x, float y) {
     r = fp_prod(-2.f * x, x);
     fp_acc(r, fp_prod(-2.f * y, y));
@@ -164,6 +178,7 @@ struct RxEFT {
 struct RxF64 {
   using Acc = double;
   using Sum = double;
+  static constexpr bool kApproxRoot = false;
   __device__ static void pair_a(Acc& r, float x, float y) { r = -2.0 * ((double)x * x + (double)y * y); }
   __device__ static void pair_b(Acc& r, float x, float n, const RelaxParams& rp) {
     r = fma(-2.0 * x, (double)x, fma(rp.c2, (double)n, r));
@@ -413,7 +428,14 @@ __global__ void __launch_bounds__(RGeom<N>::THREADS, RGeom<N>::MINB)
       bpt = rp.bad_bp_f;
       dt = 0.f;
     }
-    const float dn = 2.f * bpt / (rp.alpha_f + sqrtf(dt));
+    float dn;
+    if constexpr (AR::kApproxRoot) {
+      // D_new is an FP32 datum: the hardware square root and the full-range division (a few
+      // ulp, far below the FFTs' rounding of the fields it is computed from)
+      dn = fdiv_full(2.f * bpt, rp.alpha_f + sqrt_approx(dt));
+    } else {
+      dn = 2.f * bpt / (rp.alpha_f + sqrtf(dt));
+    }
     args.Dnew[rbase + z] = dn;
     sD[row * ROWP + z] = dn;
     if constexpr (std::is_same<AR, RxF32>::value) acc_d.hi += dn;

@@ -45,3 +45,27 @@ def test_recorded_traffic_only_for_the_captured_sources(monkeypatch):
     assert bench.recorded_traffic("relax") is None
     assert bench.recorded_traffic("no_such_kind") is None
 
+
+
+def test_sampled_steps_are_the_middles_of_equal_strata():
+    idx = bench.sampled_steps(200, 20)
+    assert idx == [5 + 10 * j for j in range(20)]
+    assert bench.sampled_steps(200, 500) == list(range(200))  # all steps when K >= the run
+    for k in (1, 3, 7, 64, 199):
+        s = bench.sampled_steps(200, k)
+        assert len(s) == k and len(set(s)) == k and s == sorted(s)
+        assert all(int(j * 200 / k) <= s[j] < int((j + 1) * 200 / k) + 1 for j in range(k))
+
+
+def test_reference_evaluations_follow_the_timed_steps():
+    assert len(bench.EVALS_PER_STEP_256) == 200
+    idx = bench.sampled_steps(200, 20)
+    assert bench.reference_evals(idx) == sum(bench.EVALS_PER_STEP_256[i] for i in idx) / 20
+
+
+def test_oracle_step_model_sums_its_pieces():
+    m = bench.OracleStepModel.__new__(bench.OracleStepModel)
+    m.times = {"deposit": [2.0], "forward": [1.0], "source": [1.5], "evaluation": [10.0, 12.0], "update": [0.5],
+               "phi_forces": [4.0], "interpolate": [1.0]}
+    # 2 + 1 + 1.5 + E 11 + (E - 1) 0.5 + 4 + 3 x 1 at E = 3
+    assert m.step_seconds(3.0) == 2.0 + 1.0 + 1.5 + 33.0 + 1.0 + 4.0 + 3.0

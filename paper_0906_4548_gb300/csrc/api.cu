@@ -364,8 +364,11 @@ class Engine : public EngineBase {
   // CUDA graph of two consecutive iterations (it odd, it + 1), one per buffer
   // holding the starting iterate; updated with each solve's parameters
   cudaGraphExec_t pair_exec[3] = {nullptr, nullptr, nullptr};
-  cudaStream_t copy_stream = nullptr;  // pm_step_host: positions back to the host during the solve
-  cudaEvent_t drift_ev = nullptr;
+  // pm_step_host: three copy streams, so that several copy engines move the six arrays at once
+  // (one array per stream), and the events that order them against the context's stream
+  static constexpr int kCopyStreams = 3;
+  cudaStream_t copy_streams[kCopyStreams] = {};
+  cudaEvent_t copy_ev[kCopyStreams + 1] = {};  // [j]: stream j's copies in; [kCopyStreams]: a fence on stream
   T* hp[6] = {};                // device copies for pm_step_host
   int64_t hp_n = 0;
   // cell sort: key and permuted copies per particle, counts / starts / cursors per cell
@@ -401,8 +404,10 @@ class Engine : public EngineBase {
     cudaFree(aP); cudaFree(aF); cudaFree(aS); cudaFree(d_adj); cudaFree(aFb);
     for (int i = 0; i < 6; ++i) cudaFree(ap[i]);
     cudaFree(d_ctl); cudaFree(d_hist); cudaFreeHost(h_ctl);
-    if (copy_stream) cudaStreamDestroy(copy_stream);
-    if (drift_ev) cudaEventDestroy(drift_ev);
+    for (int j = 0; j < kCopyStreams; ++j)
+      if (copy_streams[j]) cudaStreamDestroy(copy_streams[j]);
+    for (int j = 0; j <= kCopyStreams; ++j)
+      if (copy_ev[j]) cudaEventDestroy(copy_ev[j]);
     for (int i = 0; i < 3; ++i)
       if (pair_exec[i]) cudaGraphExecDestroy(pair_exec[i]);
     if (class_exec) cudaGraphExecDestroy(class_exec);
@@ -1385,9 +1390,10 @@ class Engine : public EngineBase {
       }
       hp_n = hpp->n;
     }
-    if (!copy_stream) {
-      DGP_CUDA(cudaStreamCreateWithFlags(&copy_stream, cudaStreamNonBlocking));
-      DGP_CUDA(cudaEventCreateWithFlags(&drift_ev, cudaEventDisableTiming));
+    if (!copy_streams[0]) {
+      for (int j = 0; j < kCopyStreams; ++j)
+        DGP_CUDA(cudaStreamCreateWithFlags(&copy_streams[j], cudaStreamNonBlocking));
+      for (int j = 0; j <= kCopyStreams; ++j) DGP_CUDA(cudaEventCreateWithFlags(&copy_ev[j], cudaEventDisableTiming));
     }
     void* src[6] = {hpp->x, hpp->y, hpp->z, hpp->px, hpp->py, hpp->pz};
     const size_t bytes = sizeof(T) * hpp->n;
@@ -1395,23 +1401,38 @@ class Engine : public EngineBase {
     // may be reused only for the host arrays that the previous host step wrote
     if (force_host != hpp->x) force_valid = false;
     force_host = nullptr;
-    for (int i = 0; i < 6; ++i) DGP_CUDA(cudaMemcpyAsync(hp[i], src[i], bytes, cudaMemcpyHostToDevice, stream));
+    // copies on the copy streams, each ordered after the work enqueued so far on the stream
+    auto fence = [&]() -> int {
+      DGP_CUDA(cudaEventRecord(copy_ev[kCopyStreams], stream));
+      for (int j = 0; j < kCopyStreams; ++j) DGP_CUDA(cudaStreamWaitEvent(copy_streams[j], copy_ev[kCopyStreams], 0));
+      return DGP_OK;
+    };
+    int rc;
+    if ((rc = fence())) return rc;
+    for (int i = 0; i < 6; ++i)
+      DGP_CUDA(cudaMemcpyAsync(hp[i], src[i], bytes, cudaMemcpyHostToDevice, copy_streams[i % kCopyStreams]));
+    for (int j = 0; j < kCopyStreams; ++j) {
+      DGP_CUDA(cudaEventRecord(copy_ev[j], copy_streams[j]));
+      DGP_CUDA(cudaStreamWaitEvent(stream, copy_ev[j], 0));
+    }
     dgp_particles dp{hp[0], hp[1], hp[2], hp[3], hp[4], hp[5], hpp->n};
     // the positions are final after the drift: copy them back while the field solve runs
     const std::function<int()> positions_out = [&]() -> int {
-      DGP_CUDA(cudaEventRecord(drift_ev, stream));
-      DGP_CUDA(cudaStreamWaitEvent(copy_stream, drift_ev, 0));
+      int r;
+      if ((r = fence())) return r;
       for (int i = 0; i < 3; ++i)
-        DGP_CUDA(cudaMemcpyAsync(src[i], hp[i], bytes, cudaMemcpyDeviceToHost, copy_stream));
+        DGP_CUDA(cudaMemcpyAsync(src[i], hp[i], bytes, cudaMemcpyDeviceToHost, copy_streams[i % kCopyStreams]));
       return DGP_OK;
     };
-    const int rc = step_impl(&dp, a, da, info, &positions_out);
+    rc = step_impl(&dp, a, da, info, &positions_out);
     if (rc != DGP_OK) {
-      cudaStreamSynchronize(copy_stream);
+      for (int j = 0; j < kCopyStreams; ++j) cudaStreamSynchronize(copy_streams[j]);
       return rc;
     }
-    for (int i = 3; i < 6; ++i) DGP_CUDA(cudaMemcpyAsync(src[i], hp[i], bytes, cudaMemcpyDeviceToHost, stream));
-    DGP_CUDA(cudaStreamSynchronize(copy_stream));
+    if ((rc = fence())) return rc;
+    for (int i = 3; i < 6; ++i)
+      DGP_CUDA(cudaMemcpyAsync(src[i], hp[i], bytes, cudaMemcpyDeviceToHost, copy_streams[i % kCopyStreams]));
+    for (int j = 0; j < kCopyStreams; ++j) DGP_CUDA(cudaStreamSynchronize(copy_streams[j]));
     DGP_CUDA(wait_stream());
     force_host = hpp->x;
     return DGP_OK;

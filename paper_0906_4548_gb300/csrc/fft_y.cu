@@ -1,7 +1,7 @@
 // y transform: in-place complex DFT along the contiguous rows of S[kz][x][y].
 //
 // Each CTA of B threads (B = 128, 256 or 512, chosen per context by timing, see
-// api.cu) owns P = B / N1 rows.  Phase 1: lane j2 < N2
+// api.cu) owns P = B / N1 rows.  Phase 1: one thread per row and j2 < N2
 // reads x[N2*j1 + j2] straight from global memory (consecutive lanes,
 // consecutive addresses), transforms over j1 and stores the twiddled result
 // to shared memory; phase 2: lane k1 reads its N2 values back with an odd
@@ -57,16 +57,24 @@ __global__ void __launch_bounds__(B, (sizeof(T) == 8 || N >= 512 ? 512 : 1024) /
   const bool active = pencil < npencils;
   V* base = f.p[blockIdx.y] + (active ? pencil : 0) * N;
   V* Tp = s_T + pl * (N1 * (N2 + 1));
+  // Phase 1 has P x N2 tasks (a row and its column j2); when N2 < N1 they go to the first
+  // P x N2 threads, so that whole warps idle rather than lanes of every warp.
+  constexpr bool PACK = N2 < N1;
+  const int p1 = PACK ? (int)threadIdx.x / N2 : pl, c1 = PACK ? (int)threadIdx.x % N2 : lane;
+  const int64_t pencil1 = PACK ? (int64_t)(blockIdx.x - (CTL ? 1 : 0)) * P + p1 : pencil;
+  const bool act1 = PACK ? (p1 < P && pencil1 < npencils) : active;
+  const V* base1 = PACK ? f.p[blockIdx.y] + (act1 ? pencil1 : 0) * N : base;
+  V* T1 = PACK ? s_T + p1 * (N1 * (N2 + 1)) : Tp;
   __syncthreads();
-  if (active && lane < N2) {
+  if (act1) {
     V v[N1];
 #pragma unroll
-    for (int j1 = 0; j1 < N1; ++j1) v[j1] = base[N2 * j1 + lane];
+    for (int j1 = 0; j1 < N1; ++j1) v[j1] = base1[N2 * j1 + c1];
     if (INV) conj_regs(v);
     dft_regs<N1, N / N1>(v, s_tw);
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1)
-      Tp[k1 * (N2 + 1) + lane] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[N + k1 * N2 + lane]);
+      T1[k1 * (N2 + 1) + c1] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[N + k1 * N2 + c1]);
   }
   __syncthreads();
   if (active) {

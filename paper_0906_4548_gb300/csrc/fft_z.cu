@@ -75,17 +75,24 @@ k_fft_z_r2c(const __grid_constant__ ZR2CBatch<T, RB> zb, int64_t in_stride, int6
   V* Tp = s_T + pl * (N1 * (N2 + 1));
   __syncthreads();
   const T sc = s_ss[0], sh = s_ss[1];
-  if (lane < N2) {
+  // stage one has P x N2 tasks (a row pair and its column j2): when N2 < N1 they go to the
+  // first P x N2 threads, so that whole warps idle rather than lanes of every warp
+  constexpr bool PACK = N2 < N1;
+  const int p1 = PACK ? (int)threadIdx.x / N2 : pl, c1 = PACK ? (int)threadIdx.x % N2 : lane;
+  if (!PACK || p1 < P) {
+    const T* ra1 = PACK ? src + ((int64_t)x * N + y0 + 2 * p1) * N : rowa;
+    const T* rb1 = ra1 + N;
+    V* T1 = PACK ? s_T + p1 * (N1 * (N2 + 1)) : Tp;
     V v[N1];
 #pragma unroll
     for (int j1 = 0; j1 < N1; ++j1) {
-      v[j1].x = rowa[N2 * j1 + lane] * sc + sh;
-      v[j1].y = rowb[N2 * j1 + lane] * sc + sh;
+      v[j1].x = ra1[N2 * j1 + c1] * sc + sh;
+      v[j1].y = rb1[N2 * j1 + c1] * sc + sh;
     }
     dft_regs<N1, N / N1>(v, s_tw);
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1)
-      Tp[k1 * (N2 + 1) + lane] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[N + k1 * N2 + lane]);
+      T1[k1 * (N2 + 1) + c1] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[N + k1 * N2 + c1]);
   }
   __syncthreads();
   {
@@ -161,14 +168,17 @@ k_fft_z_c2r(const __grid_constant__ ZC2RBatch<T, RB> zb, int nfields, const vec2
   const int lane = threadIdx.x % N1;
   const int pl = threadIdx.x / N1;
   V* Tp = s_T + pl * (N1 * (N2 + 1));
-  if (lane < N2) {
+  constexpr bool PACK = N2 < N1;  // stage one on the first P x N2 threads, as in the r2c pass
+  const int p1 = PACK ? (int)threadIdx.x / N2 : pl, c1 = PACK ? (int)threadIdx.x % N2 : lane;
+  if (!PACK || p1 < P) {
+    V* T1 = PACK ? s_T + p1 * (N1 * (N2 + 1)) : Tp;
     V v[N1];
 #pragma unroll
-    for (int j1 = 0; j1 < N1; ++j1) v[j1] = s_Z[(N2 * j1 + lane) * (P + 1) + pl];
+    for (int j1 = 0; j1 < N1; ++j1) v[j1] = s_Z[(N2 * j1 + c1) * (P + 1) + p1];
     dft_regs<N1, N / N1>(v, s_tw);
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1)
-      Tp[k1 * (N2 + 1) + lane] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[N + k1 * N2 + lane]);
+      T1[k1 * (N2 + 1) + c1] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[N + k1 * N2 + c1]);
   }
   __syncthreads();
   {

@@ -260,17 +260,23 @@ __device__ __forceinline__ void pair_inverse(unsigned char* buf, const float2* s
   constexpr int N1 = G::N1, N2 = G::N2;
   const unsigned char* TA = buf;
   const unsigned char* TB = buf + G::FIELD;
-  // With N2 a multiple of 8 and one box, row kk of a read satisfies kk = +-lane (mod 8) for
+  // The first stage has TY x N2 tasks (a row and one of its N2 columns j2) for TY x N1
+  // threads: they go to the first TY x N2 threads, so that when N2 < N1 whole warps
+  // idle instead of every warp running with lanes masked off.
+  constexpr bool PACK = N2 < N1;
+  const int t1 = threadIdx.x;
+  const bool act1 = !PACK || t1 < G::TY * N2;
+  const int r1 = PACK ? t1 / N2 : row, c1 = PACK ? t1 % N2 : lane;
+  // With N2 a multiple of 8 and one box, row kk of a read satisfies kk = +-c1 (mod 8) for
   // every j1, so the swizzle term is one constant per thread and direction.
   constexpr bool HOIST = N2 % 8 == 0 && G::NBOX == 1;
-  const unsigned off_d = (unsigned)lane * G::ROWB + (((unsigned)row * 8u) ^ (((unsigned)lane & 7u) << 4));
-  const unsigned off_m =
-      (unsigned)(N - lane) * G::ROWB + (((unsigned)row * 8u) ^ (((unsigned)(N - lane) & 7u) << 4));
+  const unsigned off_d = (unsigned)c1 * G::ROWB + (((unsigned)r1 * 8u) ^ (((unsigned)c1 & 7u) << 4));
+  const unsigned off_m = (unsigned)(N - c1) * G::ROWB + (((unsigned)r1 * 8u) ^ (((unsigned)(N - c1) & 7u) << 4));
   float2 v[N1];
-  if (lane < N2) {
+  if (act1) {
 #pragma unroll
     for (int j1 = 0; j1 < N1; ++j1) {
-      const int k = N2 * j1 + lane;
+      const int k = N2 * j1 + c1;
       float2 A, B;
       bool mirror;
       if (N2 * j1 + N2 - 1 < N / 2) mirror = false;  // j1 is a compile-time index
@@ -279,7 +285,7 @@ __device__ __forceinline__ void pair_inverse(unsigned char* buf, const float2* s
       const int kk = mirror ? N - k : k;
       unsigned off;
       if constexpr (HOIST) off = mirror ? off_m - (unsigned)(N2 * j1 * G::ROWB) : off_d + (unsigned)(N2 * j1 * G::ROWB);
-      else off = tile_off<N>(kk, row);
+      else off = tile_off<N>(kk, r1);
       A = *reinterpret_cast<const float2*>(TA + off);
       B = *reinterpret_cast<const float2*>(TB + off);
       if (mirror) {
@@ -293,13 +299,14 @@ __device__ __forceinline__ void pair_inverse(unsigned char* buf, const float2* s
     }
   }
   __syncthreads();  // the tile is read: its bytes become the transpose buffer
-  float2* Tp = reinterpret_cast<float2*>(buf) + row * (N1 * (N2 + 1));
-  if (lane < N2) {
+  if (act1) {
+    float2* T1 = reinterpret_cast<float2*>(buf) + r1 * (N1 * (N2 + 1));
     dft_regs<N1, N / N1>(v, s_tw);
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) Tp[k1 * (N2 + 1) + lane] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[k1 * N2 + lane]);
+    for (int k1 = 0; k1 < N1; ++k1) T1[k1 * (N2 + 1) + c1] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[k1 * N2 + c1]);
   }
   __syncthreads();
+  const float2* Tp = reinterpret_cast<const float2*>(buf) + row * (N1 * (N2 + 1));
   float2 u[N2];
 #pragma unroll
   for (int j2 = 0; j2 < N2; ++j2) u[j2] = Tp[lane * (N2 + 1) + j2];
@@ -447,16 +454,18 @@ __global__ void __launch_bounds__(RGeom<N>::THREADS, RGeom<N>::MINB)
     constexpr int FT = P * N1;
     const int fl = tid % N1, fp = tid / N1;
     float2* Tp = reinterpret_cast<float2*>(buf0) + fp * (N1 * (N2 + 1));
-    if (tid < FT && fl < N2) {
+    if (tid < P * N2) {  // first stage: P x N2 tasks on the first threads
+      const int q1 = tid / N2, l1 = tid % N2;
+      float2* T1 = reinterpret_cast<float2*>(buf0) + q1 * (N1 * (N2 + 1));
       float2 v[N1];
 #pragma unroll
       for (int j1 = 0; j1 < N1; ++j1) {
-        v[j1].x = sD[(2 * fp) * ROWP + N2 * j1 + fl];
-        v[j1].y = sD[(2 * fp + 1) * ROWP + N2 * j1 + fl];
+        v[j1].x = sD[(2 * q1) * ROWP + N2 * j1 + l1];
+        v[j1].y = sD[(2 * q1 + 1) * ROWP + N2 * j1 + l1];
       }
       dft_regs<N1, N / N1>(v, s_tw);
 #pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) Tp[k1 * (N2 + 1) + fl] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[k1 * N2 + fl]);
+      for (int k1 = 0; k1 < N1; ++k1) T1[k1 * (N2 + 1) + l1] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[k1 * N2 + l1]);
     }
     __syncthreads();
     float2* s_Zf = reinterpret_cast<float2*>(buf1);  // N x (P + 1); D_new has been read

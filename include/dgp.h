@@ -365,6 +365,14 @@ int dgp_set_blocking_sync(dgp_ctx *c, int on);
  *     one instead, so the valid ones still step.
  *   dgp_batch_classes: class_of[count] receives the class of each realisation
  *     and *nclasses the number of classes and lone contexts.
+ *   dgp_batch_set_plane_pass: for classes of n <= 96 (on != 0, the default)
+ *     an iteration's Hessian spectra come from one plane-resident pass: a CTA
+ *     per kz plane and realisation transforms the iterate's z spectrum along
+ *     y and x in shared memory and writes the six relaxation inputs
+ *     transformed back along x and y (Sec. III.B, Eq. FullDGP2: the second
+ *     derivatives of C and the non-local term), so each crosses HBM once;
+ *     on = 0 uses the separate x and y passes of a single context.  Both
+ *     compute the same spectra up to rounding order.
  * Calls on one batch must not overlap. */
 typedef struct dgp_batch dgp_batch;
 int dgp_batch_create(dgp_batch **out, int count, const dgp_params *params, const dgp_cosmology *cosmo);
@@ -372,6 +380,7 @@ int dgp_batch_context(dgp_batch *b, int i, dgp_ctx **out);
 int dgp_batch_step(dgp_batch *b, dgp_particles *parts, const double *a, const double *da, dgp_solve_info *info,
                    void *cuda_stream);
 int dgp_batch_classes(dgp_batch *b, int *class_of, int *nclasses);
+int dgp_batch_set_plane_pass(dgp_batch *b, int on);
 void dgp_batch_destroy(dgp_batch *b);
 
 /* Spectra of the brane-bending mode C of the context's accepted nonlinear

@@ -292,6 +292,7 @@ class EngineBase {
   int y_threads = 256;          // y-pass CTA size, chosen at init by timing (tile autotuning)
   unsigned long long wait_ns = 2000000000ull;  // bound of every in-kernel wait
   int withhold = 0;             // test hook: the relaxation pass leaves its first copy unissued
+  bool plane_pass = true;       // class solves of small meshes: the plane-resident Hessian pass
 
   // Host wait for the work enqueued so far on the context's stream.
   cudaError_t wait_stream() {
@@ -1142,6 +1143,9 @@ class Engine : public EngineBase {
     auto out_buf = [&](int k, int it) { return it & 1 ? pb1[k] : pb0[k]; };
     auto spec_in = [&](int k, int it) { return (it & 1) ? S[k]->sD2 : S[k]->sD; };
     auto spec_out = [&](int k, int it) { return (it & 1) ? S[k]->sD : S[k]->sD2; };
+    // With the plane pass an iteration starts from the z spectrum of its iterate (the pass
+    // does the y and x transforms itself); otherwise from the z and y transformed spectrum.
+    const bool plane = e0->plane_pass && plane_hessian_supported(N);
     // forward transforms of the starting iterates
     {
       const float* in[kBatchMax];
@@ -1155,7 +1159,7 @@ class Engine : public EngineBase {
         f[k] = fs(&S[k]->sD, 1);
       }
       launch_fft_z_r2c_batch<T, N>(in, out, pro, n, tw, st);
-      launch_fft_y_batch<T, N>(f, nullptr, nullptr, n, 1, false, tw, st, yt);
+      if (!plane) launch_fft_y_batch<T, N>(f, nullptr, nullptr, n, 1, false, tw, st, yt);
     }
     for (int k = 0; k < n; ++k)
       if (cudaMemsetAsync(S[k]->d_ctl, 0, sizeof(SolveCtl), st) != cudaSuccess) return DGP_E_CUDA;
@@ -1193,6 +1197,21 @@ class Engine : public EngineBase {
         f1[i] = fs(&so, 1);
         yc[i] = YControl{e->partials, e->fblocks, e->d_rstats + 4 * ob, e->d_ctl, e->d_misc + 1, e->d_hist,
                          e->p.max_iter, kPatience, e->p.tol, 1.0 / (double)M};
+      }
+      if (plane) {
+        PlaneArgs pa[kBatchMax];
+        for (int i = 0; i < m; ++i) pa[i] = PlaneArgs{spec_in(ks[i], it), f6[i], kp[ks[i]], sk[i]};
+        launch_plane_hessian_batch(N, pa, m, tw, st);
+        launch_relax_tma_batch<N>(e0->arith_mode(), ra, m, tw, st);
+        if (control) {
+          launch_control_batch(yc, sk, m, st);
+        } else {
+          for (int i = 0; i < m; ++i) {
+            Engine* e = S[ks[i]];
+            launch_finalize(e->partials, e->fblocks, 4, e->d_rstats + 4 * out_buf(ks[i], it), st, nullptr);
+          }
+        }
+        return check();
       }
       launch_fft_x_batch<T, N>(XOP_HESSIAN, xr, m, tw, st);
       launch_fft_y_batch<T, N>(f6, sk, nullptr, m, 6, true, tw, st, yt);
@@ -1290,10 +1309,19 @@ class Engine : public EngineBase {
       if (best_it == s_it) {
         accepted = in_buf(k, s_it);
         sDphi[k] = spec_in(k, s_it);
+        if (plane) {  // the accepted iterate's spectrum is transformed along z only
+          V* f1[1] = {sDphi[k]};
+          launch_fft_y<T, N>(fs(f1, 1), 1, false, tw, st, nullptr, yt);
+        }
       } else {
         // an earlier iterate: replay the iterations that produced it for this member alone
         if (best_it > 0) {
-          if ((rc = e->forward_zy(e->rD[j0[k]], e->sD, ZPrologue{nullptr, 0.0, 0}))) return rc;
+          if (plane) {
+            launch_fft_z_r2c<T, N>(e->rD[j0[k]], 0, e->sD, 0, 1, ZPrologue{nullptr, 0.0, 0}, tw, st);
+            if ((rc = check())) return rc;
+          } else if ((rc = e->forward_zy(e->rD[j0[k]], e->sD, ZPrologue{nullptr, 0.0, 0}))) {
+            return rc;
+          }
           const std::vector<int> one(1, k);
           for (int q = 0; q < best_it; ++q)
             if ((rc = enqueue(q, false, one))) return rc;
@@ -2085,6 +2113,10 @@ int step_class(dgp_ctx* const* ctxs, int count, dgp_particles* parts, const doub
     m[i] = ctxs[i]->eng;
   }
   return m[0]->step_class(m, count, parts, a, da, info);
+}
+
+void set_plane_pass(dgp_ctx* c, bool on) {
+  if (c) c->eng->plane_pass = on;
 }
 }  // namespace dgp
 

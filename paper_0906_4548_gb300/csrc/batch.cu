@@ -223,6 +223,12 @@ int dgp_batch_classes(dgp_batch* b, int* class_of, int* nclasses) {
   return DGP_OK;
 }
 
+int dgp_batch_set_plane_pass(dgp_batch* b, int on) {
+  if (!b) return DGP_E_INVALID;
+  for (dgp_ctx* c : b->ctx) dgp::set_plane_pass(c, on != 0);
+  return DGP_OK;
+}
+
 void dgp_batch_destroy(dgp_batch* b) {
   if (b) destroy_batch(b);
 }

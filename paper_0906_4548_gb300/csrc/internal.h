@@ -15,4 +15,8 @@ constexpr int kClassMax = 16;
 int step_class(dgp_ctx* const* ctxs, int count, dgp_particles* parts, const double* a, const double* da,
                dgp_solve_info* info);
 
+// Class solves of the context use the plane-resident Hessian pass where the mesh allows it
+// (on, the default) or the separate x and y passes (off).
+void set_plane_pass(dgp_ctx* c, bool on);
+
 }  // namespace dgp

@@ -199,6 +199,24 @@ template <int RB> struct RelaxTmaBatch {
 };
 template <int N>
 void launch_relax_tma_batch(int arith, const RelaxTmaArgs* a, int count, const float2* tw, cudaStream_t s);
+
+// Plane-resident Hessian pass (plane.cu) for count <= kBatchMax realisations of one mesh size
+// n (FP32 data; plane_hessian_supported(n)): from the z spectrum in (layout S[kz][x][y]) of
+// each realisation, the six relaxation inputs H_xx, H_yy, H_xy, H_xz, H_yz, N transformed back
+// along x and y, in out.p[0..5] (same layout).  Replaces the y pass of the iterate, the Hessian
+// x pass and the six-field inverse y pass of an iteration.  skip as for the other passes.
+struct PlaneArgs {
+  const float2* in;
+  FieldSet<float> out;
+  KParams kp;
+  const int* skip;
+};
+bool plane_hessian_supported(int n);
+void launch_plane_hessian_batch(int n, const PlaneArgs* a, int count, const float2* tw, cudaStream_t s);
+// The stop rules of count <= kBatchMax realisations after a relaxation pass: block r sums
+// realisation r's block partials and applies its stop rules (as the control CTA of the y pass);
+// realisations whose skip flag is set are left alone.
+void launch_control_batch(const YControl* ctl, const int* const* skip, int count, cudaStream_t s);
 template <int N> int relax_maps(float2* const* spec6, RelaxMaps* out);
 template <int N> int relax_tma_blocks();
 template <int N>

@@ -65,12 +65,41 @@ struct SumBatch {
 __global__ void __launch_bounds__(256) k_sum_batch(const __grid_constant__ SumBatch b, int64_t m, int absval) {
   const float* __restrict__ a = b.a[blockIdx.y];
   float s = 0.f, c = 0.f;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    const float v = absval ? fabsf(a[i]) : a[i];
+  auto add = [&](float v) {  // compensated (TwoSum) accumulation in the thread
+    v = absval ? fabsf(v) : v;
     const float t = s + v;
     const float bb = t - s;
     c += (s - (t - bb)) + (v - bb);
     s = t;
+  };
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((m & 3) == 0 && (reinterpret_cast<uintptr_t>(a) & 15) == 0) {
+    // 16-byte loads, four in flight per thread
+    const float4* __restrict__ a4 = reinterpret_cast<const float4*>(a);
+    const int64_t m4 = m >> 2;
+    int64_t i = i0;
+    for (; i + 3 * stride < m4; i += 4 * stride) {
+      float4 q[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) q[u] = a4[i + u * stride];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        add(q[u].x);
+        add(q[u].y);
+        add(q[u].z);
+        add(q[u].w);
+      }
+    }
+    for (; i < m4; i += stride) {
+      const float4 q = a4[i];
+      add(q.x);
+      add(q.y);
+      add(q.z);
+      add(q.w);
+    }
+  } else {
+    for (int64_t i = i0; i < m; i += stride) add(a[i]);
   }
   double v[1] = {(double)s + (double)c};
   block_sum<1>(v);
@@ -91,8 +120,10 @@ void launch_sum_batch(const float* const* a, int64_t m, bool absval, double* con
     b.partials[r] = partials[r];
     b.out[r] = out[r];
   }
-  k_sum_batch<<<dim3((unsigned)nblocks, (unsigned)count), 256, 0, s>>>(b, m, absval ? 1 : 0);
-  k_finalize_batch<<<count, 256, 0, s>>>(b, nblocks);
+  // about nblocks CTAs in all, shared among the realisations
+  const int nb = nblocks / count > 0 ? nblocks / count : 1;
+  k_sum_batch<<<dim3((unsigned)nb, (unsigned)count), 256, 0, s>>>(b, m, absval ? 1 : 0);
+  k_finalize_batch<<<count, 256, 0, s>>>(b, nb);
 }
 
 struct FillBatch {
@@ -108,6 +139,38 @@ void launch_zero_batch(float* const* a, int64_t m, int count, cudaStream_t s) {
   FillBatch b;
   for (int r = 0; r < count; ++r) b.a[r] = a[r];
   k_fill_batch<<<dim3((unsigned)(num_sms() * 4 / count + 1), (unsigned)count), 256, 0, s>>>(b, m);
+}
+
+struct ControlBatch {
+  YControl c[kBatchMax];
+  const int* skip[kBatchMax];
+};
+__global__ void __launch_bounds__(256) k_control_batch(const __grid_constant__ ControlBatch b) {
+  const YControl& yc = b.c[blockIdx.x];
+  const int* skip = b.skip[blockIdx.x];
+  if (skip && *skip) return;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k = threadIdx.x; k < yc.nblocks; k += blockDim.x) {
+    const double* pk = yc.partials + 4 * (int64_t)k;
+    v[0] += pk[0];
+    v[1] += pk[1];
+    v[2] += pk[2];
+    v[3] += pk[3];
+  }
+  block_sum<4>(v);
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < 4; ++c) yc.stats[c] = v[c];
+    relax_control_step(yc.ctl, yc.stats, yc.abs_src_sum, yc.hist, yc.max_iter, yc.patience, yc.tol, yc.inv_m);
+  }
+}
+void launch_control_batch(const YControl* ctl, const int* const* skip, int count, cudaStream_t s) {
+  if (count < 1 || count > kBatchMax) return;
+  ControlBatch b;
+  for (int r = 0; r < count; ++r) {
+    b.c[r] = ctl[r];
+    b.skip[r] = skip ? skip[r] : nullptr;
+  }
+  k_control_batch<<<count, 256, 0, s>>>(b);
 }
 
 // The stop rules as a launch of their own (relax_control.cuh).

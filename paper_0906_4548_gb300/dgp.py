@@ -28,7 +28,7 @@ EXPORTED = ["dgp_background", "dgp_init", "dgp_destroy", "dgp_strerror", "dgp_re
             "dgp_power_spectrum_adjoint", "dgp_tile_config", "dgp_set_tile_config",
             "dgp_solve_adjoint_rc", "pm_step_adjoint_rc", "dgp_zeldovich_vf_adjoint", "dgp_velocity_factor",
             "dgp_workspace_size", "dgp_time_factors", "dgp_background_drc", "dgp_profile_sampled",
-            "dgp_set_wait_limit", "dgp_batch_classes"]
+            "dgp_set_wait_limit", "dgp_batch_classes", "dgp_batch_set_plane_pass"]
 DGP_NOALLOC_MAX_N = 64
 DGP_KERNEL_KINDS = 11
 
@@ -101,6 +101,7 @@ def _load():
         "dgp_profile_sampled": (i, [vp, ctypes.c_uint]),
         "dgp_set_wait_limit": (i, [vp, d, i]),
         "dgp_batch_classes": (i, [vp, P(i), P(i)]),
+        "dgp_batch_set_plane_pass": (i, [vp, i]),
         "dgp_profile_read": (i, [vp, i, P(i64), P(d), P(i64), P(d), P(d)]),
         "dgp_kernel_name": (ctypes.c_char_p, [i]),
         "dgp_power_spectrum_noalloc": (i, [vp, i, d, i, P(d), P(d), P(i64), vp]),
@@ -248,6 +249,11 @@ def dgp_batch_classes(batch, count):
     nc = ctypes.c_int()
     _check(lib.dgp_batch_classes(batch, cls, ctypes.byref(nc)), "dgp_batch_classes")
     return list(cls), nc.value
+
+
+def dgp_batch_set_plane_pass(batch, on):
+    """Plane-resident Hessian pass for the classes of n <= 96 (on, the default) or the separate passes."""
+    _check(lib.dgp_batch_set_plane_pass(batch, 1 if on else 0), "dgp_batch_set_plane_pass")
 
 
 def dgp_batch_destroy(batch):

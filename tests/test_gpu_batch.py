@@ -129,3 +129,48 @@ def test_class_step_matches_individual_contexts_and_oracle(dgp, torch_dev, prec)
         disp = (st.pos - p + box / 2) % box - box / 2
         assert np.linalg.norm(dx) / np.linalg.norm(disp) < 1e-4, k
         assert rel_l2(got[k][3:], st.mom) < 1e-4, k
+
+
+@pytest.mark.parametrize("n,box", [(16, 40.0), (32, 70.0), (48, 110.0), (64, 160.0), (96, 150.0)])
+def test_plane_pass_matches_separate_passes_and_oracle(dgp, torch_dev, n, box):
+    """A class of three realisations stepped with the plane-resident Hessian pass and with the
+    separate x and y passes: both are the same spectra up to rounding, so the two runs agree to
+    the FP32 level, with the same evaluation counts to within one; the plane run follows the FP64
+    oracle (n <= 64)."""
+    from oracle import pm as opm
+    torch, dev = torch_dev
+    cases = [(n, box * f, rc, seed) for f, rc, seed in ((1.0, 0.7, 11), (0.8, 1.4, 12), (1.3, 1.9, 13))]
+    a0, a1, ns = 0.25, 0.4, 3
+    dl = (math.log(a1) - math.log(a0)) / ns
+    sched = [a0 * math.exp(i * dl) for i in range(ns + 1)]
+    ics = [_ics(nn, bx, rc, seed, a0) for nn, bx, rc, seed in cases]
+    ics = [(p.astype(np.float32).astype(np.float64), m.astype(np.float32).astype(np.float64)) for p, m in ics]
+    plist = [dgp.params(bx, nn, rc, precision=dgp.DGP_FP32, tol=1e-6, max_iter=200) for nn, bx, rc, _ in cases]
+    runs = {}
+    for plane in (True, False):
+        b, ctxs = dgp.dgp_batch_create(plist, OM)
+        try:
+            dgp.dgp_batch_set_plane_pass(b, plane)
+            cls, ncls = dgp.dgp_batch_classes(b, len(cases))
+            assert ncls == 1
+            tb = [[to_dev(torch_dev, v, torch.float32) for v in (*p, *m)] for p, m in ics]
+            parts = [dgp.particles(*t) for t in tb]
+            infos = [dgp.dgp_batch_step(b, parts, [sched[i]] * len(cases), [sched[i + 1] - sched[i]] * len(cases))
+                     for i in range(ns)]
+            runs[plane] = ([np.stack([v.cpu().numpy() for v in t]).astype(np.float64) for t in tb], infos)
+        finally:
+            dgp.dgp_batch_destroy(b)
+    (gp, ip), (gs, is_) = runs[True], runs[False]
+    for step_p, step_s in zip(ip, is_):
+        for x, y in zip(step_p, step_s):
+            assert x["status"] == dgp.DGP_OK and x["norm_res"] < 1e-6
+            assert abs(x["iters"] - y["iters"]) <= 1
+    for k, ((nn, bx, rc, _), (p, m)) in enumerate(zip(cases, ics)):
+        assert rel_l2(gp[k], gs[k]) < 2e-5, k
+        if nn > 64:  # the separate passes' 96^3 runs are checked against the oracle elsewhere
+            continue
+        st = opm.run(p, m, a0, a1, ns, nn, bx, OM, rc, tol=1e-10, max_iter=300)
+        dx = (gp[k][:3] - st.pos + bx / 2) % bx - bx / 2
+        disp = (st.pos - p + bx / 2) % bx - bx / 2
+        assert np.linalg.norm(dx) / np.linalg.norm(disp) < 1e-4, k
+        assert rel_l2(gp[k][3:], st.mom) < 1e-4, k

@@ -320,6 +320,21 @@ int dgp_workspace_size(const dgp_params *p, int64_t np, dgp_workspace *out);
 int dgp_tile_config(dgp_ctx *c, int *y_threads);
 int dgp_set_tile_config(dgp_ctx *c, int y_threads);
 
+/* Fused Hessian pass of the relaxation (Sec. III.B, Eq. FullDGP2: the second
+ * derivatives of C and the non-local term N, each iteration).  For FP32 mesh
+ * data at n = 128 or 256, when the device co-schedules a thread-block cluster
+ * of n / 16 CTAs, an iteration forms the six spectra and transforms them back
+ * along x and y in one launch (a cluster per kz plane exchanging through
+ * distributed shared memory) instead of an x pass and a six-field y pass; the
+ * six spectra then cross memory once instead of three times.  The results
+ * are the same up to rounding order.  On a GB300 at 256^3 the fused launch
+ * took 352 us against 240 us for the two passes it replaces, so it is off by
+ * default.  dgp_set_hessian_fusion turns it on (on != 0) or off (0, the
+ * default); dgp_hessian_fusion sets *active to 1 when the context's solves
+ * use it.  DGP_E_INVALID for a NULL argument. */
+int dgp_set_hessian_fusion(dgp_ctx *c, int on);
+int dgp_hessian_fusion(dgp_ctx *c, int *active);
+
 /* Bound of the waits inside the relaxation kernel (not part of the paper's
  * method).  The FP32-data relaxation pass waits on its own asynchronous tile
  * copies; each wait gives up after `seconds` (default 2; 0 < seconds <= 60),

@@ -16,6 +16,7 @@
 #include "fft_core.cuh"
 #include "kernels.cuh"
 #include "relax_control.cuh"
+#include "xy.cuh"
 
 namespace dgp {
 
@@ -293,6 +294,8 @@ class EngineBase {
   unsigned long long wait_ns = 2000000000ull;  // bound of every in-kernel wait
   int withhold = 0;             // test hook: the relaxation pass leaves its first copy unissued
   bool plane_pass = true;       // class solves of small meshes: the plane-resident Hessian pass
+  bool xy_on = false;           // the Hessian x pass fused with the inverse y pass (opt-in: slower)
+  bool xy_ok = false;           // set at init: the mesh and device allow the fused pass
 
   // Host wait for the work enqueued so far on the context's stream.
   cudaError_t wait_stream() {
@@ -467,6 +470,7 @@ class Engine : public EngineBase {
     if (cudaMalloc(&tw, sizeof(V) * 3 * N) != cudaSuccess) return DGP_E_NOMEM;
     DGP_CUDA(cudaMemcpy(tw, htw.data(), sizeof(V) * 3 * N, cudaMemcpyHostToDevice));
     DGP_CUDA(cudaMemset(d_rstats, 0, sizeof(double) * 12));
+    xy_ok = sizeof(T) == 4 && (N == 128 || N == 256) && xy_hessian_available(N);
     return tune_tiles();
   }
 
@@ -678,6 +682,7 @@ class Engine : public EngineBase {
       auto spec_in = [&](int it) { return (it & 1) ? sD2 : sD; };
       auto spec_out = [&](int it) { return (it & 1) ? sD : sD2; };
       const int* skip = &d_ctl->done;
+      const bool xy = xy_ok && xy_on;  // Hessian spectra and their inverse y in one launch
       // One iteration: Hessian spectra, inverse y, fused z pass + update,
       // statistics, (stop rules), forward y of the new iterate.  With control,
       // every kernel returns at entry once the controller has stopped the solve.
@@ -686,12 +691,17 @@ class Engine : public EngineBase {
         const int ib = in_buf(it), ob = out_buf(it);
         // the first iteration and replays always run; later ones may return at entry
         const double sure = (it == 0 || !control) ? 1.0 : -1.0;
-        prof.run_it(KK_X_HESSIAN, 0, sure * 7 * SB, stream, [&] {
-          launch_fft_x_op<T, N>(XOP_HESSIAN, spec_in(it), nullptr, fs(s6, 6), 0, kp, nullptr, 0, 0, 0, tw, stream,
-                                sk);
-        });
-        prof.run_it(KK_Y, 0, sure * 12 * SB, stream,
-                    [&] { launch_fft_y<T, N>(fs(s6, 6), 6, true, tw, stream, sk, y_threads); });
+        if (xy) {
+          prof.run_it(KK_X_HESSIAN, 0, sure * 7 * SB, stream,
+                      [&] { launch_xy_hessian<T, N>(spec_in(it), fs(s6, 6), kp, tw, stream, sk); });
+        } else {
+          prof.run_it(KK_X_HESSIAN, 0, sure * 7 * SB, stream, [&] {
+            launch_fft_x_op<T, N>(XOP_HESSIAN, spec_in(it), nullptr, fs(s6, 6), 0, kp, nullptr, 0, 0, 0, tw, stream,
+                                  sk);
+          });
+          prof.run_it(KK_Y, 0, sure * 12 * SB, stream,
+                      [&] { launch_fft_y<T, N>(fs(s6, 6), 6, true, tw, stream, sk, y_threads); });
+        }
         prof.run_it(KK_RELAX, 0, sure * (7 * SB + 3 * RB), stream, [&] {
           if constexpr (sizeof(T) == 4)
             launch_relax_tma<N>(arith, rmaps, rD[ib], d_rstats + 4 * ib + 1, rS, rD[ob], spec_out(it), rp, partials,
@@ -716,7 +726,7 @@ class Engine : public EngineBase {
       };
       auto credit = [&](int iters, int yfwd) {
         prof.credit(KK_X_HESSIAN, 7 * SB * iters);
-        prof.credit(KK_Y, 12 * SB * iters + (2 * SB + 32.0 * fblocks) * yfwd);
+        prof.credit(KK_Y, (xy ? 0.0 : 12 * SB * iters) + (2 * SB + 32.0 * fblocks) * yfwd);
         prof.credit(KK_RELAX, (7 * SB + 3 * RB) * iters);
       };
 
@@ -769,7 +779,7 @@ class Engine : public EngineBase {
           if (graphs && it > 0 && (it & 1)) {
             DGP_CUDA(cudaGraphLaunch(pair_exec[j0], stream));
             prof.count(KK_X_HESSIAN, 2);
-            prof.count(KK_Y, 4);
+            prof.count(KK_Y, xy ? 2 : 4);
             prof.count(KK_RELAX, 2);
             it += 2;
           } else {
@@ -1213,8 +1223,12 @@ class Engine : public EngineBase {
         }
         return check();
       }
-      launch_fft_x_batch<T, N>(XOP_HESSIAN, xr, m, tw, st);
-      launch_fft_y_batch<T, N>(f6, sk, nullptr, m, 6, true, tw, st, yt);
+      if (e0->xy_ok && e0->xy_on) {
+        launch_xy_hessian_batch<T, N>(xr, m, tw, st);
+      } else {
+        launch_fft_x_batch<T, N>(XOP_HESSIAN, xr, m, tw, st);
+        launch_fft_y_batch<T, N>(f6, sk, nullptr, m, 6, true, tw, st, yt);
+      }
       launch_relax_tma_batch<N>(e0->arith_mode(), ra, m, tw, st);
       if (control) {
         launch_fft_y_batch<T, N>(f1, sk, yc, m, 1, false, tw, st, yt);
@@ -2255,6 +2269,18 @@ int dgp_tile_config(dgp_ctx* c, int* y_threads) {
 int dgp_set_tile_config(dgp_ctx* c, int y_threads) {
   if (!c || (y_threads != 128 && y_threads != 256 && y_threads != 512)) return DGP_E_INVALID;
   c->eng->y_threads = y_threads;
+  return DGP_OK;
+}
+
+int dgp_set_hessian_fusion(dgp_ctx* c, int on) {
+  if (!c) return DGP_E_INVALID;
+  c->eng->xy_on = on != 0;
+  return DGP_OK;
+}
+
+int dgp_hessian_fusion(dgp_ctx* c, int* active) {
+  if (!c || !active) return DGP_E_INVALID;
+  *active = (c->eng->xy_ok && c->eng->xy_on) ? 1 : 0;
   return DGP_OK;
 }
 

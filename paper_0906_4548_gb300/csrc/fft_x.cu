@@ -23,10 +23,13 @@
 // Every output carries the 1 / N^3 of the three inverse transforms.
 #include <math.h>
 
+#include <cooperative_groups.h>
+
 #include "adjoint_rc.cuh"
 #include "fft_core.cuh"
 #include "kernels.cuh"
 #include "reduce.cuh"
+#include "xy.cuh"
 
 namespace dgp {
 
@@ -115,6 +118,57 @@ __device__ __forceinline__ double geff_dev(const KParams& kp, double kmag) {
   const double r = (eta * (1 + q) - 1) / (eta * (2 + q) - 2);
   const double t2 = 3.0 * kp.a / (kmag * kp.rc_H0 * (kp.kbar_fac * kp.aE)) * r * r;
   return 1.0 / (t1 + t2);
+}
+
+// The Hessian spectra (Sec. III.B): H_ab(k) = (n_a n_b / |n|^2) D(k) for (a, b) = xx, yy, xy,
+// xz, yz (outputs 0..4), with the absolute value where a component of an off-diagonal pair is
+// on its Nyquist index (on the diagonal the product is a square anyway), and N = -D / kbar
+// (output 5).  1/|n|^2 and the 1/N^3 of the inverse transforms are folded into the spectrum
+// once (hessian_prescale); each output's multiplier is then a product of the wavenumber
+// components, formed in registers, and its pair is chosen once per output, so the multiplier
+// is branch-free per element.  X[k2] holds kx = lane + N1 k2.
+template <typename T, int N>
+__device__ __forceinline__ void hessian_prescale(vec2_t<T> (&X)[Split<N>::N2], int lane, T fy, T fz, T inv_m) {
+  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+  const T nyz2 = fy * fy + fz * fz;
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) {
+    const T fx = (T)signed_index(lane + N1 * k2, N);
+    const T n2 = fx * fx + nyz2;
+    X[k2] = cscale(X[k2], n2 != (T)0 ? inv_m / n2 : (T)0);
+  }
+}
+
+// Output o of the prescaled spectrum X; ikf = 1 / (kbar_fac k_f) (0 in the local-only mode),
+// so that |n|^2 / kbar = |n| ikf.
+template <typename T, int N>
+__device__ __forceinline__ void hessian_output(const vec2_t<T> (&X)[Split<N>::N2], int o, int lane, T fy, T fz,
+                                               bool nyq_y, bool nyq_z, T ikf, vec2_t<T> (&Y)[Split<N>::N2]) {
+  constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+  if (o == 5) {
+    const T nyz2 = fy * fy + fz * fz;
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+      const T fx = (T)signed_index(lane + N1 * k2, N);
+      Y[k2] = cscale(X[k2], -sqrt(fx * fx + nyz2) * ikf);
+    }
+    return;
+  }
+  const bool a_is_x = o == 0 || o == 2 || o == 3;             // first component x, else y
+  const int b_sel = o == 0 ? 0 : (o == 1 || o == 2 ? 1 : 2);  // second: x, y or z
+  const T fb_fixed = b_sel == 1 ? fy : fz;
+  const bool nyq_fixed = (!a_is_x && nyq_y) || (b_sel == 1 && nyq_y) || (b_sel == 2 && nyq_z);
+#pragma unroll
+  for (int k2 = 0; k2 < N2; ++k2) {
+    const int kx = lane + N1 * k2;
+    const T fx = (T)signed_index(kx, N);
+    const T fa = a_is_x ? fx : fy;
+    const T fb = b_sel == 0 ? fx : fb_fixed;
+    T prod = fa * fb;
+    const bool nyq = nyq_fixed || ((a_is_x || b_sel == 0) && kx == N / 2);
+    if (nyq) prod = fabs(prod);
+    Y[k2] = cscale(X[k2], prod);
+  }
 }
 
 template <typename T, int RB> struct XBatch {
@@ -388,51 +442,16 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
   }
 
   if (OP == XOP_HESSIAN) {
-    // H_ab(k) = (n_a n_b / |n|^2) D(k) for (a, b) = xx, yy, xy, xz, yz with the
-    // absolute value where a component of an off-diagonal pair is on its Nyquist
-    // index (on the diagonal the product is a square anyway), then N = -D / kbar.
-    // 1/|n|^2 and the 1/N^3 of the inverse transforms are folded into the
-    // spectrum once (Xs); each output's multiplier is then a product of the
-    // wavenumber components, formed in registers.  The pair of each output is
-    // chosen once per output; per element the multiplier is branch-free.
     const T fy = (T)ny, fz = (T)nz;
-    const T nyz2 = fy * fy + fz * fz;
-#pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) {
-      const T fx = (T)signed_index(lane + N1 * k2, N);
-      const T n2 = fx * fx + nyz2;
-      X0[k2] = cscale(X0[k2], n2 != (T)0 ? inv_m / n2 : (T)0);
-    }
+    hessian_prescale<T, N>(X0, lane, fy, fz, inv_m);
+    const T ikf = kp.local_only ? (T)0 : (T)1 / kc<T>(kp.kbar_fac * 2.0 * M_PI / kp.box, kp.kbkf_f);
 #pragma unroll 1
-    for (int o = 0; o < 5; ++o) {
-      const bool a_is_x = o == 0 || o == 2 || o == 3;       // first component x, else y
-      const int b_sel = o == 0 ? 0 : (o == 1 || o == 2 ? 1 : 2);  // second: x, y or z
-      const T fb_fixed = b_sel == 1 ? fy : fz;
-      const bool nyq_fixed = (!a_is_x && nyq_y) || (b_sel == 1 && nyq_y) || (b_sel == 2 && nyq_z);
+    for (int o = 0; o < 6; ++o) {
       V Y[N2];
-#pragma unroll
-      for (int k2 = 0; k2 < N2; ++k2) {
-        const int kx = lane + N1 * k2;
-        const T fx = (T)signed_index(kx, N);
-        const T fa = a_is_x ? fx : fy;
-        const T fb = b_sel == 0 ? fx : fb_fixed;
-        T prod = fa * fb;
-        const bool nyq = nyq_fixed || ((a_is_x || b_sel == 0) && kx == N / 2);
-        if (nyq) prod = fabs(prod);
-        Y[k2] = cscale(X0[k2], prod);
-      }
+      hessian_output<T, N>(X0, o, lane, fy, fz, nyq_y, nyq_z, ikf, Y);
       // the outputs alternate between two transpose buffers: one barrier per output
       x_inverse<T, N, false>(Y, args.out.p[o], kz, ky0, lane, yl, (o & 1) ? s_T2 : s_T, s_tw);
     }
-    // N = -D / kbar = -(|n|^2 / kbar) Xs, |n|^2 / kbar = |n| / (kbar_fac k_f)
-    const T ikf = kp.local_only ? (T)0 : (T)1 / kc<T>(kp.kbar_fac * 2.0 * M_PI / kp.box, kp.kbkf_f);
-    V Y[N2];
-#pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) {
-      const T fx = (T)signed_index(lane + N1 * k2, N);
-      Y[k2] = cscale(X0[k2], -sqrt(fx * fx + nyz2) * ikf);
-    }
-    x_inverse<T, N, false>(Y, args.out.p[5], kz, ky0, lane, yl, s_T2, s_tw);  // output 5: odd
     return;
   }
 
@@ -697,6 +716,239 @@ void launch_fft_x_rc(const FieldSet<T>& in, int in_mask, const KParams& kp, cons
   a.in = in; a.in_mask = in_mask; a.rc = d;
   launch_x<T, N, XOP_RC>(&a, 1, tw, s);
 }
+
+// ---------------------------------------------------------------------------
+// Hessian x pass fused with the inverse y transforms of its six outputs (FP32, N = 128 or 256).
+//
+// The CTAs of one kz plane (N / TY of them, the ky blocks) form one thread-block cluster.  Each
+// does what the Hessian x pass does for its TY ky columns, but keeps every output's x inverse
+// in its own shared memory (all x, its TY ky) instead of writing it out.  After a cluster
+// barrier each CTA takes TY x rows of the plane: it reads their N ky values from the CTAs of
+// the cluster (distributed shared memory, TY consecutive values from each), transforms them
+// back along y and writes the rows of the output in the layout (kz, x, y) that the relaxation
+// pass reads.  An iteration then needs no six-field inverse y pass: its 12 S of memory traffic
+// (read and write of six half spectra) are gone and the six outputs cross memory once.  Two
+// alternating exchange buffers let one cluster barrier per output order the writes of one
+// output after the reads of the output before it; a last barrier keeps every CTA resident
+// until the others have read its buffers.  Measured on a GB300 at 256^3 (clusters of 16):
+// 352 us per launch against 240 us for the x pass and six-field y pass it replaces.  The x
+// pass is latency-bound at 16 warps per SM and the y work adds to its time rather than
+// hiding in it, so the fused pass is opt-in (dgp_set_hessian_fusion).
+template <int N> struct XYGeom {
+  static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+  static constexpr int TY = 16;                  // ky columns per CTA; x rows per CTA in the y stage
+  static constexpr int CS = N / TY;              // CTAs per cluster: one kz plane
+  static constexpr int THREADS = TY * N1;
+  static constexpr int XT = N * TY;              // x transpose (complex)
+  static constexpr int YT = TY * N1 * (N2 + 1);  // y transpose (complex)
+  static constexpr int TBUF = XT > YT ? XT : YT;
+  static constexpr int EX = N * TY;              // one exchange buffer: [x][ky in the block]
+  static constexpr size_t SMEM = sizeof(float2) * ((size_t)kTwiddleTables * N + TBUF + 2 * (size_t)EX);
+  static_assert(THREADS == 256, "TY rows of N1 lanes in both stages");
+};
+
+template <int N, int RB>
+__global__ void __launch_bounds__(256, 2) k_xy_hessian(const __grid_constant__ XBatch<float, RB> xb,
+                                                       const float2* __restrict__ g_tw) {
+  namespace cg = cooperative_groups;
+  using G = XYGeom<N>;
+  using V = float2;
+  constexpr int N1 = G::N1, N2 = G::N2, TY = G::TY;
+  const XArgs<float>& args = xb.a[RB > 1 ? blockIdx.z : 0];
+  // the flag was set by an earlier launch, so every CTA of a cluster takes the same branch
+  if (args.skip && *args.skip) return;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* s_tw = reinterpret_cast<V*>(smem_raw);
+  V* s_T = s_tw + kTwiddleTables * N;  // the x transpose, then the y transpose
+  V* s_E = s_T + G::TBUF;              // two exchange buffers
+  load_twiddles(s_tw, g_tw, N);
+  const int tid = threadIdx.x;
+  const int yl = tid % TY, lane = tid / TY;  // x stage: the TY columns fastest
+  const int kz = blockIdx.y;
+  const int rank = blockIdx.x;  // the CTA's rank in its cluster (cluster dims CS x 1 x 1, gridDim.x = CS)
+  const int ky0 = rank * TY;
+  const int ky = ky0 + yl;
+  const int nz = kz == N / 2 ? -(N / 2) : kz;
+  const int ny = signed_index(ky, N);
+  const bool nyq_y = ky == N / 2, nyq_z = kz == N / 2;
+  const KParams& kp = args.kp;
+  __syncthreads();
+  V X0[N2];
+  x_forward<float, N>(args.in0, kz, ky0, lane, yl, s_T, s_tw, X0);
+  const float fy = (float)ny, fz = (float)nz;
+  hessian_prescale<float, N>(X0, lane, fy, fz, kp.inv_m_f);
+  const float ikf = kp.local_only ? 0.f : 1.f / kp.kbkf_f;
+  // y stage: thread (row, j) of TY rows x N1; stage one's TY x N2 tasks on the first threads
+  const int row = tid / N1, j = tid % N1;
+  const int r1 = tid / N2, c1 = tid % N2;
+  const bool act1 = tid < TY * N2;
+  const int xr0 = rank * TY;  // first x row of this CTA's y stage
+#pragma unroll 1
+  for (int o = 0; o < 6; ++o) {
+    V Y[N2];
+    hessian_output<float, N>(X0, o, lane, fy, fz, nyq_y, nyq_z, ikf, Y);
+    // x inverse as in x_inverse; the result stays conjugated in the exchange buffer
+    conj_regs(Y);
+    dft_regs<N2, N / N2>(Y, s_tw);
+#pragma unroll
+    for (int m1 = 0; m1 < N2; ++m1)
+      s_T[(m1 * N1 + lane) * TY + yl] = (m1 == 0) ? Y[m1] : cmul(Y[m1], s_tw[2 * N + m1 * N1 + lane]);
+    __syncthreads();
+    V* E = s_E + (o & 1) * G::EX;
+    if (lane < N2) {
+      V w[N1];
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) w[k1] = s_T[(lane * N1 + k1) * TY + yl];
+      dft_regs<N1, N / N1>(w, s_tw);
+#pragma unroll
+      for (int m2 = 0; m2 < N1; ++m2) E[(lane + N2 * m2) * TY + yl] = w[m2];
+    }
+    cluster.sync();  // every CTA's block of this output is in its exchange buffer
+    // y inverse of rows xr0 + r as conj(DFT(conj(x))), conj(x) being what the buffers hold
+    if (act1) {
+      V v[N1];
+#pragma unroll
+      for (int j1 = 0; j1 < N1; ++j1) {
+        const int kyy = N2 * j1 + c1;
+        const V* Ep = cluster.map_shared_rank(E, kyy / TY);
+        v[j1] = Ep[(xr0 + r1) * TY + kyy % TY];
+      }
+      dft_regs<N1, N / N1>(v, s_tw);
+      V* T1 = s_T + r1 * (N1 * (N2 + 1));
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) T1[k1 * (N2 + 1) + c1] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[N + k1 * N2 + c1]);
+    }
+    __syncthreads();
+    {
+      const V* Tp = s_T + row * (N1 * (N2 + 1));
+      V u[N2];
+#pragma unroll
+      for (int j2 = 0; j2 < N2; ++j2) u[j2] = Tp[j * (N2 + 1) + j2];
+      dft_regs<N2, N / N2>(u, s_tw);
+      V* dst = args.out.p[o] + ((int64_t)kz * N + xr0 + row) * N;
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) dst[j + N1 * k2] = cconj(u[k2]);
+    }
+    __syncthreads();  // the y transpose is read before the next output's x transpose reuses it
+  }
+  cluster.sync();  // no CTA leaves while another may still read its exchange buffers
+}
+
+template <int N, int RB>
+static void xy_launch_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int count, cudaStream_t s) {
+  using G = XYGeom<N>;
+  cfg = cudaLaunchConfig_t{};
+  cfg.gridDim = dim3(G::CS, N / 2 + 1, count);
+  cfg.blockDim = dim3(G::THREADS, 1, 1);
+  cfg.dynamicSmemBytes = G::SMEM;
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = G::CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+}
+
+// Shared-memory limit and (for clusters above 8) the non-portable cluster size, once per
+// instantiation and device.
+template <int N, int RB>
+static cudaError_t xy_prepare() {
+  using G = XYGeom<N>;
+  static std::mutex mu;
+  static uint64_t done = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(mu);
+  if (dev < 64 && ((done >> dev) & 1u)) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_xy_hessian<N, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+  if (e == cudaSuccess && G::CS > 8)
+    e = cudaFuncSetAttribute(k_xy_hessian<N, RB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e == cudaSuccess && dev < 64) done |= 1ull << dev;
+  return e;
+}
+
+template <int N, int RB>
+static void launch_xy(const XArgs<float>* a, int count, const float2* tw, cudaStream_t s) {
+  if (xy_prepare<N, RB>() != cudaSuccess) return;  // the launch error check reports it
+  XBatch<float, RB> xb;
+  for (int r = 0; r < count; ++r) xb.a[r] = a[r];
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  xy_launch_config<N, RB>(cfg, attr, count, s);
+  cudaLaunchKernelEx(&cfg, k_xy_hessian<N, RB>, xb, tw);
+}
+
+template <int N>
+static int xy_probe() {
+  if (xy_prepare<N, 1>() != cudaSuccess || xy_prepare<N, kBatchMax>() != cudaSuccess) return 0;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  xy_launch_config<N, 1>(cfg, attr, 1, nullptr);
+  int nc = 0;
+  if (cudaOccupancyMaxActiveClusters(&nc, k_xy_hessian<N, 1>, &cfg) != cudaSuccess) return 0;
+  return nc > 0 ? 1 : 0;
+}
+
+bool xy_hessian_available(int n) {
+  if (n != 128 && n != 256) return false;
+  static std::mutex mu;
+  static int ok[2][64];
+  static bool init = false;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return false;
+  std::lock_guard<std::mutex> g(mu);
+  if (!init) {
+    for (auto& r : ok)
+      for (int& v : r) v = -1;
+    init = true;
+  }
+  int& v = ok[n == 256 ? 1 : 0][dev];
+  if (v < 0) {
+    v = n == 256 ? xy_probe<256>() : xy_probe<128>();
+    cudaGetLastError();
+  }
+  return v == 1;
+}
+
+template <typename T, int N>
+void launch_xy_hessian(const vec2_t<T>* in, const FieldSet<T>& out, const KParams& kp, const vec2_t<T>* tw,
+                       cudaStream_t s, const int* skip) {
+  if constexpr (sizeof(T) == 4 && (N == 128 || N == 256)) {
+    XArgs<float> a{};
+    a.in0 = in;
+    a.out = out;
+    a.kp = kp;
+    a.skip = skip;
+    launch_xy<N, 1>(&a, 1, tw, s);
+  }
+}
+
+template <typename T, int N>
+void launch_xy_hessian_batch(const XReal<T>* rz, int count, const vec2_t<T>* tw, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4 && (N == 128 || N == 256)) {
+    if (count < 1 || count > kBatchMax) return;
+    XArgs<float> a[kBatchMax];
+    for (int r = 0; r < count; ++r) {
+      a[r] = XArgs<float>{};
+      a[r].in0 = rz[r].in0;
+      a[r].out = rz[r].out;
+      a[r].kp = rz[r].kp;
+      a[r].skip = rz[r].skip;
+    }
+    launch_xy<N, kBatchMax>(a, count, tw, s);
+  }
+}
+
+#define DGP_INST_XY(N)                                                                                       \
+  template void launch_xy_hessian<float, N>(const float2*, const FieldSet<float>&, const KParams&,            \
+                                            const float2*, cudaStream_t, const int*);                          \
+  template void launch_xy_hessian<double, N>(const double2*, const FieldSet<double>&, const KParams&,         \
+                                             const double2*, cudaStream_t, const int*);                        \
+  template void launch_xy_hessian_batch<float, N>(const XReal<float>*, int, const float2*, cudaStream_t);
+DGP_INST_XY(16) DGP_INST_XY(32) DGP_INST_XY(48) DGP_INST_XY(64) DGP_INST_XY(96) DGP_INST_XY(128) DGP_INST_XY(256)
+DGP_INST_XY(512)
 
 #define DGP_INST_X(T, N)                                                                            \
   template void launch_fft_x_op<T, N>(int, const vec2_t<T>*, const vec2_t<T>*, const FieldSet<T>&, int, \

@@ -28,7 +28,8 @@ EXPORTED = ["dgp_background", "dgp_init", "dgp_destroy", "dgp_strerror", "dgp_re
             "dgp_power_spectrum_adjoint", "dgp_tile_config", "dgp_set_tile_config",
             "dgp_solve_adjoint_rc", "pm_step_adjoint_rc", "dgp_zeldovich_vf_adjoint", "dgp_velocity_factor",
             "dgp_workspace_size", "dgp_time_factors", "dgp_background_drc", "dgp_profile_sampled",
-            "dgp_set_wait_limit", "dgp_batch_classes", "dgp_batch_set_plane_pass"]
+            "dgp_set_wait_limit", "dgp_batch_classes", "dgp_batch_set_plane_pass", "dgp_set_hessian_fusion",
+            "dgp_hessian_fusion"]
 DGP_NOALLOC_MAX_N = 64
 DGP_KERNEL_KINDS = 11
 
@@ -102,6 +103,8 @@ def _load():
         "dgp_set_wait_limit": (i, [vp, d, i]),
         "dgp_batch_classes": (i, [vp, P(i), P(i)]),
         "dgp_batch_set_plane_pass": (i, [vp, i]),
+        "dgp_set_hessian_fusion": (i, [vp, i]),
+        "dgp_hessian_fusion": (i, [vp, P(i)]),
         "dgp_profile_read": (i, [vp, i, P(i64), P(d), P(i64), P(d), P(d)]),
         "dgp_kernel_name": (ctypes.c_char_p, [i]),
         "dgp_power_spectrum_noalloc": (i, [vp, i, d, i, P(d), P(d), P(i64), vp]),
@@ -249,6 +252,18 @@ def dgp_batch_classes(batch, count):
     nc = ctypes.c_int()
     _check(lib.dgp_batch_classes(batch, cls, ctypes.byref(nc)), "dgp_batch_classes")
     return list(cls), nc.value
+
+
+def dgp_set_hessian_fusion(ctx, on):
+    """Fused Hessian x pass and inverse y pass (n = 128 or 256, FP32 data) on or off (the default)."""
+    _check(lib.dgp_set_hessian_fusion(ctx, 1 if on else 0), "dgp_set_hessian_fusion")
+
+
+def dgp_hessian_fusion(ctx):
+    """True when the context's solves use the fused Hessian pass."""
+    v = ctypes.c_int()
+    _check(lib.dgp_hessian_fusion(ctx, ctypes.byref(v)), "dgp_hessian_fusion")
+    return bool(v.value)
 
 
 def dgp_batch_set_plane_pass(batch, on):

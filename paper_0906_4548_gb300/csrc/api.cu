@@ -373,6 +373,10 @@ class Engine : public EngineBase {
   static constexpr int kCopyStreams = 3;
   cudaStream_t copy_streams[kCopyStreams] = {};
   cudaEvent_t copy_ev[kCopyStreams + 1] = {};  // [j]: stream j's copies in; [kCopyStreams]: a fence on stream
+  // pm_step_host works on kHostChunks particle ranges, so that each range's kick overlaps the
+  // copies of the others: per range, its copy in, its first kick, its second kick
+  static constexpr int kHostChunks = 4;
+  cudaEvent_t chunk_ev[3][kHostChunks] = {};
   T* hp[6] = {};                // device copies for pm_step_host
   int64_t hp_n = 0;
   // cell sort: key and permuted copies per particle, counts / starts / cursors per cell
@@ -412,6 +416,9 @@ class Engine : public EngineBase {
       if (copy_streams[j]) cudaStreamDestroy(copy_streams[j]);
     for (int j = 0; j <= kCopyStreams; ++j)
       if (copy_ev[j]) cudaEventDestroy(copy_ev[j]);
+    for (auto& row : chunk_ev)
+      for (cudaEvent_t& e : row)
+        if (e) cudaEventDestroy(e);
     for (int i = 0; i < 3; ++i)
       if (pair_exec[i]) cudaGraphExecDestroy(pair_exec[i]);
     if (class_exec) cudaGraphExecDestroy(class_exec);
@@ -1424,6 +1431,7 @@ class Engine : public EngineBase {
 
   int step_host(dgp_particles* hpp, double a, double da, dgp_solve_info* info) override {
     if (!valid_parts(hpp) || hpp->n == 0) return DGP_E_INVALID;
+    if (!(a > 0.0) || !(da > 0.0) || !isfinite(a + da)) return DGP_E_INVALID;
     if (hp_n < hpp->n) {
       for (int i = 0; i < 6; ++i) {
         cudaFree(hp[i]);
@@ -1436,44 +1444,89 @@ class Engine : public EngineBase {
       for (int j = 0; j < kCopyStreams; ++j)
         DGP_CUDA(cudaStreamCreateWithFlags(&copy_streams[j], cudaStreamNonBlocking));
       for (int j = 0; j <= kCopyStreams; ++j) DGP_CUDA(cudaEventCreateWithFlags(&copy_ev[j], cudaEventDisableTiming));
+      for (auto& row : chunk_ev)
+        for (cudaEvent_t& e : row) DGP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
-    void* src[6] = {hpp->x, hpp->y, hpp->z, hpp->px, hpp->py, hpp->pz};
-    const size_t bytes = sizeof(T) * hpp->n;
+    T* src[6] = {(T*)hpp->x, (T*)hpp->y, (T*)hpp->z, (T*)hpp->px, (T*)hpp->py, (T*)hpp->pz};
+    const int64_t np = hpp->n;
     // every host step runs on the same device copies, so the end-of-step force
     // may be reused only for the host arrays that the previous host step wrote
     if (force_host != hpp->x) force_valid = false;
     force_host = nullptr;
-    // copies on the copy streams, each ordered after the work enqueued so far on the stream
-    auto fence = [&]() -> int {
-      DGP_CUDA(cudaEventRecord(copy_ev[kCopyStreams], stream));
-      for (int j = 0; j < kCopyStreams; ++j) DGP_CUDA(cudaStreamWaitEvent(copy_streams[j], copy_ev[kCopyStreams], 0));
-      return DGP_OK;
-    };
-    int rc;
-    if ((rc = fence())) return rc;
-    for (int i = 0; i < 6; ++i)
-      DGP_CUDA(cudaMemcpyAsync(hp[i], src[i], bytes, cudaMemcpyHostToDevice, copy_streams[i % kCopyStreams]));
-    for (int j = 0; j < kCopyStreams; ++j) {
-      DGP_CUDA(cudaEventRecord(copy_ev[j], copy_streams[j]));
-      DGP_CUDA(cudaStreamWaitEvent(stream, copy_ev[j], 0));
+    // particle ranges of whole 256-element blocks (16-byte aligned slices)
+    const int64_t cs = ((np + kHostChunks - 1) / kHostChunks + 255) / 256 * 256;
+    auto lo = [&](int c) { return std::min<int64_t>(np, c * cs); };
+    auto hi = [&](int c) { return std::min<int64_t>(np, (c + 1) * cs); };
+    // the copy streams start after the work enqueued so far on the stream
+    DGP_CUDA(cudaEventRecord(copy_ev[kCopyStreams], stream));
+    for (int j = 0; j < kCopyStreams; ++j) DGP_CUDA(cudaStreamWaitEvent(copy_streams[j], copy_ev[kCopyStreams], 0));
+    for (int c = 0; c < kHostChunks; ++c) {
+      cudaStream_t cp_s = copy_streams[c % kCopyStreams];
+      const size_t b = sizeof(T) * (size_t)(hi(c) - lo(c));
+      if (b)
+        for (int i = 0; i < 6; ++i) DGP_CUDA(cudaMemcpyAsync(hp[i] + lo(c), src[i] + lo(c), b, cudaMemcpyHostToDevice, cp_s));
+      DGP_CUDA(cudaEventRecord(chunk_ev[0][c], cp_s));
     }
-    dgp_particles dp{hp[0], hp[1], hp[2], hp[3], hp[4], hp[5], hpp->n};
-    // the positions are final after the drift: copy them back while the field solve runs
-    const std::function<int()> positions_out = [&]() -> int {
-      int r;
-      if ((r = fence())) return r;
-      for (int i = 0; i < 3; ++i)
-        DGP_CUDA(cudaMemcpyAsync(src[i], hp[i], bytes, cudaMemcpyDeviceToHost, copy_streams[i % kCopyStreams]));
-      return DGP_OK;
-    };
-    rc = step_impl(&dp, a, da, info, &positions_out);
-    if (rc != DGP_OK) {
+    int rc = DGP_OK;
+    auto finish_copies = [&]() {
       for (int j = 0; j < kCopyStreams; ++j) cudaStreamSynchronize(copy_streams[j]);
-      return rc;
+    };
+    dgp_particles dp{hp[0], hp[1], hp[2], hp[3], hp[4], hp[5], np};
+    // the steps of step_impl, with the two kicks taken range by range
+    const double a1 = a + da;
+    const double ah = exp(0.5 * (log(a) + log(a1)));
+    const double om = cosmo.omega_m0, rc_ = p.rc_H0;
+    const bool reuse = force_valid && force_x == dp.x && force_np == np && fabs(force_a - a) <= 1e-12 * a;
+    if (!reuse) {
+      for (int c = 0; c < kHostChunks; ++c) DGP_CUDA(cudaStreamWaitEvent(stream, chunk_ev[0][c], 0));
+      if ((rc = forces_at(&dp, a, nullptr))) { finish_copies(); return rc; }
     }
-    if ((rc = fence())) return rc;
-    for (int i = 3; i < 6; ++i)
-      DGP_CUDA(cudaMemcpyAsync(src[i], hp[i], bytes, cudaMemcpyDeviceToHost, copy_streams[i % kCopyStreams]));
+    const CicParams cp = cic();
+    const double k1 = time_integral(a, ah, om, rc_, 0), dr = time_integral(a, a1, om, rc_, 2);
+    const bool sorting = p.sort_every > 0 && (nsteps + 1) % p.sort_every == 0;
+    for (int c = 0; c < kHostChunks; ++c) {
+      const int64_t o = lo(c), m = hi(c) - lo(c);
+      if (m <= 0) continue;
+      DGP_CUDA(cudaStreamWaitEvent(stream, chunk_ev[0][c], 0));
+      prof.run(KK_GATHER, 12.0 * sizeof(T) * m + 3 * RB * (double)m / np, stream, [&] {
+        launch_gather_kick<T>(hp[0] + o, hp[1] + o, hp[2] + o, hp[3] + o, hp[4] + o, hp[5] + o, m, rG[0], rG[1],
+                              rG[2], cp, k1, dr, 1, stream);
+      });
+      if (!sorting) {  // the range's positions are final: copy them back during the field solve
+        cudaStream_t cp_s = copy_streams[c % kCopyStreams];
+        DGP_CUDA(cudaEventRecord(chunk_ev[1][c], stream));
+        DGP_CUDA(cudaStreamWaitEvent(cp_s, chunk_ev[1][c], 0));
+        for (int i = 0; i < 3; ++i)
+          DGP_CUDA(cudaMemcpyAsync(src[i] + o, hp[i] + o, sizeof(T) * m, cudaMemcpyDeviceToHost, cp_s));
+      }
+    }
+    if (cudaGetLastError() != cudaSuccess) { finish_copies(); return DGP_E_CUDA; }
+    ++nsteps;
+    if (sorting) {
+      if ((rc = sort_impl(&dp, nullptr))) { finish_copies(); return rc; }
+      DGP_CUDA(cudaEventRecord(copy_ev[kCopyStreams], stream));
+      for (int i = 0; i < 3; ++i) {
+        cudaStream_t cp_s = copy_streams[i % kCopyStreams];
+        DGP_CUDA(cudaStreamWaitEvent(cp_s, copy_ev[kCopyStreams], 0));
+        DGP_CUDA(cudaMemcpyAsync(src[i], hp[i], sizeof(T) * np, cudaMemcpyDeviceToHost, cp_s));
+      }
+    }
+    if ((rc = forces_at(&dp, a1, info))) { finish_copies(); return rc; }
+    const double k2 = time_integral(ah, a1, om, rc_, 0);
+    for (int c = 0; c < kHostChunks; ++c) {
+      const int64_t o = lo(c), m = hi(c) - lo(c);
+      if (m <= 0) continue;
+      prof.run(KK_GATHER, 9.0 * sizeof(T) * m + 3 * RB * (double)m / np, stream, [&] {
+        launch_gather_kick<T>(hp[0] + o, hp[1] + o, hp[2] + o, hp[3] + o, hp[4] + o, hp[5] + o, m, rG[0], rG[1],
+                              rG[2], cp, k2, 0.0, 0, stream);
+      });
+      cudaStream_t cp_s = copy_streams[c % kCopyStreams];
+      DGP_CUDA(cudaEventRecord(chunk_ev[2][c], stream));
+      DGP_CUDA(cudaStreamWaitEvent(cp_s, chunk_ev[2][c], 0));
+      for (int i = 3; i < 6; ++i)
+        DGP_CUDA(cudaMemcpyAsync(src[i] + o, hp[i] + o, sizeof(T) * m, cudaMemcpyDeviceToHost, cp_s));
+    }
+    if (cudaGetLastError() != cudaSuccess) { finish_copies(); return DGP_E_CUDA; }
     for (int j = 0; j < kCopyStreams; ++j) DGP_CUDA(cudaStreamSynchronize(copy_streams[j]));
     DGP_CUDA(wait_stream());
     force_host = hpp->x;

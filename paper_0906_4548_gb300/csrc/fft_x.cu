@@ -623,6 +623,107 @@ __global__ void __launch_bounds__(XGeom<T, N>::THREADS, XGeom<T, N>::MIN_BLOCKS)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Hessian x pass for FP32 data with the spectrum in shared memory (N <= 256).
+//
+// The same work as k_fft_x's Hessian operation for one kz plane and TY ky columns, with the
+// x transforms done as in-place four-step stages on a [x][ky] tile in shared memory: the
+// forward transform leaves X[k1 + N1 k2] at row N2 k1 + k2 (digit order), and each output's
+// inverse reads that order back, forming the multiplier as it reads.  No thread holds the
+// spectrum in registers, so a thread needs about half the registers of the register-resident
+// version, and three CTAs fit on an SM instead of two (more warps to hide the latency of the
+// transposes and the stores).
+template <int N> struct XSGeom {
+  static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
+  static constexpr int TY = 16 < N ? 16 : N;
+  static constexpr int THREADS = TY * N1;
+  static constexpr int TILE = N * TY;  // complex
+  static constexpr size_t SMEM = sizeof(float2) * ((size_t)kTwiddleTables * N + 2 * (size_t)TILE);
+  static constexpr int MINB = THREADS <= 256 ? 3 : 1;
+};
+
+template <int N, int RB>
+__global__ void __launch_bounds__(XSGeom<N>::THREADS, XSGeom<N>::MINB)
+    k_x_hessian_smem(const __grid_constant__ XBatch<float, RB> xb, const float2* __restrict__ g_tw) {
+  using G = XSGeom<N>;
+  using V = float2;
+  constexpr int N1 = G::N1, N2 = G::N2, TY = G::TY;
+  const XArgs<float>& args = xb.a[RB > 1 ? blockIdx.z : 0];
+  if (args.skip && *args.skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* s_tw = reinterpret_cast<V*>(smem_raw);
+  V* A = s_tw + kTwiddleTables * N;  // the spectrum, rows in digit order
+  V* B = A + G::TILE;                // one output at a time
+  load_twiddles(s_tw, g_tw, N);
+  const int tid = threadIdx.x;
+  const int yl = tid % TY, q = tid / TY;  // q: j2 / n2 (stages 1 and 4) or k1 (stages 2 and 3)
+  const int kz = blockIdx.y, ky0 = blockIdx.x * TY, ky = ky0 + yl;
+  const int nz = kz == N / 2 ? -(N / 2) : kz;
+  const bool nyq_y = ky == N / 2, nyq_z = kz == N / 2;
+  const KParams& kp = args.kp;
+  const float fy = (float)signed_index(ky, N), fz = (float)nz;
+  const bool st14 = q < N2;  // stages over N1 points: TY x N2 tasks
+  __syncthreads();
+  // forward, stage 1: x = N2 j1 + j2 from global, transform over j1, twiddle, rows N2 k1 + j2
+  if (st14) {
+    const V* plane = args.in0 + (int64_t)kz * N * N;
+    V v[N1];
+#pragma unroll
+    for (int j1 = 0; j1 < N1; ++j1) v[j1] = plane[(int64_t)(N2 * j1 + q) * N + ky];
+    dft_regs<N1, N / N1>(v, s_tw);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) A[(N2 * k1 + q) * TY + yl] = k1 == 0 ? v[k1] : cmul(v[k1], s_tw[N + k1 * N2 + q]);
+  }
+  __syncthreads();
+  // forward, stage 2 (k1 = q): transform over j2; X[k1 + N1 k2] to row N2 k1 + k2, prescaled
+  {
+    V X[N2];
+#pragma unroll
+    for (int j2 = 0; j2 < N2; ++j2) X[j2] = A[(N2 * q + j2) * TY + yl];
+    dft_regs<N2, N / N2>(X, s_tw);
+    hessian_prescale<float, N>(X, q, fy, fz, kp.inv_m_f);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) A[(N2 * q + k2) * TY + yl] = X[k2];
+  }
+  __syncthreads();
+  const float ikf = kp.local_only ? 0.f : 1.f / kp.kbkf_f;
+#pragma unroll 1
+  for (int o = 0; o < 6; ++o) {
+    // inverse, stage 1 (k1 = q): multiplier as read, conj, transform over k2, twiddle
+    {
+      V X[N2], Y[N2];
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) X[k2] = A[(N2 * q + k2) * TY + yl];
+      hessian_output<float, N>(X, o, q, fy, fz, nyq_y, nyq_z, ikf, Y);
+      conj_regs(Y);
+      dft_regs<N2, N / N2>(Y, s_tw);
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) B[(N2 * q + n2) * TY + yl] = n2 == 0 ? Y[n2] : cmul(Y[n2], s_tw[N + q * N2 + n2]);
+    }
+    __syncthreads();
+    // inverse, stage 2 (n2 = q): transform over k1, conj, x = N2 n1 + n2 to global
+    if (st14) {
+      V w[N1];
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) w[k1] = B[(N2 * k1 + q) * TY + yl];
+      dft_regs<N1, N / N1>(w, s_tw);
+      V* plane = args.out.p[o] + (int64_t)kz * N * N;
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) plane[(int64_t)(N2 * n1 + q) * N + ky] = cconj(w[n1]);
+    }
+    __syncthreads();
+  }
+}
+
+template <int N, int RB>
+static void launch_xs(const XArgs<float>* a, int count, const float2* tw, cudaStream_t s) {
+  using G = XSGeom<N>;
+  raise_smem_limit<k_x_hessian_smem<N, RB>>(G::SMEM);
+  XBatch<float, RB> xb;
+  for (int r = 0; r < count; ++r) xb.a[r] = a[r];
+  k_x_hessian_smem<N, RB><<<dim3(N / G::TY, N / 2 + 1, count), G::THREADS, G::SMEM, s>>>(xb, tw);
+}
+
 template <typename T, int N> int x_pass_blocks() { return (N / XGeom<T, N>::TY) * (N / 2 + 1); }
 
 template <typename T, int N, int OP, int RB = 1>
@@ -639,6 +740,10 @@ static void launch_x(const XArgs<T>* a, int count, const vec2_t<T>* tw, cudaStre
   const size_t per_bin = PK ? sizeof(double) * NW * NBS : 0;
   const size_t smem = base + tables + per_bin * a[0].nbins;
   raise_smem_limit<k_fft_x<T, N, OP, RB>>(base + tables + per_bin * (N / 2));
+  if constexpr (OP == XOP_HESSIAN && sizeof(T) == 4 && N <= 256) {
+    launch_xs<N, RB>(a, count, tw, s);  // the shared-memory version of the same pass
+    return;
+  }
   XBatch<T, RB> xb;
   for (int r = 0; r < count; ++r) xb.a[r] = a[r];
   dim3 grid(N / G::TY, N / 2 + 1, count);

@@ -462,7 +462,7 @@ def run_adjoint(args):
             k = rng.integers(1, n // 4, 3)
             u = np.cos(2 * np.pi / box * (k[0] * xg[:, None, None] + k[1] * xg[None, :, None]
                                           + k[2] * xg[None, None, :]) + rng.uniform(0, 2 * np.pi))
-            e = (1e-4 if fd64 else 2e-3) * WA["rms"]
+            e = (args.fd_eps if args.fd_eps else (1e-4 if fd64 else 2e-3)) * WA["rms"]
             ut = torch.tensor(u, dtype=dl.dtype, device=dev)
             lp = float(loss(dl + e * ut, False)[0])
             lm = float(loss(dl - e * ut, False)[0])
@@ -497,6 +497,7 @@ def run_adjoint(args):
             "rc_gradient": {"adjoint": rc_grad, "central_difference": fd_rc, "h": h,
                             "rel_diff": abs(fd_rc - rc_grad) / max(abs(fd_rc), 1e-300)},
             "fd_check": {"modes": len(fd), "precision": "fp64, tol 1e-10" if fd64 else "fp32, tol 1e-6",
+                         "eps_over_rms": args.fd_eps if args.fd_eps else (1e-4 if fd64 else 2e-3),
                          "max_rel_diff": max(rel) if rel else None,
                          "median_rel_diff": float(np.median(rel)) if rel else None, "cases": fd}}
     print(json.dumps(line))
@@ -695,6 +696,9 @@ def main():
     ap.add_argument("--fd-modes", type=int, default=20, help="adjoint workload: central-difference checks")
     ap.add_argument("--adjoint-steps", type=int, default=0,
                     help="adjoint workload: run only the first K of the 100 steps (0: all)")
+    ap.add_argument("--fd-eps", type=float, default=0.0,
+                    help="adjoint workload: central-difference step in units of the field rms (0: 1e-4 in FP64, "
+                         "2e-3 in FP32)")
     ap.add_argument("--fd-precision", default="fp32", choices=["fp32", "fp64"],
                     help="adjoint workload: precision of the gradient and differences that are compared")
     ap.add_argument("--no-plain", action="store_true", help="batched workload: skip the one-by-one comparison")

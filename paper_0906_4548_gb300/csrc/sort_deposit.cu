@@ -138,9 +138,10 @@ void launch_cell_sort(const ParticleSet<T>& parts, int64_t np, CicParams cp, con
 
 // ---------------------------------------------------------------- deposit
 // One particle per lane.  Lanes whose keys are equal and adjacent (a cell's
-// particles, after a sort) form a segment: a segmented shuffle scan sums the
-// eight corner weights over the segment and its last lane issues the eight
-// global atomics.  A warp with no shared keys skips the scan.
+// particles, after a sort) form a segment, cut into pieces of at most 8 lanes: a
+// segmented shuffle scan sums the eight corner weights over each piece and its
+// last lane issues the eight global atomics.  A warp with no shared keys skips
+// the scan.
 template <typename T>
 __device__ __forceinline__ void deposit_warp_body(const T* __restrict__ x, const T* __restrict__ y,
                                                   const T* __restrict__ z, int64_t np, T* __restrict__ rho,
@@ -173,12 +174,16 @@ __device__ __forceinline__ void deposit_warp_body(const T* __restrict__ x, const
     w[6] = fx * f[1] * gz;
     w[7] = fx * f[1] * f[2];
     const int prev = __shfl_up_sync(full, key, 1);
-    const unsigned heads = __ballot_sync(full, lane == 0 || prev != key);
+    unsigned heads = __ballot_sync(full, lane == 0 || prev != key);
     if (heads != full) {
+      // segments of more than 8 lanes are cut into pieces of 8 (each piece issues its own
+      // reductions), so three doubling rounds sum every piece
       const int seg_start = 31 - __clz(heads & (full >> (31 - lane)));
+      heads = __ballot_sync(full, ((lane - seg_start) & 7) == 0);
+      const int piece_start = 31 - __clz(heads & (full >> (31 - lane)));
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const bool take = lane - o >= seg_start;
+      for (int o = 1; o < 8; o <<= 1) {
+        const bool take = lane - o >= piece_start;
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
           const T v = __shfl_up_sync(full, w[t], o);

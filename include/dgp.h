@@ -132,9 +132,14 @@ typedef struct {
  * Returns DGP_E_INVALID for a <= 0, rc_H0 <= 0, omega_m0 < 0 or out == NULL. */
 int dgp_background(const dgp_cosmology *cosmo, double rc_H0, double a, dgp_background_t *out);
 
-/* Create a context: validates p, allocates all device workspace for an n^3
- * mesh, and binds cuda_stream (a cudaStream_t, may be NULL).  *out is set
- * to NULL on failure.  n must be one of the sizes listed in dgp_params. */
+/* Create a context for the problem of Sec. III: a periodic box of side p->box
+ * (Mpc/h) with an n^3 mesh (Sec. III.A: mesh points at i box / n), the DGP
+ * crossover scale p->rc_H0 and the cosmology of Sec. II (Omega_m0, c / H0).
+ * Validates p, allocates all device workspace for the mesh (the fields of
+ * Eqs. FullDGP1-2, the spectra of the relaxation, the warm-start iterates of
+ * Sec. III.B), and binds cuda_stream (a cudaStream_t, may be NULL).  *out is
+ * set to NULL on failure: DGP_E_INVALID for bad parameters (n must be one of
+ * the sizes listed in dgp_params), DGP_E_NOMEM or DGP_E_CUDA. */
 int dgp_init(dgp_ctx **out, const dgp_params *p, const dgp_cosmology *cosmo, void *cuda_stream);
 
 /* Free everything the context owns.  NULL is accepted. */

@@ -1013,7 +1013,9 @@ class Engine : public EngineBase {
                           (float)time_integral(a[r], ah, om, rcH, 0), (float)time_integral(a[r], a1[r], om, rcH, 2), 1};
         k2[r] = time_integral(ah, a1[r], om, rcH, 0);
       }
-      launch_gather_kick_batch(g, count, stream);
+      double gb = 0.0;  // gather bytes of the class (positions and momenta, the three force meshes)
+      for (int r = 0; r < count; ++r) gb += 12.0 * sizeof(T) * parts[r].n + 3 * RB;
+      prof.run(KK_GATHER, gb, stream, [&] { launch_gather_kick_batch(g, count, stream); });
       DGP_CHECK_LAUNCH();
       for (int r = 0; r < count; ++r) {
         Engine* e = E[r];
@@ -1027,7 +1029,9 @@ class Engine : public EngineBase {
         g[r].drift = 0.f;
         g[r].do_drift = 0;
       }
-      launch_gather_kick_batch(g, count, stream);
+      double gb2 = 0.0;
+      for (int r = 0; r < count; ++r) gb2 += 9.0 * sizeof(T) * parts[r].n + 3 * RB;
+      prof.run(KK_GATHER, gb2, stream, [&] { launch_gather_kick_batch(g, count, stream); });
       DGP_CHECK_LAUNCH();
       return DGP_OK;
     }
@@ -1047,8 +1051,11 @@ class Engine : public EngineBase {
       rho[k] = (float*)e->rRho;
       dep[k] = DepositArgs<T>{(const T*)pp->x, (const T*)pp->y, (const T*)pp->z, pp->n, e->rRho, e->cic()};
     }
-    launch_zero_batch(rho, M, n, s);
-    launch_cic_deposit_batch<T>(dep, n, s);
+    Profiler& pf = E[0]->prof;  // the class's kernels are accounted on its first member
+    double db = 0.0;
+    for (int k = 0; k < n; ++k) db += 3.0 * sizeof(T) * parts[sub[k]].n + RB;
+    pf.run(KK_MISC, n * RB, s, [&] { launch_zero_batch(rho, M, n, s); });
+    pf.run(KK_DEPOSIT, db, s, [&] { launch_cic_deposit_batch<T>(dep, n, s); });
     if (cudaGetLastError() != cudaSuccess) return DGP_E_CUDA;
     const int rc = class_solve(E, sub, a, info);
     if (rc != DGP_OK && rc != DGP_E_NOT_CONVERGED) return rc;
@@ -1064,7 +1071,7 @@ class Engine : public EngineBase {
 
   // Batched one-field sums of field(k) into out(k).
   template <class FA, class FO>
-  static void class_sum(std::vector<Engine*>& S, bool absval, FA field, FO out) {
+  static void class_sum(Profiler& pf, std::vector<Engine*>& S, bool absval, FA field, FO out) {
     const int n = (int)S.size();
     const float* src[kBatchMax];
     double* parts[kBatchMax];
@@ -1074,7 +1081,8 @@ class Engine : public EngineBase {
       parts[k] = S[k]->partials;
       dst[k] = out(k);
     }
-    launch_sum_batch(src, M, absval, parts, S[0]->nblocks, dst, n, S[0]->stream);
+    pf.run(KK_REDUCE, n * RB, S[0]->stream,
+           [&] { launch_sum_batch(src, M, absval, parts, S[0]->nblocks, dst, n, S[0]->stream); });
   }
 
   // The field solve of solve_impl (nonlinear mode, from a CIC mass mesh) for the members in sub.
@@ -1099,8 +1107,10 @@ class Engine : public EngineBase {
       e->last_nl_a = a[sub[k]];
     }
     auto check = [] { return cudaGetLastError() == cudaSuccess ? DGP_OK : DGP_E_CUDA; };
+    Profiler& pf = E[0]->prof;  // the class's kernels are accounted on its first member
+    const double nS = n * SB, nR = n * RB;
     // density contrast from the mass mesh, its z and y transforms
-    class_sum(S, false, [&](int k) { return S[k]->rRho; }, [&](int k) { return S[k]->d_misc + 0; });
+    class_sum(pf, S, false, [&](int k) { return S[k]->rRho; }, [&](int k) { return S[k]->d_misc + 0; });
     {
       const float* in[kBatchMax];
       V* out[kBatchMax];
@@ -1112,8 +1122,8 @@ class Engine : public EngineBase {
         pro[k] = ZPrologue{S[k]->d_misc + 0, 1.0 / (double)M, 1};
         f[k] = fs(&S[k]->sDelta, 1);
       }
-      launch_fft_z_r2c_batch<T, N>(in, out, pro, n, tw, st);
-      launch_fft_y_batch<T, N>(f, nullptr, nullptr, n, 1, false, tw, st, yt);
+      pf.run(KK_Z_R2C, nR + nS, st, [&] { launch_fft_z_r2c_batch<T, N>(in, out, pro, n, tw, st); });
+      pf.run(KK_Y, 2 * nS, st, [&] { launch_fft_y_batch<T, N>(f, nullptr, nullptr, n, 1, false, tw, st, yt); });
     }
     // source S; the linear start D_lin for members without a warm start
     for (int lin = 0; lin < 2; ++lin) {
@@ -1131,12 +1141,14 @@ class Engine : public EngineBase {
         ++m;
       }
       if (!m) continue;
-      launch_fft_x_batch<T, N>(lin ? XOP_SOURCE_LIN : XOP_SOURCE, xr, m, tw, st);
-      launch_fft_y_batch<T, N>(fi, nullptr, nullptr, m, lin ? 2 : 1, true, tw, st, yt);
-      launch_fft_z_c2r_batch<T, N>(fi, fo, lin ? 2 : 1, m, tw, st);
+      const double nf = m * (lin ? 2 : 1);
+      pf.run(KK_X_OTHER, m * SB + nf * SB, st,
+             [&] { launch_fft_x_batch<T, N>(lin ? XOP_SOURCE_LIN : XOP_SOURCE, xr, m, tw, st); });
+      pf.run(KK_Y, 2 * nf * SB, st, [&] { launch_fft_y_batch<T, N>(fi, nullptr, nullptr, m, lin ? 2 : 1, true, tw, st, yt); });
+      pf.run(KK_Z_C2R, nf * (SB + RB), st, [&] { launch_fft_z_c2r_batch<T, N>(fi, fo, lin ? 2 : 1, m, tw, st); });
     }
     // eps = <|S|> (read by the controller at the first iteration); the mean of D_lin
-    class_sum(S, true, [&](int k) { return S[k]->rS; }, [&](int k) { return S[k]->d_misc + 1; });
+    class_sum(pf, S, true, [&](int k) { return S[k]->rS; }, [&](int k) { return S[k]->d_misc + 1; });
     {
       std::vector<Engine*> L;
       std::vector<int> lk;
@@ -1146,7 +1158,7 @@ class Engine : public EngineBase {
           lk.push_back(k);
         }
       if (!L.empty())
-        class_sum(L, false, [&](int i) { return L[i]->rD[0]; }, [&](int i) { return L[i]->d_rstats + 1; });
+        class_sum(pf, L, false, [&](int i) { return L[i]->rD[0]; }, [&](int i) { return L[i]->d_rstats + 1; });
     }
     for (int k = 0; k < n; ++k) {
       int q = 0;
@@ -1175,8 +1187,8 @@ class Engine : public EngineBase {
         pro[k] = ZPrologue{nullptr, 0.0, 0};
         f[k] = fs(&S[k]->sD, 1);
       }
-      launch_fft_z_r2c_batch<T, N>(in, out, pro, n, tw, st);
-      if (!plane) launch_fft_y_batch<T, N>(f, nullptr, nullptr, n, 1, false, tw, st, yt);
+      pf.run(KK_Z_R2C, nR + nS, st, [&] { launch_fft_z_r2c_batch<T, N>(in, out, pro, n, tw, st); });
+      if (!plane) pf.run(KK_Y, 2 * nS, st, [&] { launch_fft_y_batch<T, N>(f, nullptr, nullptr, n, 1, false, tw, st, yt); });
     }
     for (int k = 0; k < n; ++k)
       if (cudaMemsetAsync(S[k]->d_ctl, 0, sizeof(SolveCtl), st) != cudaSuccess) return DGP_E_CUDA;
@@ -1218,47 +1230,54 @@ class Engine : public EngineBase {
       if (plane) {
         PlaneArgs pa[kBatchMax];
         for (int i = 0; i < m; ++i) pa[i] = PlaneArgs{spec_in(ks[i], it), f6[i], kp[ks[i]], sk[i]};
-        launch_plane_hessian_batch(N, pa, m, tw, st);
-        launch_relax_tma_batch<N>(e0->arith_mode(), ra, m, tw, st);
+        pf.run(KK_X_HESSIAN, 7.0 * m * SB, st, [&] { launch_plane_hessian_batch(N, pa, m, tw, st); });
+        pf.run(KK_RELAX, m * (7 * SB + 3 * RB), st, [&] { launch_relax_tma_batch<N>(e0->arith_mode(), ra, m, tw, st); });
         if (control) {
-          launch_control_batch(yc, sk, m, st);
+          pf.run(KK_REDUCE, 32.0 * m * e0->fblocks, st, [&] { launch_control_batch(yc, sk, m, st); });
         } else {
           for (int i = 0; i < m; ++i) {
             Engine* e = S[ks[i]];
-            launch_finalize(e->partials, e->fblocks, 4, e->d_rstats + 4 * out_buf(ks[i], it), st, nullptr);
+            pf.run(KK_REDUCE, 32.0 * e->fblocks, st, [&] {
+              launch_finalize(e->partials, e->fblocks, 4, e->d_rstats + 4 * out_buf(ks[i], it), st, nullptr);
+            });
           }
         }
         return check();
       }
       if (e0->xy_ok && e0->xy_on) {
-        launch_xy_hessian_batch<T, N>(xr, m, tw, st);
+        pf.run(KK_X_HESSIAN, 7.0 * m * SB, st, [&] { launch_xy_hessian_batch<T, N>(xr, m, tw, st); });
       } else {
-        launch_fft_x_batch<T, N>(XOP_HESSIAN, xr, m, tw, st);
-        launch_fft_y_batch<T, N>(f6, sk, nullptr, m, 6, true, tw, st, yt);
+        pf.run(KK_X_HESSIAN, 7.0 * m * SB, st, [&] { launch_fft_x_batch<T, N>(XOP_HESSIAN, xr, m, tw, st); });
+        pf.run(KK_Y, 12.0 * m * SB, st, [&] { launch_fft_y_batch<T, N>(f6, sk, nullptr, m, 6, true, tw, st, yt); });
       }
-      launch_relax_tma_batch<N>(e0->arith_mode(), ra, m, tw, st);
+      pf.run(KK_RELAX, m * (7 * SB + 3 * RB), st, [&] { launch_relax_tma_batch<N>(e0->arith_mode(), ra, m, tw, st); });
       if (control) {
-        launch_fft_y_batch<T, N>(f1, sk, yc, m, 1, false, tw, st, yt);
+        pf.run(KK_Y, 2.0 * m * SB, st, [&] { launch_fft_y_batch<T, N>(f1, sk, yc, m, 1, false, tw, st, yt); });
       } else {
         for (int i = 0; i < m; ++i) {
           Engine* e = S[ks[i]];
-          launch_finalize(e->partials, e->fblocks, 4, e->d_rstats + 4 * out_buf(ks[i], it), st, nullptr);
+          pf.run(KK_REDUCE, 32.0 * e->fblocks, st, [&] {
+            launch_finalize(e->partials, e->fblocks, 4, e->d_rstats + 4 * out_buf(ks[i], it), st, nullptr);
+          });
         }
-        launch_fft_y_batch<T, N>(f1, sk, nullptr, m, 1, false, tw, st, yt);
+        pf.run(KK_Y, 2.0 * m * SB, st, [&] { launch_fft_y_batch<T, N>(f1, sk, nullptr, m, 1, false, tw, st, yt); });
       }
       return check();
     };
     std::vector<int> everyone(n);
     for (int k = 0; k < n; ++k) everyone[k] = k;
     // iterations 1 and 2 as one graph for the class (buffers alternate with period two)
-    bool graphs = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
+    bool graphs = (pf.timing == 0 || pf.sampled) && st != nullptr && st != cudaStreamLegacy &&
+                  st != cudaStreamPerThread;
     if (graphs) {
       cudaGraph_t g = nullptr;
       if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
         cudaGetLastError();
         graphs = false;
       } else {
+        pf.capturing = true;
         const int r1 = enqueue(1, true, everyone), r2 = r1 ? r1 : enqueue(2, true, everyone);
+        pf.capturing = false;
         const cudaError_t ce = cudaStreamEndCapture(st, &g);
         cudaGraphExec_t& ex = e0->class_exec;
         if (r1 || r2 || ce != cudaSuccess || !g) {
@@ -1332,7 +1351,7 @@ class Engine : public EngineBase {
         sDphi[k] = spec_in(k, s_it);
         if (plane) {  // the accepted iterate's spectrum is transformed along z only
           V* f1[1] = {sDphi[k]};
-          launch_fft_y<T, N>(fs(f1, 1), 1, false, tw, st, nullptr, yt);
+          pf.run(KK_Y, 2 * SB, st, [&] { launch_fft_y<T, N>(fs(f1, 1), 1, false, tw, st, nullptr, yt); });
         }
       } else {
         // an earlier iterate: replay the iterations that produced it for this member alone
@@ -1382,9 +1401,9 @@ class Engine : public EngineBase {
         T* outs[3] = {e->rG[0], e->rG[1], e->rG[2]};
         for (int i = 0; i < kMaxFields; ++i) fo[k].p[i] = i < 3 ? reinterpret_cast<V*>(outs[i]) : nullptr;
       }
-      launch_fft_x_batch<T, N>(XOP_PHI_FORCE, xr, n, tw, st);
-      launch_fft_y_batch<T, N>(fi, nullptr, nullptr, n, 3, true, tw, st, yt);
-      launch_fft_z_c2r_batch<T, N>(fi, fo, 3, n, tw, st);
+      pf.run(KK_X_OTHER, 5.0 * nS, st, [&] { launch_fft_x_batch<T, N>(XOP_PHI_FORCE, xr, n, tw, st); });
+      pf.run(KK_Y, 6.0 * nS, st, [&] { launch_fft_y_batch<T, N>(fi, nullptr, nullptr, n, 3, true, tw, st, yt); });
+      pf.run(KK_Z_C2R, 3.0 * (nS + nR), st, [&] { launch_fft_z_c2r_batch<T, N>(fi, fo, 3, n, tw, st); });
     }
     if ((rc = check())) return rc;
     if (info && e0->wait_stream() != cudaSuccess) return DGP_E_CUDA;

@@ -28,8 +28,8 @@ template <int N> struct PGeom {
   static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2;
   static constexpr int PITCH = N + 1;
   static constexpr int PLANE = N * PITCH;  // complex elements of one plane buffer
-  static constexpr int THREADS = N == 96 ? 768 : N == 64 ? 256 : N == 48 ? 256 : N == 32 ? 128 : 64;
-  static constexpr int MINB = N == 96 ? 1 : N == 64 ? 2 : N == 48 ? 3 : N == 32 ? 4 : 8;
+  static constexpr int THREADS = N == 96 ? 768 : N == 64 ? 256 : N == 48 ? 192 : N == 32 ? 128 : 64;
+  static constexpr int MINB = N == 96 ? 1 : N == 64 ? 2 : N == 48 ? 4 : N == 32 ? 4 : 8;
   static constexpr size_t SMEM = sizeof(float2) * ((size_t)2 * PLANE + (size_t)kTwiddleTables * N);
   static_assert(N % 16 == 0 || N < 16, "lines of a stage are taken 16 at a time");
 };
@@ -115,6 +115,27 @@ template <int RB> struct PlaneBatch {
   PlaneArgs a[RB];
 };
 
+// Plane <-> shared-memory copies (row pitch PITCH): TY rows of N at a time when the CTA's
+// threads divide into whole rows, so no thread divides its index by N per element.
+template <int N, bool TO_SMEM>
+__device__ __forceinline__ void copy_plane(float2* __restrict__ sm, float2* __restrict__ g) {
+  using G = PGeom<N>;
+  if constexpr (G::THREADS % N == 0) {
+    constexpr int RPI = G::THREADS / N;  // rows per round
+    const int col = threadIdx.x % N, r0 = threadIdx.x / N;
+#pragma unroll 4
+    for (int r = r0; r < N; r += RPI) {
+      if (TO_SMEM) sm[r * G::PITCH + col] = g[r * N + col];
+      else g[r * N + col] = sm[r * G::PITCH + col];
+    }
+  } else {
+    for (int i = threadIdx.x; i < N * N; i += G::THREADS) {
+      if (TO_SMEM) sm[(i / N) * G::PITCH + i % N] = g[i];
+      else g[i] = sm[(i / N) * G::PITCH + i % N];
+    }
+  }
+}
+
 template <int N, int RB>
 __global__ void __launch_bounds__(PGeom<N>::THREADS, PGeom<N>::MINB)
     k_plane_hessian(const __grid_constant__ PlaneBatch<RB> pb, const float2* __restrict__ g_tw) {
@@ -128,8 +149,7 @@ __global__ void __launch_bounds__(PGeom<N>::THREADS, PGeom<N>::MINB)
   float2* s_tw = B + G::PLANE;
   load_twiddles(s_tw, g_tw, N);
   const int kz = blockIdx.x;
-  const float2* __restrict__ src = args.in + (int64_t)kz * N * N;
-  for (int i = threadIdx.x; i < N * N; i += G::THREADS) A[(i / N) * PITCH + i % N] = src[i];
+  copy_plane<N, true>(A, const_cast<float2*>(args.in) + (int64_t)kz * N * N);
   __syncthreads();
   // forward along y (lines = rows x), then along x (lines = columns)
   fwd_stage1<N, PITCH, 1>(A, s_tw);
@@ -186,8 +206,7 @@ __global__ void __launch_bounds__(PGeom<N>::THREADS, PGeom<N>::MINB)
     __syncthreads();
     inv_stage2<N, PITCH, 1, true>(B, s_tw);
     __syncthreads();
-    float2* __restrict__ dst = args.out.p[o] + (int64_t)kz * N * N;
-    for (int i = threadIdx.x; i < N * N; i += G::THREADS) dst[i] = B[(i / N) * PITCH + i % N];
+    copy_plane<N, false>(B, args.out.p[o] + (int64_t)kz * N * N);
     __syncthreads();
   }
 }

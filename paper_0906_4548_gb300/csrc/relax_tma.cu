@@ -215,17 +215,26 @@ template <int N> struct RGeom {
   static constexpr int ROWB = TY * 8;                     // bytes of one kz row of a tile
   static constexpr int BSTRIDE = align1k(BOXK * ROWB);    // each box starts on a swizzle period
   static constexpr int FIELD = NBOX * BSTRIDE;            // one spectrum's tile
-  static constexpr int TSZ = TY * N1 * (N2 + 1) * 8;      // four-step transpose of a pair
-  static constexpr int BUF0 = cmax(2 * FIELD, TSZ);
+  // row stride of the four-step transpose (complex): N1 (N2 + 1), padded when N2 < N1 so that
+  // it is N2 mod 16 and the rows a half-warp writes in the packed first stage (N2 columns
+  // each) fall on different banks
+  static constexpr int RS0 = N1 * (N2 + 1);
+  static constexpr int RS = N2 < N1 ? RS0 + ((N2 - RS0 % 16) % 16 + 16) % 16 : RS0;
+  static constexpr int TSZ = TY * RS * 8;                 // four-step transpose of a pair
+  // the second buffer receives TMA tiles with the 128-byte swizzle: it starts on 1024 bytes
+  static constexpr int BUF0 = align1k(cmax(2 * FIELD, TSZ));
   static constexpr int ROWP = N + 16;                     // padded real row (floats)
   static constexpr int P = TY / 2;                        // row pairs of the forward transform
-  static constexpr int BUF1 = cmax(cmax(2 * FIELD, 2 * TY * ROWP * 4), N * (P + 1) * 8);
+  // tiles of a pair, then their transpose; the D and S rows; the forward spectrum of D_new
+  static constexpr int BUF1 = cmax(cmax(cmax(2 * FIELD, TSZ), 2 * TY * ROWP * 4), N * (P + 1) * 8);
   static constexpr int TW = N * 8;                        // the phase table W_N^{j2 k1}
   static constexpr int EXTRA = 64 + 4 * 32 * 8 + 32;      // mbarriers, warp partials, the mean
   static constexpr size_t SMEM = 1024 + BUF0 + BUF1 + TW + EXTRA;
   static constexpr int MINB = THREADS <= 256 ? 3 : 1;
   static_assert(2 * ROWB == 256 && TY * 8 == 128, "a tile row is one 128-byte swizzle row");
-  static_assert(P * N1 * (N2 + 1) * 8 <= BUF0, "forward transpose fits the first buffer");
+  static_assert(P * RS * 8 <= BUF0, "forward transpose fits the first buffer");
+  static_assert(BUF0 % 1024 == 0 && BSTRIDE % 1024 == 0, "TMA tiles start on 1024-byte boundaries");
+  static_assert(TSZ <= BUF0 && TSZ <= BUF1, "a pair's transpose fits the buffer that held its tiles");
 };
 
 // byte offset of complex (kz, y) in a swizzled tile (relative to a 1024-aligned base)
@@ -300,13 +309,13 @@ __device__ __forceinline__ void pair_inverse(unsigned char* buf, const float2* s
   }
   __syncthreads();  // the tile is read: its bytes become the transpose buffer
   if (act1) {
-    float2* T1 = reinterpret_cast<float2*>(buf) + r1 * (N1 * (N2 + 1));
+    float2* T1 = reinterpret_cast<float2*>(buf) + r1 * G::RS;
     dft_regs<N1, N / N1>(v, s_tw);
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) T1[k1 * (N2 + 1) + c1] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[k1 * N2 + c1]);
   }
   __syncthreads();
-  const float2* Tp = reinterpret_cast<const float2*>(buf) + row * (N1 * (N2 + 1));
+  const float2* Tp = reinterpret_cast<const float2*>(buf) + row * G::RS;
   float2 u[N2];
 #pragma unroll
   for (int j2 = 0; j2 < N2; ++j2) u[j2] = Tp[lane * (N2 + 1) + j2];
@@ -453,10 +462,10 @@ __global__ void __launch_bounds__(RGeom<N>::THREADS, RGeom<N>::MINB)
   {
     constexpr int FT = P * N1;
     const int fl = tid % N1, fp = tid / N1;
-    float2* Tp = reinterpret_cast<float2*>(buf0) + fp * (N1 * (N2 + 1));
+    float2* Tp = reinterpret_cast<float2*>(buf0) + fp * G::RS;
     if (tid < P * N2) {  // first stage: P x N2 tasks on the first threads
       const int q1 = tid / N2, l1 = tid % N2;
-      float2* T1 = reinterpret_cast<float2*>(buf0) + q1 * (N1 * (N2 + 1));
+      float2* T1 = reinterpret_cast<float2*>(buf0) + q1 * G::RS;
       float2 v[N1];
 #pragma unroll
       for (int j1 = 0; j1 < N1; ++j1) {

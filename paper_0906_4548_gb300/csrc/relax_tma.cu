@@ -262,59 +262,65 @@ __device__ __forceinline__ void issue_spectra(unsigned char* dst, const CUtensor
 // over all k from the half spectra (imaginary parts of k = 0 and N/2 dropped).
 // Thread (row, lane) ends with A (ra) and B (rb) of its row at z = lane + N1 k2.
 // The transpose reuses buf, so every thread reads its tile values first.
+//
+// Stage one (pair_load, pair_stage1) has TY x N2 tasks (a row r1 and one of its N2 columns c1);
+// stage two (pair_stage2) has TY x N1 (a row and lane k1).
+
+// stage one's reads: v[j1] = conj(Z) at k = N2 j1 + c1 of row r1
 template <int N>
-__device__ __forceinline__ void pair_inverse(unsigned char* buf, const float2* s_tw, int row, int lane,
-                                             float (&ra)[Split<N>::N2], float (&rb)[Split<N>::N2]) {
+__device__ __forceinline__ void pair_load(const unsigned char* buf, int r1, int c1, float2 (&v)[Split<N>::N1]) {
   using G = RGeom<N>;
   constexpr int N1 = G::N1, N2 = G::N2;
   const unsigned char* TA = buf;
   const unsigned char* TB = buf + G::FIELD;
-  // The first stage has TY x N2 tasks (a row and one of its N2 columns j2) for TY x N1
-  // threads: they go to the first TY x N2 threads, so that when N2 < N1 whole warps
-  // idle instead of every warp running with lanes masked off.
-  constexpr bool PACK = N2 < N1;
-  const int t1 = threadIdx.x;
-  const bool act1 = !PACK || t1 < G::TY * N2;
-  const int r1 = PACK ? t1 / N2 : row, c1 = PACK ? t1 % N2 : lane;
   // With N2 a multiple of 8 and one box, row kk of a read satisfies kk = +-c1 (mod 8) for
   // every j1, so the swizzle term is one constant per thread and direction.
   constexpr bool HOIST = N2 % 8 == 0 && G::NBOX == 1;
   const unsigned off_d = (unsigned)c1 * G::ROWB + (((unsigned)r1 * 8u) ^ (((unsigned)c1 & 7u) << 4));
   const unsigned off_m = (unsigned)(N - c1) * G::ROWB + (((unsigned)r1 * 8u) ^ (((unsigned)(N - c1) & 7u) << 4));
-  float2 v[N1];
-  if (act1) {
 #pragma unroll
-    for (int j1 = 0; j1 < N1; ++j1) {
-      const int k = N2 * j1 + c1;
-      float2 A, B;
-      bool mirror;
-      if (N2 * j1 + N2 - 1 < N / 2) mirror = false;  // j1 is a compile-time index
-      else if (N2 * j1 > N / 2) mirror = true;
-      else mirror = k > N / 2;
-      const int kk = mirror ? N - k : k;
-      unsigned off;
-      if constexpr (HOIST) off = mirror ? off_m - (unsigned)(N2 * j1 * G::ROWB) : off_d + (unsigned)(N2 * j1 * G::ROWB);
-      else off = tile_off<N>(kk, r1);
-      A = *reinterpret_cast<const float2*>(TA + off);
-      B = *reinterpret_cast<const float2*>(TB + off);
-      if (mirror) {
-        A.y = -A.y;
-        B.y = -B.y;
-      } else if (kk == 0 || kk == N / 2) {
-        A.y = 0.f;
-        B.y = 0.f;
-      }
-      v[j1] = make_float2(A.x - B.y, -(A.y + B.x));  // conj(A + i B)
+  for (int j1 = 0; j1 < N1; ++j1) {
+    const int k = N2 * j1 + c1;
+    float2 A, B;
+    bool mirror;
+    if (N2 * j1 + N2 - 1 < N / 2) mirror = false;  // j1 is a compile-time index
+    else if (N2 * j1 > N / 2) mirror = true;
+    else mirror = k > N / 2;
+    const int kk = mirror ? N - k : k;
+    unsigned off;
+    if constexpr (HOIST) off = mirror ? off_m - (unsigned)(N2 * j1 * G::ROWB) : off_d + (unsigned)(N2 * j1 * G::ROWB);
+    else off = tile_off<N>(kk, r1);
+    A = *reinterpret_cast<const float2*>(TA + off);
+    B = *reinterpret_cast<const float2*>(TB + off);
+    if (mirror) {
+      A.y = -A.y;
+      B.y = -B.y;
+    } else if (kk == 0 || kk == N / 2) {
+      A.y = 0.f;
+      B.y = 0.f;
     }
+    v[j1] = make_float2(A.x - B.y, -(A.y + B.x));  // conj(A + i B)
   }
-  __syncthreads();  // the tile is read: its bytes become the transpose buffer
-  if (act1) {
-    float2* T1 = reinterpret_cast<float2*>(buf) + r1 * G::RS;
-    dft_regs<N1, N / N1>(v, s_tw);
+}
+
+// stage one's transform over j1 and its twiddled transpose into buf (row r1, column c1)
+template <int N>
+__device__ __forceinline__ void pair_stage1(unsigned char* buf, const float2* s_tw, int r1, int c1,
+                                            float2 (&v)[Split<N>::N1]) {
+  using G = RGeom<N>;
+  constexpr int N1 = G::N1, N2 = G::N2;
+  float2* T1 = reinterpret_cast<float2*>(buf) + r1 * G::RS;
+  dft_regs<N1, N / N1>(v, s_tw);
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) T1[k1 * (N2 + 1) + c1] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[k1 * N2 + c1]);
-  }
-  __syncthreads();
+  for (int k1 = 0; k1 < N1; ++k1) T1[k1 * (N2 + 1) + c1] = (k1 == 0) ? v[k1] : cmul(v[k1], s_tw[k1 * N2 + c1]);
+}
+
+// stage two: transform over j2 of (row, lane), A and B at z = lane + N1 k2
+template <int N>
+__device__ __forceinline__ void pair_stage2(const unsigned char* buf, const float2* s_tw, int row, int lane,
+                                            float (&ra)[Split<N>::N2], float (&rb)[Split<N>::N2]) {
+  using G = RGeom<N>;
+  constexpr int N2 = G::N2;
   const float2* Tp = reinterpret_cast<const float2*>(buf) + row * G::RS;
   float2 u[N2];
 #pragma unroll
@@ -325,6 +331,48 @@ __device__ __forceinline__ void pair_inverse(unsigned char* buf, const float2* s
     ra[k2] = u[k2].x;
     rb[k2] = -u[k2].y;
   }
+}
+
+template <int N>
+__device__ __forceinline__ void pair_inverse(unsigned char* buf, const float2* s_tw, int row, int lane,
+                                             float (&ra)[Split<N>::N2], float (&rb)[Split<N>::N2]) {
+  using G = RGeom<N>;
+  constexpr int N1 = G::N1, N2 = G::N2;
+  // When N2 < N1 stage one's tasks go to the first TY x N2 threads, so that whole warps
+  // idle instead of every warp running with lanes masked off.
+  constexpr bool PACK = N2 < N1;
+  const int t1 = threadIdx.x;
+  const bool act1 = !PACK || t1 < G::TY * N2;
+  const int r1 = PACK ? t1 / N2 : row, c1 = PACK ? t1 % N2 : lane;
+  float2 v[N1];
+  if (act1) pair_load<N>(buf, r1, c1, v);
+  __syncthreads();  // the tile is read: its bytes become the transpose buffer
+  if (act1) pair_stage1<N>(buf, s_tw, r1, c1, v);
+  __syncthreads();
+  pair_stage2<N>(buf, s_tw, row, lane, ra, rb);
+}
+
+// Two pairs at once (tiles in bufA and bufB) when N2 < N1: stage one of both on the first
+// 2 x TY x N2 threads, then stage two of each on every thread.
+template <int N>
+__device__ __forceinline__ void pair2_inverse(unsigned char* bufA, unsigned char* bufB, const float2* s_tw, int row,
+                                              int lane, float (&ra)[Split<N>::N2], float (&rb)[Split<N>::N2],
+                                              float (&ra2)[Split<N>::N2], float (&rb2)[Split<N>::N2]) {
+  using G = RGeom<N>;
+  constexpr int N1 = G::N1, N2 = G::N2, TN = G::TY * N2;
+  const int t = threadIdx.x;
+  const bool act1 = t < 2 * TN;
+  const int sel = t >= TN ? 1 : 0;
+  const int t1 = t - sel * TN;
+  const int r1 = t1 / N2, c1 = t1 % N2;
+  unsigned char* buf = sel ? bufB : bufA;
+  float2 v[N1];
+  if (act1) pair_load<N>(buf, r1, c1, v);
+  __syncthreads();  // both tiles are read
+  if (act1) pair_stage1<N>(buf, s_tw, r1, c1, v);
+  __syncthreads();
+  pair_stage2<N>(bufA, s_tw, row, lane, ra, rb);
+  pair_stage2<N>(bufB, s_tw, row, lane, ra2, rb2);
 }
 
 template <int N, class AR, int RB>
@@ -383,11 +431,52 @@ __global__ void __launch_bounds__(RGeom<N>::THREADS, RGeom<N>::MINB)
   float ra[N2], rb[N2];
   float* sD = reinterpret_cast<float*>(buf1);
   float* sS = sD + TY * ROWP;
-  // pairs A = (H_xy, H_xz) from buf0, B = (H_yz, N) from buf1, C = (H_xx, H_yy) from buf0 again;
-  // one barrier per pair: after it every thread is done with the previous pair's buffer, which
-  // then receives its next copy (C after A, the D and S rows after B)
+  // pairs A = (H_xy, H_xz) from buf0, B = (H_yz, N) from buf1, C = (H_xx, H_yy) from buf0 again.
+  // When N2 < N1 and stage one of two pairs fits the CTA's threads, A and B are transformed
+  // together and C and the D and S rows are issued once both buffers are read.
+  constexpr bool PACK2 = N2 < N1 && 2 * TY * N2 <= G::THREADS;
+  if constexpr (PACK2) {
+    const bool ok0 = mbar_wait_bounded(&bars[0], 0u, lim);
+    const bool ok = ok0 && mbar_wait_bounded(&bars[1], 0u, lim);
+    if (__syncthreads_or(!ok)) {
+      give_up();
+      return;
+    }
+    done0 = 1;
+    done1 = 1;
+    float ra2[N2], rb2[N2];
+    pair2_inverse<N>(buf0, buf1, s_tw, row, lane, ra, rb, ra2, rb2);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+      AR::pair_a(r[k2], ra[k2], rb[k2]);
+      AR::pair_b(r[k2], ra2[k2], rb2[k2], rp);
+    }
+    fence_proxy_async();  // this thread's accesses to both buffers precede the copies into them
+    __syncthreads();
+    if (tid == 0) issue_spectra<N>(buf0, &args.map[0], &args.map[1], x, y0, &bars[0]);
+    issued0 = 2;
+    if (tid < 32) {
+      if (tid == 0) mbar_expect_tx(&bars[1], 2u * TY * N * 4);
+      __syncwarp();
+      const int64_t rbase0 = ((int64_t)x * N + y0) * N;
+      for (int i = tid; i < 2 * TY; i += 32) {
+        const int rr = i % TY;
+        const float* src = (i < TY ? args.D : args.S) + rbase0 + (int64_t)rr * N;
+        bulk_load((i < TY ? sD : sS) + rr * ROWP, src, N * 4, &bars[1]);
+      }
+    }
+    issued1 = 2;
+    if (__syncthreads_or(!mbar_wait_bounded(&bars[0], 1u, lim))) {
+      give_up();
+      return;
+    }
+    done0 = 2;
+    pair_inverse<N>(buf0, s_tw, row, lane, ra, rb);
+  }
+  // otherwise one barrier per pair: after it every thread is done with the previous pair's
+  // buffer, which then receives its next copy (C after A, the D and S rows after B)
 #pragma unroll 1
-  for (int pr = 0; pr < 3; ++pr) {
+  for (int pr = 0; pr < (PACK2 ? 0 : 3); ++pr) {
     uint64_t* bar = &bars[pr == 1 ? 1 : 0];
     unsigned char* buf = pr == 1 ? buf1 : buf0;
     fence_proxy_async();  // this thread's accesses to the previous buffer precede the copy into it

@@ -145,9 +145,26 @@ k_fft_z_c2r(const __grid_constant__ ZC2RBatch<T, RB> zb, int nfields, const vec2
   const int y0 = blockIdx.x * TY;
   const V* src = in.p[fz];
   T* dst = reinterpret_cast<T*>(outp.p[fz]);
-  for (int item = threadIdx.x; item < NK * TY; item += blockDim.x) {
-    const int kz = item / TY, yl = item % TY;
-    s_H[kz * (TY + 1) + yl] = src[((int64_t)kz * N + x) * N + y0 + yl];
+  // the CTA's NK rows of TY values, one 8- or 16-byte segment per kz plane: for FP32 all of a
+  // thread's loads are issued before its stores, so they are in flight together
+  constexpr int ITEMS = (NK * TY + G::THREADS - 1) / G::THREADS;
+  if constexpr (sizeof(T) == 4 && ITEMS <= 24) {
+    V tmp[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      const int item = threadIdx.x + i * G::THREADS;
+      if (item < NK * TY) tmp[i] = src[((int64_t)(item / TY) * N + x) * N + y0 + item % TY];
+    }
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      const int item = threadIdx.x + i * G::THREADS;
+      if (item < NK * TY) s_H[(item / TY) * (TY + 1) + item % TY] = tmp[i];
+    }
+  } else {
+    for (int item = threadIdx.x; item < NK * TY; item += blockDim.x) {
+      const int kz = item / TY, yl = item % TY;
+      s_H[kz * (TY + 1) + yl] = src[((int64_t)kz * N + x) * N + y0 + yl];
+    }
   }
   __syncthreads();
   for (int item = threadIdx.x; item < N * P; item += blockDim.x) {
